@@ -1,0 +1,298 @@
+"""Independent brute-force poker games, written from the games' rules.
+
+Histories are explicit tuples of tokens ('k' check, 'c' call, 'f' fold, ('b', amount) bet
+or raise to `amount` chips, ('d', card) public card dealt).  Nothing here is shared with the
+oracle or the CUDA path.  Every quantity is computed from its definition by enumerating
+histories, which pins the oracle's tree rules, utilities, chance weights, counterfactual
+values (Section 3, Eq. cfv), regrets (Section 3), regret matching (Section 3, Eq. rm) and
+best responses on games small enough to enumerate.
+
+Counterfactual weighting: a subgame starts with a chance deal of (h0, h1) with probability
+r0(h0) r1(h1) / Z over pairs that share no card.  Player i's own r_i(h_i) counts as player
+i's reach; the counterfactual weight of a history is r_{-i}(h_{-i}) / Z times the
+opponent's action probabilities times the public-card chance probabilities.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+KUHN, LEDUC, HOLDEM = "kuhn", "leduc", "holdem"
+
+
+class Game:
+    """Heads-up poker subgame: Kuhn, Leduc, or a hold'em turn/river subgame."""
+
+    def __init__(self, kind, hands=None, ranges=None, board=(), strength=None, pot=2.0, stack=0.0,
+                 sizes=(), max_raises=1):
+        self.kind = kind
+        if kind == KUHN:
+            self.deck, self.hands, self.n_streets = 3, [(c,) for c in range(3)], 1
+            self.bets, self.max_raises, self.base = [1.0], 1, 1.0
+        elif kind == LEDUC:
+            self.deck, self.hands, self.n_streets = 6, [(c,) for c in range(6)], 2
+            self.bets, self.max_raises, self.base = [2.0, 4.0], 2, 1.0
+        else:
+            self.deck, self.hands = 52, [tuple(int(c) for c in h) for h in hands]
+            self.n_streets = 1 if len(board) == 5 else 2
+            self.bets, self.max_raises, self.base = None, max_raises, pot / 2.0
+            self.cap = pot / 2.0 + stack
+            self.sizes = list(sizes)
+            self.strength = np.asarray(strength)
+        self.board0 = tuple(int(c) for c in board)
+        n = len(self.hands)
+        if ranges is None:
+            ranges = np.full((2, n), 1.0 / n)
+        r = np.asarray(ranges, dtype=np.float64)
+        self.r = r / r.sum(axis=1, keepdims=True)
+        self.Z = sum(self.r[0][a] * self.r[1][b] for a in range(n) for b in range(n) if self.compatible(a, b))
+
+    # ------------------------------------------------------------ cards
+    def compatible(self, a, b):
+        return not (set(self.hands[a]) & set(self.hands[b]))
+
+    def deals(self):
+        n = len(self.hands)
+        return [(a, b) for a in range(n) for b in range(n) if self.compatible(a, b)]
+
+    # ------------------------------------------------------------ betting state
+    def state(self, hist):
+        c = [self.base, self.base]
+        street, to_act, raises, street_acts = 0, 0, 0, []
+        board = list(self.board0)
+        folded = -1
+        for tok in hist:
+            if tok[0] == "d":
+                board.append(tok[1])
+                street, to_act, raises, street_acts = street + 1, 0, 0, []
+                continue
+            p = to_act
+            if tok == "c":
+                c[p] = c[1 - p]
+            elif tok == "f":
+                folded = p
+            elif tok[0] == "b":
+                c[p] = tok[1]
+                raises += 1
+            street_acts.append(tok)
+            to_act = 1 - p
+        over = bool(street_acts) and (street_acts[-1] == "c" or street_acts[-2:] == ["k", "k"])
+        if not street_acts and street > 0 and self.kind == HOLDEM and max(c) >= self.cap:
+            over = True  # all-in: no betting on later streets
+        return dict(c=c, street=street, to_act=to_act, raises=raises, board=board, folded=folded, over=over)
+
+    def legal(self, hist):
+        s = self.state(hist)
+        c, p = s["c"], s["to_act"]
+        facing = c[1 - p] > c[p]
+        acts = ["f", "c"] if facing else ["k"]
+        if s["raises"] < self.max_raises:
+            if self.kind != HOLDEM:
+                acts.append(("b", c[1 - p] + self.bets[s["street"]]))
+            elif c[1 - p] < self.cap and c[p] < self.cap:
+                d = c[1 - p] - c[p]
+                pot = c[0] + c[1]
+                targets = []
+                for x in self.sizes:
+                    t = self.cap if x <= 0 else min(c[p] + (d + x * (pot + d)), self.cap)
+                    if t not in targets and t > c[1 - p]:
+                        targets.append(t)
+                acts += [("b", t) for t in sorted(targets)]
+        return acts
+
+    def strength_of(self, h, board):
+        if self.kind == KUHN:
+            return self.hands[h][0]
+        if self.kind == LEDUC:
+            r, br = self.hands[h][0] // 2, board[0] // 2
+            return 10 + r if r == br else r
+        row = 0 if len(self.board0) == 5 else board[4]
+        return int(self.strength[row][h])
+
+    def utility(self, hands, hist, i):
+        """u_i at a terminal history, else None."""
+        s = self.state(hist)
+        c = s["c"]
+        if s["folded"] >= 0:
+            f = s["folded"]
+            return -c[i] if f == i else c[f]
+        if s["over"] and s["street"] == self.n_streets - 1:
+            si = self.strength_of(hands[i], s["board"])
+            so = self.strength_of(hands[1 - i], s["board"])
+            return c[1 - i] if si > so else (-c[i] if si < so else 0.0)
+        return None
+
+    def chance_cards(self, hands, hist):
+        """Live public cards when the betting round is over and a card is to come, else None."""
+        s = self.state(hist)
+        if s["folded"] >= 0 or not s["over"] or s["street"] == self.n_streets - 1:
+            return None
+        dead = set(s["board"]) | set(self.hands[hands[0]]) | set(self.hands[hands[1]])
+        return [x for x in range(self.deck) if x not in dead]
+
+
+class Profile:
+    """Behaviour strategy: infoset key -> list of action probabilities; missing = uniform."""
+
+    def __init__(self, table=None):
+        self.table = dict(table or {})
+
+    def probs(self, key, n):
+        return self.table.get(key, [1.0 / n] * n)
+
+
+def infoset_key(player, hand, hist):
+    return (player, hand, tuple(hist))
+
+
+def expected_utility(g, prof, hands, hist, i, memo=None):
+    """E[u_i | history] under the profile, chance below the history included.
+
+    `memo` caches results for one fixed profile."""
+    if memo is not None:
+        key = (hands, hist, i)
+        if key in memo:
+            return memo[key]
+    u = g.utility(hands, hist, i)
+    if u is not None:
+        out = float(u)
+    else:
+        live = g.chance_cards(hands, hist)
+        if live is not None:
+            out = sum(expected_utility(g, prof, hands, hist + (("d", x),), i, memo) for x in live) / len(live)
+        else:
+            p = g.state(hist)["to_act"]
+            acts = g.legal(hist)
+            pr = prof.probs(infoset_key(p, hands[p], hist), len(acts))
+            out = sum(pr[k] * expected_utility(g, prof, hands, hist + (a,), i, memo) for k, a in enumerate(acts))
+    if memo is not None:
+        memo[key] = out
+    return out
+
+
+def decision_histories(g, prof):
+    """(hands, hist, pi0, pi1, pc) for every decision history; pi_i excludes the deal."""
+    out = []
+
+    def rec(hands, hist, pi, pc):
+        if g.utility(hands, hist, 0) is not None:
+            return
+        live = g.chance_cards(hands, hist)
+        if live is not None:
+            for x in live:
+                rec(hands, hist + (("d", x),), pi, pc / len(live))
+            return
+        out.append((hands, hist, pi[0], pi[1], pc))
+        p = g.state(hist)["to_act"]
+        acts = g.legal(hist)
+        pr = prof.probs(infoset_key(p, hands[p], hist), len(acts))
+        for k, a in enumerate(acts):
+            npi = list(pi)
+            npi[p] *= pr[k]
+            rec(hands, hist + (a,), npi, pc)
+
+    for h0, h1 in g.deals():
+        rec((h0, h1), (), [1.0, 1.0], 1.0)
+    return out
+
+
+def regrets_and_values(g, prof, i):
+    """r_i(I, a) = v_i(sigma_{I->a}, I) - v_i(sigma, I) and v_i(sigma, I) for player i."""
+    reg, val = {}, {}
+    memo = {}
+    for hands, hist, pi0, pi1, pc in decision_histories(g, prof):
+        if g.state(hist)["to_act"] != i:
+            continue
+        key = infoset_key(i, hands[i], hist)
+        w = g.r[1 - i][hands[1 - i]] / g.Z * (pi1 if i == 0 else pi0) * pc
+        eu = expected_utility(g, prof, hands, hist, i, memo)
+        val[key] = val.get(key, 0.0) + w * eu
+        acts = g.legal(hist)
+        r = reg.setdefault(key, [0.0] * len(acts))
+        for k, a in enumerate(acts):
+            r[k] += w * (expected_utility(g, prof, hands, hist + (a,), i, memo) - eu)
+    return reg, val
+
+
+def own_reach(g, prof, i):
+    """pi_i(I), including player i's range weight r_i(h_i)."""
+    out = {}
+    for hands, hist, pi0, pi1, pc in decision_histories(g, prof):
+        if g.state(hist)["to_act"] == i:
+            out[infoset_key(i, hands[i], hist)] = g.r[i][hands[i]] * (pi0 if i == 0 else pi1)
+    return out
+
+
+def regret_matching(R):
+    table = {}
+    for key, ra in R.items():
+        pos = [max(v, 0.0) for v in ra]
+        s = sum(pos)
+        table[key] = [x / s if s > 0 else 1.0 / len(ra) for x in pos]
+    return Profile(table)
+
+
+def profile_value(g, prof, i=0):
+    memo = {}
+    return sum(g.r[0][h0] * g.r[1][h1] / g.Z * expected_utility(g, prof, (h0, h1), (), i, memo)
+               for h0, h1 in g.deals())
+
+
+def run_cfr(g, iterations, variant="cfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True):
+    """CFR by definition: regrets from profile deviations, then the variant update."""
+    R, S = {}, {}
+    for t in range(1, iterations + 1):
+        ta, tb = t ** alpha, t ** beta
+        dpos, dneg, dS = ta / (ta + 1.0), tb / (tb + 1.0), (t / (t + 1.0)) ** gamma
+        players = [0, 1]
+        snap = regret_matching(R) if not alternating else None
+        for i in players:
+            prof = regret_matching(R) if alternating else snap
+            reg, _ = regrets_and_values(g, prof, i)
+            reach = own_reach(g, prof, i)
+            for key, r in reg.items():
+                old = R.get(key, [0.0] * len(r))
+                new = []
+                for a in range(len(r)):
+                    x = old[a] + r[a]
+                    if variant == "dcfr":
+                        x *= dpos if x > 0 else dneg
+                    if variant == "cfr+":
+                        x = max(x, 0.0)
+                    new.append(x)
+                R[key] = new
+            for key, pi in reach.items():
+                n = len(reg[key])
+                sig = prof.probs(key, n)
+                old = S.get(key, [0.0] * n)
+                wS = float(t) if variant == "cfr+" else 1.0
+                S[key] = [(old[a] * (dS if variant == "dcfr" else 1.0)) + wS * pi * sig[a] for a in range(n)]
+    return R, S
+
+
+def average_profile(S):
+    table = {}
+    for key, s in S.items():
+        tot = sum(s)
+        table[key] = [x / tot if tot > 0 else 1.0 / len(s) for x in s]
+    return Profile(table)
+
+
+def kuhn_pure_strategies(player):
+    """All 2^6 pure strategies of a Kuhn player, as infoset -> action probabilities."""
+    hists = [(), ("k", ("b", 2.0))] if player == 0 else [("k",), (("b", 2.0),)]
+    slots = [(card, h) for card in range(3) for h in hists]
+    for choice in itertools.product([0, 1], repeat=len(slots)):
+        yield {infoset_key(player, card, h): [float(k == c) for k in range(2)] for (card, h), c in zip(slots, choice)}
+
+
+def kuhn_best_response_bruteforce(opp_profile, i):
+    """max over the 64 pure strategies of player i of E[u_i] against the opponent profile."""
+    g = Game(KUHN)
+    best = -1e300
+    for table in kuhn_pure_strategies(i):
+        merged = dict(opp_profile.table)
+        merged.update(table)
+        best = max(best, profile_value(g, Profile(merged), i))
+    return best
