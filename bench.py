@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark: Parallel CFR iterations per second on GB300.
+
+Workload (one "step"): one complete solve of the river subgame -- 5 seeded board cards,
+1081 two-card hands per player with seeded integer showdown strengths in [0, 2000),
+Dirichlet(1) ranges, pot 100, stacks 400, bet sizes {0.5, 1.0 pot, all-in}, at most 3 bets
+or raises -- by DCFR (alpha 1.5, beta 0, gamma 2) from scratch: reset, 1000 alternating
+iterations (every stage of the paper's pipeline, Section 4.1), then the best-response
+exploitability pass.  `value` is CFR iterations per second of device time over the K
+timed steps (L2 flushed between steps with a 256 MB write, outside the timed events).
+
+Under torchrun each rank solves its own subgame (seeds offset by rank) with no
+collective: weak scaling, value = all ranks' iterations / the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (the reference for this build) on the same
+workload instead, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CFR iters/sec (ms/iter) per GB300 at fixed exploitability vs plain exact form; HBM GB/s"
+BB_CHIPS = 100.0  # big blind used for mbb/hand (the pot is 100 chips)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters-per-step", type=int, default=1000)
+    ap.add_argument("--precision", choices=["pairs", "single"], default="pairs")
+    ap.add_argument("--chunk-hands", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return dist
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(iters_local: int, seconds_local: float, world: int, dist, device=None) -> tuple[float, float]:
+    """Whole-job throughput: all ranks' iterations / the slowest rank's time."""
+    t = max_over_ranks(seconds_local, dist, device)
+    return iters_local * world / t, t
+
+
+# ------------------------------------------------------------------ workload
+
+def workload_spec(rank: int = 0):
+    from paper_2605_19928_gb300 import synth
+    return synth.river_subgame(seed=0 + 1000 * rank, range_seed=1 + 1000 * rank)
+
+
+def workload_config(args, spec, n_nodes):
+    return {"workload": "river subgame, exact (no depth limit)", "board_cards": 5, "hands": spec.n_hands,
+            "public_nodes": n_nodes, "pot": spec.pot, "stack": spec.stack, "bet_sizes": "0.5,1.0 pot,all-in",
+            "max_raises": spec.max_raises, "variant": "DCFR(1.5,0,2) alternating",
+            "iters_per_step": args.iters_per_step, "step": "reset + iterations + exploitability",
+            "values": "fp32 pairs" if args.precision == "pairs" else "fp32",
+            "l2": "flushed between steps (256 MB write, outside the timed events)",
+            "seeds": spec.seeds}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0, period_ms: int = 100):
+        self.index, self.period_ms = index, period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", f"-lms={self.period_ms}",
+                                          f"--filename={self.path}"],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(self.period_ms / 1000.0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if _num(r[3]))}
+
+
+def _num(x):
+    try:
+        float(x)
+        return True
+    except ValueError:
+        return False
+
+
+# ------------------------------------------------------------------ roofline
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def tree_shape(capi, tree):
+    n_nodes, n_hands, _ = capi.cfr_tree_info(tree)
+    rows = [0, 0]
+    terminals = 0
+    for n in range(n_nodes):
+        info = capi.cfr_node_info(tree, n)
+        if info["type"] == capi.CFR_NODE_DECISION:
+            rows[info["player"]] += info["n_actions"]
+        elif info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN):
+            terminals += 1
+    return {"nodes": n_nodes, "hands": n_hands, "rows": rows, "terminals": terminals}
+
+
+def algorithmic_bytes(shape, stage: str, value_bytes: int) -> float:
+    """Bytes one launch must move (per player for the per-iteration stages).
+
+    update:   per (decision row of the player, hand): R and S read + write (32 B), strategy
+              read + write (2 V); per (node, hand): reach read + write and value write (3 V);
+              per (terminal, hand): terminal value read (V).
+    terminal: per (terminal, hand): opponent reach read and value write (2 V)."""
+    H, V = shape["hands"], value_bytes
+    rows = max(shape["rows"])
+    if stage == "update":
+        return H * (rows * (32 + 2 * V) + shape["nodes"] * 3 * V + shape["terminals"] * V)
+    if stage == "terminal":
+        return H * shape["terminals"] * 2 * V
+    raise ValueError(stage)
+
+
+def kernels_digest() -> str:
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "pcfr_internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_19928_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(stage: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches these kernels."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_river1081.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"kernels_digest:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernels_digest():
+        return None
+    return float(t.group(1))
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+
+def oracle_sample(spec, seconds: float, threads: int | None = None):
+    """Time the FP64 oracle as it stands on this host: iterations of the same solve until
+    the budget is spent, then one exploitability pass."""
+    from oracle.oracle import Oracle
+    orc = Oracle(spec, variant="dcfr", alternating=True, threads=threads)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        orc.iterate(1)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    t_iter = time.perf_counter() - t0
+    e = orc.exploitability()[0]
+    t_all = time.perf_counter() - t0
+    return {"iters": n, "seconds": t_all, "iter_seconds": t_iter, "threads": orc.threads, "expl": e}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec = workload_spec(0)
+    budget = max(1.0, args.cpu_seconds / 4)
+    for _ in range(args.warmup):
+        oracle_sample(spec, budget / 4)
+    total_iters, total_s, threads = 0, 0.0, 1
+    for _ in range(args.steps):
+        r = oracle_sample(spec, budget)
+        total_iters += r["iters"]
+        total_s += r["seconds"]
+        threads = r["threads"]
+    value = total_iters / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, spec, None),
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{total_iters} DCFR iterations of the 1081-hand river subgame over "
+                                       f"{args.steps} steps, each followed by one exploitability pass"},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+
+    from paper_2605_19928_gb300 import capi
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device: the CUDA path has no CPU fallback"}))
+        return 2
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = dist_init(world, True)
+    capi.load()
+    capi.use_torch_allocator()
+    stream = torch.cuda.current_stream(device)
+    spec = workload_spec(rank)
+    opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
+                          precision=args.precision)
+    tree = capi.cfr_tree_create(spec, opts, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    ips = args.iters_per_step
+
+    def step():
+        capi.cfr_reset(tree)
+        capi.cfr_iterate(tree, ips)
+        capi.cfr_exploitability_async(tree)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(device)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = capi.cfr_counters(tree)["kernel_launches"]
+    clocks = ClockSampler(device.index)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(device)
+    clock_info = clocks.stop()
+    barrier(dist, device)
+    gpu_launches = capi.cfr_counters(tree)["kernel_launches"] - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_s = sum(step_ms) / 1000.0
+    value, t_max = aggregate(args.steps * ips, local_s, world, dist, device)
+    expl, br = capi.cfr_exploitability_result(tree)
+
+    # per-kernel device time (un-graphed, CUDA events between launches) for the roofline
+    shape = tree_shape(capi, tree)
+    capi.cfr_reset(tree)
+    stages = capi.cfr_stage_times(tree, min(ips, 200))
+    vbytes = 8 if args.precision == "pairs" else 4
+    per_step = {k: stages[k][0] * (2 * ips if k in ("terminal", "update") else 1) for k in stages}
+    dom = max(("update", "terminal"), key=lambda k: per_step[k])
+    alg = algorithmic_bytes(shape, dom, vbytes)
+    achieved = alg / (stages[dom][0] * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "kernel": f"k_hand<update>" if dom == "update" else "k_terminal",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs", "traffic": profiled_traffic(dom),
+                "algorithmic_bytes_per_launch": alg, "launch_ms": stages[dom][0],
+                "stage_ms": {k: v[0] for k, v in stages.items()}}
+
+    # end to end through the C ABI with host buffers: inputs from pinned host memory,
+    # create + solve + exploitability + read of the root's average strategy, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        import numpy as np
+        pinned = {}
+        for name in ("hands", "ranges", "strength", "board"):
+            a = getattr(spec, name)
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            pinned[name] = t
+        pspec = type(spec)(**{**spec.__dict__, **{k: v.numpy() for k, v in pinned.items()}})
+        root_out = np.empty((4, spec.n_hands), np.float32)
+        times, h2d, d2h = [], 0, 0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            tr = capi.cfr_tree_create(pspec, opts, stream=stream.cuda_stream)
+            capi.cfr_iterate(tr, ips)
+            ex, _ = capi.cfr_exploitability(tr)
+            a = capi.cfr_node_info(tr, 0)["n_actions"]
+            capi.cfr_strategy(tr, 0, average=True, out=root_out[:a])
+            t1 = time.perf_counter()
+            if k > 0:
+                times.append(t1 - t0)
+                h2d = capi.cfr_counters(tr)["h2d_bytes"]
+                d2h = 16 + a * spec.n_hands * vbytes
+            capi.cfr_tree_destroy(tr)
+        e2e_val, _ = aggregate(ips * len(times), sum(times), world, dist, device)
+        e2e = {"value": e2e_val, "unit": "iter/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "step": f"create from pinned host inputs + {ips} iterations + exploitability + root average "
+                       "strategy to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(spec, args.cpu_seconds)
+        cpu = {"value": r["iters"] / r["seconds"], "unit": "iter/s", "cores": r["threads"], "kind": "oracle",
+               "sample": f"{r['iters']} DCFR iterations of the same 1081-hand river subgame plus one "
+                         f"exploitability pass ({r['seconds']:.1f} s, FP64, walks every history)"}
+    capi.cfr_tree_destroy(tree)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
+                "ms_per_iter": 1000.0 * t_max / (args.steps * ips), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32x2 values, f64 R/S" if args.precision == "pairs" else
+                "f32 values, f64 R/S", "data": "synthetic",
+                "config": workload_config(args, spec, shape["nodes"]),
+                "exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS,
+                "exploitability_pct_pot": 100.0 * float(expl[0]) / spec.pot,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
+                "clocks": clock_info}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * pcfr.h -- C ABI of the GB300 Parallel CFR library (libpcfr.so).
+ *
+ * One CFR iteration over a public poker tree whose nodes hold per-private-hand range and
+ * value vectors, after "Real-Time Parallel Counterfactual Regret Minimization"
+ * (arxiv 2605.19928).  The iteration follows the paper's seven-stage pipeline (Section 4.1,
+ * Table 1): regret matching (Section 3, Eq. rm), forward reach (Section 4.2, Stages 1-2),
+ * blocker-corrected opponent reach at fold terminals (Stage 3), rank-sorted showdown values
+ * (Stage 4), depth-limit chance leaves (Stage 5, exact form), backward counterfactual values
+ * (Section 4.4, Stage 6, Eq. backward) and the regret / average-strategy update (Stage 7)
+ * for vanilla CFR, CFR+ and DCFR (Section 2).  Exploitability uses a best-response pass.
+ *
+ * Conventions
+ *   - Every function returns CFR_OK (0) or a negative CFR_E* code; cfr_last_error()
+ *     returns a thread-local message describing the last failure on the calling thread.
+ *   - All pointers in this header are HOST pointers unless stated otherwise.  Input arrays
+ *     are copied during create; the caller keeps ownership of everything it passes.
+ *     Output buffers are caller-owned host memory.
+ *   - Device memory is owned by the library.  It comes from the allocator installed with
+ *     cfr_set_allocator(), else from cudaMalloc.
+ *   - Work is enqueued on the CUDA stream given at create (NULL = the legacy default
+ *     stream).  cfr_iterate() is asynchronous; calls that return data synchronise.
+ *   - There is no CPU fallback: without a CUDA device of compute capability 10.3 the
+ *     create call fails with CFR_ECUDA.
+ *   - A tree handle must not be used from two threads at once.
+ */
+#ifndef PCFR_H
+#define PCFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CFR_OK 0
+#define CFR_EINVAL (-1)   /* bad argument or game description */
+#define CFR_ENOMEM (-2)   /* host or device allocation failed */
+#define CFR_ECUDA (-3)    /* CUDA error or no suitable device */
+#define CFR_ETIMEOUT (-4) /* a bounded device-side wait gave up (reserved) */
+#define CFR_ESTATE (-5)   /* call not valid in the handle's current state */
+
+enum { CFR_GAME_HOLDEM = 0, CFR_GAME_KUHN = 1, CFR_GAME_LEDUC = 2 };
+enum { CFR_VARIANT_CFR = 0, CFR_VARIANT_CFRPLUS = 1, CFR_VARIANT_DCFR = 2 };
+enum { CFR_NODE_DECISION = 0, CFR_NODE_FOLD = 1, CFR_NODE_SHOWDOWN = 2, CFR_NODE_CHANCE = 3 };
+enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_CFV = 3 };
+
+/*
+ * One subgame (Section 5, "Game": heads-up poker solved to the end of a betting round).
+ *   game        CFR_GAME_HOLDEM: a hold'em turn (n_board 4: turn betting, a chance node over
+ *               the river card, river betting) or river (n_board 5) subgame;
+ *               CFR_GAME_KUHN / CFR_GAME_LEDUC: the full games (board, hands, strength,
+ *               pot, stack and bet sizes are ignored; range may be NULL for uniform).
+ *   board       [n_board] card ids 0..51 (card = 4 * rank + suit), distinct.
+ *   hands       [n_hands][2] private two-card hands, none touching the board, no
+ *               duplicates; both players share this list.  NULL = every hand not blocked
+ *               by the board, in lexicographic (c1 < c2) order.
+ *   range[p]    [n_hands] player p's reach at the root, >= 0, not all zero; normalised
+ *               internally to sum 1.  NULL = uniform.
+ *   strength    showdown strength, higher wins, equal splits: [1][n_hands] for a river
+ *               subgame, [52][n_hands] for a turn subgame (row = river card; rows of board
+ *               cards are ignored).
+ *   pot, stack  chips in the pot (each player has put in pot / 2) and behind each player.
+ *   bet_sizes   [n_bet_sizes] bet sizes as pot fractions; a size <= 0 means all-in.  A size
+ *               x facing a call of d raises by d + x * (pot + d); sizes reaching the stack
+ *               become all-in; duplicates are dropped.
+ *   max_raises  bets plus raises allowed per street (the opening bet counts).
+ */
+typedef struct cfr_game_spec {
+  int game;
+  int n_board;
+  const int32_t* board;
+  int n_hands;
+  const uint8_t* hands;
+  const float* range[2];
+  const int32_t* strength;
+  int n_strength_rows;
+  double pot;
+  double stack;
+  int n_bet_sizes;
+  const double* bet_sizes;
+  int max_raises;
+} cfr_game_spec;
+
+/*
+ * Solver options.  variant: CFR_VARIANT_*.  DCFR uses alpha, beta, gamma (Section 2, "CFR
+ * algorithms"; the paper's default is DCFR): at iteration t, R <- R + r then positive
+ * regrets are scaled by t^alpha/(t^alpha+1) and the rest by t^beta/(t^beta+1);
+ * S <- S * (t/(t+1))^gamma + pi_i * sigma.  CFR+: R <- max(R + r, 0), S <- S + t pi_i sigma.
+ * alternating != 0 updates player 0 then player 1 (with player 0's new strategy) each
+ * iteration; 0 updates both from the same strategy.
+ * chunk_hands: hands per CUDA block in the per-hand passes (0 = automatic; otherwise a
+ * power of two from 1 to 32).
+ * precision: CFR_PRECISION_PAIRS (default) carries reach, strategies and counterfactual
+ * values as double-float pairs of FP32 (about 44 significant bits, computed on the FP32
+ * pipe); CFR_PRECISION_SINGLE carries them in plain FP32.  Cumulative regrets R and
+ * average-strategy sums S are FP64 in both.
+ */
+enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
+typedef struct cfr_solver_opts {
+  int variant;
+  double alpha;
+  double beta;
+  double gamma;
+  int alternating;
+  int chunk_hands;
+  int precision;
+} cfr_solver_opts;
+
+typedef struct cfr_tree cfr_tree;
+
+/* Device allocator hook used for all later allocations (NULL, NULL = cudaMalloc/cudaFree).
+ * alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, ctx) releases it. */
+typedef void* (*cfr_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cfr_free_fn)(void* ptr, void* ctx);
+int cfr_set_allocator(cfr_alloc_fn alloc, cfr_free_fn free_fn, void* ctx);
+
+/* Build the public tree and per-hand tables of one subgame on the host, upload them and
+ * initialise the solver (R = S = 0, uniform strategy).  stream: a cudaStream_t or NULL.
+ * On success *out receives a handle owned by the caller (release with cfr_tree_destroy). */
+int cfr_tree_create(const cfr_game_spec* spec, const cfr_solver_opts* opts, void* stream, cfr_tree** out);
+
+/* Same for n_games independent subgames solved together; every call below then acts on
+ * all of them at once, and `game` arguments select one subgame (0 .. n_games-1). */
+int cfr_batch_create(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream,
+                     cfr_tree** out);
+
+/* Run n_iters CFR iterations (Section 4.1 pipeline, both players), asynchronously on the
+ * handle's stream, in place.  The first call records a CUDA graph of one iteration and
+ * later calls replay it. */
+int cfr_iterate(cfr_tree* tree, int n_iters);
+
+/* Strategy at a decision node: the current one (regret matching of R, Eq. rm) or, with
+ * average != 0, the average strategy S / sum S (uniform where sum S = 0).  out is a host
+ * buffer of [n_actions][n_hands] floats; out_len is its length in floats.  Synchronises. */
+int cfr_strategy(cfr_tree* tree, int game, int node, int average, float* out, size_t out_len);
+
+/* Exploitability of the average strategy of every subgame: expl[g] = (BR_0 + BR_1) / 2 in
+ * chips, where BR_i is player i's best-response value against the other player's average
+ * strategy (root reductions in FP64).  expl: [n_games]; br: [n_games][2] or NULL.
+ * Synchronises. */
+int cfr_exploitability(cfr_tree* tree, double* expl, double* br);
+
+/* The same pass, enqueued without waiting; cfr_exploitability_result() waits for the most
+ * recent pass and returns its values (arguments as for cfr_exploitability). */
+int cfr_exploitability_async(cfr_tree* tree);
+int cfr_exploitability_result(cfr_tree* tree, double* expl, double* br);
+
+/* Start the solve again: R = S = 0, iteration count 0, uniform strategy, initial reach
+ * (asynchronous, on the handle's stream). */
+int cfr_reset(cfr_tree* tree);
+
+/* Sizes of one subgame and the number of iterations done.  Any out pointer may be NULL. */
+int cfr_tree_info(const cfr_tree* tree, int game, int* n_nodes, int* n_hands, int* iters_done);
+
+/* One node of a subgame's public tree.  Nodes are numbered level by level from the root
+ * (0); children of a node are consecutive and ordered [fold], check/call, raises by size,
+ * or by dealt card for chance nodes.  Any out pointer may be NULL; contrib receives the
+ * chips each player has put in at that node. */
+int cfr_node_info(const cfr_tree* tree, int game, int node, int* type, int* player, int* n_actions, int* parent,
+                  int* action_in_parent, int* deal_card, double* contrib);
+
+/* Read solver state into a host buffer of doubles (synchronises):
+ *   CFR_READ_REGRET, CFR_READ_AVG_SUM: a decision node's cumulative regrets R or average-
+ *     strategy sums S, [n_actions][n_hands] (player is ignored);
+ *   CFR_READ_CFV: player's counterfactual values at `node` from that player's last
+ *     traversal, [n_hands];
+ *   CFR_READ_BR_CFV: player's best-response values at `node` from the last exploitability
+ *     call, [n_hands]. */
+int cfr_read_values(cfr_tree* tree, int game, int what, int player, int node, double* out, size_t out_len);
+
+/* Block until all work queued on the handle's stream has finished. */
+int cfr_sync(cfr_tree* tree);
+
+/* Per-stage device time, after the paper's per-stage breakdown (Section 5, Table 3).
+ * Runs n_iters iterations (advancing the solve exactly like cfr_iterate) launch by launch
+ * instead of as a graph, with CUDA events around every kernel, then one exploitability
+ * pass the same way.  ms[k] receives the mean device time of one launch of stage k and
+ * launches[k] (may be NULL) the number of launches timed; both have CFR_N_STAGES entries.
+ *   CFR_STAGE_TERMINAL    fold and showdown values of one player (Stages 2-4)
+ *   CFR_STAGE_UPDATE      backward values, regret and average update, new strategy and
+ *                         forward reach of one player (Stages 6-7, then 1-2)
+ *   CFR_STAGE_AVG_REACH   average strategy and its forward reach, both players
+ *   CFR_STAGE_BR_TERMINAL terminal values against the average strategy, both players
+ *   CFR_STAGE_BR          best-response backward pass, both players
+ *   CFR_STAGE_BR_REDUCE   FP64 root reduction of the best-response values
+ * Synchronises. */
+enum {
+  CFR_STAGE_TERMINAL = 0,
+  CFR_STAGE_UPDATE = 1,
+  CFR_STAGE_AVG_REACH = 2,
+  CFR_STAGE_BR_TERMINAL = 3,
+  CFR_STAGE_BR = 4,
+  CFR_STAGE_BR_REDUCE = 5,
+  CFR_N_STAGES = 6
+};
+int cfr_stage_times(cfr_tree* tree, int n_iters, double* ms, int64_t* launches);
+
+/* Counters of the handle (any out pointer may be NULL): kernels launched so far (graph
+ * replays count every kernel they contain), device bytes allocated, and bytes copied host
+ * to device when the handle was created. */
+int cfr_counters(const cfr_tree* tree, int64_t* kernel_launches, int64_t* device_bytes, int64_t* h2d_bytes);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void cfr_tree_destroy(cfr_tree* tree);
+
+/* Thread-local description of the last error ("" if none). */
+const char* cfr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCFR_H */

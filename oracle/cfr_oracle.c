@@ -18,7 +18,9 @@
  *     algorithms), with the average strategy weighted by the player's own reach
  *     (Section 4.2, Stage 1);
  *   - a best response against the average strategy, by per-infoset maximisation over the
- *     same enumeration, and the exploitability (BR_0 + BR_1) / 2 in chips.
+ *     same enumeration, and the exploitability (BR_0 + BR_1) / 2 in chips; its per-node
+ *     values are counterfactual values like those of the walk (chance probabilities inside
+ *     the counterfactual reach).
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
  *   - the subgame starts with a chance deal of private hands with probability
@@ -531,31 +533,54 @@ static void update_player(Oracle* o, int i, int t) {
   for (int h = 0; h < o->nh; ++h) own_reach(o, 0, i, h, o->r[i][h], wS);
 }
 
+/* Player i's update at iteration t: regret matching of the current R of both players,
+ * player i's traversal, player i's update.  The iteration count is not advanced. */
+void ocfr_update_player(Oracle* o, int i, int t) {
+  regret_match(o, o->R, o->sig);
+  traverse(o, o->sig, i, 1);
+  update_player(o, i, t);
+}
+
+/* Both players' updates at iteration t from one strategy (simultaneous updates). */
+void ocfr_update_both(Oracle* o, int t) {
+  regret_match(o, o->R, o->sig);
+  double* saved = (double*)malloc(sizeof(double) * (size_t)o->nrows * o->nh);
+  traverse(o, o->sig, 0, 1);
+  memcpy(saved, o->rinst, sizeof(double) * (size_t)o->nrows * o->nh);
+  traverse(o, o->sig, 1, 1);
+  /* player 1's regrets are in rinst; apply them, then player 0's */
+  update_player(o, 1, t);
+  memcpy(o->rinst, saved, sizeof(double) * (size_t)o->nrows * o->nh);
+  update_player(o, 0, t);
+  free(saved);
+}
+
 /* One iteration (both players), Section 4.1 pipeline order: profile, values, update. */
 void ocfr_iterate(Oracle* o, int n_iters) {
   for (int it = 0; it < n_iters; ++it) {
     int t = o->t + 1;
     if (o->alternating) {
-      for (int i = 0; i < 2; ++i) {
-        regret_match(o, o->R, o->sig);
-        traverse(o, o->sig, i, 1);
-        update_player(o, i, t);
-      }
+      ocfr_update_player(o, 0, t);
+      ocfr_update_player(o, 1, t);
     } else {
-      regret_match(o, o->R, o->sig);
-      double* saved = (double*)malloc(sizeof(double) * (size_t)o->nrows * o->nh);
-      traverse(o, o->sig, 0, 1);
-      memcpy(saved, o->rinst, sizeof(double) * (size_t)o->nrows * o->nh);
-      traverse(o, o->sig, 1, 1);
-      /* player 1's regrets are in rinst; apply them, then player 0's */
-      update_player(o, 1, t);
-      memcpy(o->rinst, saved, sizeof(double) * (size_t)o->nrows * o->nh);
-      update_player(o, 0, t);
-      free(saved);
+      ocfr_update_both(o, t);
     }
     o->t = t;
   }
 }
+
+/* Overwrite one decision node's cumulative regrets and average-strategy sums ([nkids][nh]
+ * each), so that a test can start an update from another implementation's state. */
+int ocfr_set_node_state(Oracle* o, int node, const double* R, const double* S) {
+  if (node < 0 || node >= o->nn || o->nodes[node].type != T_DEC) return -1;
+  const Node* nd = &o->nodes[node];
+  size_t off = (size_t)nd->row * o->nh, len = (size_t)nd->nkids * o->nh;
+  memcpy(o->R + off, R, sizeof(double) * len);
+  memcpy(o->S + off, S, sizeof(double) * len);
+  return 0;
+}
+
+void ocfr_set_iterations(Oracle* o, int t) { o->t = t; }
 
 /* ------------------------------------------------------------------ profiles and best response */
 
@@ -604,11 +629,11 @@ static double br_rec(const BRWork* w, int node, int h) {
       if (cm[ho] && q[ho] != 0.0) v += q[ho] * utility(o, n, i, h, ho);
     v /= o->Z;
   } else if (n->type == T_CHANCE) {
-    int K = o->deck - n->nboard - 2 * o->hsize;
+    /* the card probability is inside the opponent-and-chance reach q below this node */
     for (int k = 0; k < n->nkids; ++k) {
       int kid = n->kids[k];
       if (hand_has(o, h, o->nodes[kid].deal)) continue;
-      v += br_rec(w, kid, h) / K;
+      v += br_rec(w, kid, h);
     }
   } else if (n->player == i) {
     v = -INFINITY;
@@ -629,8 +654,10 @@ static void* br_worker(void* arg) {
   return NULL;
 }
 
-/* Opponent reach of every (node, hand) under the loaded profile; cards dealt on the path
- * remove the hands that hold them. */
+/* Counterfactual reach of every (node, opponent hand) under the loaded profile: the
+ * opponent's range and action probabilities times the probability of the public cards dealt
+ * on the path (1/K per card, K the cards left given both hands), as in Eq. (cfv); cards
+ * dealt on the path remove the hands that hold them. */
 static void opponent_reach(const Oracle* o, int opp, double* q) {
   for (int h = 0; h < o->nh; ++h) q[h] = o->r[opp][h];
   for (int n = 0; n < o->nn; ++n) {  /* parents are created before children */
@@ -641,10 +668,11 @@ static void opponent_reach(const Oracle* o, int opp, double* q) {
           q[(size_t)nd->kids[a] * o->nh + h] =
               q[(size_t)n * o->nh + h] * (nd->player == opp ? o->prof[(size_t)(nd->row + a) * o->nh + h] : 1.0);
     } else if (nd->type == T_CHANCE) {
+      double K = (double)(o->deck - nd->nboard - 2 * o->hsize);
       for (int k = 0; k < nd->nkids; ++k) {
         int kid = nd->kids[k];
         for (int h = 0; h < o->nh; ++h)
-          q[(size_t)kid * o->nh + h] = hand_has(o, h, o->nodes[kid].deal) ? 0.0 : q[(size_t)n * o->nh + h];
+          q[(size_t)kid * o->nh + h] = hand_has(o, h, o->nodes[kid].deal) ? 0.0 : q[(size_t)n * o->nh + h] / K;
       }
     }
   }

@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     """Compile cfr_oracle.c into liboracle.so next to it (gcc, no CUDA)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +70,11 @@ def _load():
         lib.ocfr_exploitability.argtypes = [P, pd]
         lib.ocfr_exploitability.restype = D
         lib.ocfr_values_current.argtypes = [P, I]
+        lib.ocfr_update_player.argtypes = [P, I, I]
+        lib.ocfr_update_both.argtypes = [P, I]
+        lib.ocfr_set_node_state.argtypes = [P, I, pd, pd]
+        lib.ocfr_set_node_state.restype = I
+        lib.ocfr_set_iterations.argtypes = [P, I]
         _lib = lib
         return lib
 
@@ -185,6 +190,24 @@ class Oracle:
         out = np.zeros(self.n_hands, np.float64)
         self._lib.ocfr_get_cfv(self._h, i, n, _ptr(out, C.c_double))
         return out
+
+    def update_player(self, i: int, t: int):
+        """Player i's update at iteration t (regret matching, traversal, update)."""
+        self._lib.ocfr_update_player(self._h, int(i), int(t))
+
+    def update_both(self, t: int):
+        """Both players' updates at iteration t from one strategy (simultaneous)."""
+        self._lib.ocfr_update_both(self._h, int(t))
+
+    def set_node_state(self, n: int, R, S):
+        """Overwrite a decision node's regrets and average sums ([n_actions][n_hands])."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        if self._lib.ocfr_set_node_state(self._h, n, _ptr(R, C.c_double), _ptr(S, C.c_double)) != 0:
+            raise ValueError(f"node {n} is not a decision node")
+
+    def set_iterations(self, t: int):
+        self._lib.ocfr_set_iterations(self._h, int(t))
 
     def values_current(self, i: int):
         """Counterfactual values of player i under the current strategy (no update)."""

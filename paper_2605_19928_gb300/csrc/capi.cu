@@ -1,0 +1,580 @@
+// C ABI of libpcfr.so (declared in include/pcfr.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pcfr.h"
+#include "pcfr_internal.h"
+#include "tree.h"
+
+using namespace pcfr;
+
+namespace {
+
+thread_local std::string g_last_error;
+cfr_alloc_fn g_alloc = nullptr;
+cfr_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(CFR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+}  // namespace
+
+struct cfr_tree {
+  std::vector<HostGame> host;
+  std::vector<GameDev> dev;     // host copies of the device structs
+  GameDev* d_games = nullptr;
+  Work* d_chunk_work = nullptr;
+  Work* d_term_work = nullptr;
+  int* d_iter = nullptr;
+  unsigned* d_done = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t iter_graph = nullptr;
+  cudaGraphExec_t expl_graph = nullptr;
+  cfr_solver_opts opts{};
+  LaunchCtx ctx{};
+  int iters_done = 0;
+  int64_t launches = 0;         // kernels launched (graph replays included)
+  int64_t device_bytes = 0;
+  int64_t h2d_bytes = 0;
+  int launches_per_iteration = 0;
+  std::vector<std::pair<void*, bool>> blocks;  // (pointer, from hook)
+  void* stream_arg = nullptr;
+
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    void* p = nullptr;
+    bool hook = g_alloc != nullptr;
+    if (hook) {
+      p = g_alloc(bytes, stream_arg, g_alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) {
+      blocks.push_back({p, hook});
+      device_bytes += (int64_t)bytes;
+    }
+    return p;
+  }
+  ~cfr_tree() {
+    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    if (expl_graph) cudaGraphExecDestroy(expl_graph);
+    cudaStreamSynchronize(stream);
+    for (auto& b : blocks) {
+      if (b.second) {
+        if (g_free) g_free(b.first, g_alloc_ctx);
+      } else {
+        cudaFree(b.first);
+      }
+    }
+    if (capture) cudaStreamDestroy(capture);
+  }
+};
+
+namespace {
+
+template <typename T>
+int upload(cfr_tree* t, const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return CFR_OK;
+  void* p = t->alloc(v.size() * sizeof(T));
+  if (!p) return fail(CFR_ENOMEM, "device allocation failed");
+  CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, t->stream));
+  t->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+  *out = (T*)p;
+  return CFR_OK;
+}
+
+template <typename T>
+int zeros(cfr_tree* t, size_t n, T** out) {
+  void* p = t->alloc(std::max<size_t>(n, 1) * sizeof(T));
+  if (!p) return fail(CFR_ENOMEM, "device allocation failed");
+  CK(cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(T), t->stream));
+  *out = (T*)p;
+  return CFR_OK;
+}
+
+// Shared memory of the per-hand kernel for one game with W hands per block: values and
+// reach [n_nodes][W], strategy rows [rows_p][W] (value size es), R and S rows [rows_p][W].
+size_t hand_smem(const HostGame& g, int W, size_t es) {
+  const int rows_max = std::max(g.row_begin[1] - g.row_begin[0], g.row_begin[2] - g.row_begin[1]);
+  return (size_t)(2 * g.nodes.size() + rows_max) * W * es + (size_t)2 * rows_max * W * 8;
+}
+
+// Host copy of a per-hand vector in the value type: one float, or a (hi, lo) float pair.
+std::vector<float> to_value_type(const std::vector<double>& x, int precision) {
+  std::vector<float> out;
+  if (precision == kPrecisionSingle) {
+    for (double v : x) out.push_back((float)v);
+  } else {
+    for (double v : x) {
+      const float hi = (float)v;
+      out.push_back(hi);
+      out.push_back((float)(v - (double)hi));
+    }
+  }
+  return out;
+}
+
+int check_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(CFR_ECUDA, "libpcfr needs a compute capability 10.3 (GB300) device, found " +
+                               std::to_string(prop.major) + "." + std::to_string(prop.minor));
+  return CFR_OK;
+}
+
+int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream,
+                cfr_tree** out) {
+  if (!out) return fail(CFR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!specs || n_games <= 0) return fail(CFR_EINVAL, "no game given");
+  cfr_solver_opts o{CFR_VARIANT_DCFR, 1.5, 0.0, 2.0, 1, 0, CFR_PRECISION_PAIRS};
+  if (opts) o = *opts;
+  if (o.variant < 0 || o.variant > 2) return fail(CFR_EINVAL, "unknown CFR variant");
+  if (o.precision != CFR_PRECISION_PAIRS && o.precision != CFR_PRECISION_SINGLE)
+    return fail(CFR_EINVAL, "unknown precision");
+  const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
+  if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
+    return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
+  int rc = check_device();
+  if (rc != CFR_OK) return rc;
+  static int configured = configure_kernels();
+  if (configured != 0) return fail(CFR_ECUDA, "kernel attribute setup failed");
+
+  cfr_tree* t = new cfr_tree();
+  t->opts = o;
+  t->stream = (cudaStream_t)stream;
+  t->stream_arg = stream;
+  t->host.resize(n_games);
+  for (int g = 0; g < n_games; ++g) {
+    std::string err;
+    rc = build_game(specs[g], t->host[g], err);
+    if (rc != CFR_OK) {
+      delete t;
+      return fail(rc, "game " + std::to_string(g) + ": " + err);
+    }
+  }
+  // Block shape: W hands per block (8 by default).  The per-hand pass keeps its chunk's
+  // state in shared memory when that fits in 96 KB (two blocks per SM), else it works on
+  // the global arrays, which stay in L2 for trees of this size.
+  size_t smem_hand = 0, smem_term = 0;
+  std::vector<int> chunk(n_games);
+  std::vector<int> use_smem(n_games);
+  for (int g = 0; g < n_games; ++g) {
+    const HostGame& h = t->host[g];
+    const int W = o.chunk_hands ? o.chunk_hands : 8;
+    chunk[g] = W;
+    use_smem[g] = hand_smem(h, W, es) <= 96 * 1024;
+    if (use_smem[g]) smem_hand = std::max(smem_hand, hand_smem(h, W, es));
+    smem_term = std::max(smem_term, (size_t)(h.n_hands + 1 + h.cl_len + 1) * 8 + (size_t)h.n_hands * es);
+  }
+
+  std::vector<Work> chunk_work, term_work;
+  t->dev.resize(n_games);
+  for (int g = 0; g < n_games; ++g) {
+    const HostGame& h = t->host[g];
+    GameDev& d = t->dev[g];
+    memset(&d, 0, sizeof(d));
+    const size_t N = h.nodes.size(), S = (size_t)h.hstride;
+    d.n_nodes = (int)N;
+    d.n_levels = (int)h.level_start.size() - 1;
+    d.n_hands = h.n_hands;
+    d.hstride = h.hstride;
+    d.hand_size = h.hand_size;
+    d.n_rows = h.n_rows;
+    d.n_terminals = (int)h.terminals.size();
+    d.deck = h.deck;
+    d.chunk = chunk[g];
+    d.n_chunks = (h.n_hands + chunk[g] - 1) / chunk[g];
+    d.smem = use_smem[g];
+    for (int k = 0; k < 3; ++k) d.row_begin[k] = h.row_begin[k];
+    d.n_boards = h.n_boards;
+    d.cl_len = h.cl_len;
+    d.kappa64 = 1.0 / h.Z;
+    std::vector<double> r64(2 * S, 0.0);
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < h.n_hands; ++k) r64[p * S + k] = h.range[p][k];
+    const std::vector<float> rv = to_value_type(r64, o.precision);
+    NodeDev* nodes;
+    int32_t *ls, *perm, *gs, *ge, *clh, *clo, *cllo, *clhi;
+    uint64_t* hm;
+    uint8_t* hc;
+    float* rrv;
+    double *rr64, *pay;
+    if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) ||
+        (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, h.hand_cards, &hc)) || (rc = upload(t, rv, &rrv)) ||
+        (rc = upload(t, r64, &rr64)) || (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, h.sd_perm, &perm)) ||
+        (rc = upload(t, h.sd_gs, &gs)) || (rc = upload(t, h.sd_ge, &ge)) || (rc = upload(t, h.cl_hand, &clh)) ||
+        (rc = upload(t, h.cl_off, &clo)) || (rc = upload(t, h.cl_lo, &cllo)) || (rc = upload(t, h.cl_hi, &clhi))) {
+      delete t;
+      return rc;
+    }
+    d.nodes = nodes; d.level_start = ls; d.hand_mask = hm; d.hand_cards = hc; d.range_v = rrv;
+    d.range64 = rr64; d.payoff = pay; d.sd_perm = perm; d.sd_gs = gs; d.sd_ge = ge; d.cl_hand = clh;
+    d.cl_off = clo; d.cl_lo = cllo; d.cl_hi = clhi;
+    const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
+    const size_t vf = es / 4;  // floats per value
+    float *sig, *sigb, *rch, *rchb, *cf, *cfb;
+    if ((rc = zeros(t, rows, &d.R)) || (rc = zeros(t, rows, &d.S)) || (rc = zeros(t, rows * vf, &sig)) ||
+        (rc = zeros(t, rows * vf, &sigb)) || (rc = zeros(t, cells * vf, &rch)) || (rc = zeros(t, cells * vf, &rchb)) ||
+        (rc = zeros(t, cells * vf, &cf)) || (rc = zeros(t, cells * vf, &cfb)) ||
+        (rc = zeros(t, (size_t)2 * d.n_chunks, &d.br_partial)) || (rc = zeros(t, 2, &d.br_out))) {
+      delete t;
+      return rc;
+    }
+    d.sigma = sig; d.sigbar = sigb; d.reach = rch; d.reach_bar = rchb; d.cfv = cf; d.cfv_br = cfb;
+    for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
+    for (int n : h.terminals) term_work.push_back({g, n});
+  }
+  if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
+      (rc = upload(t, term_work, &t->d_term_work)) || (rc = zeros(t, 1, &t->d_iter)) ||
+      (rc = zeros(t, 1, &t->d_done))) {
+    delete t;
+    return rc;
+  }
+  LaunchCtx& c = t->ctx;
+  c.games = t->d_games;
+  c.n_games = n_games;
+  c.chunk_work = t->d_chunk_work;
+  c.n_chunk_work = (int)chunk_work.size();
+  c.term_work = t->d_term_work;
+  c.n_term_work = (int)term_work.size();
+  c.iter = t->d_iter;
+  c.done = t->d_done;
+  c.smem_hand = smem_hand;
+  c.smem_term = smem_term;
+  c.variant = o.variant;
+  c.precision = o.precision;
+  c.alpha = o.alpha;
+  c.beta = o.beta;
+  c.gamma = o.gamma;
+  t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
+  t->launches += 1;
+  if (launch_init(c, stream) != 0) {
+    delete t;
+    return fail(CFR_ECUDA, "initial strategy launch failed");
+  }
+  cudaError_t e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) {
+    delete t;
+    return cuda_fail(e, "create");
+  }
+  *out = t;
+  return CFR_OK;
+}
+
+// One iteration: alternating = terminal + update for player 0, then for player 1.
+int enqueue_iteration(cfr_tree* t, cudaStream_t s) {
+  const LaunchCtx& c = t->ctx;
+  if (t->opts.alternating) {
+    if (launch_terminal(c, 1, 0, s) || launch_update(c, 1, 0, s) || launch_terminal(c, 2, 0, s) ||
+        launch_update(c, 2, 1, s))
+      return -1;
+  } else {
+    if (launch_terminal(c, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
+  }
+  return 0;
+}
+
+int check_game(const cfr_tree* t, int game) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (game < 0 || game >= (int)t->host.size()) return fail(CFR_EINVAL, "game index out of range");
+  return CFR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cfr_set_allocator(cfr_alloc_fn alloc, cfr_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(CFR_EINVAL, "give both alloc and free, or neither");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return CFR_OK;
+}
+
+int cfr_tree_create(const cfr_game_spec* spec, const cfr_solver_opts* opts, void* stream, cfr_tree** out) {
+  return create_impl(spec, 1, opts, stream, out);
+}
+
+int cfr_batch_create(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream,
+                     cfr_tree** out) {
+  return create_impl(specs, n_games, opts, stream, out);
+}
+
+int cfr_iterate(cfr_tree* t, int n_iters) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (n_iters < 0) return fail(CFR_EINVAL, "n_iters < 0");
+  if (n_iters == 0) return CFR_OK;
+  if (!t->iter_graph) {
+    if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_iteration(t, t->capture);
+    cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
+    if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&t->iter_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  for (int k = 0; k < n_iters; ++k) CK(cudaGraphLaunch(t->iter_graph, t->stream));
+  t->iters_done += n_iters;
+  t->launches += (int64_t)n_iters * t->launches_per_iteration;
+  return CFR_OK;
+}
+
+int cfr_sync(cfr_tree* t) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  CK(cudaStreamSynchronize(t->stream));
+  return CFR_OK;
+}
+
+int cfr_strategy(cfr_tree* t, int game, int node, int average, float* out, size_t out_len) {
+  int rc = check_game(t, game);
+  if (rc) return rc;
+  const HostGame& h = t->host[game];
+  if (node < 0 || node >= (int)h.nodes.size() || h.nodes[node].type != kDecision)
+    return fail(CFR_EINVAL, "node is not a decision node");
+  const NodeDev& nd = h.nodes[node];
+  const size_t need = (size_t)nd.n_kids * h.n_hands;
+  if (!out || out_len < need) return fail(CFR_EINVAL, "output buffer too small");
+  if (average && launch_average_rows(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "average launch failed");
+  if (average) t->launches += 1;
+  const size_t vf = t->opts.precision == CFR_PRECISION_SINGLE ? 1 : 2;
+  std::vector<float> tmp(need * vf);
+  const float* src = static_cast<const float*>(average ? t->dev[game].sigbar : t->dev[game].sigma);
+  CK(cudaMemcpy2DAsync(tmp.data(), (size_t)h.n_hands * 4 * vf, src + (size_t)nd.row * h.hstride * vf,
+                       (size_t)h.hstride * 4 * vf, (size_t)h.n_hands * 4 * vf, nd.n_kids, cudaMemcpyDeviceToHost,
+                       t->stream));
+  CK(cudaStreamSynchronize(t->stream));
+  for (size_t k = 0; k < need; ++k) out[k] = vf == 1 ? tmp[k] : (float)((double)tmp[2 * k] + (double)tmp[2 * k + 1]);
+  return CFR_OK;
+}
+
+int cfr_exploitability_async(cfr_tree* t) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (!t->expl_graph) {
+    if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
+    const LaunchCtx& c = t->ctx;
+    const int rc = launch_avg_reach(c, t->capture) || launch_terminal(c, 3, 1, t->capture) ||
+                   launch_br(c, t->capture) || launch_br_reduce(c, t->capture);
+    cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
+    if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&t->expl_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  CK(cudaGraphLaunch(t->expl_graph, t->stream));
+  t->launches += t->ctx.n_term_work > 0 ? 4 : 3;
+  return CFR_OK;
+}
+
+int cfr_exploitability_result(cfr_tree* t, double* expl, double* br) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (!expl) return fail(CFR_EINVAL, "expl is NULL");
+  const int G = (int)t->host.size();
+  std::vector<double> vals(2 * G);
+  for (int g = 0; g < G; ++g)
+    CK(cudaMemcpyAsync(&vals[2 * g], t->dev[g].br_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, t->stream));
+  CK(cudaStreamSynchronize(t->stream));
+  for (int g = 0; g < G; ++g) {
+    expl[g] = 0.5 * (vals[2 * g] + vals[2 * g + 1]);
+    if (br) {
+      br[2 * g] = vals[2 * g];
+      br[2 * g + 1] = vals[2 * g + 1];
+    }
+  }
+  return CFR_OK;
+}
+
+int cfr_exploitability(cfr_tree* t, double* expl, double* br) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (!expl) return fail(CFR_EINVAL, "expl is NULL");
+  const int rc = cfr_exploitability_async(t);
+  return rc ? rc : cfr_exploitability_result(t, expl, br);
+}
+
+int cfr_reset(cfr_tree* t) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  for (const GameDev& d : t->dev) {
+    const size_t rows = (size_t)d.n_rows * d.hstride * sizeof(double);
+    CK(cudaMemsetAsync(d.R, 0, rows, t->stream));
+    CK(cudaMemsetAsync(d.S, 0, rows, t->stream));
+  }
+  CK(cudaMemsetAsync(t->d_iter, 0, sizeof(int), t->stream));
+  if (launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "initial strategy launch failed");
+  t->launches += 1;
+  t->iters_done = 0;
+  return CFR_OK;
+}
+
+int cfr_tree_info(const cfr_tree* t, int game, int* n_nodes, int* n_hands, int* iters_done) {
+  int rc = check_game(t, game);
+  if (rc) return rc;
+  if (n_nodes) *n_nodes = (int)t->host[game].nodes.size();
+  if (n_hands) *n_hands = t->host[game].n_hands;
+  if (iters_done) *iters_done = t->iters_done;
+  return CFR_OK;
+}
+
+int cfr_node_info(const cfr_tree* t, int game, int node, int* type, int* player, int* n_actions, int* parent,
+                  int* action_in_parent, int* deal_card, double* contrib) {
+  int rc = check_game(t, game);
+  if (rc) return rc;
+  const HostGame& h = t->host[game];
+  if (node < 0 || node >= (int)h.nodes.size()) return fail(CFR_EINVAL, "node index out of range");
+  const NodeDev& nd = h.nodes[node];
+  if (type) *type = nd.type;
+  if (player) *player = (nd.type == kDecision || nd.type == kFold) ? nd.player : -1;
+  if (n_actions) *n_actions = nd.n_kids;
+  if (parent) *parent = nd.parent;
+  if (action_in_parent) *action_in_parent = nd.parent < 0 ? -1 : nd.paction;
+  if (deal_card) *deal_card = nd.deal == kNoCard ? -1 : nd.deal;
+  if (contrib) {
+    contrib[0] = h.contrib[2 * (size_t)node];
+    contrib[1] = h.contrib[2 * (size_t)node + 1];
+  }
+  return CFR_OK;
+}
+
+int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, double* out, size_t out_len) {
+  int rc = check_game(t, game);
+  if (rc) return rc;
+  const HostGame& h = t->host[game];
+  const GameDev& d = t->dev[game];
+  if (node < 0 || node >= (int)h.nodes.size()) return fail(CFR_EINVAL, "node index out of range");
+  if (!out) return fail(CFR_EINVAL, "out is NULL");
+  const NodeDev& nd = h.nodes[node];
+  const int H = h.n_hands;
+  const size_t S = (size_t)h.hstride;
+  if (what == CFR_READ_REGRET || what == CFR_READ_AVG_SUM) {
+    if (nd.type != kDecision) return fail(CFR_EINVAL, "node is not a decision node");
+    const size_t need = (size_t)nd.n_kids * H;
+    if (out_len < need) return fail(CFR_EINVAL, "output buffer too small");
+    const double* src = (what == CFR_READ_REGRET ? d.R : d.S) + (size_t)nd.row * S;
+    CK(cudaMemcpy2DAsync(out, (size_t)H * 8, src, S * 8, (size_t)H * 8, nd.n_kids, cudaMemcpyDeviceToHost,
+                         t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return CFR_OK;
+  }
+  if (what == CFR_READ_CFV || what == CFR_READ_BR_CFV) {
+    if (player < 0 || player > 1) return fail(CFR_EINVAL, "player must be 0 or 1");
+    if (out_len < (size_t)H) return fail(CFR_EINVAL, "output buffer too small");
+    const size_t vf = t->opts.precision == CFR_PRECISION_SINGLE ? 1 : 2;
+    std::vector<float> tmp((size_t)H * vf);
+    const float* src = static_cast<const float*>(what == CFR_READ_CFV ? d.cfv : d.cfv_br) +
+                       ((size_t)player * h.nodes.size() + node) * S * vf;
+    CK(cudaMemcpyAsync(tmp.data(), src, (size_t)H * 4 * vf, cudaMemcpyDeviceToHost, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    for (int k = 0; k < H; ++k) out[k] = vf == 1 ? (double)tmp[k] : (double)tmp[2 * k] + (double)tmp[2 * k + 1];
+    return CFR_OK;
+  }
+  return fail(CFR_EINVAL, "unknown read kind");
+}
+
+int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (!ms || n_iters < 0) return fail(CFR_EINVAL, "bad arguments");
+  const LaunchCtx& c = t->ctx;
+  cudaStream_t s = t->stream;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> stage_of;
+  auto mark = [&](int stage) -> cudaError_t {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    ev.push_back(e);
+    stage_of.push_back(stage);
+    return cudaEventRecord(e, s);
+  };
+  int rc = 0;
+  cudaError_t err = mark(-1);
+  for (int it = 0; it < n_iters && !rc && err == cudaSuccess; ++it) {
+    if (t->opts.alternating) {
+      for (int p = 0; p < 2 && !rc && err == cudaSuccess; ++p) {
+        rc = launch_terminal(c, 1 << p, 0, s);
+        if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
+        if (!rc && err == cudaSuccess) rc = launch_update(c, 1 << p, p == 1, s);
+        if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
+      }
+    } else {
+      rc = launch_terminal(c, 3, 0, s);
+      if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
+      if (!rc && err == cudaSuccess) rc = launch_update(c, 3, 1, s);
+      if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
+    }
+  }
+  if (!rc && err == cudaSuccess) rc = launch_avg_reach(c, s);
+  if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_AVG_REACH);
+  if (!rc && err == cudaSuccess) rc = launch_terminal(c, 3, 1, s);
+  if (!rc && err == cudaSuccess && c.n_term_work > 0) err = mark(CFR_STAGE_BR_TERMINAL);
+  if (!rc && err == cudaSuccess) rc = launch_br(c, s);
+  if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_BR);
+  if (!rc && err == cudaSuccess) rc = launch_br_reduce(c, s);
+  if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_BR_REDUCE);
+  cudaError_t serr = cudaStreamSynchronize(s);
+  double tot[CFR_N_STAGES] = {0};
+  int64_t cnt[CFR_N_STAGES] = {0};
+  for (size_t k = 1; k < ev.size() && serr == cudaSuccess && err == cudaSuccess && !rc; ++k) {
+    float m = 0.f;
+    cudaEventElapsedTime(&m, ev[k - 1], ev[k]);
+    tot[stage_of[k]] += m;
+    cnt[stage_of[k]] += 1;
+  }
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  if (rc) return fail(CFR_ECUDA, "stage launch failed");
+  if (err != cudaSuccess) return cuda_fail(err, "cudaEventRecord");
+  if (serr != cudaSuccess) return cuda_fail(serr, "cudaStreamSynchronize");
+  t->iters_done += n_iters;
+  int64_t total = 0;
+  for (int k = 0; k < CFR_N_STAGES; ++k) {
+    ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;
+    if (launches) launches[k] = cnt[k];
+    total += cnt[k];
+  }
+  t->launches += total;
+  return CFR_OK;
+}
+
+int cfr_counters(const cfr_tree* t, int64_t* kernel_launches, int64_t* device_bytes, int64_t* h2d_bytes) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (kernel_launches) *kernel_launches = t->launches;
+  if (device_bytes) *device_bytes = t->device_bytes;
+  if (h2d_bytes) *h2d_bytes = t->h2d_bytes;
+  return CFR_OK;
+}
+
+void cfr_tree_destroy(cfr_tree* t) { delete t; }
+
+const char* cfr_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,447 @@
+// Host-side subgame construction (see tree.h).
+//
+// Betting rules (Section 5, "Game": heads-up poker with a fixed action abstraction,
+// Section 2 "Abstraction"): player 0 acts first on every street; facing a bet the actions
+// are fold, call and raises, otherwise check and bets; "max raises" counts the opening bet.
+// Limit games (Kuhn, Leduc) raise by a fixed amount per street.  Hold'em subgames raise by
+// pot fractions: a fraction x facing a call of d raises by d + x * (pot + d), amounts that
+// reach the stack become all-in, duplicates are dropped and raises are ordered by size.
+#include "tree.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <numeric>
+
+namespace pcfr {
+namespace {
+
+struct Pending {
+  uint8_t type;
+  uint8_t player;  // decision: to act; fold: folder
+  int parent;
+  int paction;
+  int level;
+  double c[2];
+  int street;
+  int raises;
+  bool checked;    // the first player checked on this street
+  int nboard;
+  int board[5];
+  int deal;
+  double chance;   // probability of the public cards dealt on the path (given both hands)
+};
+
+struct Rules {
+  int game;
+  int deck;
+  int n_streets;
+  double cap;            // hold'em: all-in contribution
+  double limit_bet[2];   // limit games: raise amount per street
+  std::vector<double> sizes;
+  int max_raises;
+};
+
+uint64_t board_bits(const Pending& s) {
+  uint64_t b = 0;
+  for (int k = 0; k < s.nboard; ++k) b |= 1ull << s.board[k];
+  return b;
+}
+
+// The betting on s.street is over: deal the next card or show down.
+Pending street_over(const Rules& R, const Pending& s) {
+  Pending e = s;
+  e.type = s.street + 1 >= R.n_streets ? kShowdown : kChance;
+  e.deal = kNoCard;
+  return e;
+}
+
+void decision_children(const Rules& R, const Pending& s, std::vector<Pending>& kids) {
+  const int p = s.player, q = 1 - p;
+  const bool facing = s.c[q] > s.c[p];
+  Pending base = s;
+  base.deal = kNoCard;
+  if (facing) {
+    Pending f = base;
+    f.type = kFold;
+    f.player = (uint8_t)p;
+    kids.push_back(f);
+    Pending call = base;
+    call.c[p] = s.c[q];
+    kids.push_back(street_over(R, call));
+  } else if (p == 1 || s.checked) {
+    kids.push_back(street_over(R, base));
+  } else {
+    Pending chk = base;
+    chk.type = kDecision;
+    chk.player = (uint8_t)q;
+    chk.checked = true;
+    kids.push_back(chk);
+  }
+  if (s.raises >= R.max_raises) return;
+  std::vector<double> to;
+  if (R.game == CFR_GAME_HOLDEM) {
+    if (!(s.c[q] < R.cap && s.c[p] < R.cap)) return;
+    const double d = s.c[q] - s.c[p], pot = s.c[0] + s.c[1];
+    for (double x : R.sizes) {
+      double t = R.cap;
+      if (x > 0.0) t = std::min(s.c[p] + (d + x * (pot + d)), R.cap);
+      if (t > s.c[q] && std::find(to.begin(), to.end(), t) == to.end()) to.push_back(t);
+    }
+    std::sort(to.begin(), to.end());
+  } else {
+    to.push_back(s.c[q] + R.limit_bet[s.street]);
+  }
+  for (double t : to) {
+    Pending r = base;
+    r.type = kDecision;
+    r.player = (uint8_t)q;
+    r.c[p] = t;
+    r.raises = s.raises + 1;
+    kids.push_back(r);
+  }
+}
+
+void chance_children(const Rules& R, const Pending& s, std::vector<Pending>& kids) {
+  const uint64_t on = board_bits(s);
+  const bool all_in = R.game == CFR_GAME_HOLDEM && std::max(s.c[0], s.c[1]) >= R.cap;
+  for (int card = 0; card < R.deck; ++card) {
+    if ((on >> card) & 1ull) continue;
+    Pending k = s;
+    k.board[k.nboard++] = card;
+    k.street = s.street + 1;
+    k.raises = 0;
+    k.checked = false;
+    if (all_in) {
+      k = street_over(R, k);  // nobody can bet: run the cards out
+    } else {
+      k.type = kDecision;
+      k.player = 0;
+    }
+    k.deal = card;
+    kids.push_back(k);
+  }
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+}  // namespace
+
+int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
+  g = HostGame();
+  g.game = spec.game;
+  Rules R{};
+  R.game = spec.game;
+  R.max_raises = spec.max_raises;
+  Pending root{};
+  root.type = kDecision;
+  root.player = 0;
+  root.parent = -1;
+  root.deal = kNoCard;
+  root.chance = 1.0;
+  std::vector<int> board0;
+
+  if (spec.game == CFR_GAME_KUHN || spec.game == CFR_GAME_LEDUC) {
+    const bool kuhn = spec.game == CFR_GAME_KUHN;
+    g.deck = kuhn ? 3 : 6;
+    g.hand_size = 1;
+    g.n_streets = kuhn ? 1 : 2;
+    R.limit_bet[0] = kuhn ? 1.0 : 2.0;
+    R.limit_bet[1] = 4.0;
+    R.max_raises = kuhn ? 1 : 2;
+    root.c[0] = root.c[1] = 1.0;  // antes
+    g.n_hands = g.deck;
+    if (spec.n_hands != 0 && spec.n_hands != g.deck) {
+      err = "Kuhn and Leduc deal one card per player from their own deck";
+      return CFR_EINVAL;
+    }
+    for (int c = 0; c < g.deck; ++c) {
+      g.hand_cards.push_back((uint8_t)c);
+      g.hand_cards.push_back(kNoCard);
+      g.hand_mask.push_back(1ull << c);
+    }
+  } else if (spec.game == CFR_GAME_HOLDEM) {
+    g.deck = 52;
+    g.hand_size = 2;
+    if (spec.n_board != 4 && spec.n_board != 5) {
+      err = "hold'em subgames start on the turn (4 board cards) or the river (5)";
+      return CFR_EINVAL;
+    }
+    if (!spec.board) {
+      err = "board is NULL";
+      return CFR_EINVAL;
+    }
+    g.n_streets = spec.n_board == 5 ? 1 : 2;
+    uint64_t bm = 0;
+    for (int k = 0; k < spec.n_board; ++k) {
+      const int c = spec.board[k];
+      if (c < 0 || c >= 52 || ((bm >> c) & 1ull)) {
+        err = "board cards must be distinct ids in 0..51";
+        return CFR_EINVAL;
+      }
+      bm |= 1ull << c;
+      board0.push_back(c);
+      root.board[root.nboard++] = c;
+    }
+    if (!(spec.pot > 0.0) || !std::isfinite(spec.pot) || !finite_nonneg(spec.stack)) {
+      err = "pot must be positive and stack non-negative";
+      return CFR_EINVAL;
+    }
+    if (spec.max_raises < 0 || spec.n_bet_sizes < 0 || spec.n_bet_sizes > kMaxActions - 2 ||
+        (spec.n_bet_sizes > 0 && !spec.bet_sizes)) {
+      err = "bad bet-size list or raise cap";
+      return CFR_EINVAL;
+    }
+    for (int k = 0; k < spec.n_bet_sizes; ++k) {
+      if (!std::isfinite(spec.bet_sizes[k])) {
+        err = "bet sizes must be finite";
+        return CFR_EINVAL;
+      }
+      R.sizes.push_back(spec.bet_sizes[k]);
+    }
+    R.cap = spec.pot / 2.0 + spec.stack;
+    root.c[0] = root.c[1] = spec.pot / 2.0;
+    if (spec.hands) {
+      if (spec.n_hands <= 0) {
+        err = "n_hands must be positive";
+        return CFR_EINVAL;
+      }
+      g.n_hands = spec.n_hands;
+      std::vector<uint64_t> seen;
+      for (int h = 0; h < spec.n_hands; ++h) {
+        const int a = spec.hands[2 * h], b = spec.hands[2 * h + 1];
+        if (a >= 52 || b >= 52 || a == b || ((bm >> a) & 1ull) || ((bm >> b) & 1ull)) {
+          err = "hand " + std::to_string(h) + " has an invalid card or a card on the board";
+          return CFR_EINVAL;
+        }
+        const uint64_t m = (1ull << a) | (1ull << b);
+        seen.push_back(m);
+        g.hand_cards.push_back((uint8_t)a);
+        g.hand_cards.push_back((uint8_t)b);
+        g.hand_mask.push_back(m);
+      }
+      std::sort(seen.begin(), seen.end());
+      if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+        err = "duplicate hands";
+        return CFR_EINVAL;
+      }
+    } else {
+      for (int a = 0; a < 52; ++a)
+        for (int b = a + 1; b < 52; ++b) {
+          if (((bm >> a) & 1ull) || ((bm >> b) & 1ull)) continue;
+          g.hand_cards.push_back((uint8_t)a);
+          g.hand_cards.push_back((uint8_t)b);
+          g.hand_mask.push_back((1ull << a) | (1ull << b));
+        }
+      g.n_hands = (int)g.hand_mask.size();
+    }
+    const int want_rows = spec.n_board == 5 ? 1 : 52;
+    if (!spec.strength || spec.n_strength_rows != want_rows) {
+      err = "strength must have 1 row (river) or 52 rows (turn)";
+      return CFR_EINVAL;
+    }
+  } else {
+    err = "unknown game";
+    return CFR_EINVAL;
+  }
+  R.deck = g.deck;
+  R.n_streets = g.n_streets;
+  const int H = g.n_hands;
+  g.hstride = (H + 31) / 32 * 32;
+
+  // ranges: non-negative, finite, normalised to sum 1
+  for (int p = 0; p < 2; ++p) {
+    g.range[p].assign(H, 1.0 / H);
+    if (spec.range[p]) {
+      double s = 0.0;
+      for (int h = 0; h < H; ++h) {
+        const double x = spec.range[p][h];
+        if (!finite_nonneg(x)) {
+          err = "ranges must be finite and non-negative";
+          return CFR_EINVAL;
+        }
+        s += x;
+      }
+      if (!(s > 0.0)) {
+        err = "a range sums to zero";
+        return CFR_EINVAL;
+      }
+      for (int h = 0; h < H; ++h) g.range[p][h] = spec.range[p][h] / s;
+    }
+  }
+  double Z = 0.0;
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < H; ++b)
+      if (!(g.hand_mask[a] & g.hand_mask[b])) Z += g.range[0][a] * g.range[1][b];
+  if (!(Z > 0.0)) {
+    err = "no pair of hands can be dealt with positive probability";
+    return CFR_EINVAL;
+  }
+  g.Z = Z;
+
+  // ---- public tree, breadth first: ids are level order, children consecutive
+  std::deque<Pending> queue;
+  queue.push_back(root);
+  std::vector<Pending> kids;
+  while (!queue.empty()) {
+    Pending s = queue.front();
+    queue.pop_front();
+    const int id = (int)g.nodes.size();
+    NodeDev nd{};
+    nd.parent = s.parent;
+    nd.first_kid = -1;
+    nd.row = -1;
+    nd.type = s.type;
+    nd.player = s.player;
+    nd.deal = (uint8_t)(s.deal < 0 ? kNoCard : s.deal);
+    nd.paction = (uint8_t)(s.paction < 0 ? 0 : s.paction);
+    if (s.level > 255) {
+      err = "tree deeper than 255 levels";
+      return CFR_EINVAL;
+    }
+    nd.level = (uint8_t)s.level;
+    nd.board = board_bits(s);
+    kids.clear();
+    if (s.type == kDecision) decision_children(R, s, kids);
+    else if (s.type == kChance) chance_children(R, s, kids);
+    // Terminal payoffs carry the probability of the public cards dealt on their path, so
+    // the values the kernels compute are counterfactual values with chance inside the
+    // counterfactual reach (Eq. cfv).  A chance node's value is then the plain sum of its
+    // children over the cards the hand does not hold.
+    const double per_card = 1.0 / (double)(g.deck - s.nboard - 2 * g.hand_size);
+    double pay = 0.0;
+    if (s.type == kFold) pay = s.c[s.player] * s.chance;
+    if (s.type == kShowdown) pay = s.c[0] * s.chance;
+    nd.value = (float)pay;
+    if (s.type == kChance) {
+      nd.value = (float)per_card;
+      for (Pending& kp : kids) kp.chance = s.chance * per_card;
+    }
+    if (s.type == kShowdown) {
+      // showdown board table: 0 for boards fixed at the root, else by the last dealt card
+      if (spec.game == CFR_GAME_LEDUC) nd.row = s.board[0];
+      else if (spec.game == CFR_GAME_HOLDEM && g.n_streets == 2) nd.row = s.board[4];
+      else nd.row = 0;
+    }
+    if (s.type == kDecision ? kids.size() > (size_t)kMaxActions : kids.size() > (size_t)kMaxDeck) {
+      err = "too many actions at one node";
+      return CFR_EINVAL;
+    }
+    nd.n_kids = (uint8_t)kids.size();
+    if (!kids.empty()) nd.first_kid = id + 1 + (int)queue.size();
+    for (size_t k = 0; k < kids.size(); ++k) {
+      kids[k].parent = id;
+      kids[k].paction = (int)k;
+      kids[k].level = s.level + 1;
+      queue.push_back(kids[k]);
+    }
+    g.nodes.push_back(nd);
+    g.contrib.push_back(s.c[0]);
+    g.contrib.push_back(s.c[1]);
+    g.payoff.push_back(pay);
+    if (g.nodes.size() > (size_t)(1 << 24)) {
+      err = "tree too large";
+      return CFR_EINVAL;
+    }
+  }
+  const int N = (int)g.nodes.size();
+  int levels = g.nodes.back().level + 1;
+  g.level_start.assign(levels + 1, 0);
+  for (int n = 0; n < N; ++n) g.level_start[g.nodes[n].level + 1] = n + 1;
+  for (int l = 1; l <= levels; ++l) g.level_start[l] = std::max(g.level_start[l], g.level_start[l - 1]);
+  // rows: player 0's decision nodes first, then player 1's
+  int row = 0;
+  for (int p = 0; p < 2; ++p) {
+    g.row_begin[p] = row;
+    for (int n = 0; n < N; ++n)
+      if (g.nodes[n].type == kDecision && g.nodes[n].player == p) {
+        g.nodes[n].row = row;
+        row += g.nodes[n].n_kids;
+      }
+  }
+  g.row_begin[2] = row;
+  g.n_rows = row;
+  for (int n = 0; n < N; ++n)
+    if (g.nodes[n].type == kFold || g.nodes[n].type == kShowdown) g.terminals.push_back(n);
+
+  // ---- showdown tables, one per board the tree can show down on
+  std::vector<std::vector<int>> strengths;  // [board table][hand]
+  if (spec.game == CFR_GAME_KUHN) {
+    strengths.assign(1, std::vector<int>(H));
+    for (int h = 0; h < H; ++h) strengths[0][h] = h;
+  } else if (spec.game == CFR_GAME_LEDUC) {
+    strengths.assign(6, std::vector<int>(H));
+    for (int b = 0; b < 6; ++b)
+      for (int h = 0; h < H; ++h) strengths[b][h] = (h / 2 == b / 2) ? 10 + h / 2 : h / 2;
+  } else if (g.n_streets == 1) {
+    strengths.assign(1, std::vector<int>(spec.strength, spec.strength + H));
+  } else {
+    strengths.assign(52, std::vector<int>(H));
+    for (int r = 0; r < 52; ++r)
+      for (int h = 0; h < H; ++h) strengths[r][h] = spec.strength[(size_t)r * H + h];
+  }
+  const int B = (int)strengths.size();
+  const int k = g.hand_size;
+  g.n_boards = B;
+  g.cl_len = k * H;
+  g.sd_perm.resize((size_t)B * H);
+  g.sd_gs.resize((size_t)B * H);
+  g.sd_ge.resize((size_t)B * H);
+  g.cl_hand.resize((size_t)B * g.cl_len);
+  g.cl_off.resize((size_t)B * (g.deck + 1));
+  g.cl_lo.assign((size_t)B * H * 2, 0);
+  g.cl_hi.assign((size_t)B * H * 2, 0);
+  std::vector<int> order(H), pos(H);
+  for (int b = 0; b < B; ++b) {
+    const std::vector<int>& s = strengths[b];
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return s[x] < s[y]; });
+    int32_t* perm = &g.sd_perm[(size_t)b * H];
+    int32_t* gs = &g.sd_gs[(size_t)b * H];
+    int32_t* ge = &g.sd_ge[(size_t)b * H];
+    for (int j = 0; j < H; ++j) {
+      perm[j] = order[j];
+      pos[order[j]] = j;
+    }
+    for (int j = 0; j < H;) {
+      int e = j;
+      while (e < H && s[order[e]] == s[order[j]]) ++e;
+      for (int t = j; t < e; ++t) {
+        gs[order[t]] = j;
+        ge[order[t]] = e;
+      }
+      j = e;
+    }
+    // per-card lists of hands in sorted order
+    int32_t* off = &g.cl_off[(size_t)b * (g.deck + 1)];
+    int32_t* lst = &g.cl_hand[(size_t)b * g.cl_len];
+    std::vector<int> count(g.deck, 0);
+    for (int h = 0; h < H; ++h)
+      for (int t = 0; t < k; ++t) count[g.hand_cards[2 * h + t]]++;
+    off[0] = 0;
+    for (int c = 0; c < g.deck; ++c) off[c + 1] = off[c] + count[c];
+    std::vector<int> fill(off, off + g.deck);
+    for (int j = 0; j < H; ++j) {
+      const int h = order[j];
+      for (int t = 0; t < k; ++t) lst[fill[g.hand_cards[2 * h + t]]++] = h;
+    }
+    int32_t* lo = &g.cl_lo[(size_t)b * H * 2];
+    int32_t* hi = &g.cl_hi[(size_t)b * H * 2];
+    for (int h = 0; h < H; ++h)
+      for (int t = 0; t < k; ++t) {
+        const int c = g.hand_cards[2 * h + t];
+        int a = off[c], z = off[c + 1];
+        // entries of card c's list are in increasing sorted position
+        int x = a;
+        while (x < z && pos[lst[x]] < gs[h]) ++x;
+        lo[2 * h + t] = x;
+        int y = x;
+        while (y < z && pos[lst[y]] < ge[h]) ++y;
+        hi[2 * h + t] = y;
+      }
+  }
+  return CFR_OK;
+}
+
+}  // namespace pcfr

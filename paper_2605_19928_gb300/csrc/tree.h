@@ -1,0 +1,36 @@
+// Host-side construction of one subgame: the public tree in level order and the per-hand
+// tables the kernels read (card masks, rank-sorted showdown order, per-card hand lists).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "pcfr.h"
+#include "pcfr_internal.h"
+
+namespace pcfr {
+
+struct HostGame {
+  int game = 0, deck = 0, hand_size = 0, n_streets = 0;
+  // public tree, level order (children of a node are consecutive)
+  std::vector<NodeDev> nodes;
+  std::vector<double> contrib;        // [n_nodes][2]
+  std::vector<double> payoff;         // [n_nodes] terminal payoff times chance probability
+  std::vector<int32_t> level_start;   // [n_levels + 1]
+  int n_rows = 0;
+  int row_begin[3] = {0, 0, 0};
+  std::vector<int32_t> terminals;     // fold and showdown node ids
+  // hands
+  int n_hands = 0, hstride = 0;
+  std::vector<uint8_t> hand_cards;    // [n_hands][2]
+  std::vector<uint64_t> hand_mask;    // [n_hands]
+  std::vector<double> range[2];       // normalised
+  double Z = 0.0;
+  // showdown boards
+  int n_boards = 0, cl_len = 0;
+  std::vector<int32_t> sd_perm, sd_gs, sd_ge, cl_hand, cl_off, cl_lo, cl_hi;
+};
+
+// Validates `spec` and fills `out`; returns CFR_OK or CFR_EINVAL with a message in `err`.
+int build_game(const cfr_game_spec& spec, HostGame& out, std::string& err);
+
+}  // namespace pcfr

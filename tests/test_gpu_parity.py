@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs, element by element, after each of the first 10 iterations, plus exploitability."""
+import numpy as np
+import pytest
+
+from gpu_helpers import compare_player, compare_state, compare_strategies, forced_step, inject, node_map
+from paper_2605_19928_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2605_19928_gb300 import build as pbuild
+    pbuild.build()
+    capi.load()
+    import torch
+    assert torch.cuda.is_available()
+    capi.use_torch_allocator()
+
+
+def river(n_hands, seed=3, **kw):
+    return synth.river_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
+
+
+def turn(n_hands, seed=5, **kw):
+    kw.setdefault("bet_sizes", (1.0, synth.ALL_IN))
+    kw.setdefault("max_raises", 2)
+    return synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
+
+
+def kuhn_random(seed=7):
+    g = synth.kuhn()
+    g.ranges[:] = synth.random_ranges(3, seed)
+    return g
+
+
+def leduc_random(seed=11):
+    g = synth.leduc()
+    g.ranges[:] = synth.random_ranges(6, seed)
+    return g
+
+
+# Two checks per case.  "forced": every iteration starts the oracle from the GPU's own
+# state (gpu_helpers.forced_step), so each player's update is compared from identical
+# inputs.  "free": both run 10 iterations independently; this needs inputs whose trajectory
+# has no exact ties between action values, which FP64 and double-float may break
+# differently (with few hands, or uniform deals, such ties appear within a few iterations
+# and send two correct runs down different paths).
+CASES = {
+    "kuhn": (kuhn_random, ["cfr", "cfr+", "dcfr"], False),
+    "leduc": (leduc_random, ["cfr", "cfr+", "dcfr"], False),
+    "river_203": (lambda: river(203), ["dcfr", "cfr+"], True),        # 26 blocks, ragged tail
+    "river_64_r4": (lambda: river(64, seed=9, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
+                    ["dcfr"], False),
+    "turn_40": (lambda: turn(40), ["dcfr"], False),
+}
+
+
+def check_exploitability(tree, orc, mapping, pot, game=0, n_games=1):
+    """The GPU's best-response pass against the oracle's on the GPU's own average strategy."""
+    inject(tree, orc, mapping, game)
+    expl_g, br_g = capi.cfr_exploitability(tree, n_games=n_games)
+    e_o, b0, b1 = orc.exploitability()
+    assert expl_g[game] == pytest.approx(e_o, rel=1e-5, abs=1e-9 * pot)
+    assert br_g[game, 0] == pytest.approx(b0, rel=1e-5, abs=1e-9 * pot)
+    assert br_g[game, 1] == pytest.approx(b1, rel=1e-5, abs=1e-9 * pot)
+    for i in (0, 1):
+        orc.load_profile("average")
+        _, _, allv = orc.best_response(i, all_nodes=True)
+        for g, o, info in mapping:
+            got = capi.cfr_read_values(tree, capi.CFR_READ_BR_CFV, g, player=i, game=game)
+            want = allv[o]
+            scale = float(np.max(np.abs(want)))
+            assert float(np.max(np.abs(got - want))) <= 1e-5 * scale + 1e-8 * pot, (i, g)
+
+
+def run_pair(spec, variant, iters=10, alternating=True, chunk=0, forced=True, check_every=1):
+    from oracle.oracle import Oracle
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, alternating=alternating, chunk_hands=chunk))
+    try:
+        orc = Oracle(spec, variant=variant, alternating=alternating)
+        mapping = node_map(tree, orc)
+        worst = {}
+        for t in range(1, iters + 1):
+            if forced:
+                w = forced_step(tree, orc, mapping, t, alternating)
+            else:
+                capi.cfr_iterate(tree, 1)
+                orc.iterate(1)
+                if t % check_every and t != iters:
+                    continue
+                w = compare_state(tree, orc, mapping)
+            worst = {k: max(worst.get(k, 0.0), v) for k, v in w.items()}
+        if not forced:
+            e_g, _ = capi.cfr_exploitability(tree)
+            assert e_g[0] == pytest.approx(orc.exploitability()[0], rel=1e-2)
+        check_exploitability(tree, orc, mapping, spec.pot)
+        return worst
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("case,variant", [(c, v) for c, (_, vs, _) in CASES.items() for v in vs])
+def test_each_iteration_matches_oracle_from_the_same_state(case, variant):
+    worst = run_pair(CASES[case][0](), variant, forced=True)
+    print(case, variant, "forced", worst)
+
+
+@pytest.mark.parametrize("case,variant", [(c, v) for c, (_, vs, free) in CASES.items() if free for v in vs])
+def test_first_ten_iterations_match_oracle(case, variant):
+    worst = run_pair(CASES[case][0](), variant, forced=False)
+    print(case, variant, "free", worst)
+
+
+@pytest.mark.parametrize("game,variant,iters,bound", [
+    ("kuhn", "cfr", 1000, 2e-3), ("kuhn", "cfr+", 1000, 1e-3),
+    ("leduc", "cfr", 1000, 0.02), ("leduc", "cfr+", 1000, 2e-3), ("leduc", "dcfr", 1000, 2e-3)])
+def test_uniform_kuhn_and_leduc_converge_like_the_oracle(game, variant, iters, bound):
+    """Config: Leduc (936 infosets) and Kuhn with uniform deals, 1000 iterations, FP32 GPU vs
+    FP64 oracle.  Exact ties make the trajectories differ, so compare what is unique: both
+    reach the same small exploitability and the Kuhn game value -1/18."""
+    from oracle.oracle import Oracle
+    spec = synth.kuhn() if game == "kuhn" else synth.leduc()
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant))
+    try:
+        orc = Oracle(spec, variant=variant, threads=1)
+        capi.cfr_iterate(tree, iters)
+        orc.iterate(iters)
+        expl, br = capi.cfr_exploitability(tree)
+        e_o, b0, b1 = orc.exploitability()
+        assert 0.0 <= expl[0] < bound and e_o < bound
+        assert expl[0] < 3.0 * e_o + 1e-4
+        if game == "kuhn":
+            # BR_0 >= game value >= -BR_1, both within the exploitability of -1/18
+            assert br[0, 0] >= -1.0 / 18 - 1e-6 and -br[0, 1] <= -1.0 / 18 + 1e-6
+            assert abs(br[0, 0] + 1.0 / 18) <= 2 * expl[0] + 1e-6
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_full_size_river_ten_iterations():
+    """The benchmarked workload itself: 1081 hands, pot 100, stacks 400, {0.5, 1, all-in},
+    3 raises, DCFR(1.5, 0, 2), in the benchmark's launch configuration."""
+    worst = run_pair(synth.river_subgame(), "dcfr", iters=10, forced=False, check_every=5)
+    print("full river", worst)
+
+
+def test_simultaneous_updates_match_oracle():
+    run_pair(river(97, seed=21), "dcfr", iters=5, alternating=False)
+
+
+@pytest.mark.parametrize("chunk", [1, 4, 32])
+def test_block_shape_does_not_change_results(chunk):
+    run_pair(river(77, seed=13), "dcfr", iters=3, chunk=chunk)
+
+
+def test_all_strengths_equal_gives_zero_showdown_values():
+    spec = river(120, seed=17)
+    spec.strength[:] = 777
+    run_pair(spec, "dcfr", iters=3)
+
+
+def test_degenerate_ranges_and_tiny_trees():
+    spec = river(50, seed=19, max_raises=0)  # check / check only
+    spec.ranges[0, ::2] = 0.0
+    run_pair(spec, "dcfr", iters=3)
+    spec = river(50, seed=23, stack=0.0)     # no chips behind: no bets
+    run_pair(spec, "cfr", iters=2)
+
+
+def test_batch_matches_independent_solves():
+    from oracle.oracle import Oracle
+    specs = [river(60, seed=31), river(45, seed=32, bet_sizes=(1.0, synth.ALL_IN), max_raises=2),
+             leduc_random(seed=5), river(150, seed=33, stack=900.0, bet_sizes=(0.75, synth.ALL_IN))]
+    tree = capi.cfr_batch_create(specs, capi.make_opts("dcfr"))
+    try:
+        orcs = [Oracle(s, variant="dcfr") for s in specs]
+        maps = [node_map(tree, o, game=k) for k, o in enumerate(orcs)]
+        capi.cfr_iterate(tree, 4)  # reach a non-trivial state first
+        # the batch advances all games together, so compare each game's update from its
+        # own state: load, iterate the batch once, and check every game
+        for t in range(5, 8):
+            for k, (o, m) in enumerate(zip(orcs, maps)):
+                inject(tree, o, m, game=k)
+            capi.cfr_iterate(tree, 1)
+            for k, (o, m) in enumerate(zip(orcs, maps)):
+                o.update_player(0, t)
+                compare_player(tree, o, m, 0, game=k)
+                inject(tree, o, m, game=k, player=0)
+                o.update_player(1, t)
+                compare_player(tree, o, m, 1, game=k)
+                o.set_iterations(t)
+        for k, (o, m) in enumerate(zip(orcs, maps)):
+            check_exploitability(tree, o, m, specs[k].pot, game=k, n_games=len(specs))
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_average_strategy_readback():
+    from oracle.oracle import Oracle
+    spec = river(88, seed=41)
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr"))
+    try:
+        orc = Oracle(spec, variant="dcfr")
+        mapping = node_map(tree, orc)
+        capi.cfr_iterate(tree, 6)
+        inject(tree, orc, mapping)
+        orc.load_profile("average")
+        for g, o, info in mapping:
+            if info["type"] == capi.CFR_NODE_DECISION:
+                got = capi.cfr_strategy(tree, g, average=True)
+                compare_strategies(got, orc.avg_sums(o), what=f"average strategy node {g}", plus_part=False)
+                cur = capi.cfr_strategy(tree, g, average=False)
+                compare_strategies(cur, orc.regrets(o), what=f"current strategy node {g}")
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_invalid_specs_are_rejected():
+    spec = river(30, seed=5)
+    spec.hands[0, 0] = spec.board[0]
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_tree_create(spec)
+    assert e.value.code == capi.CFR_EINVAL
+    spec = river(30, seed=5)
+    spec.ranges[1, :] = 0.0
+    with pytest.raises(capi.CfrError):
+        capi.cfr_tree_create(spec)
+    spec = river(30, seed=5)
+    spec.ranges[0, 3] = np.nan
+    with pytest.raises(capi.CfrError):
+        capi.cfr_tree_create(spec)
