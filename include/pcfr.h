@@ -38,7 +38,7 @@ extern "C" {
 #define CFR_EINVAL (-1)   /* bad argument or game description */
 #define CFR_ENOMEM (-2)   /* host or device allocation failed */
 #define CFR_ECUDA (-3)    /* CUDA error or no suitable device */
-#define CFR_ETIMEOUT (-4) /* a bounded device-side wait gave up (reserved) */
+#define CFR_ETIMEOUT (-4) /* a bounded device-side wait gave up (reported by synchronising calls) */
 #define CFR_ESTATE (-5)   /* call not valid in the handle's current state */
 
 enum { CFR_GAME_HOLDEM = 0, CFR_GAME_KUHN = 1, CFR_GAME_LEDUC = 2 };
@@ -183,8 +183,7 @@ int cfr_sync(cfr_tree* tree);
  *                         forward reach of one player (Stages 6-7, then 1-2)
  *   CFR_STAGE_AVG_REACH   average strategy and its forward reach, both players
  *   CFR_STAGE_BR_TERMINAL terminal values against the average strategy, both players
- *   CFR_STAGE_BR          best-response backward pass, both players
- *   CFR_STAGE_BR_REDUCE   FP64 root reduction of the best-response values
+ *   CFR_STAGE_BR          best-response backward pass and FP64 root reduction, both players
  * Synchronises. */
 enum {
   CFR_STAGE_TERMINAL = 0,
@@ -192,8 +191,7 @@ enum {
   CFR_STAGE_AVG_REACH = 2,
   CFR_STAGE_BR_TERMINAL = 3,
   CFR_STAGE_BR = 4,
-  CFR_STAGE_BR_REDUCE = 5,
-  CFR_N_STAGES = 6
+  CFR_N_STAGES = 5
 };
 int cfr_stage_times(cfr_tree* tree, int n_iters, double* ms, int64_t* launches);
 

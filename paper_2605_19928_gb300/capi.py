@@ -24,7 +24,7 @@ CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV = 0, 1, 2, 3
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
 VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR}
-CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br", "br_reduce")
+CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",

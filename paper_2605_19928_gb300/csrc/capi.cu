@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -45,6 +46,9 @@ struct cfr_tree {
   Work* d_term_work = nullptr;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
+  int* d_err = nullptr;
+  Discount* d_disc = nullptr;
+  int disc_capacity = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
   cudaGraphExec_t iter_graph = nullptr;
@@ -112,11 +116,31 @@ int zeros(cfr_tree* t, size_t n, T** out) {
   return CFR_OK;
 }
 
-// Shared memory of the per-hand kernel for one game with W hands per block: values and
-// reach [n_nodes][W], strategy rows [rows_p][W] (value size es), R and S rows [rows_p][W].
+// Shared memory the per-hand kernel needs to stage one game with W hands per block.
 size_t hand_smem(const HostGame& g, int W, size_t es) {
   const int rows_max = std::max(g.row_begin[1] - g.row_begin[0], g.row_begin[2] - g.row_begin[1]);
-  return (size_t)(2 * g.nodes.size() + rows_max) * W * es + (size_t)2 * rows_max * W * 8;
+  return hand_smem_size((int)g.nodes.size(), (int)g.level_start.size() - 1, rows_max, W, es);
+}
+
+// Update weights of iterations 1 .. capacity (Stage 7; CFR+ and DCFR from Section 2):
+// DCFR multiplies positive regrets by t^a / (t^a + 1), the others by t^b / (t^b + 1) and
+// the average by (t / (t + 1))^g; CFR+ weighs the new average contribution by t.
+std::vector<Discount> discount_table(const cfr_solver_opts& o, int capacity) {
+  std::vector<Discount> d((size_t)capacity);
+  for (int k = 0; k < capacity; ++k) {
+    const double t = (double)(k + 1);
+    Discount x{1.0, 1.0, 1.0, 1.0};
+    if (o.variant == CFR_VARIANT_DCFR) {
+      const double ta = std::pow(t, o.alpha), tb = std::pow(t, o.beta);
+      x.dpos = ta / (ta + 1.0);
+      x.dneg = tb / (tb + 1.0);
+      x.dS = std::pow(t / (t + 1.0), o.gamma);
+    } else if (o.variant == CFR_VARIANT_CFRPLUS) {
+      x.wS = t;
+    }
+    d[(size_t)k] = x;
+  }
+  return d;
 }
 
 // Host copy of a per-hand vector in the value type: one float, or a (hi, lo) float pair.
@@ -190,7 +214,9 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     chunk[g] = W;
     use_smem[g] = hand_smem(h, W, es) <= 96 * 1024;
     if (use_smem[g]) smem_hand = std::max(smem_hand, hand_smem(h, W, es));
-    smem_term = std::max(smem_term, (size_t)(h.n_hands + 1 + h.cl_len + 1) * 8 + (size_t)h.n_hands * es);
+    const TermTab tt(h.n_hands, h.hand_size, h.deck);
+    smem_term = std::max(smem_term, (size_t)tt.len * 2 + (size_t)h.hstride * es +
+                                        (size_t)(h.hand_size * h.n_hands + 1 + h.n_hands + 1) * 8);
   }
 
   std::vector<Work> chunk_work, term_work;
@@ -213,36 +239,35 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     d.smem = use_smem[g];
     for (int k = 0; k < 3; ++k) d.row_begin[k] = h.row_begin[k];
     d.n_boards = h.n_boards;
-    d.cl_len = h.cl_len;
     d.kappa64 = 1.0 / h.Z;
     std::vector<double> r64(2 * S, 0.0);
     for (int p = 0; p < 2; ++p)
       for (int k = 0; k < h.n_hands; ++k) r64[p * S + k] = h.range[p][k];
     const std::vector<float> rv = to_value_type(r64, o.precision);
+    const std::vector<uint16_t> tab = pack_term_tables(h);
+    const std::vector<int32_t> rown = row_nodes(h);
     NodeDev* nodes;
-    int32_t *ls, *perm, *gs, *ge, *clh, *clo, *cllo, *clhi;
+    int32_t *ls, *rn;
+    uint16_t* tb;
     uint64_t* hm;
-    uint8_t* hc;
     float* rrv;
     double *rr64, *pay;
-    if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) ||
-        (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, h.hand_cards, &hc)) || (rc = upload(t, rv, &rrv)) ||
-        (rc = upload(t, r64, &rr64)) || (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, h.sd_perm, &perm)) ||
-        (rc = upload(t, h.sd_gs, &gs)) || (rc = upload(t, h.sd_ge, &ge)) || (rc = upload(t, h.cl_hand, &clh)) ||
-        (rc = upload(t, h.cl_off, &clo)) || (rc = upload(t, h.cl_lo, &cllo)) || (rc = upload(t, h.cl_hi, &clhi))) {
+    if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
+        (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
+        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb))) {
       delete t;
       return rc;
     }
-    d.nodes = nodes; d.level_start = ls; d.hand_mask = hm; d.hand_cards = hc; d.range_v = rrv;
-    d.range64 = rr64; d.payoff = pay; d.sd_perm = perm; d.sd_gs = gs; d.sd_ge = ge; d.cl_hand = clh;
-    d.cl_off = clo; d.cl_lo = cllo; d.cl_hi = clhi;
+    d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
+    d.payoff = pay; d.term_tab = tb;
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value
     float *sig, *sigb, *rch, *rchb, *cf, *cfb;
     if ((rc = zeros(t, rows, &d.R)) || (rc = zeros(t, rows, &d.S)) || (rc = zeros(t, rows * vf, &sig)) ||
         (rc = zeros(t, rows * vf, &sigb)) || (rc = zeros(t, cells * vf, &rch)) || (rc = zeros(t, cells * vf, &rchb)) ||
         (rc = zeros(t, cells * vf, &cf)) || (rc = zeros(t, cells * vf, &cfb)) ||
-        (rc = zeros(t, (size_t)2 * d.n_chunks, &d.br_partial)) || (rc = zeros(t, 2, &d.br_out))) {
+        (rc = zeros(t, (size_t)2 * d.n_chunks, &d.br_partial)) || (rc = zeros(t, 2, &d.br_out)) ||
+        (rc = zeros(t, 1, &d.br_done))) {
       delete t;
       return rc;
     }
@@ -252,7 +277,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   }
   if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
       (rc = upload(t, term_work, &t->d_term_work)) || (rc = zeros(t, 1, &t->d_iter)) ||
-      (rc = zeros(t, 1, &t->d_done))) {
+      (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) ||
+      (rc = upload(t, discount_table(o, kDiscountCapacity), &t->d_disc))) {
     delete t;
     return rc;
   }
@@ -265,13 +291,13 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.n_term_work = (int)term_work.size();
   c.iter = t->d_iter;
   c.done = t->d_done;
+  c.err = t->d_err;
+  c.disc = t->d_disc;
+  t->disc_capacity = kDiscountCapacity;
   c.smem_hand = smem_hand;
   c.smem_term = smem_term;
   c.variant = o.variant;
   c.precision = o.precision;
-  c.alpha = o.alpha;
-  c.beta = o.beta;
-  c.gamma = o.gamma;
   t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
   t->launches += 1;
   if (launch_init(c, stream) != 0) {
@@ -298,6 +324,33 @@ int enqueue_iteration(cfr_tree* t, cudaStream_t s) {
     if (launch_terminal(c, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
   }
   return 0;
+}
+
+// Make sure the discount table covers iterations up to `last`; a larger table replaces the
+// old one, and the recorded graphs (which hold its address) are recorded again.
+int ensure_discounts(cfr_tree* t, int64_t last) {
+  if (last <= t->disc_capacity) return CFR_OK;
+  int64_t cap = t->disc_capacity;
+  while (cap < last) cap *= 2;
+  if (cap > (1 << 30)) return fail(CFR_EINVAL, "too many iterations for one solve");
+  Discount* d = nullptr;
+  int rc = upload(t, discount_table(t->opts, (int)cap), &d);
+  if (rc) return rc;
+  t->d_disc = d;
+  t->ctx.disc = d;
+  t->disc_capacity = (int)cap;
+  if (t->iter_graph) cudaGraphExecDestroy(t->iter_graph);
+  t->iter_graph = nullptr;
+  return CFR_OK;
+}
+
+// Read the device error flag (synchronises): a bounded device-side wait that gave up.
+int check_device_flag(cfr_tree* t) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+  CK(cudaStreamSynchronize(t->stream));
+  if (flag) return fail(CFR_ETIMEOUT, "a bounded device-side wait gave up (bulk copy did not complete)");
+  return CFR_OK;
 }
 
 int check_game(const cfr_tree* t, int game) {
@@ -331,6 +384,8 @@ int cfr_iterate(cfr_tree* t, int n_iters) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   if (n_iters < 0) return fail(CFR_EINVAL, "n_iters < 0");
   if (n_iters == 0) return CFR_OK;
+  int rc0 = ensure_discounts(t, (int64_t)t->iters_done + n_iters);
+  if (rc0) return rc0;
   if (!t->iter_graph) {
     if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
     cudaGraph_t graph;
@@ -352,7 +407,7 @@ int cfr_iterate(cfr_tree* t, int n_iters) {
 int cfr_sync(cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   CK(cudaStreamSynchronize(t->stream));
-  return CFR_OK;
+  return check_device_flag(t);
 }
 
 int cfr_strategy(cfr_tree* t, int game, int node, int average, float* out, size_t out_len) {
@@ -385,7 +440,7 @@ int cfr_exploitability_async(cfr_tree* t) {
     CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
     const LaunchCtx& c = t->ctx;
     const int rc = launch_avg_reach(c, t->capture) || launch_terminal(c, 3, 1, t->capture) ||
-                   launch_br(c, t->capture) || launch_br_reduce(c, t->capture);
+                   launch_br(c, t->capture);
     cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
     if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -394,7 +449,7 @@ int cfr_exploitability_async(cfr_tree* t) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
   CK(cudaGraphLaunch(t->expl_graph, t->stream));
-  t->launches += t->ctx.n_term_work > 0 ? 4 : 3;
+  t->launches += t->ctx.n_term_work > 0 ? 3 : 2;
   return CFR_OK;
 }
 
@@ -406,6 +461,8 @@ int cfr_exploitability_result(cfr_tree* t, double* expl, double* br) {
   for (int g = 0; g < G; ++g)
     CK(cudaMemcpyAsync(&vals[2 * g], t->dev[g].br_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, t->stream));
   CK(cudaStreamSynchronize(t->stream));
+  const int frc = check_device_flag(t);
+  if (frc) return frc;
   for (int g = 0; g < G; ++g) {
     expl[g] = 0.5 * (vals[2 * g] + vals[2 * g + 1]);
     if (br) {
@@ -504,6 +561,8 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
 int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   if (!ms || n_iters < 0) return fail(CFR_EINVAL, "bad arguments");
+  const int drc = ensure_discounts(t, (int64_t)t->iters_done + n_iters);
+  if (drc) return drc;
   const LaunchCtx& c = t->ctx;
   cudaStream_t s = t->stream;
   std::vector<cudaEvent_t> ev;
@@ -539,8 +598,6 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (!rc && err == cudaSuccess && c.n_term_work > 0) err = mark(CFR_STAGE_BR_TERMINAL);
   if (!rc && err == cudaSuccess) rc = launch_br(c, s);
   if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_BR);
-  if (!rc && err == cudaSuccess) rc = launch_br_reduce(c, s);
-  if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_BR_REDUCE);
   cudaError_t serr = cudaStreamSynchronize(s);
   double tot[CFR_N_STAGES] = {0};
   int64_t cnt[CFR_N_STAGES] = {0};

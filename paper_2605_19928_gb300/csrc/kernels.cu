@@ -12,7 +12,9 @@
 //     inclusion-exclusion at folds, rank-sorted prefix sums with per-card corrections at
 //     showdowns.
 // One player's update is therefore two launches (terminal, then hand), recorded once in
-// a CUDA graph.
+// a CUDA graph.  Inside k_hand the FP64 regret / average update is one fully parallel pass
+// over (row, hand) items after the backward levels, so GB300's long FP64 latency is paid
+// once per launch rather than once per tree level.
 //
 // Precision: cumulative regrets R and average sums S are FP64 (GB300 runs FP64 at about
 // 1/64 of the FP32 rate, so FP64 is kept to those updates).  Reach, strategies and values
@@ -200,6 +202,45 @@ __device__ __forceinline__ ff block_exclusive_scan(int n, F value_at, ff* out, f
   return total;
 }
 
+// ------------------------------------------------------------------ bulk copies (TMA) into shared memory
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Make the barrier's initialisation visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// One-dimensional bulk copy global -> shared; both addresses and the size are multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of the barrier: false if it did not complete in time.
+constexpr long kWaitLimit = 1l << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (long k = 0; k < kWaitLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // ------------------------------------------------------------------ terminal values (Stages 2-4)
 
 // One block per (player, terminal node).  q is the opponent's reach at the node, kappa = 1/Z,
@@ -211,11 +252,12 @@ __device__ __forceinline__ ff block_exclusive_scan(int n, F value_at, ff* out, f
 //                     stronger hands that share no card with h, from exclusive prefix sums
 //                     over the rank-sorted order minus per-card prefix sums; the tie group
 //                     of h is excluded from both (a split pot pays 0).
-// Sums and differences are taken in double-float in both precisions.
+// The board's index tables and the reach row arrive in shared memory by two bulk (TMA)
+// copies; sums and differences are taken in double-float in both precisions.
 template <typename P>
 __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __restrict__ games,
                                                             const Work* __restrict__ work, int n_work,
-                                                            int player_mask, int use_bar) {
+                                                            int player_mask, int use_bar, int* err) {
   using V = typename P::V;
   int item = blockIdx.x;
   int i;
@@ -229,69 +271,95 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
   const GameDev& G = games[wk.game];
   const int n = wk.unit;
   const NodeDev nd = G.nodes[n];
-  const int H = G.n_hands;
+  const int H = G.n_hands, k = G.hand_size;
   const size_t stride = (size_t)G.hstride;
+  const TermTab tt(H, k, G.deck);
+  const bool show = nd.type == kShowdown;
+  const int b = show ? nd.row : 0;
+  const unsigned tab_bytes = (unsigned)(show ? tt.len : tt.fold_len) * 2u;
+  const unsigned q_bytes = (unsigned)(stride * sizeof(V));
   const V* __restrict__ q =
       static_cast<const V*>(use_bar ? G.reach_bar : G.reach) + ((size_t)(1 - i) * G.n_nodes + n) * stride;
   V* __restrict__ out = static_cast<V*>(use_bar ? G.cfv_br : G.cfv) + ((size_t)i * G.n_nodes + n) * stride;
 
-  extern __shared__ __align__(16) unsigned char smt[];
+  extern __shared__ __align__(128) unsigned char smt[];
+  __shared__ __align__(8) uint64_t bar;
   __shared__ ff red[33];
-  ff* Psc = reinterpret_cast<ff*>(smt);                   // [H + 1]
-  ff* CP = Psc + H + 1;                                   // [cl_len + 1]
-  V* qs = reinterpret_cast<V*>(CP + G.cl_len + 1);        // [H]
-  for (int h = threadIdx.x; h < H; h += kTermThreads) qs[h] = q[h];
-  __syncthreads();
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smt);                             // [tt.len]
+  V* qs = reinterpret_cast<V*>(smt + (size_t)tt.len * 2);                        // [hstride]
+  ff* CP = reinterpret_cast<ff*>(smt + (size_t)tt.len * 2 + q_bytes);            // [k H + 1]
+  ff* Psc = CP + (k * H + 1);                                                    // [H + 1]
 
-  // payoff for player i per unit of (opponent reach) x kappa, formed in FP64 once per block
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, tab_bytes + q_bytes);
+    bulk_copy_g2s(tab, G.term_tab + (size_t)b * tt.len, tab_bytes, &bar);
+    bulk_copy_g2s(qs, q, q_bytes, &bar);
+  }
+  // payoff for player i per unit of (opponent reach) x kappa, in FP64 while the copies land
   const double pay = G.payoff[n];
   const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
   const ff u = d2ff(u64);
-  const int b = nd.type == kShowdown ? nd.row : 0;
-  const int32_t* __restrict__ clh = G.cl_hand + (size_t)b * G.cl_len;
-  const int32_t* __restrict__ clo = G.cl_off + (size_t)b * (G.deck + 1);
-  block_exclusive_scan<kTermThreads>(G.cl_len, [&](int j) { return P::to_ff(qs[clh[j]]); }, CP, red);
-  const int k = G.hand_size;
   const uint64_t board = nd.board;
+  const bool ok = mbar_wait_bounded(&bar, 0);
+  if (__syncthreads_or(!ok)) {  // the copies did not land: report, let them drain, leave
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      mbar_wait_bounded(&bar, 0);
+    }
+    __syncthreads();
+    return;
+  }
 
-  if (nd.type == kFold) {
+  const uint16_t* clh = tab + tt.clh;
+  const uint16_t* cards = tab + tt.cards;
+  const uint16_t* cloff = tab + tt.cloff;
+  block_exclusive_scan<kTermThreads>(k * H, [&](int j) { return P::to_ff(qs[clh[j]]); }, CP, red);
+
+  if (!show) {
     ff loc = ff_of(0.f);
     for (int h = threadIdx.x; h < H; h += kTermThreads) loc = ff_add(loc, P::to_ff(qs[h]));
     const ff T = block_sum_ff<kTermThreads>(loc, red);
     for (int h = threadIdx.x; h < H; h += kTermThreads) {
-      ff m = T;
-      for (int s = 0; s < k; ++s) {
-        const int c = G.hand_cards[2 * h + s];
-        m = ff_sub(m, ff_sub(CP[clo[c + 1]], CP[clo[c]]));
+      const unsigned cw = cards[h];
+      const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
+      ff m = ff_sub(T, ff_sub(CP[cloff[c1 + 1]], CP[cloff[c1]]));
+      bool blocked = (board >> c1) & 1ull;
+      if (k == 2) {
+        m = ff_sub(m, ff_sub(CP[cloff[c2 + 1]], CP[cloff[c2]]));
+        m = ff_add(m, P::to_ff(qs[h]));
+        blocked = blocked || ((board >> c2) & 1ull);
       }
-      if (k == 2) m = ff_add(m, P::to_ff(qs[h]));
-      out[h] = (G.hand_mask[h] & board) ? P::zero() : P::of_ff(ff_mul(u, m));
+      out[h] = blocked ? P::zero() : P::of_ff(ff_mul(u, m));
     }
   } else {
-    const int32_t* __restrict__ perm = G.sd_perm + (size_t)b * H;
-    const int32_t* __restrict__ gs = G.sd_gs + (size_t)b * H;
-    const int32_t* __restrict__ ge = G.sd_ge + (size_t)b * H;
-    const int32_t* __restrict__ lo = G.cl_lo + (size_t)b * H * 2;
-    const int32_t* __restrict__ hi = G.cl_hi + (size_t)b * H * 2;
+    const uint16_t* perm = tab + tt.perm;
+    const uint16_t* gs = tab + tt.gs;
+    const uint16_t* ge = tab + tt.ge;
+    const uint16_t* lo = tab + tt.lo;
+    const uint16_t* hi = tab + tt.hi;
     const ff T = block_exclusive_scan<kTermThreads>(H, [&](int j) { return P::to_ff(qs[perm[j]]); }, Psc, red);
     for (int h = threadIdx.x; h < H; h += kTermThreads) {
+      const unsigned cw = cards[h];
       ff Wn = Psc[gs[h]];
       ff Ln = ff_sub(T, Psc[ge[h]]);
+      bool blocked = false;
       for (int s = 0; s < k; ++s) {
-        const int c = G.hand_cards[2 * h + s];
-        Wn = ff_sub(Wn, ff_sub(CP[lo[2 * h + s]], CP[clo[c]]));
-        Ln = ff_sub(Ln, ff_sub(CP[clo[c + 1]], CP[hi[2 * h + s]]));
+        const unsigned c = s == 0 ? (cw & 0xffu) : (cw >> 8);
+        Wn = ff_sub(Wn, ff_sub(CP[lo[2 * h + s]], CP[cloff[c]]));
+        Ln = ff_sub(Ln, ff_sub(CP[cloff[c + 1]], CP[hi[2 * h + s]]));
+        blocked = blocked || ((board >> c) & 1ull);
       }
-      out[h] = (G.hand_mask[h] & board) ? P::zero() : P::of_ff(ff_mul(u, ff_sub(Wn, Ln)));
+      out[h] = blocked ? P::zero() : P::of_ff(ff_mul(u, ff_sub(Wn, Ln)));
     }
   }
 }
 
 // ------------------------------------------------------------------ per-hand passes
-
-struct Discount {
-  double dpos, dneg, dS, wS;
-};
 
 // One column of a [rows][*] array: shared memory (row stride W, column w) or global
 // memory (row stride hstride, column h).
@@ -302,20 +370,30 @@ struct Col {
   __device__ __forceinline__ T& operator[](int row) const { return base[(size_t)row * rs]; }
 };
 
+__host__ __device__ inline size_t round16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Shared memory of the per-hand kernel for one game (must match the layout in k_hand):
+// nodes, level offsets, row -> node map, R and S rows, then values, reach and strategy.
+__host__ __device__ inline size_t hand_smem_bytes(int n_nodes, int n_levels, int rows_max, int W, size_t es) {
+  return round16((size_t)n_nodes * sizeof(NodeDev)) + round16((size_t)(n_levels + 1) * 4) +
+         round16((size_t)rows_max * 4) + 2 * round16((size_t)rows_max * W * 8) +
+         (size_t)(2 * n_nodes + rows_max) * W * es;
+}
+
 // Per-hand tree passes for one chunk of W hands of player p (grid: (player, chunk)).
 //   kModeInit:   sigma_p = RM(R_p) (Eq. rm), forward reach of p (Stage 1).
 //   kModeUpdate: backward values of p (Stage 6, Eq. backward) from the terminal values,
 //                regret and average update (Stage 7), new sigma_p, forward reach of p.
 //   kModeAvg:    average strategy S / sum S of p, forward reach of p under it.
-//   kModeBR:     best-response backward pass of p (max over p's actions), root sum.
-// With G.smem set the block keeps v[n_nodes][W], reach[n_nodes][W], the strategy rows
-// [rows_p][W] and (updates) the R and S rows [rows_p][W] of its hands in shared memory;
-// otherwise it works on the global arrays directly.
+//   kModeBR:     best-response backward pass of p (max over p's actions) and the FP64
+//                root sum r_p(h) v*_p(root, h), reduced by the last block of each game.
+// With G.smem set the block stages the tree and its hands' state in shared memory;
+// otherwise it works on the global arrays directly (trees too large to stage).
 template <int MODE, typename P>
 __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict__ games,
                                                        const Work* __restrict__ work, int n_work, int player_mask,
-                                                       int advance, int* iter, unsigned* done, int variant,
-                                                       double alpha, double beta, double gamma) {
+                                                       int advance, int* iter, unsigned* done,
+                                                       const Discount* __restrict__ disc_tab, int variant) {
   using V = typename P::V;
   int item = blockIdx.x;
   int p;
@@ -328,19 +406,20 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   const Work wk = work[item];
   const GameDev& G = games[wk.game];
   const int W = G.chunk;
-  const int w = threadIdx.x % W;
-  const int slot = threadIdx.x / W;
+  const int tid = threadIdx.x;
+  const int w = tid % W;
+  const int slot = tid / W;
   const int nslots = kHandThreads / W;
   const int h = wk.unit * W + w;  // < hstride: hstride is a multiple of 32 and W divides 32
   const bool valid = h < G.n_hands;
-  const int N = G.n_nodes;
+  const int N = G.n_nodes, L = G.n_levels;
   const size_t stride = (size_t)G.hstride;
   const int rb = G.row_begin[p], re = G.row_begin[p + 1];
   const int nrows = re - rb;
-  const NodeDev* __restrict__ nodes = G.nodes;
-  const int32_t* __restrict__ ls = G.level_start;
+  const int rows_max = max(G.row_begin[1] - G.row_begin[0], G.row_begin[2] - G.row_begin[1]);
   const uint64_t hmask = valid ? G.hand_mask[h] : 0ull;
   const bool sm = G.smem != 0;
+  const bool wr = sm || valid;  // this lane may write its column of the working arrays
 
   // global arrays of this player, at column h
   V* gv = static_cast<V*>(MODE == kModeBR ? G.cfv_br : G.cfv) + (size_t)p * N * stride + h;
@@ -349,86 +428,63 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   double* gR = G.R + (size_t)rb * stride + h;
   double* gS = G.S + (size_t)rb * stride + h;
 
+  // shared layout (see hand_smem_bytes)
   extern __shared__ __align__(16) unsigned char smraw[];
-  const bool stage_rs = sm && MODE == kModeUpdate;
-  double* sR = reinterpret_cast<double*>(smraw);                          // [nrows][W]
-  double* sS = sR + (stage_rs ? (size_t)nrows * W : 0);                   // [nrows][W]
-  V* sv = reinterpret_cast<V*>(sS + (stage_rs ? (size_t)nrows * W : 0));  // [N][W]
-  V* srch = sv + (size_t)N * W;                                           // [N][W]
-  V* ssg = srch + (size_t)N * W;                                          // [nrows][W]
+  unsigned char* cur = smraw;
+  NodeDev* snodes = reinterpret_cast<NodeDev*>(cur);
+  cur += round16((size_t)N * sizeof(NodeDev));
+  int* sls = reinterpret_cast<int*>(cur);
+  cur += round16((size_t)(L + 1) * 4);
+  int* srow = reinterpret_cast<int*>(cur);
+  cur += round16((size_t)rows_max * 4);
+  double* sR = reinterpret_cast<double*>(cur);
+  cur += round16((size_t)rows_max * W * 8);
+  double* sS = reinterpret_cast<double*>(cur);
+  cur += round16((size_t)rows_max * W * 8);
+  V* sv = reinterpret_cast<V*>(cur);
+  V* srch = sv + (size_t)N * W;
+  V* ssg = srch + (size_t)N * W;
 
+  const NodeDev* nodes = sm ? snodes : G.nodes;
+  const int* ls = sm ? sls : G.level_start;
+  const int* rown = sm ? srow : G.row_node + rb;
   const Col<V> v = sm ? Col<V>{sv + w, (size_t)W} : Col<V>{gv, stride};
   const Col<V> rch = sm ? Col<V>{srch + w, (size_t)W} : Col<V>{grch, stride};
   const Col<V> sg = sm ? Col<V>{ssg + w, (size_t)W} : Col<V>{gsg, stride};
-  const Col<double> Rc = stage_rs ? Col<double>{sR + w, (size_t)W} : Col<double>{gR, stride};
-  const Col<double> Sc = stage_rs ? Col<double>{sS + w, (size_t)W} : Col<double>{gS, stride};
+  const Col<double> Rc = sm ? Col<double>{sR + w, (size_t)W} : Col<double>{gR, stride};
+  const Col<double> Sc = sm ? Col<double>{sS + w, (size_t)W} : Col<double>{gS, stride};
   __shared__ Discount disc;
+  __shared__ int s_last;
+  __shared__ double red64[kHandThreads];
 
-  if (MODE == kModeUpdate && threadIdx.x == 0) {
-    const int t = *iter + 1;
-    Discount d{1.0, 1.0, 1.0, 1.0};
-    if (variant == 2) {
-      const double ta = pow((double)t, alpha), tb = pow((double)t, beta);
-      d.dpos = ta / (ta + 1.0);
-      d.dneg = tb / (tb + 1.0);
-      d.dS = pow((double)t / (double)(t + 1), gamma);
-    } else if (variant == 1) {
-      d.wS = (double)t;
-    }
-    disc = d;
-  }
-
-  // ---- stage what the pass starts from
-  if (sm && (MODE == kModeUpdate || MODE == kModeBR)) {
-    for (int n = slot; n < N; n += nslots) {
-      const uint8_t ty = nodes[n].type;
-      if (ty == kFold || ty == kShowdown) v[n] = gv[(size_t)n * stride];
-    }
-  }
-  if (sm && MODE == kModeUpdate) {
-    for (int n = slot; n < N; n += nslots) rch[n] = grch[(size_t)n * stride];
-    for (int r = slot; r < nrows; r += nslots) {
-      sg[r] = gsg[(size_t)r * stride];
-      Rc[r] = gR[(size_t)r * stride];
-      Sc[r] = gS[(size_t)r * stride];
-    }
-  }
-  if (MODE == kModeInit || MODE == kModeAvg) {
-    // strategy rows of player p: regret matching of R (Eq. rm), or S / sum S
-    const double* src = (MODE == kModeInit ? G.R : G.S) + h;
-    for (int n = slot; n < N; n += nslots) {
-      const NodeDev nd = nodes[n];
-      if (nd.type != kDecision || nd.player != p) continue;
-      const int A = nd.n_kids;
-      V tot = P::zero();
-      int npos = 0, last = 0;
-      for (int a = 0; a < A; ++a) {
-        const double x = src[(size_t)(nd.row + a) * stride];
-        const V xv = x > 0.0 ? P::of_double(x) : P::zero();
-        if (x > 0.0) ++npos, last = a;
-        if (sm || valid) sg[nd.row - rb + a] = xv;
-        tot = P::add(tot, xv);
-      }
-      if (npos == 1) {  // x / x = 1 exactly, as the definition gives
-        for (int a = 0; a < A; ++a)
-          if (sm || valid) sg[nd.row - rb + a] = a == last ? P::of_double(1.0) : P::zero();
-      } else if (P::positive(tot)) {
-        const V inv = P::recip(tot);
-        for (int a = 0; a < A; ++a)
-          if (sm || valid) sg[nd.row - rb + a] = P::mul(sg[nd.row - rb + a], inv);
-      } else {
-        const V uni = P::of_double(1.0 / A);
-        for (int a = 0; a < A; ++a)
-          if (sm || valid) sg[nd.row - rb + a] = uni;
+  // ---- stage: every load is independent of the others, so they are all in flight at once
+  if (MODE == kModeUpdate && tid == 0) disc = disc_tab[*iter];
+  if (sm) {
+    const int4* gn = reinterpret_cast<const int4*>(G.nodes);
+    int4* sn = reinterpret_cast<int4*>(snodes);
+    for (int k = tid; k < 2 * N; k += kHandThreads) sn[k] = gn[k];
+    for (int k = tid; k <= L; k += kHandThreads) sls[k] = G.level_start[k];
+    for (int k = tid; k < nrows; k += kHandThreads) srow[k] = G.row_node[rb + k];
+    if (MODE == kModeUpdate || MODE == kModeBR)
+      for (int n = slot; n < N; n += nslots) v[n] = gv[(size_t)n * stride];
+    if (MODE == kModeUpdate) {
+      for (int n = slot; n < N; n += nslots) rch[n] = grch[(size_t)n * stride];
+      for (int r = slot; r < nrows; r += nslots) {
+        sg[r] = gsg[(size_t)r * stride];
+        Rc[r] = gR[(size_t)r * stride];
+        Sc[r] = gS[(size_t)r * stride];
       }
     }
+    if (MODE == kModeInit)
+      for (int r = slot; r < nrows; r += nslots) Rc[r] = gR[(size_t)r * stride];
+    if (MODE == kModeAvg)
+      for (int r = slot; r < nrows; r += nslots) Sc[r] = gS[(size_t)r * stride];
   }
   __syncthreads();
 
-  // ---- backward pass (Stage 6) with the Stage 7 update, or the best-response pass
+  // ---- backward pass (Stage 6), double-float only, level by level from the leaves
   if (MODE == kModeUpdate || MODE == kModeBR) {
-    const Discount d = disc;
-    for (int l = G.n_levels - 1; l >= 0; --l) {
+    for (int l = L - 1; l >= 0; --l) {
       const int a0 = ls[l], cnt = ls[l + 1] - a0;
       for (int idx = slot; idx < cnt; idx += nslots) {
         const int n = a0 + idx;
@@ -438,10 +494,8 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
         V val = P::zero();
         if (nd.type == kChance) {
           // children values already carry the card probabilities; cards in the hand are out
-          for (int a = 0; a < A; ++a) {
-            const int card = nodes[k0 + a].deal;
-            if (!((hmask >> card) & 1ull)) val = P::add(val, v[k0 + a]);
-          }
+          for (int a = 0; a < A; ++a)
+            if (!((hmask >> nodes[k0 + a].deal) & 1ull)) val = P::add(val, v[k0 + a]);
         } else if (nd.player != p) {
           for (int a = 0; a < A; ++a) val = P::add(val, v[k0 + a]);
         } else if (MODE == kModeBR) {
@@ -450,94 +504,129 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
         } else {
           const int r0 = nd.row - rb;
           for (int a = 0; a < A; ++a) val = P::add(val, P::mul(sg[r0 + a], v[k0 + a]));
-          const V own = rch[n];
-          V pos = P::zero();
-          int npos = 0, last = 0;
-          for (int a = 0; a < A; ++a) {
-            const V r = P::sub(v[k0 + a], val);                            // instantaneous regret
-            const double contrib = P::to_double(P::mul(own, sg[r0 + a]));  // pi_i(I) sigma(I, a)
-            double x = Rc[r0 + a] + P::to_double(r);
-            if (variant == 2) x *= x > 0.0 ? d.dpos : d.dneg;
-            if (variant == 1 && x < 0.0) x = 0.0;
-            const double s = fma(Sc[r0 + a], d.dS, d.wS * contrib);
-            const V xv = x > 0.0 ? P::of_double(x) : P::zero();  // positive part of the new R
-            if (x > 0.0) ++npos, last = a;
-            if (sm || valid) {
-              Rc[r0 + a] = x;
-              Sc[r0 + a] = s;
-              sg[r0 + a] = xv;
-            }
-            pos = P::add(pos, xv);
-          }
-          // regret matching of the updated R (Eq. rm); sg holds its positive part
-          if (npos == 1) {  // x / x = 1 exactly, as the definition gives
-            for (int a = 0; a < A; ++a)
-              if (sm || valid) sg[r0 + a] = a == last ? P::of_double(1.0) : P::zero();
-          } else if (P::positive(pos)) {
-            const V inv = P::recip(pos);
-            for (int a = 0; a < A; ++a)
-              if (sm || valid) sg[r0 + a] = P::mul(sg[r0 + a], inv);
-          } else {
-            const V uni = P::of_double(1.0 / A);
-            for (int a = 0; a < A; ++a)
-              if (sm || valid) sg[r0 + a] = uni;
-          }
         }
-        if (sm || valid) v[n] = val;
+        if (wr) v[n] = val;
       }
       __syncthreads();
     }
     if (sm && valid)
       for (int n = slot; n < N; n += nslots) gv[(size_t)n * stride] = v[n];
-    if (MODE == kModeBR) {
-      if (threadIdx.x == 0) {
-        double acc = 0.0;
-        const double* r64 = G.range64 + (size_t)p * stride;
-        const V* root = static_cast<const V*>(G.cfv_br) + (size_t)p * N * stride;
-        for (int j = 0; j < W; ++j) {
-          const int hh = wk.unit * W + j;
-          if (hh < G.n_hands) acc += r64[hh] * P::to_double(sm ? sv[j] : root[hh]);
-        }
-        G.br_partial[(size_t)p * G.n_chunks + wk.unit] = acc;
-      }
-      return;
-    }
-    if (sm && valid)
-      for (int r = slot; r < nrows; r += nslots) {
-        gR[(size_t)r * stride] = Rc[r];
-        gS[(size_t)r * stride] = Sc[r];
-      }
   }
 
-  // ---- forward reach of player p (Stages 1-2) under the strategy in sg
-  {
-    if (slot == 0) {
-      const V r0 = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
-      if (sm || valid) rch[0] = r0;
+  // ---- best response: FP64 root sum of this chunk, then the last block of the game
+  //      reduces all chunks of both players in a fixed order
+  if (MODE == kModeBR) {
+    if (tid < W) {  // slot 0: one lane per hand of the chunk, all in warp 0
+      double x = valid ? G.range64[(size_t)p * stride + h] * P::to_double(v[0]) : 0.0;
+      const unsigned mask = W == 32 ? 0xffffffffu : (1u << W) - 1u;
+      for (int o = W / 2; o > 0; o >>= 1) x += __shfl_down_sync(mask, x, o, W);
+      if (tid == 0) G.br_partial[(size_t)p * G.n_chunks + wk.unit] = x;
     }
     __syncthreads();
-    for (int l = 1; l < G.n_levels; ++l) {
-      const int a0 = ls[l], cnt = ls[l + 1] - a0;
-      for (int idx = slot; idx < cnt; idx += nslots) {
-        const int n = a0 + idx;
-        const NodeDev nd = nodes[n];
-        const NodeDev par = nodes[nd.parent];
-        V x = (sm || valid) ? rch[nd.parent] : P::zero();
-        if (par.type == kDecision && par.player == p) x = P::mul(x, sg[par.row - rb + nd.paction]);
-        if (par.type == kChance && ((hmask >> nd.deal) & 1ull)) x = P::zero();
-        if (sm || valid) rch[n] = x;
+    if (tid == 0) {
+      __threadfence();
+      s_last = atomicAdd(G.br_done, 1u) == (unsigned)(2 * G.n_chunks - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int q = 0; q < 2; ++q) {
+        double x = 0.0;
+        for (int c = tid; c < G.n_chunks; c += kHandThreads) x += G.br_partial[(size_t)q * G.n_chunks + c];
+        red64[tid] = x;
+        __syncthreads();
+        for (int o = kHandThreads / 2; o > 0; o >>= 1) {
+          if (tid < o) red64[tid] += red64[tid + o];
+          __syncthreads();
+        }
+        if (tid == 0) G.br_out[q] = red64[0];
+        __syncthreads();
       }
-      __syncthreads();
+      if (tid == 0) *G.br_done = 0u;
     }
-    if (sm && valid) {
-      for (int n = slot; n < N; n += nslots) grch[(size_t)n * stride] = rch[n];
-      for (int r = slot; r < nrows; r += nslots) gsg[(size_t)r * stride] = sg[r];
+    return;
+  }
+
+  // ---- positive parts of the strategy source, one (row, hand) item per thread:
+  //      update: the Stage 7 update of R and S, then the positive part of the new R;
+  //      init: the positive part of R;  average: S
+  {
+    const Discount d = disc;
+    for (int r = slot; r < nrows; r += nslots) {
+      V pos;
+      if (MODE == kModeUpdate) {
+        const int n = rown[r];
+        const NodeDev nd = nodes[n];
+        const int a = rb + r - nd.row;
+        const V rr = P::sub(v[nd.first_kid + a], v[n]);                 // instantaneous regret
+        const double contrib = P::to_double(P::mul(rch[n], sg[r]));     // pi_i(I) sigma(I, a)
+        double x = Rc[r] + P::to_double(rr);
+        if (variant == 2) x *= x > 0.0 ? d.dpos : d.dneg;
+        if (variant == 1 && x < 0.0) x = 0.0;
+        const double s = fma(Sc[r], d.dS, d.wS * contrib);
+        if (valid) {
+          gR[(size_t)r * stride] = x;
+          gS[(size_t)r * stride] = s;
+        }
+        pos = x > 0.0 ? P::of_double(x) : P::zero();
+      } else {
+        const double x = MODE == kModeInit ? Rc[r] : Sc[r];
+        pos = x > 0.0 ? P::of_double(x) : P::zero();
+      }
+      if (wr) sg[r] = pos;
     }
+  }
+  __syncthreads();
+
+  // ---- regret matching (Eq. rm) / normalisation of the average, per decision node of p
+  for (int n = slot; n < N; n += nslots) {
+    const NodeDev nd = nodes[n];
+    if (nd.type != kDecision || nd.player != p) continue;
+    const int A = nd.n_kids, r0 = nd.row - rb;
+    V tot = P::zero();
+    int npos = 0, last = 0;
+    for (int a = 0; a < A; ++a) {
+      const V x = sg[r0 + a];
+      if (P::positive(x)) ++npos, last = a;
+      tot = P::add(tot, x);
+    }
+    if (!wr) continue;
+    if (npos == 1) {  // x / x = 1 exactly, as the definition gives
+      for (int a = 0; a < A; ++a) sg[r0 + a] = a == last ? P::of_double(1.0) : P::zero();
+    } else if (npos > 1) {
+      const V inv = P::recip(tot);
+      for (int a = 0; a < A; ++a) sg[r0 + a] = P::mul(sg[r0 + a], inv);
+    } else {
+      const V uni = P::of_double(1.0 / A);
+      for (int a = 0; a < A; ++a) sg[r0 + a] = uni;
+    }
+  }
+  __syncthreads();
+
+  // ---- forward reach of player p (Stages 1-2) under the strategy in sg
+  if (slot == 0 && wr) rch[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
+  __syncthreads();
+  for (int l = 1; l < L; ++l) {
+    const int a0 = ls[l], cnt = ls[l + 1] - a0;
+    for (int idx = slot; idx < cnt; idx += nslots) {
+      const int n = a0 + idx;
+      const NodeDev nd = nodes[n];
+      const NodeDev par = nodes[nd.parent];
+      V x = wr ? rch[nd.parent] : P::zero();
+      if (par.type == kDecision && par.player == p) x = P::mul(x, sg[par.row - rb + nd.paction]);
+      if (par.type == kChance && ((hmask >> nd.deal) & 1ull)) x = P::zero();
+      if (wr) rch[n] = x;
+    }
+    __syncthreads();
+  }
+  if (sm && valid) {
+    for (int n = slot; n < N; n += nslots) grch[(size_t)n * stride] = rch[n];
+    for (int r = slot; r < nrows; r += nslots) gsg[(size_t)r * stride] = sg[r];
   }
 
   if (MODE == kModeUpdate && advance) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       __threadfence();
       const unsigned prev = atomicAdd(done, 1u);
       if (prev == gridDim.x - 1) {  // last block of the launch: every block has read *iter
@@ -546,17 +635,6 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
         __threadfence();
       }
     }
-  }
-}
-
-// FP64 sum of the per-chunk best-response partials: one block per game, fixed order.
-__global__ void k_br_reduce(const GameDev* __restrict__ games) {
-  const GameDev& G = games[blockIdx.x];
-  if (threadIdx.x < 2) {
-    const int p = threadIdx.x;
-    double acc = 0.0;
-    for (int c = 0; c < G.n_chunks; ++c) acc += G.br_partial[(size_t)p * G.n_chunks + c];
-    G.br_out[p] = acc;
   }
 }
 
@@ -595,9 +673,13 @@ static int check_launch(const char* what) {
 
 int hand_kernel_smem_limit() { return 227 * 1024; }
 
+size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es) {
+  return hand_smem_bytes(n_nodes, n_levels, rows_max, W, es);
+}
+
 template <typename P>
 static cudaError_t configure_precision() {
-  const int smem = hand_kernel_smem_limit() - 1024;
+  const int smem = hand_kernel_smem_limit() - 4096;
   cudaError_t e = cudaFuncSetAttribute(k_hand<kModeInit, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_hand<kModeUpdate, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -623,8 +705,7 @@ template <int MODE, typename P>
 static int launch_hand_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   const int players = player_mask == 3 ? 2 : 1;
   k_hand<MODE, P><<<c.n_chunk_work * players, kHandThreads, c.smem_hand, (cudaStream_t)stream>>>(
-      c.games, c.chunk_work, c.n_chunk_work, player_mask, advance, c.iter, c.done, c.variant, c.alpha, c.beta,
-      c.gamma);
+      c.games, c.chunk_work, c.n_chunk_work, player_mask, advance, c.iter, c.done, c.disc, c.variant);
   return check_launch("k_hand");
 }
 
@@ -646,16 +727,11 @@ int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stre
   const int players = player_mask == 3 ? 2 : 1;
   if (c.precision == kPrecisionSingle)
     k_terminal<Single><<<c.n_term_work * players, kTermThreads, c.smem_term, (cudaStream_t)stream>>>(
-        c.games, c.term_work, c.n_term_work, player_mask, use_bar);
+        c.games, c.term_work, c.n_term_work, player_mask, use_bar, c.err);
   else
     k_terminal<Pairs><<<c.n_term_work * players, kTermThreads, c.smem_term, (cudaStream_t)stream>>>(
-        c.games, c.term_work, c.n_term_work, player_mask, use_bar);
+        c.games, c.term_work, c.n_term_work, player_mask, use_bar, c.err);
   return check_launch("k_terminal");
-}
-
-int launch_br_reduce(const LaunchCtx& c, void* stream) {
-  k_br_reduce<<<c.n_games, 32, 0, (cudaStream_t)stream>>>(c.games);
-  return check_launch("k_br_reduce");
 }
 
 int launch_average_rows(const LaunchCtx& c, void* stream) {

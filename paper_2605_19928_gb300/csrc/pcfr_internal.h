@@ -10,25 +10,42 @@
 //   reach_bar    V    [2][n_nodes][hstride]   reach under the average strategy
 //   cfv, cfv_br  V    [2][n_nodes][hstride]   counterfactual values (last traversal / BR)
 // A decision node with A actions owns rows [row, row + A); player 0's rows come first.
+//
+// Terminal tables, one block of uint16 per showdown board (TermTab gives the offsets), all
+// indices below 2^15 because a player has at most 1326 hands:
+//   clh    [k * H]   per-card lists of hands, each list in rank-sorted order, concatenated
+//   cards  [H]       card ids of each hand, c1 | c2 << 8 (c2 = 255 for one-card hands)
+//   cloff  [deck+1]  start of each card's list in clh
+//   perm   [H]       hand at each rank-sorted position
+//   gs, ge [H]       first / one-past-last sorted position of each hand's tie group
+//   lo, hi [2 * H]   per (hand, card) the clh index of the first entry at or after gs / ge
+// Fold nodes need only the first three (board 0); the block is padded to 16 bytes so that
+// the terminal kernel can stage it with one bulk (TMA) copy.
 #pragma once
+#include <cstddef>
 #include <cstdint>
+
+#ifndef __CUDACC__  // host-only translation units share the small helpers below
+#define __host__
+#define __device__
+#endif
 
 namespace pcfr {
 
 enum NodeType : uint8_t { kDecision = 0, kFold = 1, kShowdown = 2, kChance = 3 };
 
 constexpr int kMaxActions = 16;
-constexpr int kPrecisionPairs = 0;   // values as double-float FP32 pairs
-constexpr int kPrecisionSingle = 1;  // values as FP32
 constexpr int kMaxDeck = 52;
 constexpr uint8_t kNoCard = 255;
+constexpr int kPrecisionPairs = 0;   // values as double-float FP32 pairs
+constexpr int kPrecisionSingle = 1;  // values as FP32
+constexpr int kDiscountCapacity = 1 << 16;  // iterations covered by one discount table
 
 struct alignas(16) NodeDev {
   int32_t parent;     // -1 at the root
   int32_t first_kid;  // children are consecutive: [first_kid, first_kid + n_kids)
   int32_t row;        // decision: first row; showdown: board table; otherwise -1
-  float value;        // terminal payoff (as in GameDev::payoff, rounded) or chance card probability;
-                      // chance: probability of one card given both private hands
+  float value;        // terminal payoff (as in GameDev::payoff, rounded) or chance card probability
   uint8_t type;       // NodeType
   uint8_t player;     // decision: acting player; fold: folding player
   uint8_t n_kids;
@@ -40,31 +57,42 @@ struct alignas(16) NodeDev {
 };
 static_assert(sizeof(NodeDev) == 32, "NodeDev is 32 bytes");
 
+// Offsets (in uint16) of the terminal-table sections for H hands of k cards from a deck.
+struct TermTab {
+  int clh, cards, cloff, fold_len, perm, gs, ge, lo, hi, len;
+  __host__ __device__ static int round8(int x) { return (x + 7) / 8 * 8; }
+  __host__ __device__ TermTab(int H, int k, int deck) {
+    clh = 0;
+    cards = k * H;
+    cloff = cards + H;
+    fold_len = round8(cloff + deck + 1);
+    perm = fold_len;
+    gs = perm + H;
+    ge = gs + H;
+    lo = ge + H;
+    hi = lo + 2 * H;
+    len = round8(hi + 2 * H);
+  }
+};
+
 // Everything one subgame's kernels need: read-only tables and the solver state.
 struct GameDev {
   int n_nodes, n_levels, n_hands, hstride, hand_size, n_rows, n_terminals, deck;
   int chunk, n_chunks;  // hands per block in the per-hand passes
   int smem;             // per-hand pass keeps its chunk's state in shared memory
   int row_begin[3];     // player p owns rows [row_begin[p], row_begin[p + 1])
-  int n_boards, cl_len;
-  double kappa64;       // 1 / Z, Z = sum of r0(h0) r1(h1) over hand pairs sharing no card
+  int n_boards;
+  double kappa64;              // 1 / Z, Z = sum of r0(h0) r1(h1) over hand pairs sharing no card
   const NodeDev* nodes;
   const double* payoff;        // [n_nodes] terminal payoff magnitude times the probability of
                                // the public cards dealt on the path (fold: folder's chips in,
                                // showdown: each player's chips in); 0 elsewhere
   const int32_t* level_start;  // [n_levels + 1]
+  const int32_t* row_node;     // [n_rows] decision node owning each row
   const uint64_t* hand_mask;   // [n_hands]
-  const uint8_t* hand_cards;   // [n_hands][2] (second = kNoCard for one-card hands)
   const void* range_v;         // [2][hstride] normalised ranges, value type V
   const double* range64;       // [2][hstride]
-  // showdown tables for board b (offsets b * n_hands, b * cl_len, b * (deck + 1)):
-  const int32_t* sd_perm;      // hand at each rank-sorted position
-  const int32_t* sd_gs;        // first sorted position of each hand's tie group
-  const int32_t* sd_ge;        // one past the last sorted position of the tie group
-  const int32_t* cl_hand;      // per-card hand lists in sorted order, concatenated
-  const int32_t* cl_off;       // [deck + 1] start of each card's list
-  const int32_t* cl_lo;        // [n_hands][2] list index of the first entry at or after gs
-  const int32_t* cl_hi;        // [n_hands][2] list index of the first entry at or after ge
+  const uint16_t* term_tab;    // [n_boards][TermTab.len]
   // state
   double* R;
   double* S;
@@ -76,11 +104,18 @@ struct GameDev {
   void* cfv_br;
   double* br_partial;          // [2][n_chunks] per-block sums of r_i(h) v*_i(root, h)
   double* br_out;              // [2]
+  unsigned* br_done;           // blocks of the best-response pass that have finished
 };
 
 struct Work {
   int game;
   int unit;  // chunk index (per-hand passes) or node id (terminal pass)
+};
+
+// Per-iteration update weights for iteration t (entry t - 1): DCFR's positive / negative
+// regret discounts and average discount, and the weight of the new average contribution.
+struct Discount {
+  double dpos, dneg, dS, wS;
 };
 
 // Kernel entry points (kernels.cu), all asynchronous on `stream`.
@@ -93,11 +128,12 @@ struct LaunchCtx {
   int n_term_work;
   int* iter;                   // device: iterations completed
   unsigned* done;              // device: block arrival counter
+  int* err;                    // device: nonzero after a bounded wait gave up
+  const Discount* disc;        // device [kDiscountCapacity]
   size_t smem_hand;            // dynamic shared memory of the per-hand kernel
   size_t smem_term;            // dynamic shared memory of the terminal kernel
   int variant;
   int precision;               // kPrecisionPairs or kPrecisionSingle
-  double alpha, beta, gamma;
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
@@ -105,9 +141,10 @@ int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stre
 int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream);
 int launch_avg_reach(const LaunchCtx& c, void* stream);
 int launch_br(const LaunchCtx& c, void* stream);
-int launch_br_reduce(const LaunchCtx& c, void* stream);
 int launch_average_rows(const LaunchCtx& c, void* stream);
 int hand_kernel_smem_limit();
+// Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
+size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
 
 }  // namespace pcfr

@@ -444,4 +444,35 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
   return CFR_OK;
 }
 
+std::vector<uint16_t> pack_term_tables(const HostGame& g) {
+  const int H = g.n_hands, k = g.hand_size, D = g.deck;
+  const TermTab tt(H, k, D);
+  std::vector<uint16_t> out((size_t)g.n_boards * tt.len, 0);
+  for (int b = 0; b < g.n_boards; ++b) {
+    uint16_t* t = &out[(size_t)b * tt.len];
+    for (int j = 0; j < k * H; ++j) t[tt.clh + j] = (uint16_t)g.cl_hand[(size_t)b * g.cl_len + j];
+    for (int h = 0; h < H; ++h)
+      t[tt.cards + h] = (uint16_t)(g.hand_cards[2 * h] | (g.hand_cards[2 * h + 1] << 8));
+    for (int c = 0; c <= D; ++c) t[tt.cloff + c] = (uint16_t)g.cl_off[(size_t)b * (D + 1) + c];
+    for (int h = 0; h < H; ++h) {
+      t[tt.perm + h] = (uint16_t)g.sd_perm[(size_t)b * H + h];
+      t[tt.gs + h] = (uint16_t)g.sd_gs[(size_t)b * H + h];
+      t[tt.ge + h] = (uint16_t)g.sd_ge[(size_t)b * H + h];
+      for (int s = 0; s < 2; ++s) {
+        t[tt.lo + 2 * h + s] = (uint16_t)g.cl_lo[((size_t)b * H + h) * 2 + s];
+        t[tt.hi + 2 * h + s] = (uint16_t)g.cl_hi[((size_t)b * H + h) * 2 + s];
+      }
+    }
+  }
+  return out;
+}
+
+std::vector<int32_t> row_nodes(const HostGame& g) {
+  std::vector<int32_t> out((size_t)g.n_rows, -1);
+  for (size_t n = 0; n < g.nodes.size(); ++n)
+    if (g.nodes[n].type == kDecision)
+      for (int a = 0; a < g.nodes[n].n_kids; ++a) out[(size_t)g.nodes[n].row + a] = (int32_t)n;
+  return out;
+}
+
 }  // namespace pcfr

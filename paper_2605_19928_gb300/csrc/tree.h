@@ -33,4 +33,10 @@ struct HostGame {
 // Validates `spec` and fills `out`; returns CFR_OK or CFR_EINVAL with a message in `err`.
 int build_game(const cfr_game_spec& spec, HostGame& out, std::string& err);
 
+// The terminal kernel's per-board uint16 tables (layout: TermTab in pcfr_internal.h).
+std::vector<uint16_t> pack_term_tables(const HostGame& g);
+
+// Decision node owning each regret row.
+std::vector<int32_t> row_nodes(const HostGame& g);
+
 }  // namespace pcfr
