@@ -202,18 +202,23 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       return fail(rc, "game " + std::to_string(g) + ": " + err);
     }
   }
-  // Block shape: W hands per block (8 by default).  The per-hand pass keeps its chunk's
-  // state in shared memory when that fits in 96 KB (two blocks per SM), else it works on
-  // the global arrays, which stay in L2 for trees of this size.
+  // Block shape: W hands per block (8 by default).  The per-hand pass stages each chunk's
+  // tree and state in shared memory when every game of the handle fits in 96 KB (two blocks
+  // per SM); otherwise all games work on the global arrays, which stay in L2 for trees of
+  // this size.
   size_t smem_hand = 0, smem_term = 0;
   std::vector<int> chunk(n_games);
   std::vector<int> use_smem(n_games);
+  bool all_fit = true;
   for (int g = 0; g < n_games; ++g) {
-    const HostGame& h = t->host[g];
     const int W = o.chunk_hands ? o.chunk_hands : 8;
     chunk[g] = W;
-    use_smem[g] = hand_smem(h, W, es) <= 96 * 1024;
-    if (use_smem[g]) smem_hand = std::max(smem_hand, hand_smem(h, W, es));
+    all_fit = all_fit && hand_smem(t->host[g], W, es) <= 96 * 1024;
+  }
+  for (int g = 0; g < n_games; ++g) {
+    const HostGame& h = t->host[g];
+    use_smem[g] = all_fit;
+    if (all_fit) smem_hand = std::max(smem_hand, hand_smem(h, chunk[g], es));
     const TermTab tt(h.n_hands, h.hand_size, h.deck);
     smem_term = std::max(smem_term, (size_t)tt.len * 2 + (size_t)h.hstride * es +
                                         (size_t)(h.hand_size * h.n_hands + 1 + h.n_hands + 1) * 8);
@@ -246,20 +251,21 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     const std::vector<float> rv = to_value_type(r64, o.precision);
     const std::vector<uint16_t> tab = pack_term_tables(h);
     const std::vector<int32_t> rown = row_nodes(h);
+    const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
     NodeDev* nodes;
-    int32_t *ls, *rn;
+    int32_t *ls, *rn, *dn;
     uint16_t* tb;
     uint64_t* hm;
     float* rrv;
     double *rr64, *pay;
     if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
         (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
-        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb))) {
+        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb)) || (rc = upload(t, decn, &dn))) {
       delete t;
       return rc;
     }
     d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.term_tab = tb;
+    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn;
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value
     float *sig, *sigb, *rch, *rchb, *cf, *cfb;
@@ -298,6 +304,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.smem_term = smem_term;
   c.variant = o.variant;
   c.precision = o.precision;
+  c.pdl = 1;
   t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
   t->launches += 1;
   if (launch_init(c, stream) != 0) {

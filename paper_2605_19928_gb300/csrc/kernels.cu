@@ -70,6 +70,15 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return {s1, s2};
 }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+// Sum of two double-floats of the same sign (no cancellation possible): TwoSum of the high
+// parts, low parts added in FP32, one renormalisation -- about half the operations of ff_add.
+__device__ __forceinline__ ff ff_add_pos(ff a, ff b) {
+  float s, e, hi, lo;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  fast_two_sum(s, e, hi, lo);
+  return {hi, lo};
+}
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -79,6 +88,42 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   fast_two_sum(p, e, hi, lo);
   return {hi, lo};
 }
+// Compensated accumulation (Ogita, Rump and Oishi 2005, "Accurate sum and dot product",
+// Sum2 / Dot2): a running FP32 sum s, with every rounding error -- found exactly by TwoSum
+// and by the FMA form of TwoProduct -- added into a separate FP32 error sum e.  The
+// critical path is one FP32 addition per term, and s + e, kept as a pair, carries about
+// twice the working precision.
+struct acc2 {
+  float s, e;
+};
+__device__ __forceinline__ acc2 acc_zero() { return {0.f, 0.f}; }
+__device__ __forceinline__ void acc_add(acc2& a, ff x) {
+  float t, err;
+  two_sum(a.s, x.hi, t, err);
+  a.s = t;
+  a.e = __fadd_rn(a.e, __fadd_rn(err, x.lo));
+}
+__device__ __forceinline__ void acc_fma(acc2& a, ff x, ff y) {  // a += x * y
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = __fmaf_rn(x.hi, y.hi, -p);
+  const float cross = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+  float t, err;
+  two_sum(a.s, p, t, err);
+  a.s = t;
+  a.e = __fadd_rn(a.e, __fadd_rn(err, __fadd_rn(pe, cross)));
+}
+__device__ __forceinline__ void acc_merge(acc2& a, acc2 b) {
+  float t, err;
+  two_sum(a.s, b.s, t, err);
+  a.s = t;
+  a.e = __fadd_rn(a.e, __fadd_rn(err, b.e));
+}
+__device__ __forceinline__ ff acc_value(acc2 a) {
+  float hi, lo;
+  two_sum(a.s, a.e, hi, lo);
+  return {hi, lo};
+}
+
 // 1 / b: the FP32 reciprocal refined by one Newton step in double-float.
 __device__ __forceinline__ ff ff_recip(ff b) {
   const ff r = ff_of(__frcp_rn(b.hi));
@@ -120,10 +165,17 @@ struct Pairs {  // double-float values
   static __device__ __forceinline__ V vmax(V a, V b) { return ff_gt(b, a) ? b : a; }
   static __device__ __forceinline__ bool positive(V a) { return a.hi > 0.f; }
   static __device__ __forceinline__ V recip(V a) { return ff_recip(a); }
+  static __device__ __forceinline__ V one() { return ff_of(1.f); }
+  static __device__ __forceinline__ V uniform(int A) { return ff_recip(ff_of((float)A)); }  // 1 / A
   static __device__ __forceinline__ V of_double(double x) { return d2ff(x); }
   static __device__ __forceinline__ double to_double(V a) { return ff2d(a); }
   static __device__ __forceinline__ ff to_ff(V a) { return a; }
   static __device__ __forceinline__ V of_ff(ff a) { return a; }
+  using Acc = acc2;
+  static __device__ __forceinline__ Acc acc0() { return acc_zero(); }
+  static __device__ __forceinline__ void acc(Acc& a, V x) { acc_add(a, x); }
+  static __device__ __forceinline__ void acc_mul(Acc& a, V x, V y) { acc_fma(a, x, y); }
+  static __device__ __forceinline__ V value(Acc a) { return acc_value(a); }
 };
 
 struct Single {  // plain FP32 values
@@ -135,69 +187,64 @@ struct Single {  // plain FP32 values
   static __device__ __forceinline__ V vmax(V a, V b) { return fmaxf(a, b); }
   static __device__ __forceinline__ bool positive(V a) { return a > 0.f; }
   static __device__ __forceinline__ V recip(V a) { return 1.f / a; }
+  static __device__ __forceinline__ V one() { return 1.f; }
+  static __device__ __forceinline__ V uniform(int A) { return 1.f / (float)A; }
   static __device__ __forceinline__ V of_double(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ double to_double(V a) { return f2d(a); }
   static __device__ __forceinline__ ff to_ff(V a) { return ff_of(a); }
   static __device__ __forceinline__ V of_ff(ff a) { return ff_round(a); }
+  using Acc = float;
+  static __device__ __forceinline__ Acc acc0() { return 0.f; }
+  static __device__ __forceinline__ void acc(Acc& a, V x) { a += x; }
+  static __device__ __forceinline__ void acc_mul(Acc& a, V x, V y) { a = fmaf(x, y, a); }
+  static __device__ __forceinline__ V value(Acc a) { return a; }
 };
 
 // ------------------------------------------------------------------ block primitives (double-float)
 
-template <int NT>
-__device__ __forceinline__ ff block_sum_ff(ff x, ff* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
-  if (lane == 0) red[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    ff y = lane < NT / 32 ? red[lane] : ff_of(0.f);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y = ff_add(y, ff_shfl_xor(y, o));
-    if (lane == 0) red[32] = y;
-  }
-  __syncthreads();
-  const ff t = red[32];
-  __syncthreads();
-  return t;
+__device__ __forceinline__ acc2 acc_shfl_up(acc2 a, int o) {
+  return {__shfl_up_sync(0xffffffffu, a.s, o), __shfl_up_sync(0xffffffffu, a.e, o)};
 }
 
-// Exclusive prefix sum of value_at(0 .. n-1) into out[0 .. n]; out[n] is the total.  Each
-// thread owns a contiguous run; runs are combined by a warp-shuffle scan and a scan over
-// the warp totals.
-template <int NT, typename F>
-__device__ __forceinline__ ff block_exclusive_scan(int n, F value_at, ff* out, ff* red) {
-  const int per = (n + NT - 1) / NT;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int begin = min(tid * per, n), end = min(begin + per, n);
-  ff local = ff_of(0.f);
-  for (int j = begin; j < end; ++j) local = ff_add(local, value_at(j));
-  ff x = local;
+// Exclusive prefix sum of the non-negative values value_at(0 .. n-1) into out[0 .. n]
+// (out[n] = total) by one group of GT consecutive threads (gtid = rank in the group; every
+// thread of the block must call it, so that the block barriers inside line up).  Each
+// thread owns a contiguous run; runs are combined by a warp-shuffle scan and a scan over the
+// group's warp totals in red[GT / 32].  Sums are compensated (acc2).
+template <int GT, typename F>
+__device__ __forceinline__ ff group_exclusive_scan(int n, F value_at, ff* out, acc2* red, int gtid) {
+  const int per = (n + GT - 1) / GT;
+  const int lane = gtid & 31, warp = gtid >> 5;
+  const int begin = min(gtid * per, n), end = min(begin + per, n);
+  acc2 local = acc_zero();
+  for (int j = begin; j < end; ++j) acc_add(local, value_at(j));
+  acc2 x = local;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const ff y = ff_shfl_up(x, o);
-    if (lane >= o) x = ff_add(x, y);
+    const acc2 y = acc_shfl_up(x, o);
+    if (lane >= o) acc_merge(x, y);
   }
+  acc2 run = acc_shfl_up(x, 1);
+  if (lane == 0) run = acc_zero();
   if (lane == 31) red[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    ff wv = lane < NT / 32 ? red[lane] : ff_of(0.f);
+    acc2 wv = lane < GT / 32 ? red[lane] : acc_zero();
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const ff y = ff_shfl_up(wv, o);
-      if (lane >= o) wv = ff_add(wv, y);
+      const acc2 y = acc_shfl_up(wv, o);
+      if (lane >= o) acc_merge(wv, y);
     }
-    if (lane < NT / 32) red[lane] = wv;
+    if (lane < GT / 32) red[lane] = wv;
   }
   __syncthreads();
-  ff run = ff_sub(x, local);
-  if (warp > 0) run = ff_add(run, red[warp - 1]);
+  if (warp > 0) acc_merge(run, red[warp - 1]);
   for (int j = begin; j < end; ++j) {
-    out[j] = run;
-    run = ff_add(run, value_at(j));
+    out[j] = acc_value(run);
+    acc_add(run, value_at(j));
   }
-  const ff total = red[NT / 32 - 1];
-  if (tid == 0) out[n] = total;
+  const ff total = acc_value(red[GT / 32 - 1]);
+  if (gtid == 0) out[n] = total;
   __syncthreads();
   return total;
 }
@@ -233,6 +280,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// Asynchronous element copies global -> shared (cp.async): every copy of a block is in
+// flight at once instead of one load-then-store round trip per loop iteration.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Programmatic dependent launch.  Every kernel first stages what launches two or more steps
+// back produced, then waits for its immediate predecessor (griddepcontrol.wait returns once
+// that grid has completed and its writes are visible), and only then lets its own dependent
+// start.  So whenever a kernel is running, everything but its immediate predecessor has
+// completed, which is what makes the early staging safe.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Bounded wait for phase `parity` of the barrier: false if it did not complete in time.
 constexpr long kWaitLimit = 1l << 20;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
@@ -284,7 +351,7 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
 
   extern __shared__ __align__(128) unsigned char smt[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ ff red[33];
+  __shared__ acc2 red[2][kTermThreads / 64];
   uint16_t* tab = reinterpret_cast<uint16_t*>(smt);                             // [tt.len]
   V* qs = reinterpret_cast<V*>(smt + (size_t)tt.len * 2);                        // [hstride]
   ff* CP = reinterpret_cast<ff*>(smt + (size_t)tt.len * 2 + q_bytes);            // [k H + 1]
@@ -295,15 +362,17 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
     fence_barrier_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // the board tables are static: copy them before waiting
     mbar_arrive_expect_tx(&bar, tab_bytes + q_bytes);
     bulk_copy_g2s(tab, G.term_tab + (size_t)b * tt.len, tab_bytes, &bar);
-    bulk_copy_g2s(qs, q, q_bytes, &bar);
   }
   // payoff for player i per unit of (opponent reach) x kappa, in FP64 while the copies land
   const double pay = G.payoff[n];
   const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
   const ff u = d2ff(u64);
+  pdl_wait();  // the reach row comes from the launch just before this one
+  pdl_trigger();
+  if (threadIdx.x == 0) bulk_copy_g2s(qs, q, q_bytes, &bar);
   const uint64_t board = nd.board;
   const bool ok = mbar_wait_bounded(&bar, 0);
   if (__syncthreads_or(!ok)) {  // the copies did not land: report, let them drain, leave
@@ -318,12 +387,23 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
   const uint16_t* clh = tab + tt.clh;
   const uint16_t* cards = tab + tt.cards;
   const uint16_t* cloff = tab + tt.cloff;
-  block_exclusive_scan<kTermThreads>(k * H, [&](int j) { return P::to_ff(qs[clh[j]]); }, CP, red);
+  const uint16_t* perm = tab + tt.perm;
+  // Two scans at once, one per half of the block: the first half takes the reach in
+  // rank-sorted order (showdown) or in hand order (fold, for the total T), the second half
+  // the reach along the per-card hand lists.
+  {
+    constexpr int half = kTermThreads / 2;
+    const bool first = threadIdx.x < half;
+    const int gtid = first ? threadIdx.x : threadIdx.x - half;
+    if (first)
+      group_exclusive_scan<half>(
+          H, [&](int j) { return P::to_ff(qs[show ? perm[j] : j]); }, Psc, red[0], gtid);
+    else
+      group_exclusive_scan<half>(k * H, [&](int j) { return P::to_ff(qs[clh[j]]); }, CP, red[1], gtid);
+  }
+  const ff T = Psc[H];
 
   if (!show) {
-    ff loc = ff_of(0.f);
-    for (int h = threadIdx.x; h < H; h += kTermThreads) loc = ff_add(loc, P::to_ff(qs[h]));
-    const ff T = block_sum_ff<kTermThreads>(loc, red);
     for (int h = threadIdx.x; h < H; h += kTermThreads) {
       const unsigned cw = cards[h];
       const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
@@ -337,12 +417,10 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
       out[h] = blocked ? P::zero() : P::of_ff(ff_mul(u, m));
     }
   } else {
-    const uint16_t* perm = tab + tt.perm;
     const uint16_t* gs = tab + tt.gs;
     const uint16_t* ge = tab + tt.ge;
     const uint16_t* lo = tab + tt.lo;
     const uint16_t* hi = tab + tt.hi;
-    const ff T = block_exclusive_scan<kTermThreads>(H, [&](int j) { return P::to_ff(qs[perm[j]]); }, Psc, red);
     for (int h = threadIdx.x; h < H; h += kTermThreads) {
       const unsigned cw = cards[h];
       ff Wn = Psc[gs[h]];
@@ -373,10 +451,11 @@ struct Col {
 __host__ __device__ inline size_t round16(size_t x) { return (x + 15) / 16 * 16; }
 
 // Shared memory of the per-hand kernel for one game (must match the layout in k_hand):
-// nodes, level offsets, row -> node map, R and S rows, then values, reach and strategy.
+// nodes, level offsets, row -> node map, decision-node list (fewer entries than rows), R and
+// S rows, then values, reach and strategy.
 __host__ __device__ inline size_t hand_smem_bytes(int n_nodes, int n_levels, int rows_max, int W, size_t es) {
   return round16((size_t)n_nodes * sizeof(NodeDev)) + round16((size_t)(n_levels + 1) * 4) +
-         round16((size_t)rows_max * 4) + 2 * round16((size_t)rows_max * W * 8) +
+         2 * round16((size_t)rows_max * 4) + 2 * round16((size_t)rows_max * W * 8) +
          (size_t)(2 * n_nodes + rows_max) * W * es;
 }
 
@@ -389,8 +468,8 @@ __host__ __device__ inline size_t hand_smem_bytes(int n_nodes, int n_levels, int
 //                root sum r_p(h) v*_p(root, h), reduced by the last block of each game.
 // With G.smem set the block stages the tree and its hands' state in shared memory;
 // otherwise it works on the global arrays directly (trees too large to stage).
-template <int MODE, typename P>
-__global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict__ games,
+template <int MODE, typename P, bool SM>
+__global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restrict__ games,
                                                        const Work* __restrict__ work, int n_work, int player_mask,
                                                        int advance, int* iter, unsigned* done,
                                                        const Discount* __restrict__ disc_tab, int variant) {
@@ -418,7 +497,7 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   const int nrows = re - rb;
   const int rows_max = max(G.row_begin[1] - G.row_begin[0], G.row_begin[2] - G.row_begin[1]);
   const uint64_t hmask = valid ? G.hand_mask[h] : 0ull;
-  const bool sm = G.smem != 0;
+  constexpr bool sm = SM;       // the launch stages every game in shared memory
   const bool wr = sm || valid;  // this lane may write its column of the working arrays
 
   // global arrays of this player, at column h
@@ -437,6 +516,8 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   cur += round16((size_t)(L + 1) * 4);
   int* srow = reinterpret_cast<int*>(cur);
   cur += round16((size_t)rows_max * 4);
+  int* sdec = reinterpret_cast<int*>(cur);
+  cur += round16((size_t)rows_max * 4);
   double* sR = reinterpret_cast<double*>(cur);
   cur += round16((size_t)rows_max * W * 8);
   double* sS = reinterpret_cast<double*>(cur);
@@ -448,6 +529,8 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   const NodeDev* nodes = sm ? snodes : G.nodes;
   const int* ls = sm ? sls : G.level_start;
   const int* rown = sm ? srow : G.row_node + rb;
+  const int db = G.dec_begin[p], ndec = G.dec_begin[p + 1] - db;
+  const int* decs = sm ? sdec : G.dec_nodes + db;
   const Col<V> v = sm ? Col<V>{sv + w, (size_t)W} : Col<V>{gv, stride};
   const Col<V> rch = sm ? Col<V>{srch + w, (size_t)W} : Col<V>{grch, stride};
   const Col<V> sg = sm ? Col<V>{ssg + w, (size_t)W} : Col<V>{gsg, stride};
@@ -459,26 +542,34 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
 
   // ---- stage: every load is independent of the others, so they are all in flight at once
   if (MODE == kModeUpdate && tid == 0) disc = disc_tab[*iter];
-  if (sm) {
+  if constexpr (SM) {
+    constexpr int VB = (int)sizeof(V);
     const int4* gn = reinterpret_cast<const int4*>(G.nodes);
     int4* sn = reinterpret_cast<int4*>(snodes);
-    for (int k = tid; k < 2 * N; k += kHandThreads) sn[k] = gn[k];
-    for (int k = tid; k <= L; k += kHandThreads) sls[k] = G.level_start[k];
-    for (int k = tid; k < nrows; k += kHandThreads) srow[k] = G.row_node[rb + k];
-    if (MODE == kModeUpdate || MODE == kModeBR)
-      for (int n = slot; n < N; n += nslots) v[n] = gv[(size_t)n * stride];
+    for (int k = tid; k < 2 * N; k += kHandThreads) cp_async<16>(sn + k, gn + k);
+    for (int k = tid; k <= L; k += kHandThreads) cp_async<4>(sls + k, G.level_start + k);
+    for (int k = tid; k < nrows; k += kHandThreads) cp_async<4>(srow + k, G.row_node + rb + k);
+    for (int k = tid; k < ndec; k += kHandThreads) cp_async<4>(sdec + k, G.dec_nodes + db + k);
     if (MODE == kModeUpdate) {
-      for (int n = slot; n < N; n += nslots) rch[n] = grch[(size_t)n * stride];
+      for (int n = slot; n < N; n += nslots) cp_async<VB>(&rch[n], grch + (size_t)n * stride);
       for (int r = slot; r < nrows; r += nslots) {
-        sg[r] = gsg[(size_t)r * stride];
-        Rc[r] = gR[(size_t)r * stride];
-        Sc[r] = gS[(size_t)r * stride];
+        cp_async<VB>(&sg[r], gsg + (size_t)r * stride);
+        cp_async<8>(&Rc[r], gR + (size_t)r * stride);
+        cp_async<8>(&Sc[r], gS + (size_t)r * stride);
       }
     }
     if (MODE == kModeInit)
-      for (int r = slot; r < nrows; r += nslots) Rc[r] = gR[(size_t)r * stride];
+      for (int r = slot; r < nrows; r += nslots) cp_async<8>(&Rc[r], gR + (size_t)r * stride);
     if (MODE == kModeAvg)
-      for (int r = slot; r < nrows; r += nslots) Sc[r] = gS[(size_t)r * stride];
+      for (int r = slot; r < nrows; r += nslots) cp_async<8>(&Sc[r], gS + (size_t)r * stride);
+  }
+  pdl_wait();  // terminal values come from the launch just before this one
+  pdl_trigger();
+  if constexpr (SM) {
+    constexpr int VB = (int)sizeof(V);
+    if (MODE == kModeUpdate || MODE == kModeBR)
+      for (int n = slot; n < N; n += nslots) cp_async<VB>(&v[n], gv + (size_t)n * stride);
+    cp_async_wait_all();
   }
   __syncthreads();
 
@@ -491,19 +582,23 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
         const NodeDev nd = nodes[n];
         if (nd.type == kFold || nd.type == kShowdown) continue;
         const int A = nd.n_kids, k0 = nd.first_kid;
-        V val = P::zero();
-        if (nd.type == kChance) {
-          // children values already carry the card probabilities; cards in the hand are out
-          for (int a = 0; a < A; ++a)
-            if (!((hmask >> nodes[k0 + a].deal) & 1ull)) val = P::add(val, v[k0 + a]);
-        } else if (nd.player != p) {
-          for (int a = 0; a < A; ++a) val = P::add(val, v[k0 + a]);
-        } else if (MODE == kModeBR) {
+        V val;
+        if (MODE == kModeBR && nd.type == kDecision && nd.player == p) {
           val = v[k0];
           for (int a = 1; a < A; ++a) val = P::vmax(val, v[k0 + a]);
         } else {
-          const int r0 = nd.row - rb;
-          for (int a = 0; a < A; ++a) val = P::add(val, P::mul(sg[r0 + a], v[k0 + a]));
+          typename P::Acc acc = P::acc0();
+          if (nd.type == kChance) {
+            // children values already carry the card probabilities; cards in the hand are out
+            for (int a = 0; a < A; ++a)
+              if (!((hmask >> nodes[k0 + a].deal) & 1ull)) P::acc(acc, v[k0 + a]);
+          } else if (nd.player != p) {
+            for (int a = 0; a < A; ++a) P::acc(acc, v[k0 + a]);
+          } else {
+            const int r0 = nd.row - rb;
+            for (int a = 0; a < A; ++a) P::acc_mul(acc, sg[r0 + a], v[k0 + a]);
+          }
+          val = P::value(acc);
         }
         if (wr) v[n] = val;
       }
@@ -548,40 +643,38 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
   }
 
   // ---- positive parts of the strategy source, one (row, hand) item per thread:
+  //      (sign tests of FP64 values read the sign bit on the integer pipe: x > 0 exactly
+  //      when the bits, as a signed integer, are positive)
   //      update: the Stage 7 update of R and S, then the positive part of the new R;
   //      init: the positive part of R;  average: S
   {
     const Discount d = disc;
     for (int r = slot; r < nrows; r += nslots) {
-      V pos;
+      double x;
       if (MODE == kModeUpdate) {
         const int n = rown[r];
         const NodeDev nd = nodes[n];
-        const int a = rb + r - nd.row;
-        const V rr = P::sub(v[nd.first_kid + a], v[n]);                 // instantaneous regret
+        const V rr = P::sub(v[nd.first_kid + (rb + r - nd.row)], v[n]);  // instantaneous regret
         const double contrib = P::to_double(P::mul(rch[n], sg[r]));     // pi_i(I) sigma(I, a)
-        double x = Rc[r] + P::to_double(rr);
-        if (variant == 2) x *= x > 0.0 ? d.dpos : d.dneg;
-        if (variant == 1 && x < 0.0) x = 0.0;
-        const double s = fma(Sc[r], d.dS, d.wS * contrib);
+        x = Rc[r] + P::to_double(rr);
+        if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+        if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
+        const double sn = fma(Sc[r], d.dS, d.wS * contrib);
         if (valid) {
           gR[(size_t)r * stride] = x;
-          gS[(size_t)r * stride] = s;
+          gS[(size_t)r * stride] = sn;
         }
-        pos = x > 0.0 ? P::of_double(x) : P::zero();
       } else {
-        const double x = MODE == kModeInit ? Rc[r] : Sc[r];
-        pos = x > 0.0 ? P::of_double(x) : P::zero();
+        x = MODE == kModeInit ? Rc[r] : Sc[r];
       }
-      if (wr) sg[r] = pos;
+      if (wr) sg[r] = __double_as_longlong(x) > 0 ? P::of_double(x) : P::zero();
     }
   }
   __syncthreads();
 
   // ---- regret matching (Eq. rm) / normalisation of the average, per decision node of p
-  for (int n = slot; n < N; n += nslots) {
-    const NodeDev nd = nodes[n];
-    if (nd.type != kDecision || nd.player != p) continue;
+  for (int k = slot; k < ndec; k += nslots) {
+    const NodeDev nd = nodes[decs[k]];
     const int A = nd.n_kids, r0 = nd.row - rb;
     V tot = P::zero();
     int npos = 0, last = 0;
@@ -592,12 +685,12 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
     }
     if (!wr) continue;
     if (npos == 1) {  // x / x = 1 exactly, as the definition gives
-      for (int a = 0; a < A; ++a) sg[r0 + a] = a == last ? P::of_double(1.0) : P::zero();
+      for (int a = 0; a < A; ++a) sg[r0 + a] = a == last ? P::one() : P::zero();
     } else if (npos > 1) {
       const V inv = P::recip(tot);
       for (int a = 0; a < A; ++a) sg[r0 + a] = P::mul(sg[r0 + a], inv);
     } else {
-      const V uni = P::of_double(1.0 / A);
+      const V uni = P::uniform(A);
       for (int a = 0; a < A; ++a) sg[r0 + a] = uni;
     }
   }
@@ -611,10 +704,9 @@ __global__ void __launch_bounds__(kHandThreads) k_hand(const GameDev* __restrict
     for (int idx = slot; idx < cnt; idx += nslots) {
       const int n = a0 + idx;
       const NodeDev nd = nodes[n];
-      const NodeDev par = nodes[nd.parent];
       V x = wr ? rch[nd.parent] : P::zero();
-      if (par.type == kDecision && par.player == p) x = P::mul(x, sg[par.row - rb + nd.paction]);
-      if (par.type == kChance && ((hmask >> nd.deal) & 1ull)) x = P::zero();
+      if (nd.aplayer == p) x = P::mul(x, sg[nd.arow - rb]);
+      if (nd.deal != kNoCard && ((hmask >> nd.deal) & 1ull)) x = P::zero();
       if (wr) rch[n] = x;
     }
     __syncthreads();
@@ -677,17 +769,32 @@ size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es)
   return hand_smem_bytes(n_nodes, n_levels, rows_max, W, es);
 }
 
+// Every kernel asks for the same shared-memory carveout (the maximum), so the SMs never
+// have to be reconfigured between the terminal and per-hand launches of an iteration.
+template <typename K>
+static cudaError_t configure_one(K kernel, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+template <typename P, bool SM>
+static cudaError_t configure_hand() {
+  const int smem = hand_kernel_smem_limit() - 4096;
+  cudaError_t e = configure_one(k_hand<kModeInit, P, SM>, smem);
+  if (e == cudaSuccess) e = configure_one(k_hand<kModeUpdate, P, SM>, smem);
+  if (e == cudaSuccess) e = configure_one(k_hand<kModeAvg, P, SM>, smem);
+  if (e == cudaSuccess) e = configure_one(k_hand<kModeBR, P, SM>, smem);
+  return e;
+}
+
 template <typename P>
 static cudaError_t configure_precision() {
-  const int smem = hand_kernel_smem_limit() - 4096;
-  cudaError_t e = cudaFuncSetAttribute(k_hand<kModeInit, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hand<kModeUpdate, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_hand<kModeAvg, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hand<kModeBR, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_terminal<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = configure_hand<P, true>();
+  if (e == cudaSuccess) e = configure_hand<P, false>();
+  if (e == cudaSuccess) e = configure_one(k_terminal<P>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_average_rows<P>, 0);
   return e;
 }
 
@@ -701,36 +808,71 @@ int configure_kernels() {
   return 0;
 }
 
+// Launch with programmatic stream serialisation (c.pdl) so the kernel may start while its
+// predecessor finishes; kernels order their reads with pdl_wait().
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, void* stream, bool pdl,
+                                 Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <int MODE, typename P>
-static int launch_hand_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
+static int launch_hand_p(const LaunchCtx& c, int player_mask, int advance, void* stream, bool pdl) {
   const int players = player_mask == 3 ? 2 : 1;
-  k_hand<MODE, P><<<c.n_chunk_work * players, kHandThreads, c.smem_hand, (cudaStream_t)stream>>>(
-      c.games, c.chunk_work, c.n_chunk_work, player_mask, advance, c.iter, c.done, c.disc, c.variant);
+  const int grid = c.n_chunk_work * players;
+  cudaError_t e;
+  if (c.smem_hand > 0)
+    e = launch_kernel(k_hand<MODE, P, true>, grid, kHandThreads, c.smem_hand, stream, pdl, c.games, c.chunk_work,
+                      c.n_chunk_work, player_mask, advance, c.iter, c.done, c.disc, c.variant);
+  else
+    e = launch_kernel(k_hand<MODE, P, false>, grid, kHandThreads, 0, stream, pdl, c.games, c.chunk_work,
+                      c.n_chunk_work, player_mask, advance, c.iter, c.done, c.disc, c.variant);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of k_hand failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
   return check_launch("k_hand");
 }
 
 template <int MODE>
-static int launch_hand(const LaunchCtx& c, int player_mask, int advance, void* stream) {
-  return c.precision == kPrecisionSingle ? launch_hand_p<MODE, Single>(c, player_mask, advance, stream)
-                                         : launch_hand_p<MODE, Pairs>(c, player_mask, advance, stream);
+static int launch_hand(const LaunchCtx& c, int player_mask, int advance, void* stream, bool pdl) {
+  return c.precision == kPrecisionSingle ? launch_hand_p<MODE, Single>(c, player_mask, advance, stream, pdl)
+                                         : launch_hand_p<MODE, Pairs>(c, player_mask, advance, stream, pdl);
 }
 
-int launch_init(const LaunchCtx& c, void* stream) { return launch_hand<kModeInit>(c, 3, 0, stream); }
+int launch_init(const LaunchCtx& c, void* stream) { return launch_hand<kModeInit>(c, 3, 0, stream, false); }
 int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream) {
-  return launch_hand<kModeUpdate>(c, player_mask, advance, stream);
+  return launch_hand<kModeUpdate>(c, player_mask, advance, stream, c.pdl != 0);
 }
-int launch_avg_reach(const LaunchCtx& c, void* stream) { return launch_hand<kModeAvg>(c, 3, 0, stream); }
-int launch_br(const LaunchCtx& c, void* stream) { return launch_hand<kModeBR>(c, 3, 0, stream); }
+int launch_avg_reach(const LaunchCtx& c, void* stream) { return launch_hand<kModeAvg>(c, 3, 0, stream, false); }
+int launch_br(const LaunchCtx& c, void* stream) { return launch_hand<kModeBR>(c, 3, 0, stream, c.pdl != 0); }
 
 int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stream) {
   if (c.n_term_work == 0) return 0;
   const int players = player_mask == 3 ? 2 : 1;
+  const int grid = c.n_term_work * players;
+  const bool pdl = c.pdl != 0;
+  cudaError_t e;
   if (c.precision == kPrecisionSingle)
-    k_terminal<Single><<<c.n_term_work * players, kTermThreads, c.smem_term, (cudaStream_t)stream>>>(
-        c.games, c.term_work, c.n_term_work, player_mask, use_bar, c.err);
+    e = launch_kernel(k_terminal<Single>, grid, kTermThreads, c.smem_term, stream, pdl, c.games, c.term_work,
+                      c.n_term_work, player_mask, use_bar, c.err);
   else
-    k_terminal<Pairs><<<c.n_term_work * players, kTermThreads, c.smem_term, (cudaStream_t)stream>>>(
-        c.games, c.term_work, c.n_term_work, player_mask, use_bar, c.err);
+    e = launch_kernel(k_terminal<Pairs>, grid, kTermThreads, c.smem_term, stream, pdl, c.games, c.term_work,
+                      c.n_term_work, player_mask, use_bar, c.err);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of k_terminal failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
   return check_launch("k_terminal");
 }
 

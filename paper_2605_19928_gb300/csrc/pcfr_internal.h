@@ -45,14 +45,15 @@ struct alignas(16) NodeDev {
   int32_t parent;     // -1 at the root
   int32_t first_kid;  // children are consecutive: [first_kid, first_kid + n_kids)
   int32_t row;        // decision: first row; showdown: board table; otherwise -1
-  float value;        // terminal payoff (as in GameDev::payoff, rounded) or chance card probability
+  int32_t arow;       // row of the action that leads here (parent's row + paction), or -1
   uint8_t type;       // NodeType
   uint8_t player;     // decision: acting player; fold: folding player
   uint8_t n_kids;
   uint8_t deal;       // card dealt by the chance parent, else kNoCard
   uint8_t paction;    // index among the parent's children
   uint8_t level;
-  uint8_t pad[2];
+  uint8_t aplayer;    // player acting at the parent decision, else kNoCard
+  uint8_t pad;
   uint64_t board;     // public cards at this node (bit c = card c)
 };
 static_assert(sizeof(NodeDev) == 32, "NodeDev is 32 bytes");
@@ -79,7 +80,8 @@ struct TermTab {
 struct GameDev {
   int n_nodes, n_levels, n_hands, hstride, hand_size, n_rows, n_terminals, deck;
   int chunk, n_chunks;  // hands per block in the per-hand passes
-  int smem;             // per-hand pass keeps its chunk's state in shared memory
+  int smem;             // per-hand pass keeps its chunk's state in shared memory (the same
+                        // for every game of a handle)
   int row_begin[3];     // player p owns rows [row_begin[p], row_begin[p + 1])
   int n_boards;
   double kappa64;              // 1 / Z, Z = sum of r0(h0) r1(h1) over hand pairs sharing no card
@@ -89,6 +91,8 @@ struct GameDev {
                                // showdown: each player's chips in); 0 elsewhere
   const int32_t* level_start;  // [n_levels + 1]
   const int32_t* row_node;     // [n_rows] decision node owning each row
+  const int32_t* dec_nodes;    // decision nodes of player 0, then of player 1
+  int dec_begin[3];            // player p's are dec_nodes[dec_begin[p] .. dec_begin[p + 1])
   const uint64_t* hand_mask;   // [n_hands]
   const void* range_v;         // [2][hstride] normalised ranges, value type V
   const double* range64;       // [2][hstride]
@@ -130,10 +134,12 @@ struct LaunchCtx {
   unsigned* done;              // device: block arrival counter
   int* err;                    // device: nonzero after a bounded wait gave up
   const Discount* disc;        // device [kDiscountCapacity]
-  size_t smem_hand;            // dynamic shared memory of the per-hand kernel
+  size_t smem_hand;            // dynamic shared memory of the per-hand kernel; 0 = every game
+                               // works on the global arrays (some tree is too large to stage)
   size_t smem_term;            // dynamic shared memory of the terminal kernel
   int variant;
   int precision;               // kPrecisionPairs or kPrecisionSingle
+  int pdl;                     // chain launches with programmatic dependent launch
 };
 
 int launch_init(const LaunchCtx& c, void* stream);

@@ -313,11 +313,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     double pay = 0.0;
     if (s.type == kFold) pay = s.c[s.player] * s.chance;
     if (s.type == kShowdown) pay = s.c[0] * s.chance;
-    nd.value = (float)pay;
-    if (s.type == kChance) {
-      nd.value = (float)per_card;
+    nd.arow = -1;
+    nd.aplayer = kNoCard;
+    if (s.type == kChance)
       for (Pending& kp : kids) kp.chance = s.chance * per_card;
-    }
     if (s.type == kShowdown) {
       // showdown board table: 0 for boards fixed at the root, else by the last dealt card
       if (spec.game == CFR_GAME_LEDUC) nd.row = s.board[0];
@@ -362,6 +361,13 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
   }
   g.row_begin[2] = row;
   g.n_rows = row;
+  for (int n = 1; n < N; ++n) {
+    const NodeDev& par = g.nodes[g.nodes[n].parent];
+    if (par.type == kDecision) {
+      g.nodes[n].arow = par.row + g.nodes[n].paction;
+      g.nodes[n].aplayer = par.player;
+    }
+  }
   for (int n = 0; n < N; ++n)
     if (g.nodes[n].type == kFold || g.nodes[n].type == kShowdown) g.terminals.push_back(n);
 
@@ -464,6 +470,17 @@ std::vector<uint16_t> pack_term_tables(const HostGame& g) {
       }
     }
   }
+  return out;
+}
+
+std::vector<int32_t> decision_nodes(const HostGame& g, int begin[3]) {
+  std::vector<int32_t> out;
+  for (int p = 0; p < 2; ++p) {
+    begin[p] = (int)out.size();
+    for (size_t n = 0; n < g.nodes.size(); ++n)
+      if (g.nodes[n].type == kDecision && g.nodes[n].player == p) out.push_back((int32_t)n);
+  }
+  begin[2] = (int)out.size();
   return out;
 }
 

@@ -36,6 +36,9 @@ int build_game(const cfr_game_spec& spec, HostGame& out, std::string& err);
 // The terminal kernel's per-board uint16 tables (layout: TermTab in pcfr_internal.h).
 std::vector<uint16_t> pack_term_tables(const HostGame& g);
 
+// Decision nodes of player 0 then player 1; begin[p] .. begin[p + 1] are player p's.
+std::vector<int32_t> decision_nodes(const HostGame& g, int begin[3]);
+
 // Decision node owning each regret row.
 std::vector<int32_t> row_nodes(const HostGame& g);
 
