@@ -147,6 +147,19 @@ int cfr_exploitability(cfr_tree* tree, double* expl, double* br);
 int cfr_exploitability_async(cfr_tree* tree);
 int cfr_exploitability_result(cfr_tree* tree, double* expl, double* br);
 
+/* The cfr_exploitability pass without any allocation (the paper has no counterpart: it is
+ * an interface for callers that may not allocate, e.g. a serving loop under a fixed
+ * device-memory budget).  Launches the passes directly on the handle's stream (no graph)
+ * and keeps the FP64 root reduction's scratch in one static device array of the library
+ * (148 KiB per device), so at most 1024 games and 8192 hand chunks per player per handle
+ * (a chunk is chunk_hands hands, 8 by default); larger handles get CFR_EINVAL.  expl:
+ * [n_games]; br: [n_games][2], both required, host memory.  The first call on each device
+ * does a one-time setup (resolves the array's address, loads the reduction kernel): make
+ * it before any stream capture begins.  All calls on one device share the array, so calls
+ * must not overlap: two calls in flight at once (other threads or other streams) race.
+ * Synchronises. */
+int cfr_exploitability_noalloc(cfr_tree* tree, double* expl, double* br);
+
 /* Start the solve again: R = S = 0, iteration count 0, uniform strategy, initial reach
  * (asynchronous, on the handle's stream). */
 int cfr_reset(cfr_tree* tree);

@@ -28,7 +28,7 @@ CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
-           "cfr_reset", "cfr_tree_destroy", "cfr_last_error")
+           "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc")
 
 
 class CfrError(RuntimeError):
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         lib.cfr_exploitability_async.argtypes = [P]
         lib.cfr_exploitability_result.argtypes = [P, pd, pd]
         lib.cfr_reset.argtypes = [P]
+        lib.cfr_exploitability_noalloc.argtypes = [P, pd, pd]
         lib.cfr_tree_destroy.argtypes = [P]
         lib.cfr_tree_destroy.restype = None
         lib.cfr_last_error.restype = C.c_char_p
@@ -259,6 +260,17 @@ def cfr_exploitability_result(tree, n_games: int = 1):
     br = np.zeros((n_games, 2), np.float64)
     _check(load().cfr_exploitability_result(tree, expl.ctypes.data_as(C.POINTER(C.c_double)),
                                             br.ctypes.data_as(C.POINTER(C.c_double))))
+    return expl, br
+
+
+def cfr_exploitability_noalloc(tree, expl: np.ndarray, br: np.ndarray):
+    """cfr_exploitability into caller-owned float64 arrays expl [n_games] and br [n_games, 2]
+    (the library allocates nothing during the call)."""
+    for a, n in ((expl, br.shape[0]), (br, 2 * br.shape[0])):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+            raise ValueError("expl must be float64 [n_games] and br float64 [n_games, 2], C-contiguous")
+    _check(load().cfr_exploitability_noalloc(tree, expl.ctypes.data_as(C.POINTER(C.c_double)),
+                                             br.ctypes.data_as(C.POINTER(C.c_double))))
     return expl, br
 
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -642,3 +643,138 @@ void cfr_tree_destroy(cfr_tree* t) { delete t; }
 const char* cfr_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Exploitability without allocation.
+//
+// cfr_exploitability records and instantiates a CUDA graph on its first call and keeps
+// its per-block best-response sums in buffers of the handle.  Some callers cannot let a
+// call allocate: a serving loop that runs under a fixed device-memory budget, or a
+// real-time thread that must not wait in an allocator between two decisions (freeing
+// device memory synchronises the whole device).  This variant launches
+// the same passes directly on the handle's stream and replaces the final FP64 root
+// reduction with a copy whose scratch (per-block sums, per-game arrival counters and
+// results) lives in one statically sized device array of this file.  The call makes no
+// device or host allocation; its only setup is resolving that array's address.
+
+namespace {
+
+constexpr int kStaticMaxChunks = 8192;  // hand chunks of one handle (blocks per player)
+constexpr int kStaticMaxGames = 1024;   // games of one handle
+constexpr size_t kStaticPartialBytes = (size_t)2 * kStaticMaxChunks * sizeof(double);
+constexpr size_t kStaticOutBytes = (size_t)2 * kStaticMaxGames * sizeof(double);
+constexpr size_t kStaticDoneBytes = (size_t)kStaticMaxGames * sizeof(unsigned);
+constexpr size_t kStaticScratchBytes = kStaticPartialBytes + kStaticOutBytes + kStaticDoneBytes;  // 148 KiB
+
+// Layout: partial [2][kStaticMaxChunks] FP64 (player-major, indexed by chunk-work item),
+// out [kStaticMaxGames][2] FP64, done [kStaticMaxGames] uint32.  Only `done` has to start
+// at zero: the call clears the counters of its games on its stream before the reduction,
+// and the last block of each game clears its counter again after reading it.
+static __device__ __align__(256) unsigned char g_expl_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+
+// FP64 root best-response value of one chunk of hands, sum_h r_p(h) v*_p(root, h), and the
+// per-game reduction by the last block of the game.  One warp per (player, chunk); the
+// root is node 0 and the per-hand pass has left v* in cfv_br.
+__global__ void __launch_bounds__(32) k_br_root_static(const GameDev* __restrict__ games,
+                                                       const Work* __restrict__ work, int n_work, int precision,
+                                                       unsigned char* __restrict__ scratch) {
+  double* partial = reinterpret_cast<double*>(scratch);
+  double* out = reinterpret_cast<double*>(scratch + kStaticPartialBytes);
+  unsigned* done = reinterpret_cast<unsigned*>(scratch + kStaticPartialBytes + kStaticOutBytes);
+  const int p = blockIdx.x >= (unsigned)n_work;
+  const int item = blockIdx.x - p * n_work;
+  const Work wk = work[item];
+  const GameDev& G = games[wk.game];
+  const int lane = threadIdx.x;
+  const int h = wk.unit * G.chunk + lane;
+  double x = 0.0;
+  if (lane < G.chunk && h < G.n_hands) {
+    const size_t at = ((size_t)p * G.n_nodes) * G.hstride + h;  // (player p, node 0, hand h)
+    double v;
+    if (precision == kPrecisionSingle) {
+      v = (double)static_cast<const float*>(G.cfv_br)[at];
+    } else {
+      const float2 hl = static_cast<const float2*>(G.cfv_br)[at];
+      v = (double)hl.x + (double)hl.y;
+    }
+    x = G.range64[(size_t)p * G.hstride + h] * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  __shared__ bool s_last;
+  if (lane == 0) {
+    partial[(size_t)p * kStaticMaxChunks + item] = x;
+    __threadfence();
+    s_last = atomicAdd(&done[wk.game], 1u) == (unsigned)(2 * G.n_chunks - 1);
+  }
+  __syncwarp();
+  if (!s_last) return;
+  __threadfence();
+  // first chunk-work item of this game: the list is game-major, chunks in order
+  int first = 0;
+  for (int g = lane; g < wk.game; g += 32) first += games[g].n_chunks;
+  for (int o = 16; o > 0; o >>= 1) first += __shfl_down_sync(0xffffffffu, first, o);
+  first = __shfl_sync(0xffffffffu, first, 0);
+  for (int q = 0; q < 2; ++q) {
+    double s = 0.0;
+    for (int c = lane; c < G.n_chunks; c += 32) s += __ldcg(&partial[(size_t)q * kStaticMaxChunks + first + c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[2 * (size_t)wk.game + q] = s;
+  }
+  if (lane == 0) done[wk.game] = 0u;
+}
+
+// Once per device, with that device current: the address of this device's copy of the
+// scratch array.  Also loads the reduction kernel, so that later calls do no setup.
+int static_scratch(unsigned char** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(CFR_ECUDA, "device ordinal beyond the scratch table");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_expl_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_expl_scratch)");
+    cudaFuncAttributes attr;
+    e = cudaFuncGetAttributes(&attr, k_br_root_static);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes(k_br_root_static)");
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return CFR_OK;
+}
+
+}  // namespace
+
+extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (!expl || !br) return fail(CFR_EINVAL, "expl and br are both required");
+  const LaunchCtx& c = t->ctx;
+  if (c.n_games > kStaticMaxGames)
+    return fail(CFR_EINVAL, "cfr_exploitability_noalloc: the handle has " + std::to_string(c.n_games) +
+                                " games; its static scratch holds at most " + std::to_string(kStaticMaxGames));
+  if (c.n_chunk_work > kStaticMaxChunks)
+    return fail(CFR_EINVAL, "cfr_exploitability_noalloc: the handle has " + std::to_string(c.n_chunk_work) +
+                                " hand chunks per player; its static scratch holds at most " +
+                                std::to_string(kStaticMaxChunks));
+  unsigned char* scratch = nullptr;
+  int rc = static_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t s = t->stream;
+  CK(cudaMemsetAsync(scratch + kStaticPartialBytes + kStaticOutBytes, 0, (size_t)c.n_games * sizeof(unsigned), s));
+  if (launch_avg_reach(c, s) || launch_terminal(c, 3, 1, s) || launch_br(c, s))
+    return fail(CFR_ECUDA, "exploitability launch failed");
+  k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);
+  CK(cudaGetLastError());
+  t->launches += c.n_term_work > 0 ? 4 : 3;
+  CK(cudaMemcpyAsync(br, scratch + kStaticPartialBytes, (size_t)c.n_games * 2 * sizeof(double),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  rc = check_device_flag(t);
+  if (rc) return rc;
+  for (int g = 0; g < c.n_games; ++g) expl[g] = 0.5 * (br[2 * g] + br[2 * g + 1]);
+  return CFR_OK;
+}

@@ -1,0 +1,89 @@
+"""cfr_exploitability_noalloc (static device scratch, no allocation) against cfr_exploitability
+on the same solver state, two calls in a row each, through the C ABI.  Collected last so it
+also runs after every other test of the session has used the library."""
+import numpy as np
+import pytest
+
+from paper_2605_19928_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12  # the two differ only in the summation order of the FP64 root reduction
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2605_19928_gb300 import build as pbuild
+    pbuild.build()
+    capi.load()
+    import torch
+    assert torch.cuda.is_available()
+    capi.use_torch_allocator()
+
+
+def _both(tree, n_games):
+    e_ref, br_ref = capi.cfr_exploitability(tree, n_games)
+    expl = np.full(n_games, np.nan)
+    br = np.full((n_games, 2), np.nan)
+    before = capi.cfr_counters(tree)["device_bytes"]
+    capi.cfr_exploitability_noalloc(tree, expl, br)
+    assert capi.cfr_counters(tree)["device_bytes"] == before
+    return e_ref, br_ref, expl, br
+
+
+def _check(tree, n_games, pot):
+    e_ref, br_ref, expl, br = _both(tree, n_games)
+    scale = np.maximum(np.abs(br_ref), 1e-9 * pot)
+    assert np.all(np.abs(br - br_ref) <= RTOL * scale), (br, br_ref)
+    assert np.allclose(expl, 0.5 * br.sum(axis=1), rtol=0, atol=0)
+    assert np.all(np.abs(expl - e_ref) <= RTOL * np.maximum(np.abs(e_ref), 1e-9 * pot))
+    return expl
+
+
+@pytest.mark.parametrize("precision", ["pairs", "single"])
+def test_noalloc_matches_on_river_two_calls(precision):
+    spec = synth.river_subgame(n_hands=1081, seed=0, range_seed=1)
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision=precision))
+    try:
+        capi.cfr_iterate(tree, 30)
+        e1 = _check(tree, 1, spec.pot)
+        e1_again = _check(tree, 1, spec.pot)   # second call in a row, same state
+        assert e1_again[0] == e1[0]
+        capi.cfr_iterate(tree, 20)
+        e2 = _check(tree, 1, spec.pot)
+        assert e2[0] != e1[0]
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_noalloc_matches_on_batch_two_calls():
+    specs = [synth.river_subgame(n_hands=n, seed=s, range_seed=s + 1) for n, s in ((1081, 2), (203, 3), (64, 4))]
+    leduc = synth.leduc()
+    leduc.ranges[:] = synth.random_ranges(6, 11)
+    specs.append(leduc)
+    tree = capi.cfr_batch_create(specs, capi.make_opts("dcfr"))
+    try:
+        for _ in range(2):
+            capi.cfr_iterate(tree, 10)
+            _check(tree, len(specs), 100.0)
+            _check(tree, len(specs), 100.0)
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_noalloc_rejects_handles_beyond_its_scratch():
+    # 8 rivers at one hand per chunk: 8 * 1081 = 8648 chunks per player > 8192
+    specs = [synth.river_subgame(n_hands=1081, seed=s, range_seed=s + 1, max_raises=1) for s in range(8)]
+    tree = capi.cfr_batch_create(specs, capi.make_opts("dcfr", chunk_hands=1))
+    try:
+        expl = np.zeros(8)
+        br = np.zeros((8, 2))
+        with pytest.raises(capi.CfrError) as ei:
+            capi.cfr_exploitability_noalloc(tree, expl, br)
+        assert ei.value.code == capi.CFR_EINVAL
+        assert "8192" in str(ei.value)
+        # the handle still works through the allocating entry point
+        e, _ = capi.cfr_exploitability(tree, 8)
+        assert np.all(np.isfinite(e))
+    finally:
+        capi.cfr_tree_destroy(tree)
