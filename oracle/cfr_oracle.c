@@ -22,7 +22,7 @@
  *     values are counterfactual values like those of the walk (chance probabilities inside
  *     the counterfactual reach).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - the subgame starts with a chance deal of private hands with probability
  *     r_0(h_0) r_1(h_1) / Z over non-conflicting pairs; r_i(h_i) counts as player i's own
  *     reach, r_{-i}(h_{-i}) / Z as the opponent-and-chance part;
