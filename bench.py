@@ -42,9 +42,13 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--iters-per-step", type=int, default=1000)
+    ap.add_argument("--workload", choices=["river", "batch"], default="river",
+                    help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle")
+    ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--iters-per-step", type=int, default=None, help="default 1000 (river) or 500 (batch)")
     ap.add_argument("--precision", choices=["pairs", "single"], default="pairs")
     ap.add_argument("--chunk-hands", type=int, default=0)
+    ap.add_argument("--schedule", choices=["auto", "level", "stream"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -97,6 +101,13 @@ def workload_spec(rank: int = 0):
     return synth.river_subgame(seed=0 + 1000 * rank, range_seed=1 + 1000 * rank)
 
 
+def workload_specs(args, rank: int = 0):
+    from paper_2605_19928_gb300 import synth
+    if args.workload == "batch":
+        return synth.batch_rivers(args.batch_size, seed=rank)
+    return [workload_spec(rank)]
+
+
 def workload_config(args, spec, n_nodes):
     return {"workload": "river subgame, exact (no depth limit)", "board_cards": 5, "hands": spec.n_hands,
             "public_nodes": n_nodes, "pot": spec.pot, "stack": spec.stack, "bet_sizes": "0.5,1.0 pot,all-in",
@@ -105,6 +116,19 @@ def workload_config(args, spec, n_nodes):
             "values": "fp32 pairs" if args.precision == "pairs" else "fp32",
             "l2": "flushed between steps (256 MB write, outside the timed events)",
             "seeds": spec.seeds}
+
+
+def batch_config(args, specs, shapes):
+    nodes = [sh["nodes"] for sh in shapes]
+    return {"workload": f"batched serving: {len(specs)} uneven river subgames in one handle, exact",
+            "subgames": len(specs), "hands": specs[0].n_hands, "public_nodes_min_median_max":
+                [min(nodes), sorted(nodes)[len(nodes) // 2], max(nodes)], "public_nodes_total": sum(nodes),
+            "pot": 100.0, "stacks": "100-1000", "bet_sizes": "1-4 pot fractions + all-in", "max_raises": "2-3",
+            "variant": "DCFR(1.5,0,2) alternating", "iters_per_step": args.iters_per_step,
+            "step": "reset + iterations + exploitability, all subgames together",
+            "values": "fp32 pairs" if args.precision == "pairs" else "fp32",
+            "l2": "inputs larger than L2 (state of all subgames) and 256 MB flush between steps",
+            "seeds": {"batch": "synth.batch_rivers(seed=rank)", "boards_strengths": "1000+k", "ranges": "5000+k"}}
 
 
 # ------------------------------------------------------------------ clocks
@@ -176,12 +200,12 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def tree_shape(capi, tree):
-    n_nodes, n_hands, _ = capi.cfr_tree_info(tree)
+def tree_shape(capi, tree, game: int = 0):
+    n_nodes, n_hands, _ = capi.cfr_tree_info(tree, game)
     rows = [0, 0]
     terminals = 0
     for n in range(n_nodes):
-        info = capi.cfr_node_info(tree, n)
+        info = capi.cfr_node_info(tree, n, game)
         if info["type"] == capi.CFR_NODE_DECISION:
             rows[info["player"]] += info["n_actions"]
         elif info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN):
@@ -190,14 +214,14 @@ def tree_shape(capi, tree):
 
 
 def algorithmic_bytes(shape, stage: str, value_bytes: int) -> float:
-    """Bytes one launch must move (per player for the per-iteration stages).
+    """Bytes one launch must move, for one player's launch (the mean of the two players').
 
     update:   per (decision row of the player, hand): R and S read + write (32 B), strategy
               read + write (2 V); per (node, hand): reach read + write and value write (3 V);
               per (terminal, hand): terminal value read (V).
     terminal: per (terminal, hand): opponent reach read and value write (2 V)."""
     H, V = shape["hands"], value_bytes
-    rows = max(shape["rows"])
+    rows = 0.5 * (shape["rows"][0] + shape["rows"][1])
     if stage == "update":
         return H * (rows * (32 + 2 * V) + shape["nodes"] * 3 * V + shape["terminals"] * V)
     if stage == "terminal":
@@ -213,9 +237,9 @@ def kernels_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(stage: str):
+def profiled_traffic(stage: str, workload: str = "river1081"):
     """DRAM bytes per launch from the committed ncu summary, if it matches these kernels."""
-    path = os.path.join(ROOT, "profiles", f"{stage}_river1081.md")
+    path = os.path.join(ROOT, "profiles", f"{stage}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -250,32 +274,64 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    spec = workload_spec(0)
+    batch = args.workload == "batch"
+    specs = workload_specs(args, 0)
+    picks = sorted(set(int(k * len(specs) / 4) for k in range(4))) if batch else [0]
     budget = max(1.0, args.cpu_seconds / 4)
-    for _ in range(args.warmup):
-        oracle_sample(spec, budget / 4)
+    for k in range(args.warmup):
+        oracle_sample(specs[picks[k % len(picks)]], budget / 4)
     total_iters, total_s, threads = 0, 0.0, 1
-    for _ in range(args.steps):
-        r = oracle_sample(spec, budget)
+    for k in range(args.steps):
+        r = oracle_sample(specs[picks[k % len(picks)]], budget)
         total_iters += r["iters"]
         total_s += r["seconds"]
         threads = r["threads"]
     value = total_iters / total_s
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+    unit = "subgame iter/s" if batch else "iter/s"
+    what = f"subgames {picks} of the {len(specs)}-subgame batch in turn" if batch else "the 1081-hand river subgame"
+    config = batch_config(args, specs, [{"nodes": 0}]) if batch else workload_config(args, specs[0], None)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, spec, None),
-            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{total_iters} DCFR iterations of the 1081-hand river subgame over "
-                                       f"{args.steps} steps, each followed by one exploitability pass"},
-            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": f"{total_iters} DCFR iterations of {what} over {args.steps} steps "
+                                       f"of {budget:.1f} s, each followed by one exploitability pass"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm
 
+def time_to_target(capi, tree, n_games, max_iters, every, target_mbb):
+    """Iterations each subgame needs until its exploitability is at most target_mbb
+    (checked every `every` iterations; None if not reached within max_iters)."""
+    capi.cfr_reset(tree)
+    need = [None] * n_games
+    done = 0
+    while done < max_iters and any(x is None for x in need):
+        capi.cfr_iterate(tree, every)
+        done += every
+        expl, _ = capi.cfr_exploitability(tree, n_games)
+        for g in range(n_games):
+            if need[g] is None and 1000.0 * float(expl[g]) / BB_CHIPS <= target_mbb:
+                need[g] = done
+    return need
+
+
+def pinned_copy(torch, spec):
+    out = {}
+    for name in ("hands", "ranges", "strength", "board"):
+        a = getattr(spec, name)
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        out[name] = t
+    return type(spec)(**{**spec.__dict__, **{k: v.numpy() for k, v in out.items()}}), out
+
+
 def run_ours(args):
+    import numpy as np
     import torch
 
     from paper_2605_19928_gb300 import capi
@@ -290,10 +346,18 @@ def run_ours(args):
     capi.load()
     capi.use_torch_allocator()
     stream = torch.cuda.current_stream(device)
-    spec = workload_spec(rank)
+    batch = args.workload == "batch"
+    specs = workload_specs(args, rank)
+    G = len(specs)
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
-                          precision=args.precision)
-    tree = capi.cfr_tree_create(spec, opts, stream=stream.cuda_stream)
+                          precision=args.precision, schedule=args.schedule)
+
+    def create(sp):
+        if batch:
+            return capi.cfr_batch_create(sp, opts, stream=stream.cuda_stream)
+        return capi.cfr_tree_create(sp[0], opts, stream=stream.cuda_stream)
+
+    tree = create(specs)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     ips = args.iters_per_step
 
@@ -325,74 +389,92 @@ def run_ours(args):
     gpu_launches = capi.cfr_counters(tree)["kernel_launches"] - launches0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     local_s = sum(step_ms) / 1000.0
-    value, t_max = aggregate(args.steps * ips, local_s, world, dist, device)
-    expl, br = capi.cfr_exploitability_result(tree)
+    value, t_max = aggregate(args.steps * ips * G, local_s, world, dist, device)
+    expl, br = capi.cfr_exploitability_result(tree, G)
+    ms_per_iter = 1000.0 * t_max / (args.steps * ips)
 
     # per-kernel device time (un-graphed, CUDA events between launches) for the roofline
-    shape = tree_shape(capi, tree)
+    shapes = [tree_shape(capi, tree, g) for g in range(G)]
     capi.cfr_reset(tree)
-    stages = capi.cfr_stage_times(tree, min(ips, 200))
+    stages = capi.cfr_stage_times(tree, min(ips, 200 if not batch else 20))
     vbytes = 8 if args.precision == "pairs" else 4
     per_step = {k: stages[k][0] * (2 * ips if k in ("terminal", "update") else 1) for k in stages}
     dom = max(("update", "terminal"), key=lambda k: per_step[k])
-    alg = algorithmic_bytes(shape, dom, vbytes)
+    alg = sum(algorithmic_bytes(sh, dom, vbytes) for sh in shapes)
     achieved = alg / (stages[dom][0] * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    roofline = {"bound": "hbm", "kernel": f"k_hand<update>" if dom == "update" else "k_terminal",
+    schedule = "stream" if capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_STREAM else "level"
+    upd_kernel = "k_stream_update" if schedule == "stream" else "k_hand<update>"
+    roofline = {"bound": "hbm", "kernel": upd_kernel if dom == "update" else "k_terminal",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs", "traffic": profiled_traffic(dom),
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": profiled_traffic(dom, "batch256" if batch else "river1081"),
                 "algorithmic_bytes_per_launch": alg, "launch_ms": stages[dom][0],
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
 
+    target = None
+    if batch:
+        need = time_to_target(capi, tree, G, max_iters=ips, every=10, target_mbb=1.0)
+        got = sorted(x for x in need if x is not None)
+        pct = (lambda q: None if len(got) < G else got[min(G - 1, int(q * G))])
+        target = {"target_mbb_per_hand": 1.0, "reached": len(got), "of": G, "checked_every_iters": 10,
+                  "iters_p50": pct(0.50), "iters_p99": pct(0.99),
+                  "ms_p50": None if pct(0.50) is None else pct(0.50) * ms_per_iter,
+                  "ms_p99": None if pct(0.99) is None else pct(0.99) * ms_per_iter,
+                  "note": "iterations of the whole batch (all subgames advance together) times the "
+                          "measured ms per batch iteration"}
+
     # end to end through the C ABI with host buffers: inputs from pinned host memory,
-    # create + solve + exploitability + read of the root's average strategy, every step
+    # create + solve + exploitability + read of each root's average strategy, every step
     e2e = None
     if args.e2e_steps > 0:
-        import numpy as np
-        pinned = {}
-        for name in ("hands", "ranges", "strength", "board"):
-            a = getattr(spec, name)
-            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
-            t.numpy()[...] = a
-            pinned[name] = t
-        pspec = type(spec)(**{**spec.__dict__, **{k: v.numpy() for k, v in pinned.items()}})
-        root_out = np.empty((4, spec.n_hands), np.float32)
+        pspecs = [pinned_copy(torch, sp)[0] for sp in specs]
+        roots = []
         times, h2d, d2h = [], 0, 0
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
-            tr = capi.cfr_tree_create(pspec, opts, stream=stream.cuda_stream)
+            tr = create(pspecs)
             capi.cfr_iterate(tr, ips)
-            ex, _ = capi.cfr_exploitability(tr)
-            a = capi.cfr_node_info(tr, 0)["n_actions"]
-            capi.cfr_strategy(tr, 0, average=True, out=root_out[:a])
+            ex, _ = capi.cfr_exploitability(tr, G)
+            nbytes = 16 * G
+            for g in range(G):
+                a = capi.cfr_node_info(tr, 0, g)["n_actions"]
+                roots.append(capi.cfr_strategy(tr, 0, average=True, game=g))
+                nbytes += a * specs[g].n_hands * vbytes
             t1 = time.perf_counter()
             if k > 0:
                 times.append(t1 - t0)
                 h2d = capi.cfr_counters(tr)["h2d_bytes"]
-                d2h = 16 + a * spec.n_hands * vbytes
+                d2h = nbytes
             capi.cfr_tree_destroy(tr)
-        e2e_val, _ = aggregate(ips * len(times), sum(times), world, dist, device)
-        e2e = {"value": e2e_val, "unit": "iter/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            roots.clear()
+        e2e_val, _ = aggregate(ips * G * len(times), sum(times), world, dist, device)
+        e2e = {"value": e2e_val, "unit": "subgame iter/s" if batch else "iter/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
                "step": f"create from pinned host inputs + {ips} iterations + exploitability + root average "
-                       "strategy to host"}
+                       "strateg" + ("ies of every subgame" if batch else "y") + " to host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(spec, args.cpu_seconds)
-        cpu = {"value": r["iters"] / r["seconds"], "unit": "iter/s", "cores": r["threads"], "kind": "oracle",
-               "sample": f"{r['iters']} DCFR iterations of the same 1081-hand river subgame plus one "
-                         f"exploitability pass ({r['seconds']:.1f} s, FP64, walks every history)"}
+        cpu = cpu_baseline(specs, args.cpu_seconds, batch)
     capi.cfr_tree_destroy(tree)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+        if batch:
+            config = {**batch_config(args, specs, shapes), "schedule": schedule}
+            e_mbb = sorted(1000.0 * float(x) / BB_CHIPS for x in expl)
+            quality = {"exploitability_mbb_median": e_mbb[G // 2], "exploitability_mbb_max": e_mbb[-1],
+                       "time_to_1mbb": target}
+        else:
+            config = {**workload_config(args, specs[0], shapes[0]["nodes"]), "schedule": schedule}
+            quality = {"exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS,
+                       "exploitability_pct_pot": 100.0 * float(expl[0]) / specs[0].pot}
+        line = {"metric": METRIC, "value": value, "unit": "subgame iter/s" if batch else "iter/s",
+                "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
-                "ms_per_iter": 1000.0 * t_max / (args.steps * ips), "higher_is_better": True, "scaling": "weak",
+                "ms_per_iter": ms_per_iter, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32x2 values, f64 R/S" if args.precision == "pairs" else
-                "f32 values, f64 R/S", "data": "synthetic",
-                "config": workload_config(args, spec, shape["nodes"]),
-                "exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS,
-                "exploitability_pct_pot": 100.0 * float(expl[0]) / spec.pot,
+                "f32 values, f64 R/S", "data": "synthetic", "config": config, **quality,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
                 "clocks": clock_info}
         print(json.dumps(line))
@@ -401,8 +483,31 @@ def run_ours(args):
     return 0
 
 
+def cpu_baseline(specs, seconds, batch):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+    if not batch:
+        r = oracle_sample(specs[0], seconds)
+        return {"value": r["iters"] / r["seconds"], "unit": "iter/s", "cores": r["threads"], "kind": "oracle",
+                "sample": f"{r['iters']} DCFR iterations of the same 1081-hand river subgame plus one "
+                          f"exploitability pass ({r['seconds']:.1f} s, FP64, walks every history)"}
+    picks = sorted(set(int(k * len(specs) / 4) for k in range(4)))
+    sec_per_iter, iters, total, threads = [], 0, 0.0, 1
+    for g in picks:
+        r = oracle_sample(specs[g], seconds / len(picks))
+        sec_per_iter.append(r["seconds"] / r["iters"])
+        iters += r["iters"]
+        total += r["seconds"]
+        threads = r["threads"]
+    value = 1.0 / (sum(sec_per_iter) / len(sec_per_iter))
+    return {"value": value, "unit": "subgame iter/s", "cores": threads, "kind": "oracle",
+            "sample": f"{iters} DCFR iterations (+ one exploitability pass each) of subgames {picks} of the "
+                      f"batch ({total:.1f} s); value = 1 / mean seconds per subgame iteration"}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.iters_per_step is None:
+        args.iters_per_step = 500 if args.workload == "batch" else 1000
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

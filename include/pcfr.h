@@ -96,8 +96,16 @@ typedef struct cfr_game_spec {
  * values as double-float pairs of FP32 (about 44 significant bits, computed on the FP32
  * pipe); CFR_PRECISION_SINGLE carries them in plain FP32.  Cumulative regrets R and
  * average-strategy sums S are FP64 in both.
+ * schedule: how the update launch (Stages 1, 6 and 7 of one player) is laid out; results
+ * are the same bits either way.  CFR_SCHEDULE_LEVEL: one CUDA block per chunk_hands hands
+ * walks the tree level by level (lowest latency for one subgame).  CFR_SCHEDULE_STREAM: one
+ * warp per 32 hands walks a depth-first program of its tree with no block barriers and no
+ * inner-node state in DRAM (highest throughput for batches; needs at most 8 actions per
+ * decision node).  CFR_SCHEDULE_AUTO (0) picks STREAM when the handle has at least 1216
+ * such warps (8 per SM) and every tree allows it, else LEVEL.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
+enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2 };
 typedef struct cfr_solver_opts {
   int variant;
   double alpha;
@@ -106,6 +114,7 @@ typedef struct cfr_solver_opts {
   int alternating;
   int chunk_hands;
   int precision;
+  int schedule;
 } cfr_solver_opts;
 
 typedef struct cfr_tree cfr_tree;
@@ -163,6 +172,10 @@ int cfr_exploitability_noalloc(cfr_tree* tree, double* expl, double* br);
 /* Start the solve again: R = S = 0, iteration count 0, uniform strategy, initial reach
  * (asynchronous, on the handle's stream). */
 int cfr_reset(cfr_tree* tree);
+
+/* The update schedule the handle uses (CFR_SCHEDULE_LEVEL or CFR_SCHEDULE_STREAM), or a
+ * negative status. */
+int cfr_schedule(const cfr_tree* tree);
 
 /* Sizes of one subgame and the number of iterations done.  Any out pointer may be NULL. */
 int cfr_tree_info(const cfr_tree* tree, int game, int* n_nodes, int* n_hands, int* iters_done);

@@ -23,12 +23,14 @@ CFR_NODE_DECISION, CFR_NODE_FOLD, CFR_NODE_SHOWDOWN, CFR_NODE_CHANCE = 0, 1, 2, 
 CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV = 0, 1, 2, 3
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
+CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM = 0, 1, 2
+SCHEDULES = {"auto": CFR_SCHEDULE_AUTO, "level": CFR_SCHEDULE_LEVEL, "stream": CFR_SCHEDULE_STREAM}
 VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR}
 CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
-           "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc")
+           "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule")
 
 
 class CfrError(RuntimeError):
@@ -47,7 +49,7 @@ class cfr_game_spec(C.Structure):
 
 class cfr_solver_opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("alternating", C.c_int), ("chunk_hands", C.c_int), ("precision", C.c_int)]
+                ("alternating", C.c_int), ("chunk_hands", C.c_int), ("precision", C.c_int), ("schedule", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -86,6 +88,7 @@ def load(path: str = LIB_PATH):
         lib.cfr_exploitability_result.argtypes = [P, pd, pd]
         lib.cfr_reset.argtypes = [P]
         lib.cfr_exploitability_noalloc.argtypes = [P, pd, pd]
+        lib.cfr_schedule.argtypes = [P]
         lib.cfr_tree_destroy.argtypes = [P]
         lib.cfr_tree_destroy.restype = None
         lib.cfr_last_error.restype = C.c_char_p
@@ -168,10 +171,11 @@ def make_spec(g) -> tuple[cfr_game_spec, tuple]:
 
 
 def make_opts(variant="dcfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True, chunk_hands=0,
-              precision="pairs") -> cfr_solver_opts:
+              precision="pairs", schedule="auto") -> cfr_solver_opts:
     return cfr_solver_opts(VARIANTS[variant] if isinstance(variant, str) else int(variant), alpha, beta, gamma,
                            int(alternating), int(chunk_hands),
-                           PRECISIONS[precision] if isinstance(precision, str) else int(precision))
+                           PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                           SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule))
 
 
 def _stream_arg(stream):
@@ -217,6 +221,13 @@ def cfr_iterate(tree, n_iters: int = 1):
 
 def cfr_sync(tree):
     _check(load().cfr_sync(tree))
+
+
+def cfr_schedule(tree) -> int:
+    rc = load().cfr_schedule(tree)
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def cfr_tree_info(tree, game: int = 0):

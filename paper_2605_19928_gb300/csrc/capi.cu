@@ -45,6 +45,7 @@ struct cfr_tree {
   GameDev* d_games = nullptr;
   Work* d_chunk_work = nullptr;
   Work* d_term_work = nullptr;
+  Work* d_warp_work = nullptr;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
   int* d_err = nullptr;
@@ -57,6 +58,9 @@ struct cfr_tree {
   cfr_solver_opts opts{};
   LaunchCtx ctx{};
   int iters_done = 0;
+  int64_t state_gen = 0;        // bumped whenever R or S may change
+  int64_t avg_gen = -1;         // state_gen for which sigbar holds k_average_rows' output
+  int64_t cur_gen = -1;         // state_gen for which sigma holds RM(R) (stream schedule)
   int64_t launches = 0;         // kernels launched (graph replays included)
   int64_t device_bytes = 0;
   int64_t h2d_bytes = 0;
@@ -177,7 +181,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if (!out) return fail(CFR_EINVAL, "out is NULL");
   *out = nullptr;
   if (!specs || n_games <= 0) return fail(CFR_EINVAL, "no game given");
-  cfr_solver_opts o{CFR_VARIANT_DCFR, 1.5, 0.0, 2.0, 1, 0, CFR_PRECISION_PAIRS};
+  cfr_solver_opts o{CFR_VARIANT_DCFR, 1.5, 0.0, 2.0, 1, 0, CFR_PRECISION_PAIRS, CFR_SCHEDULE_AUTO};
   if (opts) o = *opts;
   if (o.variant < 0 || o.variant > 2) return fail(CFR_EINVAL, "unknown CFR variant");
   if (o.precision != CFR_PRECISION_PAIRS && o.precision != CFR_PRECISION_SINGLE)
@@ -185,6 +189,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
   if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
     return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
+  if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_STREAM) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
   static int configured = configure_kernels();
@@ -225,7 +230,36 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
                                         (size_t)(h.hand_size * h.n_hands + 1 + h.n_hands + 1) * 8);
   }
 
-  std::vector<Work> chunk_work, term_work;
+  // Update schedule: one warp per 32 hands when the handle has enough of them to fill the
+  // GPU (8 warps per SM) and every tree fits the warp's registers and stack.
+  std::vector<std::vector<int32_t>> programs(n_games);
+  int stream_depth = 1, stream_warps = 0;
+  bool stream_ok = true;
+  for (int g = 0; g < n_games; ++g) {
+    int depth = 0, amax = 0;
+    programs[g] = dfs_program(t->host[g], &depth, &amax);
+    stream_depth = std::max(stream_depth, depth);
+    stream_ok = stream_ok && amax <= kStreamMaxActions;
+    stream_warps += (t->host[g].n_hands + 31) / 32;
+  }
+  // the program of the largest tree is staged in shared memory when it takes at most 64 KB
+  int max_nodes = 0;
+  for (int g = 0; g < n_games; ++g) max_nodes = std::max(max_nodes, (int)t->host[g].nodes.size());
+  const int stream_prog = max_nodes * (int)sizeof(ProgOp) <= 64 * 1024 ? max_nodes : 0;
+  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_depth, es) <= 200 * 1024;
+  int schedule = kScheduleLevel;
+  if (o.schedule == CFR_SCHEDULE_STREAM) {
+    if (!stream_ok) {
+      delete t;
+      return fail(CFR_EINVAL, "the stream schedule needs at most " + std::to_string(kStreamMaxActions) +
+                                  " actions per decision node and a stack that fits shared memory");
+    }
+    schedule = kScheduleStream;
+  } else if (o.schedule == CFR_SCHEDULE_AUTO && stream_ok && stream_warps >= 8 * 152) {
+    schedule = kScheduleStream;
+  }
+
+  std::vector<Work> chunk_work, term_work, warp_work;
   t->dev.resize(n_games);
   for (int g = 0; g < n_games; ++g) {
     const HostGame& h = t->host[g];
@@ -254,19 +288,23 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     const std::vector<int32_t> rown = row_nodes(h);
     const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
     NodeDev* nodes;
-    int32_t *ls, *rn, *dn;
+    int32_t *ls, *rn, *dn, *chk;
+    ProgOp* prog;
+    const std::vector<ProgOp> ops = program_ops(h, programs[g]);
+    const std::vector<int32_t> chunks = stream_chunks(h, programs[g], kStreamHalf, d.chunk_off, d.chunk_count);
     uint16_t* tb;
     uint64_t* hm;
     float* rrv;
     double *rr64, *pay;
     if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
         (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
-        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb)) || (rc = upload(t, decn, &dn))) {
+        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb)) || (rc = upload(t, decn, &dn)) ||
+        (rc = upload(t, ops, &prog)) || (rc = upload(t, chunks, &chk))) {
       delete t;
       return rc;
     }
     d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn;
+    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk;
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value
     float *sig, *sigb, *rch, *rchb, *cf, *cfb;
@@ -280,10 +318,20 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     }
     d.sigma = sig; d.sigbar = sigb; d.reach = rch; d.reach_bar = rchb; d.cfv = cf; d.cfv_br = cfb;
     for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
+
     for (int n : h.terminals) term_work.push_back({g, n});
   }
+  // stream schedule: blocks of kStreamWarps warps of one game, largest trees first so that
+  // their long walks start at once and the small trees fill in behind them
+  std::vector<int> by_size(n_games);
+  for (int g = 0; g < n_games; ++g) by_size[g] = g;
+  std::stable_sort(by_size.begin(), by_size.end(),
+                   [&](int a, int b) { return t->host[a].nodes.size() > t->host[b].nodes.size(); });
+  for (int g : by_size)
+    for (int u = 0; u < (t->host[g].n_hands + 31) / 32; u += kStreamWarps) warp_work.push_back({g, u});
   if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
-      (rc = upload(t, term_work, &t->d_term_work)) || (rc = zeros(t, 1, &t->d_iter)) ||
+      (rc = upload(t, term_work, &t->d_term_work)) || (rc = upload(t, warp_work, &t->d_warp_work)) ||
+      (rc = zeros(t, 1, &t->d_iter)) ||
       (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) ||
       (rc = upload(t, discount_table(o, kDiscountCapacity), &t->d_disc))) {
     delete t;
@@ -306,6 +354,11 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.variant = o.variant;
   c.precision = o.precision;
   c.pdl = 1;
+  c.schedule = schedule;
+  c.warp_work = t->d_warp_work;
+  c.n_warp_work = (int)warp_work.size();
+  c.stream_depth = stream_depth;
+  c.stream_prog = stream_prog;
   t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
   t->launches += 1;
   if (launch_init(c, stream) != 0) {
@@ -406,6 +459,7 @@ int cfr_iterate(cfr_tree* t, int n_iters) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
+  t->state_gen += 1;
   for (int k = 0; k < n_iters; ++k) CK(cudaGraphLaunch(t->iter_graph, t->stream));
   t->iters_done += n_iters;
   t->launches += (int64_t)n_iters * t->launches_per_iteration;
@@ -427,8 +481,17 @@ int cfr_strategy(cfr_tree* t, int game, int node, int average, float* out, size_
   const NodeDev& nd = h.nodes[node];
   const size_t need = (size_t)nd.n_kids * h.n_hands;
   if (!out || out_len < need) return fail(CFR_EINVAL, "output buffer too small");
-  if (average && launch_average_rows(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "average launch failed");
-  if (average) t->launches += 1;
+  if (average && t->avg_gen != t->state_gen) {  // all games at once; reused until R or S change
+    if (launch_average_rows(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "average launch failed");
+    t->launches += 1;
+    t->avg_gen = t->state_gen;
+  }
+  if (!average && t->ctx.schedule == kScheduleStream && t->cur_gen != t->state_gen) {
+    // the stream schedule keeps no strategy rows: regret-match R for the read-back
+    if (launch_current_rows(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "strategy launch failed");
+    t->launches += 1;
+    t->cur_gen = t->state_gen;
+  }
   const size_t vf = t->opts.precision == CFR_PRECISION_SINGLE ? 1 : 2;
   std::vector<float> tmp(need * vf);
   const float* src = static_cast<const float*>(average ? t->dev[game].sigbar : t->dev[game].sigma);
@@ -456,6 +519,7 @@ int cfr_exploitability_async(cfr_tree* t) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
+  t->avg_gen = -1;  // the pass rewrites sigbar with its own normalisation
   CK(cudaGraphLaunch(t->expl_graph, t->stream));
   t->launches += t->ctx.n_term_work > 0 ? 3 : 2;
   return CFR_OK;
@@ -496,10 +560,16 @@ int cfr_reset(cfr_tree* t) {
     CK(cudaMemsetAsync(d.S, 0, rows, t->stream));
   }
   CK(cudaMemsetAsync(t->d_iter, 0, sizeof(int), t->stream));
+  t->state_gen += 1;
   if (launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "initial strategy launch failed");
   t->launches += 1;
   t->iters_done = 0;
   return CFR_OK;
+}
+
+int cfr_schedule(const cfr_tree* t) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  return t->ctx.schedule == kScheduleStream ? CFR_SCHEDULE_STREAM : CFR_SCHEDULE_LEVEL;
 }
 
 int cfr_tree_info(const cfr_tree* t, int game, int* n_nodes, int* n_hands, int* iters_done) {
@@ -573,6 +643,8 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (drc) return drc;
   const LaunchCtx& c = t->ctx;
   cudaStream_t s = t->stream;
+  t->state_gen += 1;
+  t->avg_gen = -1;
   std::vector<cudaEvent_t> ev;
   std::vector<int> stage_of;
   auto mark = [&](int stage) -> cudaError_t {
@@ -765,6 +837,7 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
   if (rc) return rc;
   cudaStream_t s = t->stream;
   CK(cudaMemsetAsync(scratch + kStaticPartialBytes + kStaticOutBytes, 0, (size_t)c.n_games * sizeof(unsigned), s));
+  t->avg_gen = -1;
   if (launch_avg_reach(c, s) || launch_terminal(c, 3, 1, s) || launch_br(c, s))
     return fail(CFR_ECUDA, "exploitability launch failed");
   k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);

@@ -181,21 +181,21 @@ struct Pairs {  // double-float values
 struct Single {  // plain FP32 values
   using V = float;
   static __device__ __forceinline__ V zero() { return 0.f; }
-  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-  static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
-  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ V vmax(V a, V b) { return fmaxf(a, b); }
   static __device__ __forceinline__ bool positive(V a) { return a > 0.f; }
-  static __device__ __forceinline__ V recip(V a) { return 1.f / a; }
+  static __device__ __forceinline__ V recip(V a) { return __fdiv_rn(1.f, a); }
   static __device__ __forceinline__ V one() { return 1.f; }
-  static __device__ __forceinline__ V uniform(int A) { return 1.f / (float)A; }
+  static __device__ __forceinline__ V uniform(int A) { return __fdiv_rn(1.f, (float)A); }
   static __device__ __forceinline__ V of_double(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ double to_double(V a) { return f2d(a); }
   static __device__ __forceinline__ ff to_ff(V a) { return ff_of(a); }
   static __device__ __forceinline__ V of_ff(ff a) { return ff_round(a); }
   using Acc = float;
   static __device__ __forceinline__ Acc acc0() { return 0.f; }
-  static __device__ __forceinline__ void acc(Acc& a, V x) { a += x; }
+  static __device__ __forceinline__ void acc(Acc& a, V x) { a = __fadd_rn(a, x); }
   static __device__ __forceinline__ void acc_mul(Acc& a, V x, V y) { a = fmaf(x, y, a); }
   static __device__ __forceinline__ V value(Acc a) { return a; }
 };
@@ -730,6 +730,347 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
   }
 }
 
+
+// ------------------------------------------------------------------ stream schedule
+//
+// The throughput form of the update launch (Stages 6, 7 and then 1 of one player), for
+// handles whose hands fill the GPU many times over (batches of subgames).  One warp owns 32
+// consecutive hands of one subgame and walks the subgame's depth-first program alone: no
+// block barriers, every access to an R, S, reach or value row is one coalesced 32-lane
+// segment, and the only per-node state kept is a stack per lane in shared memory.
+//   1. bottom-up over the program in reverse: values of Eq. (backward) from the terminal
+//      values, and at each of the player's decision nodes the regrets and the Stage 7
+//      update of R and S with sigma = RM(R) (Eq. rm) and the player's reach there (stored
+//      by the previous update of this player, or by the initial pass);
+//   2. top-down over the program with the new strategy RM(R'): the player's reach at its
+//      decision nodes (for its next update) and at the terminals (for the opponent's next
+//      terminal launch).
+// Strategies and the values of inner nodes never go to DRAM.  Every address a pass reads
+// is fixed by the program, so each pass is cut into chunks (stream_chunks) that are loaded
+// into a per-lane ring in shared memory with cp.async one chunk ahead of the computation.
+// The arithmetic (regret matching, child order of every sum, the update) is that of k_hand,
+// so both schedules give the same bits.
+
+
+// Regret matching of one node's A rows (Eq. rm), as k_hand computes it: positive parts in
+// the value type, their sum in action order, exactly 1 for a lone positive action.
+template <typename P>
+__device__ __forceinline__ void regret_match(const double (&Rv)[kStreamMaxActions], int A,
+                                             typename P::V (&sg)[kStreamMaxActions]) {
+  using V = typename P::V;
+  V tot = P::zero();
+  int npos = 0, last = 0;
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a) {
+    if (a < A) {
+      const V x = __double_as_longlong(Rv[a]) > 0 ? P::of_double(Rv[a]) : P::zero();
+      sg[a] = x;
+      if (P::positive(x)) ++npos, last = a;
+      tot = P::add(tot, x);
+    }
+  }
+  if (npos == 1) {
+#pragma unroll
+    for (int a = 0; a < kStreamMaxActions; ++a) sg[a] = a == last ? P::one() : P::zero();
+  } else if (npos > 1) {
+    const V inv = P::recip(tot);
+#pragma unroll
+    for (int a = 0; a < kStreamMaxActions; ++a)
+      if (a < A) sg[a] = P::mul(sg[a], inv);
+  } else {
+    const V uni = P::uniform(A);
+#pragma unroll
+    for (int a = 0; a < kStreamMaxActions; ++a) sg[a] = uni;
+  }
+}
+
+__device__ __forceinline__ void load_rows(const double* __restrict__ base, size_t stride, int A,
+                                          double (&out)[kStreamMaxActions]) {
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a) out[a] = a < A ? base[(size_t)a * stride] : 0.0;
+}
+
+// A program node, decoded.
+struct Op {
+  int n, row, type, player, A, deal, first_kid;
+};
+__device__ __forceinline__ Op decode(const ProgOp& o) {
+  return {o.node, o.row, (int)(o.code & 0xffu), (int)((o.code >> 8) & 0xffu), (int)((o.code >> 16) & 0xffu),
+          (int)(o.code >> 24), o.first_kid};
+}
+
+// One lane's view of its subgame for the stream passes.
+template <typename P>
+struct StreamLane {
+  using V = typename P::V;
+  const GameDev& G;
+  const ProgOp* prog;  // the program (shared memory when staged)
+  int p;
+  bool valid;
+  uint64_t hmask;
+  size_t stride;
+  double* R;        // column h of R
+  double* S;
+  V* reach;         // column h of player p's reach plane
+  V* cfv;           // column h of player p's value plane
+  uint64_t* ring;   // this lane's prefetch ring: unit u at ring[u * 32]
+  V* st;            // this lane's stack: slot s at st[s * 32]
+};
+
+// Issue the loads of chunk [k0, k1) of a pass into ring half `half` (one commit group).
+template <typename P, bool BACKWARD>
+__device__ __forceinline__ void stream_issue(const StreamLane<P>& L, int k0, int k1, int half) {
+  using V = typename P::V;
+  const int N = L.G.n_nodes;
+  uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  int u = 0;
+  for (int k = k0; k < k1; ++k) {
+    const Op nd = decode(L.prog[BACKWARD ? N - 1 - k : k]);
+    const int n = nd.n;
+    if (nd.type == kDecision && nd.player == L.p) {
+      const int A = nd.A;
+      const double* r = L.R + (size_t)nd.row * L.stride;
+      for (int a = 0; a < A; ++a) cp_async<8>(ring + (size_t)(u + a) * 32, r + (size_t)a * L.stride);
+      u += A;
+      if (BACKWARD) {
+        const double* s = L.S + (size_t)nd.row * L.stride;
+        for (int a = 0; a < A; ++a) cp_async<8>(ring + (size_t)(u + a) * 32, s + (size_t)a * L.stride);
+        u += A;
+        cp_async<(int)sizeof(V)>(ring + (size_t)u * 32, L.reach + (size_t)n * L.stride);
+        ++u;
+      }
+    } else if (BACKWARD && (nd.type == kFold || nd.type == kShowdown)) {
+      cp_async<(int)sizeof(V)>(ring + (size_t)u * 32, L.cfv + (size_t)n * L.stride);
+      ++u;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename P>
+__device__ __forceinline__ typename P::V ring_value(const uint64_t* slot) {
+  return *reinterpret_cast<const typename P::V*>(slot);
+}
+
+// Bottom-up pass over chunk [k0, k1) (program positions counted from its end).
+template <typename P>
+__device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp,
+                                                      const Discount& d, int variant) {
+  using V = typename P::V;
+  const int N = L.G.n_nodes;
+  const uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  V* st = L.st;
+  int u = 0;
+  for (int k = k0; k < k1; ++k) {
+    const Op nd = decode(L.prog[N - 1 - k]);
+    const int A = nd.A;
+    if (nd.type == kFold || nd.type == kShowdown) {
+      st[sp * 32] = ring_value<P>(ring + (size_t)u * 32);
+      ++u;
+      ++sp;
+      continue;
+    }
+    V val;
+    if (nd.type == kChance) {  // children values carry the card probabilities
+      typename P::Acc acc = P::acc0();
+      for (int a = 0; a < A; ++a) {
+        const V x = st[(sp - 1 - a) * 32];
+        if (!((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull)) P::acc(acc, x);
+      }
+      val = P::value(acc);
+    } else if (nd.player != L.p) {
+      typename P::Acc acc = P::acc0();
+      for (int a = 0; a < A; ++a) P::acc(acc, st[(sp - 1 - a) * 32]);
+      val = P::value(acc);
+    } else {
+      const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
+      const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
+      const V pi = ring_value<P>(ring + (size_t)(u + 2 * A) * 32);
+      u += 2 * A + 1;
+      double Rv[kStreamMaxActions];
+      V sg[kStreamMaxActions];
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+      regret_match<P>(Rv, A, sg);
+      typename P::Acc acc = P::acc0();
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a)
+        if (a < A) P::acc_mul(acc, sg[a], st[(sp - 1 - a) * 32]);
+      val = P::value(acc);
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a) {
+        if (a < A) {
+          const V rr = P::sub(st[(sp - 1 - a) * 32], val);          // instantaneous regret
+          const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
+          double x = Rv[a] + P::to_double(rr);
+          if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+          if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
+          const double sn = fma(Sr[(size_t)a * 32], d.dS, d.wS * contrib);
+          if (L.valid) {
+            L.R[(size_t)(nd.row + a) * L.stride] = x;
+            L.S[(size_t)(nd.row + a) * L.stride] = sn;
+          }
+        }
+      }
+    }
+    sp -= A;
+    st[sp * 32] = val;
+    ++sp;
+  }
+}
+
+// Top-down pass over chunk [k0, k1) with sigma = RM(R): records the reach at the player's
+// decision nodes and at the terminals.
+template <typename P>
+__device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp) {
+  using V = typename P::V;
+  const uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  V* st = L.st;
+  int u = 0;
+  for (int k = k0; k < k1; ++k) {
+    const Op nd = decode(L.prog[k]);
+    const int n = nd.n;
+    --sp;
+    V x = st[sp * 32];
+    if (nd.deal != kNoCard && ((L.hmask >> nd.deal) & 1ull)) x = P::zero();
+    const int A = nd.A;
+    if (nd.type == kFold || nd.type == kShowdown) {
+      if (L.valid) L.reach[(size_t)n * L.stride] = x;
+    } else if (nd.type == kDecision && nd.player == L.p) {
+      if (L.valid) L.reach[(size_t)n * L.stride] = x;
+      const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
+      u += A;
+      double Rv[kStreamMaxActions];
+      V sg[kStreamMaxActions];
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+      regret_match<P>(Rv, A, sg);
+#pragma unroll
+      for (int a = kStreamMaxActions - 1; a >= 0; --a)
+        if (a < A) st[(sp + A - 1 - a) * 32] = P::mul(x, sg[a]);  // child 0 on top
+      sp += A;
+    } else {  // opponent decision or chance: the player's reach passes through
+      for (int a = 0; a < A; ++a) st[(sp + a) * 32] = x;
+      sp += A;
+    }
+  }
+}
+
+// One pass: chunk c + 1 loads while chunk c computes.
+template <typename P, bool BACKWARD, typename F>
+__device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int list, F compute) {
+  const int32_t* ch = L.G.chunks + L.G.chunk_off[list];
+  const int nch = L.G.chunk_count[list];
+  stream_issue<P, BACKWARD>(L, ch[0], ch[1], 0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch)
+      stream_issue<P, BACKWARD>(L, ch[c + 1], ch[c + 2], (c + 1) & 1);
+    else
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    cp_async_wait_group<1>();  // chunk c has landed (each lane reads only its own column)
+    compute(ch[c], ch[c + 1], c & 1);
+  }
+  cp_async_wait_group<0>();
+}
+
+// Grid: one block per (player, work item); a work item is a game and the first of the
+// kStreamWarps consecutive groups of 32 hands its warps own.
+template <typename P>
+__global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
+    const GameDev* __restrict__ games, const Work* __restrict__ work, int n_work, int player_mask, int advance,
+    int* iter, unsigned* done, const Discount* __restrict__ disc_tab, int variant, int depth, int prog_nodes) {
+  using V = typename P::V;
+  extern __shared__ __align__(16) unsigned char sms[];
+  __shared__ Discount disc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int item = blockIdx.x;
+  int p = player_mask == 2 ? 1 : 0;
+  if (player_mask == 3 && item >= n_work) p = 1, item -= n_work;
+  const Work wk = work[item];
+  const GameDev& G = games[wk.game];
+  const int unit = wk.unit + warp;
+  const bool active = unit * 32 < G.n_hands;
+  if (threadIdx.x == 0) disc = disc_tab[*iter];
+  // shared memory: the program, then per warp a prefetch ring (2 halves of kStreamHalf
+  // 8-byte units per lane) and a stack
+  ProgOp* sprog = reinterpret_cast<ProgOp*>(sms);
+  uint64_t* ring = reinterpret_cast<uint64_t*>(sms + (size_t)prog_nodes * sizeof(ProgOp)) +
+                   (size_t)warp * 2 * kStreamHalf * 32 + lane;
+  V* st = reinterpret_cast<V*>(sms + (size_t)prog_nodes * sizeof(ProgOp) +
+                               (size_t)kStreamWarps * 2 * kStreamHalf * 32 * 8) +
+          (size_t)warp * depth * 32 + lane;
+  if (prog_nodes > 0) {  // static: staged while the previous launch finishes
+    const int4* src = reinterpret_cast<const int4*>(G.prog);
+    int4* dst = reinterpret_cast<int4*>(sprog);
+    for (int k = threadIdx.x; k < G.n_nodes; k += blockDim.x) dst[k] = __ldg(src + k);
+  }
+  pdl_wait();  // the terminal values come from the launch just before this one
+  pdl_trigger();
+  __syncthreads();  // disc, program
+  if (active) {
+    const int h = unit * 32 + lane;  // < hstride (a multiple of 32)
+    const bool valid = h < G.n_hands;
+    const size_t stride = (size_t)G.hstride;
+    const size_t plane = (size_t)p * G.n_nodes * stride + h;
+    const StreamLane<P> L{G, prog_nodes > 0 ? sprog : G.prog, p, valid, valid ? G.hand_mask[h] : 0ull, stride,
+                          G.R + h, G.S + h, static_cast<V*>(G.reach) + plane, static_cast<V*>(G.cfv) + plane, ring,
+                          st};
+    const Discount d = disc;
+    int sp = 0;
+    stream_pass<P, true>(L, p, [&](int k0, int k1, int half) {
+      stream_backward_chunk<P>(L, k0, k1, half, sp, d, variant);
+    });
+    if (valid) L.cfv[0] = st[0];  // root value (read-back)
+    __threadfence_block();       // the new R rows are read back by this lane's own copies below
+    st[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
+    sp = 1;
+    stream_pass<P, false>(L, 2 + p, [&](int k0, int k1, int half) { stream_forward_chunk<P>(L, k0, k1, half, sp); });
+  }
+
+  if (advance) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(done, 1u);
+      if (prev == gridDim.x - 1) {  // last block of the launch: every block has read *iter
+        *done = 0u;
+        *iter += 1;
+        __threadfence();
+      }
+    }
+  }
+}
+
+// sigma = RM(R) at every decision node of every game (current strategy, for read-back when
+// the update launches do not store it).
+template <typename P>
+__global__ void k_current_rows(const GameDev* __restrict__ games, int n_games) {
+  using V = typename P::V;
+  for (int g = 0; g < n_games; ++g) {
+    const GameDev& G = games[g];
+    const size_t stride = (size_t)G.hstride;
+    const int total = G.n_nodes * G.n_hands;
+    V* out = static_cast<V*>(G.sigma);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+      const int n = e / G.n_hands, h = e - n * G.n_hands;
+      const NodeDev nd = G.nodes[n];
+      if (nd.type != kDecision || nd.n_kids > kStreamMaxActions) continue;
+      double Rv[kStreamMaxActions];
+      V sg[kStreamMaxActions];
+      load_rows(G.R + (size_t)nd.row * stride + h, stride, nd.n_kids, Rv);
+      regret_match<P>(Rv, nd.n_kids, sg);
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a)
+        if (a < nd.n_kids) out[(size_t)(nd.row + a) * stride + h] = sg[a];
+    }
+  }
+}
+
 // Average strategy S / sum S of every decision node of every game (for read-back).
 template <typename P>
 __global__ void k_average_rows(const GameDev* __restrict__ games, int n_games) {
@@ -795,6 +1136,8 @@ static cudaError_t configure_precision() {
   if (e == cudaSuccess) e = configure_hand<P, false>();
   if (e == cudaSuccess) e = configure_one(k_terminal<P>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_average_rows<P>, 0);
+  if (e == cudaSuccess) e = configure_one(k_stream_update<P>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_current_rows<P>, 0);
   return e;
 }
 
@@ -851,8 +1194,34 @@ static int launch_hand(const LaunchCtx& c, int player_mask, int advance, void* s
 }
 
 int launch_init(const LaunchCtx& c, void* stream) { return launch_hand<kModeInit>(c, 3, 0, stream, false); }
+template <typename P>
+static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
+  const int players = player_mask == 3 ? 2 : 1;
+  const int grid = c.n_warp_work * players;
+  const size_t smem = stream_smem_size(c.stream_prog, c.stream_depth, sizeof(typename P::V));
+  const cudaError_t e = launch_kernel(k_stream_update<P>, grid, kStreamWarps * 32, smem, stream, c.pdl != 0,
+                                      c.games, c.warp_work, c.n_warp_work, player_mask, advance, c.iter, c.done,
+                                      c.disc, c.variant, c.stream_depth, c.stream_prog);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of k_stream_update failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
+  return check_launch("k_stream_update");
+}
+
 int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream) {
+  if (c.schedule == kScheduleStream)
+    return c.precision == kPrecisionSingle ? launch_stream_p<Single>(c, player_mask, advance, stream)
+                                           : launch_stream_p<Pairs>(c, player_mask, advance, stream);
   return launch_hand<kModeUpdate>(c, player_mask, advance, stream, c.pdl != 0);
+}
+
+int launch_current_rows(const LaunchCtx& c, void* stream) {
+  if (c.precision == kPrecisionSingle)
+    k_current_rows<Single><<<152, 256, 0, (cudaStream_t)stream>>>(c.games, c.n_games);
+  else
+    k_current_rows<Pairs><<<152, 256, 0, (cudaStream_t)stream>>>(c.games, c.n_games);
+  return check_launch("k_current_rows");
 }
 int launch_avg_reach(const LaunchCtx& c, void* stream) { return launch_hand<kModeAvg>(c, 3, 0, stream, false); }
 int launch_br(const LaunchCtx& c, void* stream) { return launch_hand<kModeBR>(c, 3, 0, stream, c.pdl != 0); }

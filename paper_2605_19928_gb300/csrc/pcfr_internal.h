@@ -40,6 +40,11 @@ constexpr uint8_t kNoCard = 255;
 constexpr int kPrecisionPairs = 0;   // values as double-float FP32 pairs
 constexpr int kPrecisionSingle = 1;  // values as FP32
 constexpr int kDiscountCapacity = 1 << 16;  // iterations covered by one discount table
+constexpr int kScheduleLevel = 1;   // per-hand passes: one block per chunk of hands, level by level
+constexpr int kScheduleStream = 2;  // update pass: one warp per 32 hands walks a depth-first program
+constexpr int kStreamMaxActions = 8;  // actions at a decision node the stream schedule holds in registers
+constexpr int kStreamHalf = 20;       // 8-byte units per lane in each half of a warp's prefetch ring
+constexpr int kStreamWarps = 4;       // warps per block of the stream schedule (one game per block)
 
 struct alignas(16) NodeDev {
   int32_t parent;     // -1 at the root
@@ -57,6 +62,15 @@ struct alignas(16) NodeDev {
   uint64_t board;     // public cards at this node (bit c = card c)
 };
 static_assert(sizeof(NodeDev) == 32, "NodeDev is 32 bytes");
+
+// One node of the stream schedule's program (pre-order), 16 bytes.
+struct alignas(16) ProgOp {
+  int32_t node;
+  int32_t row;        // decision: first row; showdown: board table; otherwise -1
+  uint32_t code;      // type | player << 8 | n_kids << 16 | deal << 24
+  int32_t first_kid;
+};
+static_assert(sizeof(ProgOp) == 16, "ProgOp is 16 bytes");
 
 // Offsets (in uint16) of the terminal-table sections for H hands of k cards from a deck.
 struct TermTab {
@@ -97,6 +111,9 @@ struct GameDev {
   const void* range_v;         // [2][hstride] normalised ranges, value type V
   const double* range64;       // [2][hstride]
   const uint16_t* term_tab;    // [n_boards][TermTab.len]
+  const ProgOp* prog;          // [n_nodes] the tree in depth-first pre-order (stream schedule)
+  const int32_t* chunks;       // load chunks of the stream schedule (see stream_chunks)
+  int chunk_off[4], chunk_count[4];
   // state
   double* R;
   double* S;
@@ -140,11 +157,19 @@ struct LaunchCtx {
   int variant;
   int precision;               // kPrecisionPairs or kPrecisionSingle
   int pdl;                     // chain launches with programmatic dependent launch
+  int schedule;                // kScheduleLevel or kScheduleStream (update launches)
+  const Work* warp_work;       // device [n_warp_work]: (game, first group of 32 hands) of each
+                               // block of the stream schedule, largest trees first
+  int n_warp_work;
+  int stream_depth;            // stack slots per lane of the stream schedule
+  int stream_prog;             // nodes of the largest tree, if its program is staged in shared
+                               // memory; 0 = read from global memory
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
 int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stream);
-int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream);
+int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream);  // either schedule
+int launch_current_rows(const LaunchCtx& c, void* stream);  // sigma = RM(R), every game (read-back)
 int launch_avg_reach(const LaunchCtx& c, void* stream);
 int launch_br(const LaunchCtx& c, void* stream);
 int launch_average_rows(const LaunchCtx& c, void* stream);
@@ -152,5 +177,10 @@ int hand_kernel_smem_limit();
 // Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
+// Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes),
+// a prefetch ring and a stack of `depth` slots (es bytes each) per lane.
+inline size_t stream_smem_size(int prog_nodes, int depth, size_t es) {
+  return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)kStreamWarps * 32 * (2 * kStreamHalf * 8 + (size_t)depth * es);
+}
 
 }  // namespace pcfr

@@ -492,4 +492,74 @@ std::vector<int32_t> row_nodes(const HostGame& g) {
   return out;
 }
 
+std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions) {
+  std::vector<int32_t> pre;
+  pre.reserve(g.nodes.size());
+  std::vector<int32_t> todo{0};
+  while (!todo.empty()) {
+    const int n = todo.back();
+    todo.pop_back();
+    pre.push_back(n);
+    const NodeDev& nd = g.nodes[(size_t)n];
+    for (int a = nd.n_kids - 1; a >= 0; --a) todo.push_back(nd.first_kid + a);  // child 0 first
+  }
+  int sp = 1, most = 1, amax = 0;
+  for (int n : pre) {  // top-down: pop the node's reach, push its children's
+    sp += g.nodes[(size_t)n].n_kids - 1;
+    most = std::max(most, sp);
+    if (g.nodes[(size_t)n].type == kDecision) amax = std::max(amax, (int)g.nodes[(size_t)n].n_kids);
+  }
+  sp = 0;
+  for (size_t k = pre.size(); k-- > 0;) {  // bottom-up: pop the children's values, push the node's
+    sp += 1 - g.nodes[(size_t)pre[k]].n_kids;
+    most = std::max(most, sp + g.nodes[(size_t)pre[k]].n_kids - 1);
+    most = std::max(most, sp);
+  }
+  *depth = most;
+  *max_actions = amax;
+  return pre;
+}
+
+std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& pre) {
+  std::vector<ProgOp> out;
+  out.reserve(pre.size());
+  for (int n : pre) {
+    const NodeDev& nd = g.nodes[(size_t)n];
+    ProgOp op;
+    op.node = n;
+    op.row = nd.row;
+    op.code = (uint32_t)nd.type | (uint32_t)nd.player << 8 | (uint32_t)nd.n_kids << 16 | (uint32_t)nd.deal << 24;
+    op.first_kid = nd.first_kid;
+    out.push_back(op);
+  }
+  return out;
+}
+
+std::vector<int32_t> stream_chunks(const HostGame& g, const std::vector<int32_t>& pre, int half, int off[4],
+                                   int count[4]) {
+  std::vector<int32_t> out;
+  const int N = (int)pre.size();
+  for (int q = 0; q < 4; ++q) {
+    const int p = q & 1;
+    const bool backward = q < 2;
+    off[q] = (int)out.size();
+    out.push_back(0);
+    int used = 0;
+    for (int k = 0; k < N; ++k) {
+      const NodeDev& nd = g.nodes[(size_t)pre[(size_t)(backward ? N - 1 - k : k)]];
+      int units = 0;
+      if (nd.type == kDecision && nd.player == p) units = backward ? 2 * nd.n_kids + 1 : nd.n_kids;
+      if (backward && (nd.type == kFold || nd.type == kShowdown)) units = 1;
+      if (used + units > half) {
+        out.push_back(k);
+        used = 0;
+      }
+      used += units;
+    }
+    count[q] = (int)out.size() - off[q];
+    out.push_back(N);
+  }
+  return out;
+}
+
 }  // namespace pcfr

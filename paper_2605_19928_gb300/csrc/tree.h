@@ -42,4 +42,26 @@ std::vector<int32_t> decision_nodes(const HostGame& g, int begin[3]);
 // Decision node owning each regret row.
 std::vector<int32_t> row_nodes(const HostGame& g);
 
+// Program of the one-warp-per-32-hands schedule: the nodes in depth-first pre-order
+// (children in their natural order).  Walked forwards it is a top-down order in which a
+// stack of reach values pops each node's reach and pushes its children's (child 0 on top);
+// walked backwards it is a bottom-up order in which a stack of values pushes each node's
+// value and pops its children's in the order 0, 1, ...  `depth` receives the deepest either
+// stack gets, `max_actions` the most actions at any decision node.
+std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions);
+
+// The program as the stream kernel reads it: one ProgOp per node in pre-order.
+std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& pre);
+
+// Load chunks of the stream schedule: the program cut into runs of consecutive nodes whose
+// rows fit half of a warp's prefetch ring (`half` 8-byte units per lane), so that one run
+// can load while the previous one computes.  Four lists, one after the other in the result:
+// the bottom-up pass of player 0 and of player 1 (units per node: 2A + 1 at the player's
+// decision nodes for R, S and the reach; 1 at terminals for the value) and the top-down pass
+// of player 0 and of player 1 (A at the player's decision nodes for R).  List q holds the
+// program positions where its chunks start, then the program length; off[q] is where it
+// begins in the result and count[q] its number of chunks.
+std::vector<int32_t> stream_chunks(const HostGame& g, const std::vector<int32_t>& pre, int half, int off[4],
+                                   int count[4]);
+
 }  // namespace pcfr

@@ -128,15 +128,22 @@ def random_ranges(n_hands: int, seed: int) -> np.ndarray:
 
 
 def batch_rivers(n: int = 256, seed: int = 0, n_hands: int | None = None) -> list[GameSpec]:
-    """Uneven river subgames: seeded boards, 1-4 bet sizes, stacks 100-1000 behind a pot of 100."""
+    """Uneven river subgames for batched serving: seeded boards, strengths and ranges (seeds
+    1000 + k and 5000 + k), 1-4 pot-fraction bet sizes (at least one below 1 pot) plus
+    all-in, stacks 100-1000 behind a pot of 100, and 2-3 bets/raises (2 when four sizes meet
+    a stack above 400), which gives 27 to 357 public nodes per tree."""
     rng = np.random.default_rng(10_000 + seed)
     menu = np.array([0.33, 0.5, 0.75, 1.0, 1.5, 2.0])
     out = []
     for k in range(n):
         n_sizes = int(rng.integers(1, 5))
-        sizes = tuple(sorted(float(x) for x in rng.choice(menu, size=n_sizes - 1, replace=False))) + (ALL_IN,)
+        small = float(rng.choice(menu[:3]))  # one size below 1 pot stays distinct from all-in
+        rest = rng.choice(menu[menu != small], size=n_sizes - 1, replace=False)
+        sizes = tuple(sorted([small] + [float(x) for x in rest])) + (ALL_IN,)
         stack = float(rng.integers(100, 1001))
-        max_raises = int(rng.integers(2, 5))
+        max_raises = int(rng.integers(2, 4))
+        if n_sizes == 4 and stack > 400:
+            max_raises = 2
         g = river_subgame(n_hands=n_hands, seed=1000 + k, range_seed=5000 + k, pot=100.0, stack=stack,
                           bet_sizes=sizes, max_raises=max_raises)
         g.name = f"river_batch_{k}"

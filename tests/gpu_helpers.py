@@ -94,7 +94,7 @@ def compare_state(tree, oracle, mapping, game=0, check_cfv=True, check_strategy=
             if check_strategy:
                 sig = capi.cfr_strategy(tree, g, average=False, game=game)
                 worst["sigma"] = max(worst["sigma"], compare_strategies(sig, R_o, what=f"sigma node {g}"))
-        if check_cfv:
+        if check_cfv and stored_cfv(tree, g, info):
             for i in (0, 1):
                 v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=i, game=game)
                 v_o = oracle.cfv(i, o)
@@ -110,6 +110,14 @@ def inject(tree, oracle, mapping, game=0, player=None):
                                   capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, g, game=game))
 
 
+def stored_cfv(tree, g, info):
+    """Whether the handle keeps node g's counterfactual values: the level schedule stores
+    every node's, the stream schedule the terminals' and the root's."""
+    if capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL:
+        return True
+    return g == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN)
+
+
 def compare_player(tree, oracle, mapping, player, game=0, pot=None):
     """R and S of one player's decision nodes and that player's counterfactual values."""
     pot = oracle.spec.pot if pot is None else pot
@@ -121,6 +129,8 @@ def compare_player(tree, oracle, mapping, player, game=0, pot=None):
             S_g = capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, g, game=game)
             worst["R"] = max(worst["R"], close(R_g, oracle.regrets(o), floor=floor, what=f"R node {g}"))
             worst["S"] = max(worst["S"], close(S_g, oracle.avg_sums(o), what=f"S node {g}"))
+        if not stored_cfv(tree, g, info):
+            continue
         v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=player, game=game)
         worst["cfv"] = max(worst["cfv"], close(v_g, oracle.cfv(player, o), floor=floor,
                                                what=f"cfv player {player} node {g}"))

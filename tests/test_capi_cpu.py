@@ -82,3 +82,5 @@ def test_bad_options_are_rejected_before_any_device_call(lib):
     assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL
     bad = capi.make_opts(precision=5)
     assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL
+    bad = capi.make_opts(schedule=5)
+    assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL

@@ -75,9 +75,10 @@ def check_exploitability(tree, orc, mapping, pot, game=0, n_games=1):
             assert float(np.max(np.abs(got - want))) <= 1e-5 * scale + 1e-8 * pot, (i, g)
 
 
-def run_pair(spec, variant, iters=10, alternating=True, chunk=0, forced=True, check_every=1):
+def run_pair(spec, variant, iters=10, alternating=True, chunk=0, forced=True, check_every=1, schedule="auto"):
     from oracle.oracle import Oracle
-    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, alternating=alternating, chunk_hands=chunk))
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, alternating=alternating, chunk_hands=chunk,
+                                                     schedule=schedule))
     try:
         orc = Oracle(spec, variant=variant, alternating=alternating)
         mapping = node_map(tree, orc)
@@ -231,3 +232,89 @@ def test_invalid_specs_are_rejected():
     spec.ranges[0, 3] = np.nan
     with pytest.raises(capi.CfrError):
         capi.cfr_tree_create(spec)
+
+
+# ---------------------------------------------------------------- stream schedule
+# The one-warp-per-32-hands update (chosen automatically for large batches) must agree with
+# the oracle exactly like the level schedule, and with the level schedule bit for bit.
+
+STREAM_CASES = [("kuhn", "cfr"), ("leduc", "cfr+"), ("river_203", "dcfr"), ("turn_40", "dcfr"),
+                ("river_64_r4", "dcfr")]
+
+
+@pytest.mark.parametrize("case,variant", STREAM_CASES)
+def test_stream_schedule_matches_oracle_from_the_same_state(case, variant):
+    worst = run_pair(CASES[case][0](), variant, forced=True, schedule="stream")
+    print(case, variant, "stream forced", worst)
+
+
+def test_stream_schedule_first_ten_iterations_match_oracle():
+    run_pair(river(203), "dcfr", forced=False, schedule="stream")
+
+
+def test_stream_schedule_simultaneous_updates_match_oracle():
+    run_pair(river(97, seed=21), "dcfr", iters=5, alternating=False, schedule="stream")
+
+
+def _state(tree, n_games):
+    out = []
+    for game in range(n_games):
+        n_nodes = capi.cfr_tree_info(tree, game)[0]
+        for n in range(n_nodes):
+            info = capi.cfr_node_info(tree, n, game)
+            if info["type"] == capi.CFR_NODE_DECISION:
+                out.append(capi.cfr_read_values(tree, capi.CFR_READ_REGRET, n, game=game))
+                out.append(capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, n, game=game))
+                out.append(capi.cfr_strategy(tree, n, average=False, game=game))
+                out.append(capi.cfr_strategy(tree, n, average=True, game=game))
+            if n == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN):
+                for i in (0, 1):
+                    out.append(capi.cfr_read_values(tree, capi.CFR_READ_CFV, n, player=i, game=game))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["pairs", "single"])
+@pytest.mark.parametrize("variant,alternating", [("dcfr", True), ("cfr+", True), ("cfr", False)])
+def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alternating):
+    specs = [river(203, seed=51), river(64, seed=52, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
+             leduc_random(seed=53), turn(40, seed=54), kuhn_random(seed=55)]
+    states, expl = [], []
+    for schedule in ("level", "stream"):
+        tree = capi.cfr_batch_create(specs, capi.make_opts(variant, alternating=alternating, precision=precision,
+                                                           schedule=schedule))
+        try:
+            assert capi.cfr_schedule(tree) == capi.SCHEDULES[schedule]
+            capi.cfr_iterate(tree, 7)
+            states.append(_state(tree, len(specs)))
+            expl.append(capi.cfr_exploitability(tree, len(specs)))
+        finally:
+            capi.cfr_tree_destroy(tree)
+    assert len(states[0]) == len(states[1])
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
+    assert np.array_equal(expl[0][0], expl[1][0]) and np.array_equal(expl[0][1], expl[1][1])
+
+
+def test_schedule_selection():
+    tree = capi.cfr_tree_create(river(203))
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL  # one subgame: latency form
+    finally:
+        capi.cfr_tree_destroy(tree)
+    # 36 full rivers = 36 * 34 warps of 32 hands >= 8 per SM: throughput form
+    specs = [synth.river_subgame(seed=60 + k, range_seed=61 + k, max_raises=1) for k in range(36)]
+    tree = capi.cfr_batch_create(specs)
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_STREAM
+    finally:
+        capi.cfr_tree_destroy(tree)
+    # more than 8 actions at a node: the stream form is refused, auto falls back to level
+    wide = river(40, seed=62, bet_sizes=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0, synth.ALL_IN), max_raises=2)
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_tree_create(wide, capi.make_opts(schedule="stream"))
+    assert e.value.code == capi.CFR_EINVAL
+    tree = capi.cfr_tree_create(wide, capi.make_opts(schedule="auto"))
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL
+    finally:
+        capi.cfr_tree_destroy(tree)
