@@ -45,6 +45,7 @@ struct cfr_tree {
   GameDev* d_games = nullptr;
   Work* d_chunk_work = nullptr;
   Work* d_term_work = nullptr;
+  Work* d_term_runs = nullptr;
   Work* d_warp_work = nullptr;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
@@ -226,7 +227,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     use_smem[g] = all_fit;
     if (all_fit) smem_hand = std::max(smem_hand, hand_smem(h, chunk[g], es));
     const TermTab tt(h.n_hands, h.hand_size, h.deck);
-    smem_term = std::max(smem_term, (size_t)tt.len * 2 + (size_t)h.hstride * es +
+    smem_term = std::max(smem_term, (size_t)tt.len * 2 + 2 * (size_t)h.hstride * es +
                                         (size_t)(h.hand_size * h.n_hands + 1 + h.n_hands + 1) * 8);
   }
 
@@ -246,7 +247,12 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   int max_nodes = 0;
   for (int g = 0; g < n_games; ++g) max_nodes = std::max(max_nodes, (int)t->host[g].nodes.size());
   const int stream_prog = max_nodes * (int)sizeof(ProgOp) <= 64 * 1024 ? max_nodes : 0;
-  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_depth, es) <= 200 * 1024;
+  int amax_all = 0;
+  for (int g = 0; g < n_games; ++g)
+    for (const NodeDev& nd : t->host[g].nodes)
+      if (nd.type == kDecision) amax_all = std::max(amax_all, (int)nd.n_kids);
+  const int stream_half = std::max(kStreamHalfMin, 2 * amax_all + 1);
+  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_half, stream_depth, es) <= 200 * 1024;
   int schedule = kScheduleLevel;
   if (o.schedule == CFR_SCHEDULE_STREAM) {
     if (!stream_ok) {
@@ -291,7 +297,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     int32_t *ls, *rn, *dn, *chk;
     ProgOp* prog;
     const std::vector<ProgOp> ops = program_ops(h, programs[g]);
-    const std::vector<int32_t> chunks = stream_chunks(h, programs[g], kStreamHalf, d.chunk_off, d.chunk_count);
+    const std::vector<int32_t> chunks = stream_chunks(h, programs[g], stream_half, d.chunk_off, d.chunk_count);
     uint16_t* tb;
     uint64_t* hm;
     float* rrv;
@@ -319,7 +325,32 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     d.sigma = sig; d.sigbar = sigb; d.reach = rch; d.reach_bar = rchb; d.cfv = cf; d.cfv_br = cfb;
     for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
 
-    for (int n : h.terminals) term_work.push_back({g, n});
+    // terminals grouped by board table (fold nodes read only the board-free part of table 0)
+    std::vector<int> term = h.terminals;
+    auto table = [&](int n) { return h.nodes[(size_t)n].type == kShowdown ? h.nodes[(size_t)n].row : 0; };
+    std::stable_sort(term.begin(), term.end(), [&](int a, int b2) { return table(a) < table(b2); });
+    for (int n : term) term_work.push_back({g, n});
+  }
+  // terminal runs: one node per block while the nodes do not fill the GPU many times over,
+  // up to four per block (same game and board table) when they do
+  std::vector<Work> term_runs;
+  {
+    const int per = std::max(1, std::min(4, (int)term_work.size() / (152 * 8)));
+    size_t a = 0;
+    while (a < term_work.size()) {
+      const Work w = term_work[a];
+      const NodeDev& nd = t->host[w.game].nodes[(size_t)w.unit];
+      const int tb = nd.type == kShowdown ? nd.row : 0;
+      int cnt = 1;
+      while (cnt < per && a + cnt < term_work.size()) {
+        const Work w2 = term_work[a + cnt];
+        const NodeDev& n2 = t->host[w2.game].nodes[(size_t)w2.unit];
+        if (w2.game != w.game || (n2.type == kShowdown ? n2.row : 0) != tb) break;
+        ++cnt;
+      }
+      term_runs.push_back({(int)a, cnt});
+      a += cnt;
+    }
   }
   // stream schedule: blocks of kStreamWarps warps of one game, largest trees first so that
   // their long walks start at once and the small trees fill in behind them
@@ -331,6 +362,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     for (int u = 0; u < (t->host[g].n_hands + 31) / 32; u += kStreamWarps) warp_work.push_back({g, u});
   if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
       (rc = upload(t, term_work, &t->d_term_work)) || (rc = upload(t, warp_work, &t->d_warp_work)) ||
+      (rc = upload(t, term_runs, &t->d_term_runs)) ||
       (rc = zeros(t, 1, &t->d_iter)) ||
       (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) ||
       (rc = upload(t, discount_table(o, kDiscountCapacity), &t->d_disc))) {
@@ -344,6 +376,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.n_chunk_work = (int)chunk_work.size();
   c.term_work = t->d_term_work;
   c.n_term_work = (int)term_work.size();
+  c.term_runs = t->d_term_runs;
+  c.n_term_runs = (int)term_runs.size();
   c.iter = t->d_iter;
   c.done = t->d_done;
   c.err = t->d_err;
@@ -359,6 +393,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.n_warp_work = (int)warp_work.size();
   c.stream_depth = stream_depth;
   c.stream_prog = stream_prog;
+  c.stream_half = stream_half;
   t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
   t->launches += 1;
   if (launch_init(c, stream) != 0) {

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 
 #include "pcfr_internal.h"
 
@@ -249,6 +250,46 @@ __device__ __forceinline__ ff group_exclusive_scan(int n, F value_at, ff* out, a
   return total;
 }
 
+// The same exclusive prefix sum in plain FP32 (values of the single-precision path; the
+// error of a prefix stays within a few dozen ulps of the total).
+template <int GT, typename F>
+__device__ __forceinline__ float group_exclusive_scan_f32(int n, F value_at, float* out, float* red, int gtid) {
+  const int per = (n + GT - 1) / GT;
+  const int lane = gtid & 31, warp = gtid >> 5;
+  const int begin = min(gtid * per, n), end = min(begin + per, n);
+  float local = 0.f;
+  for (int j = begin; j < end; ++j) local = __fadd_rn(local, value_at(j));
+  float x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = __fadd_rn(x, y);
+  }
+  float run = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) run = 0.f;
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    float wv = lane < GT / 32 ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, wv, o);
+      if (lane >= o) wv = __fadd_rn(wv, y);
+    }
+    if (lane < GT / 32) red[lane] = wv;
+  }
+  __syncthreads();
+  if (warp > 0) run = __fadd_rn(run, red[warp - 1]);
+  for (int j = begin; j < end; ++j) {
+    out[j] = run;
+    run = __fadd_rn(run, value_at(j));
+  }
+  const float total = red[GT / 32 - 1];
+  if (gtid == 0) out[n] = total;
+  __syncthreads();
+  return total;
+}
+
 // ------------------------------------------------------------------ bulk copies (TMA) into shared memory
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -310,84 +351,82 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 
 // ------------------------------------------------------------------ terminal values (Stages 2-4)
 
-// One block per (player, terminal node).  q is the opponent's reach at the node, kappa = 1/Z,
-// and the node's payoff already carries the probability of the public cards dealt on its
-// path, so every value is a counterfactual value in the sense of Eq. (cfv).
+// Values of player i at one fold or showdown node n (Stages 2-4), the opponent's reach q
+// at n already in shared memory.  kappa = 1/Z, and the node's payoff already carries the
+// probability of the public cards dealt on its path, so every value is a counterfactual
+// value in the sense of Eq. (cfv).
 //   fold (Stage 3):   v_i(h) = u_i kappa (T - C[c1] - C[c2] + q[h]),  T = sum_o q[o],
 //                     C[c] = sum_{o holds c} q[o]  (inclusion-exclusion over the two cards)
 //   showdown (Stage 4): v_i(h) = c kappa (W(h) - L(h)), W / L the opponent reach of weaker /
 //                     stronger hands that share no card with h, from exclusive prefix sums
 //                     over the rank-sorted order minus per-card prefix sums; the tie group
 //                     of h is excluded from both (a split pot pays 0).
-// The board's index tables and the reach row arrive in shared memory by two bulk (TMA)
-// copies; sums and differences are taken in double-float in both precisions.
+// Sums and differences are double-float with FP32-pair values, plain FP32 with FP32
+// values.  Every thread of the block calls it (it holds block barriers).
 template <typename P>
-__global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __restrict__ games,
-                                                            const Work* __restrict__ work, int n_work,
-                                                            int player_mask, int use_bar, int* err) {
+__device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev& nd, int i, double u64,
+                                                const TermTab& tt, const uint16_t* tab,
+                                                const typename P::V* __restrict__ qs, ff* CP, ff* Psc,
+                                                typename P::V* __restrict__ out) {
   using V = typename P::V;
-  int item = blockIdx.x;
-  int i;
-  if (player_mask == 3) {
-    i = item >= n_work;
-    item -= i * n_work;
-  } else {
-    i = player_mask == 1 ? 0 : 1;
-  }
-  const Work wk = work[item];
-  const GameDev& G = games[wk.game];
-  const int n = wk.unit;
-  const NodeDev nd = G.nodes[n];
-  const int H = G.n_hands, k = G.hand_size;
-  const size_t stride = (size_t)G.hstride;
-  const TermTab tt(H, k, G.deck);
-  const bool show = nd.type == kShowdown;
-  const int b = show ? nd.row : 0;
-  const unsigned tab_bytes = (unsigned)(show ? tt.len : tt.fold_len) * 2u;
-  const unsigned q_bytes = (unsigned)(stride * sizeof(V));
-  const V* __restrict__ q =
-      static_cast<const V*>(use_bar ? G.reach_bar : G.reach) + ((size_t)(1 - i) * G.n_nodes + n) * stride;
-  V* __restrict__ out = static_cast<V*>(use_bar ? G.cfv_br : G.cfv) + ((size_t)i * G.n_nodes + n) * stride;
-
-  extern __shared__ __align__(128) unsigned char smt[];
-  __shared__ __align__(8) uint64_t bar;
   __shared__ acc2 red[2][kTermThreads / 64];
-  uint16_t* tab = reinterpret_cast<uint16_t*>(smt);                             // [tt.len]
-  V* qs = reinterpret_cast<V*>(smt + (size_t)tt.len * 2);                        // [hstride]
-  ff* CP = reinterpret_cast<ff*>(smt + (size_t)tt.len * 2 + q_bytes);            // [k H + 1]
-  ff* Psc = CP + (k * H + 1);                                                    // [H + 1]
-
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {  // the board tables are static: copy them before waiting
-    mbar_arrive_expect_tx(&bar, tab_bytes + q_bytes);
-    bulk_copy_g2s(tab, G.term_tab + (size_t)b * tt.len, tab_bytes, &bar);
-  }
-  // payoff for player i per unit of (opponent reach) x kappa, in FP64 while the copies land
-  const double pay = G.payoff[n];
-  const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
-  const ff u = d2ff(u64);
-  pdl_wait();  // the reach row comes from the launch just before this one
-  pdl_trigger();
-  if (threadIdx.x == 0) bulk_copy_g2s(qs, q, q_bytes, &bar);
+  const int H = G.n_hands, k = G.hand_size;
+  const bool show = nd.type == kShowdown;
   const uint64_t board = nd.board;
-  const bool ok = mbar_wait_bounded(&bar, 0);
-  if (__syncthreads_or(!ok)) {  // the copies did not land: report, let them drain, leave
-    if (threadIdx.x == 0) {
-      atomicExch(err, 1);
-      mbar_wait_bounded(&bar, 0);
-    }
-    __syncthreads();
-    return;
-  }
-
+  const ff u = d2ff(u64);
   const uint16_t* clh = tab + tt.clh;
   const uint16_t* cards = tab + tt.cards;
   const uint16_t* cloff = tab + tt.cloff;
   const uint16_t* perm = tab + tt.perm;
+  if constexpr (std::is_same<P, Single>::value) {
+    // FP32 values: the same scans and differences in plain FP32 (a value's error stays
+    // within about 1e-6 of the largest value at the node)
+    __shared__ float redf[2][kTermThreads / 64];
+    float* CPf = reinterpret_cast<float*>(CP);  // [k H + 1]
+    float* Pf = CPf + (k * H + 1);             // [H + 1]
+    constexpr int half = kTermThreads / 2;
+    const bool first = threadIdx.x < half;
+    const int gtid = first ? threadIdx.x : threadIdx.x - half;
+    if (first)
+      group_exclusive_scan_f32<half>(H, [&](int j) { return qs[show ? perm[j] : j]; }, Pf, redf[0], gtid);
+    else
+      group_exclusive_scan_f32<half>(k * H, [&](int j) { return qs[clh[j]]; }, CPf, redf[1], gtid);
+    const float T = Pf[H];
+    const float uf = __double2float_rn(u64);
+    if (!show) {
+      for (int h = threadIdx.x; h < H; h += kTermThreads) {
+        const unsigned cw = cards[h];
+        const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
+        float m = __fsub_rn(T, __fsub_rn(CPf[cloff[c1 + 1]], CPf[cloff[c1]]));
+        bool blocked = (board >> c1) & 1ull;
+        if (k == 2) {
+          m = __fsub_rn(m, __fsub_rn(CPf[cloff[c2 + 1]], CPf[cloff[c2]]));
+          m = __fadd_rn(m, qs[h]);
+          blocked = blocked || ((board >> c2) & 1ull);
+        }
+        out[h] = blocked ? 0.f : __fmul_rn(uf, m);
+      }
+    } else {
+      const uint16_t* gs = tab + tt.gs;
+      const uint16_t* ge = tab + tt.ge;
+      const uint16_t* lo = tab + tt.lo;
+      const uint16_t* hi = tab + tt.hi;
+      for (int h = threadIdx.x; h < H; h += kTermThreads) {
+        const unsigned cw = cards[h];
+        float Wn = Pf[gs[h]];
+        float Ln = __fsub_rn(T, Pf[ge[h]]);
+        bool blocked = false;
+        for (int s = 0; s < k; ++s) {
+          const unsigned c = s == 0 ? (cw & 0xffu) : (cw >> 8);
+          Wn = __fsub_rn(Wn, __fsub_rn(CPf[lo[2 * h + s]], CPf[cloff[c]]));
+          Ln = __fsub_rn(Ln, __fsub_rn(CPf[cloff[c + 1]], CPf[hi[2 * h + s]]));
+          blocked = blocked || ((board >> c) & 1ull);
+        }
+        out[h] = blocked ? 0.f : __fmul_rn(uf, __fsub_rn(Wn, Ln));
+      }
+    }
+    return;
+  }
   // Two scans at once, one per half of the block: the first half takes the reach in
   // rank-sorted order (showdown) or in hand order (fold, for the total T), the second half
   // the reach along the per-card hand lists.
@@ -433,6 +472,97 @@ __global__ void __launch_bounds__(kTermThreads) k_terminal(const GameDev* __rest
         blocked = blocked || ((board >> c) & 1ull);
       }
       out[h] = blocked ? P::zero() : P::of_ff(ff_mul(u, ff_sub(Wn, Ln)));
+    }
+  }
+}
+
+// Terminal values (Stages 2-4).  One block per (player, run): a run is up to four fold or
+// showdown nodes of one game that read the same board table, which is staged once by a
+// bulk (TMA) copy; the opponent reach rows of the run's nodes arrive by bulk copies into
+// two alternating buffers, each node's row landing while the node before it computes.
+// Every wait is bounded: on a timeout the block sets *err, lets its copies drain and leaves.
+// RUNS = false is the one-node form (latency: all registers it wants); RUNS = true fits four
+// blocks per SM for handles whose terminal nodes fill the GPU many times over.
+template <typename P, bool RUNS>
+__global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const GameDev* __restrict__ games,
+                                                            const Work* __restrict__ work,
+                                                            const Work* __restrict__ runs, int n_runs,
+                                                            int player_mask, int use_bar, int* err) {
+  using V = typename P::V;
+  int item = blockIdx.x;
+  int i;
+  if (player_mask == 3) {
+    i = item >= n_runs;
+    item -= i * n_runs;
+  } else {
+    i = player_mask == 1 ? 0 : 1;
+  }
+  const Work run = runs[item];  // (first entry of `work`, count)
+  const int first = run.game, count = RUNS ? run.unit : 1;
+  const GameDev& G = games[work[first].game];
+  const int H = G.n_hands, k = G.hand_size;
+  const size_t stride = (size_t)G.hstride;
+  const TermTab tt(H, k, G.deck);
+  bool show_any = false;
+  int b = 0;
+  for (int j = 0; j < count; ++j) {
+    const NodeDev nd = G.nodes[work[first + j].unit];
+    if (nd.type == kShowdown) show_any = true, b = nd.row;
+  }
+  const unsigned tab_bytes = (unsigned)(show_any ? tt.len : tt.fold_len) * 2u;
+  const unsigned q_bytes = (unsigned)(stride * sizeof(V));
+  const V* qsrc = static_cast<const V*>(use_bar ? G.reach_bar : G.reach) + (size_t)(1 - i) * G.n_nodes * stride;
+  V* dst = static_cast<V*>(use_bar ? G.cfv_br : G.cfv) + (size_t)i * G.n_nodes * stride;
+
+  extern __shared__ __align__(128) unsigned char smt[];
+  __shared__ __align__(8) uint64_t bar[2];
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smt);                                // [tt.len]
+  V* qbuf = reinterpret_cast<V*>(smt + (size_t)tt.len * 2);                         // [2][hstride]
+  ff* CP = reinterpret_cast<ff*>(smt + (size_t)tt.len * 2 + 2 * (size_t)q_bytes);   // [k H + 1]
+  ff* Psc = CP + (k * H + 1);                                                       // [H + 1]
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the board tables are static: copy them before waiting
+    mbar_arrive_expect_tx(&bar[0], tab_bytes + q_bytes);
+    bulk_copy_g2s(tab, G.term_tab + (size_t)b * tt.len, tab_bytes, &bar[0]);
+  }
+  pdl_wait();  // the reach rows come from the launch just before this one
+  pdl_trigger();
+  if (threadIdx.x == 0) {
+    bulk_copy_g2s(qbuf, qsrc + (size_t)work[first].unit * stride, q_bytes, &bar[0]);
+    if (RUNS && count > 1) {
+      mbar_arrive_expect_tx(&bar[1], q_bytes);
+      bulk_copy_g2s(qbuf + stride, qsrc + (size_t)work[first + 1].unit * stride, q_bytes, &bar[1]);
+    }
+  }
+  for (int j = 0; j < count; ++j) {
+    const int n = work[first + j].unit;
+    const NodeDev nd = G.nodes[n];
+    // payoff for player i per unit of (opponent reach) x kappa, in FP64
+    const double pay = G.payoff[n];
+    const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
+    const bool ok = threadIdx.x >= 32 || mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1);  // one warp polls
+    if (__syncthreads_or(!ok)) {  // a copy did not land: report, let the copies drain, leave
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1);
+        if (j + 1 < count) mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1);
+      }
+      __syncthreads();
+      return;
+    }
+    terminal_values<P>(G, nd, i, u64, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc, dst + (size_t)n * stride);
+    if (!RUNS) break;
+    __syncthreads();  // buffer j & 1 and the scan arrays are free again
+    if (threadIdx.x == 0 && j + 2 < count) {
+      mbar_arrive_expect_tx(&bar[j & 1], q_bytes);
+      bulk_copy_g2s(qbuf + (size_t)(j & 1) * stride, qsrc + (size_t)work[first + j + 2].unit * stride, q_bytes,
+                    &bar[j & 1]);
     }
   }
 }
@@ -659,7 +789,7 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
         x = Rc[r] + P::to_double(rr);
         if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
         if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
-        const double sn = fma(Sc[r], d.dS, d.wS * contrib);
+        const double sn = fma(Sc[r], d.dS, variant == 1 ? d.wS * contrib : contrib);  // wS = 1 unless CFR+
         if (valid) {
           gR[(size_t)r * stride] = x;
           gS[(size_t)r * stride] = sn;
@@ -813,7 +943,8 @@ struct StreamLane {
   double* S;
   V* reach;         // column h of player p's reach plane
   V* cfv;           // column h of player p's value plane
-  uint64_t* ring;   // this lane's prefetch ring: unit u at ring[u * 32]
+  uint64_t* ring;   // this lane's prefetch ring: unit u of half k at ring[(k * half + u) * 32]
+  int half;         // 8-byte units per lane in each half of the ring
   V* st;            // this lane's stack: slot s at st[s * 32]
 };
 
@@ -822,7 +953,7 @@ template <typename P, bool BACKWARD>
 __device__ __forceinline__ void stream_issue(const StreamLane<P>& L, int k0, int k1, int half) {
   using V = typename P::V;
   const int N = L.G.n_nodes;
-  uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  uint64_t* ring = L.ring + (size_t)half * L.half * 32;
   int u = 0;
   for (int k = k0; k < k1; ++k) {
     const Op nd = decode(L.prog[BACKWARD ? N - 1 - k : k]);
@@ -863,7 +994,7 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
                                                       const Discount& d, int variant) {
   using V = typename P::V;
   const int N = L.G.n_nodes;
-  const uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  const uint64_t* ring = L.ring + (size_t)half * L.half * 32;
   V* st = L.st;
   int u = 0;
   for (int k = k0; k < k1; ++k) {
@@ -910,7 +1041,7 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
           double x = Rv[a] + P::to_double(rr);
           if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
           if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
-          const double sn = fma(Sr[(size_t)a * 32], d.dS, d.wS * contrib);
+          const double sn = fma(Sr[(size_t)a * 32], d.dS, variant == 1 ? d.wS * contrib : contrib);
           if (L.valid) {
             L.R[(size_t)(nd.row + a) * L.stride] = x;
             L.S[(size_t)(nd.row + a) * L.stride] = sn;
@@ -929,7 +1060,7 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
 template <typename P>
 __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp) {
   using V = typename P::V;
-  const uint64_t* ring = L.ring + (size_t)half * kStreamHalf * 32;
+  const uint64_t* ring = L.ring + (size_t)half * L.half * 32;
   V* st = L.st;
   int u = 0;
   for (int k = k0; k < k1; ++k) {
@@ -983,7 +1114,8 @@ __device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int list, F 
 template <typename P>
 __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const GameDev* __restrict__ games, const Work* __restrict__ work, int n_work, int player_mask, int advance,
-    int* iter, unsigned* done, const Discount* __restrict__ disc_tab, int variant, int depth, int prog_nodes) {
+    int* iter, unsigned* done, const Discount* __restrict__ disc_tab, int variant, int depth, int prog_nodes,
+    int half_units) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char sms[];
   __shared__ Discount disc;
@@ -996,13 +1128,13 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
   const int unit = wk.unit + warp;
   const bool active = unit * 32 < G.n_hands;
   if (threadIdx.x == 0) disc = disc_tab[*iter];
-  // shared memory: the program, then per warp a prefetch ring (2 halves of kStreamHalf
+  // shared memory: the program, then per warp a prefetch ring (2 halves of half_units
   // 8-byte units per lane) and a stack
   ProgOp* sprog = reinterpret_cast<ProgOp*>(sms);
   uint64_t* ring = reinterpret_cast<uint64_t*>(sms + (size_t)prog_nodes * sizeof(ProgOp)) +
-                   (size_t)warp * 2 * kStreamHalf * 32 + lane;
+                   (size_t)warp * 2 * half_units * 32 + lane;
   V* st = reinterpret_cast<V*>(sms + (size_t)prog_nodes * sizeof(ProgOp) +
-                               (size_t)kStreamWarps * 2 * kStreamHalf * 32 * 8) +
+                               (size_t)kStreamWarps * 2 * half_units * 32 * 8) +
           (size_t)warp * depth * 32 + lane;
   if (prog_nodes > 0) {  // static: staged while the previous launch finishes
     const int4* src = reinterpret_cast<const int4*>(G.prog);
@@ -1019,7 +1151,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const size_t plane = (size_t)p * G.n_nodes * stride + h;
     const StreamLane<P> L{G, prog_nodes > 0 ? sprog : G.prog, p, valid, valid ? G.hand_mask[h] : 0ull, stride,
                           G.R + h, G.S + h, static_cast<V*>(G.reach) + plane, static_cast<V*>(G.cfv) + plane, ring,
-                          st};
+                          half_units, st};
     const Discount d = disc;
     int sp = 0;
     stream_pass<P, true>(L, p, [&](int k0, int k1, int half) {
@@ -1134,7 +1266,8 @@ template <typename P>
 static cudaError_t configure_precision() {
   cudaError_t e = configure_hand<P, true>();
   if (e == cudaSuccess) e = configure_hand<P, false>();
-  if (e == cudaSuccess) e = configure_one(k_terminal<P>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_terminal<P, false>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_terminal<P, true>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_average_rows<P>, 0);
   if (e == cudaSuccess) e = configure_one(k_stream_update<P>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_current_rows<P>, 0);
@@ -1198,10 +1331,10 @@ template <typename P>
 static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   const int players = player_mask == 3 ? 2 : 1;
   const int grid = c.n_warp_work * players;
-  const size_t smem = stream_smem_size(c.stream_prog, c.stream_depth, sizeof(typename P::V));
+  const size_t smem = stream_smem_size(c.stream_prog, c.stream_half, c.stream_depth, sizeof(typename P::V));
   const cudaError_t e = launch_kernel(k_stream_update<P>, grid, kStreamWarps * 32, smem, stream, c.pdl != 0,
                                       c.games, c.warp_work, c.n_warp_work, player_mask, advance, c.iter, c.done,
-                                      c.disc, c.variant, c.stream_depth, c.stream_prog);
+                                      c.disc, c.variant, c.stream_depth, c.stream_prog, c.stream_half);
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_stream_update failed: %s\n", cudaGetErrorString(e));
     return -1;
@@ -1227,17 +1360,22 @@ int launch_avg_reach(const LaunchCtx& c, void* stream) { return launch_hand<kMod
 int launch_br(const LaunchCtx& c, void* stream) { return launch_hand<kModeBR>(c, 3, 0, stream, c.pdl != 0); }
 
 int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stream) {
-  if (c.n_term_work == 0) return 0;
+  if (c.n_term_runs == 0) return 0;
   const int players = player_mask == 3 ? 2 : 1;
-  const int grid = c.n_term_work * players;
+  const int grid = c.n_term_runs * players;
   const bool pdl = c.pdl != 0;
   cudaError_t e;
+  const bool runs = c.n_term_runs < c.n_term_work;
   if (c.precision == kPrecisionSingle)
-    e = launch_kernel(k_terminal<Single>, grid, kTermThreads, c.smem_term, stream, pdl, c.games, c.term_work,
-                      c.n_term_work, player_mask, use_bar, c.err);
+    e = runs ? launch_kernel(k_terminal<Single, true>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
+                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
+             : launch_kernel(k_terminal<Single, false>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
+                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
   else
-    e = launch_kernel(k_terminal<Pairs>, grid, kTermThreads, c.smem_term, stream, pdl, c.games, c.term_work,
-                      c.n_term_work, player_mask, use_bar, c.err);
+    e = runs ? launch_kernel(k_terminal<Pairs, true>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
+                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
+             : launch_kernel(k_terminal<Pairs, false>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
+                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_terminal failed: %s\n", cudaGetErrorString(e));
     return -1;

@@ -43,7 +43,8 @@ constexpr int kDiscountCapacity = 1 << 16;  // iterations covered by one discoun
 constexpr int kScheduleLevel = 1;   // per-hand passes: one block per chunk of hands, level by level
 constexpr int kScheduleStream = 2;  // update pass: one warp per 32 hands walks a depth-first program
 constexpr int kStreamMaxActions = 8;  // actions at a decision node the stream schedule holds in registers
-constexpr int kStreamHalf = 20;       // 8-byte units per lane in each half of a warp's prefetch ring
+constexpr int kStreamHalfMin = 12;   // 8-byte units per lane in each half of a warp's prefetch ring,
+                                      // at least (or the most one node needs, 2 A + 1)
 constexpr int kStreamWarps = 4;       // warps per block of the stream schedule (one game per block)
 
 struct alignas(16) NodeDev {
@@ -145,8 +146,12 @@ struct LaunchCtx {
   int n_games;
   const Work* chunk_work;      // device [n_chunk_work]: (game, chunk)
   int n_chunk_work;
-  const Work* term_work;       // device [n_term_work]: (game, terminal node)
+  const Work* term_work;       // device [n_term_work]: (game, terminal node), grouped by game and
+                               // board table
   int n_term_work;
+  const Work* term_runs;       // device [n_term_runs]: (first entry of term_work, count), the
+                               // terminal nodes one block evaluates
+  int n_term_runs;
   int* iter;                   // device: iterations completed
   unsigned* done;              // device: block arrival counter
   int* err;                    // device: nonzero after a bounded wait gave up
@@ -164,6 +169,7 @@ struct LaunchCtx {
   int stream_depth;            // stack slots per lane of the stream schedule
   int stream_prog;             // nodes of the largest tree, if its program is staged in shared
                                // memory; 0 = read from global memory
+  int stream_half;             // units per lane in each half of the stream prefetch ring
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
@@ -178,9 +184,9 @@ int hand_kernel_smem_limit();
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
 // Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes),
-// a prefetch ring and a stack of `depth` slots (es bytes each) per lane.
-inline size_t stream_smem_size(int prog_nodes, int depth, size_t es) {
-  return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)kStreamWarps * 32 * (2 * kStreamHalf * 8 + (size_t)depth * es);
+// a prefetch ring of 2 x half 8-byte units and a stack of `depth` slots (es bytes) per lane.
+inline size_t stream_smem_size(int prog_nodes, int half, int depth, size_t es) {
+  return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)kStreamWarps * 32 * (2 * (size_t)half * 8 + (size_t)depth * es);
 }
 
 }  // namespace pcfr

@@ -118,26 +118,26 @@ def stored_cfv(tree, g, info):
     return g == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN)
 
 
-def compare_player(tree, oracle, mapping, player, game=0, pot=None):
+def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, floor_frac=FLOOR):
     """R and S of one player's decision nodes and that player's counterfactual values."""
     pot = oracle.spec.pot if pot is None else pot
-    floor = FLOOR * pot
+    floor = floor_frac * pot
     worst = {"R": 0.0, "S": 0.0, "cfv": 0.0}
     for g, o, info in mapping:
         if info["type"] == capi.CFR_NODE_DECISION and info["player"] == player:
             R_g = capi.cfr_read_values(tree, capi.CFR_READ_REGRET, g, game=game)
             S_g = capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, g, game=game)
-            worst["R"] = max(worst["R"], close(R_g, oracle.regrets(o), floor=floor, what=f"R node {g}"))
-            worst["S"] = max(worst["S"], close(S_g, oracle.avg_sums(o), what=f"S node {g}"))
+            worst["R"] = max(worst["R"], close(R_g, oracle.regrets(o), rtol, floor=floor, what=f"R node {g}"))
+            worst["S"] = max(worst["S"], close(S_g, oracle.avg_sums(o), rtol, what=f"S node {g}"))
         if not stored_cfv(tree, g, info):
             continue
         v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=player, game=game)
-        worst["cfv"] = max(worst["cfv"], close(v_g, oracle.cfv(player, o), floor=floor,
+        worst["cfv"] = max(worst["cfv"], close(v_g, oracle.cfv(player, o), rtol, floor=floor,
                                                what=f"cfv player {player} node {g}"))
     return worst
 
 
-def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=True):
+def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=True, rtol=RTOL, floor_frac=FLOOR):
     """Iteration t from identical state.
 
     The GPU's R and S are loaded into the oracle, then the GPU runs one iteration and the
@@ -152,15 +152,15 @@ def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=
     worst = {}
     if alternating:
         oracle.update_player(0, t)
-        w0 = compare_player(tree, oracle, mapping, 0, game)
+        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac)
         inject(tree, oracle, mapping, game, player=0)
         oracle.update_player(1, t)
-        w1 = compare_player(tree, oracle, mapping, 1, game)
+        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac)
         worst = {k: max(w0[k], w1[k]) for k in w0}
     else:
         oracle.update_both(t)
-        w0 = compare_player(tree, oracle, mapping, 0, game)
-        w1 = compare_player(tree, oracle, mapping, 1, game)
+        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac)
+        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac)
         worst = {k: max(w0[k], w1[k]) for k in w0}
     oracle.set_iterations(t)
     return worst

@@ -318,3 +318,64 @@ def test_schedule_selection():
         assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL
     finally:
         capi.cfr_tree_destroy(tree)
+
+
+# ---------------------------------------------------------------- FP32 values
+# CFR_PRECISION_SINGLE carries reach, strategies and values in plain FP32 (R and S stay
+# FP64).  Compared from the GPU's own state each iteration, it meets the same bar as the
+# default precision (1e-5 of the largest oracle magnitude in each node's vector); the test
+# prints the worst errors it saw.  Free-running FP32 trajectories drift further, because
+# rounding decides near-ties between actions differently from FP64.
+
+@pytest.mark.parametrize("case,variant,schedule", [("river_203", "dcfr", "level"), ("river_203", "dcfr", "stream"),
+                                                   ("turn_40", "dcfr", "stream"), ("leduc", "cfr+", "stream")])
+def test_single_precision_error_against_oracle(case, variant, schedule):
+    from oracle.oracle import Oracle
+    spec = CASES[case][0]()
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, precision="single", schedule=schedule))
+    try:
+        orc = Oracle(spec, variant=variant)
+        mapping = node_map(tree, orc)
+        worst = {}
+        for t in range(1, 11):
+            w = forced_step(tree, orc, mapping, t, rtol=1e-5, floor_frac=1e-8)
+            worst = {k: max(worst.get(k, 0.0), v) for k, v in w.items()}
+        print(case, variant, schedule, "single forced (relative to node max)", worst)
+        inject(tree, orc, mapping)
+        e_g, _ = capi.cfr_exploitability(tree)
+        assert e_g[0] == pytest.approx(orc.exploitability()[0], rel=1e-4, abs=1e-7 * spec.pot)
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_terminal_runs_match_one_node_blocks():
+    """Large handles evaluate up to four terminal nodes per block; small ones one.  The same
+    subgames solved in one large handle and one handle each must agree bit for bit."""
+    specs = [river(64, seed=70 + k, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4) for k in range(40)]
+    big = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="single", schedule="level"))
+    try:
+        n_term = sum(1 for g in range(len(specs)) for n in range(capi.cfr_tree_info(big, g)[0])
+                     if capi.cfr_node_info(big, n, g)["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN))
+        assert n_term >= 4 * 152 * 8  # runs of four
+        capi.cfr_iterate(big, 3)
+        e_big, _ = capi.cfr_exploitability(big, len(specs))
+        for g in (0, 17, 39):
+            one = capi.cfr_tree_create(specs[g], capi.make_opts("dcfr", precision="single", schedule="level"))
+            try:
+                capi.cfr_iterate(one, 3)
+                e_one, _ = capi.cfr_exploitability(one)
+                assert e_one[0] == e_big[g]
+                for n in range(capi.cfr_tree_info(one)[0]):
+                    info = capi.cfr_node_info(one, n)
+                    if info["type"] == capi.CFR_NODE_DECISION:
+                        for what in (capi.CFR_READ_REGRET, capi.CFR_READ_AVG_SUM):
+                            assert np.array_equal(capi.cfr_read_values(one, what, n),
+                                                  capi.cfr_read_values(big, what, n, game=g))
+                    elif info["type"] != capi.CFR_NODE_CHANCE:
+                        for i in (0, 1):
+                            assert np.array_equal(capi.cfr_read_values(one, capi.CFR_READ_CFV, n, player=i),
+                                                  capi.cfr_read_values(big, capi.CFR_READ_CFV, n, player=i, game=g))
+            finally:
+                capi.cfr_tree_destroy(one)
+    finally:
+        capi.cfr_tree_destroy(big)
