@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -238,21 +239,38 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   bool stream_ok = true;
   for (int g = 0; g < n_games; ++g) {
     int depth = 0, amax = 0;
-    programs[g] = dfs_program(t->host[g], &depth, &amax);
+    bool fits = false;
+    programs[g] = dfs_program(t->host[g], &depth, &amax, &fits);
+    stream_ok = stream_ok && fits;
     stream_depth = std::max(stream_depth, depth);
     stream_ok = stream_ok && amax <= kStreamMaxActions;
     stream_warps += (t->host[g].n_hands + 31) / 32;
   }
   // the program of the largest tree is staged in shared memory when it takes at most 64 KB
-  int max_nodes = 0;
-  for (int g = 0; g < n_games; ++g) max_nodes = std::max(max_nodes, (int)t->host[g].nodes.size());
-  const int stream_prog = max_nodes * (int)sizeof(ProgOp) <= 64 * 1024 ? max_nodes : 0;
-  int amax_all = 0;
-  for (int g = 0; g < n_games; ++g)
-    for (const NodeDev& nd : t->host[g].nodes)
-      if (nd.type == kDecision) amax_all = std::max(amax_all, (int)nd.n_kids);
-  const int stream_half = std::max(kStreamHalfMin, 2 * amax_all + 1);
-  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_half, stream_depth, es) <= 200 * 1024;
+  int max_prog = 0, max_loads = 0;
+  for (int g = 0; g < n_games; ++g) {
+    max_prog = std::max(max_prog, (int)programs[g].size());
+    for (int n : programs[g])
+      for (int p = 0; p < 2; ++p)
+        max_loads = std::max(max_loads, (int)node_loads(t->host[g], n, p, true, (uint32_t)t->host[g].hstride).size());
+  }
+  const int stream_prog = max_prog * (int)sizeof(ProgOp) <= 64 * 1024 ? max_prog : 0;
+  const int stream_half = std::max(kStreamHalfMin, max_loads);
+  // load tables of every game (units per player: both passes), and their largest size
+  std::vector<std::vector<uint32_t>> unit_lists(n_games);
+  std::vector<std::vector<int32_t>> chunk_lists(n_games);
+  std::vector<std::array<int, 16>> table_meta(n_games);
+  int stream_units_max = 0;
+  for (int g = 0; g < n_games; ++g) {
+    std::array<int, 16>& m = table_meta[g];
+    chunk_lists[g] = stream_tables(t->host[g], programs[g], stream_half, unit_lists[g], &m[0], &m[4], &m[8], &m[12]);
+    for (int p = 0; p < 2; ++p) stream_units_max = std::max(stream_units_max, m[4 + p] + m[4 + 2 + p]);
+    const size_t span = std::max(t->host[g].nodes.size(), (size_t)t->host[g].n_rows) * (size_t)t->host[g].hstride;
+    stream_ok = stream_ok && span < (1u << 30);
+  }
+  stream_units_max = (stream_units_max + 3) / 4 * 4;  // keeps the ring 16-byte aligned
+  const int stream_units = stream_prog ? stream_units_max : 0;
+  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_units, stream_half, stream_depth, es) <= 200 * 1024;
   int schedule = kScheduleLevel;
   if (o.schedule == CFR_SCHEDULE_STREAM) {
     if (!stream_ok) {
@@ -295,9 +313,15 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
     NodeDev* nodes;
     int32_t *ls, *rn, *dn, *chk;
+    uint32_t* un;
     ProgOp* prog;
     const std::vector<ProgOp> ops = program_ops(h, programs[g]);
-    const std::vector<int32_t> chunks = stream_chunks(h, programs[g], stream_half, d.chunk_off, d.chunk_count);
+    for (int q = 0; q < 4; ++q) {
+      d.unit_off[q] = table_meta[g][q];
+      d.unit_count[q] = table_meta[g][4 + q];
+      d.chunk_off[q] = table_meta[g][8 + q];
+      d.chunk_count[q] = table_meta[g][12 + q];
+    }
     uint16_t* tb;
     uint64_t* hm;
     float* rrv;
@@ -305,12 +329,14 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
         (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
         (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb)) || (rc = upload(t, decn, &dn)) ||
-        (rc = upload(t, ops, &prog)) || (rc = upload(t, chunks, &chk))) {
+        (rc = upload(t, ops, &prog)) || (rc = upload(t, chunk_lists[g], &chk)) ||
+        (rc = upload(t, unit_lists[g], &un))) {
       delete t;
       return rc;
     }
     d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk;
+    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
+    d.prog_len = (int)programs[g].size();
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value
     float *sig, *sigb, *rch, *rchb, *cf, *cfb;
@@ -394,6 +420,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_depth = stream_depth;
   c.stream_prog = stream_prog;
   c.stream_half = stream_half;
+  c.stream_units = stream_units;
   t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
   t->launches += 1;
   if (launch_init(c, stream) != 0) {

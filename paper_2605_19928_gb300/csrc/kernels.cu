@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
 //      decision nodes (for its next update) and at the terminals (for the opponent's next
 //      terminal launch).
 // Strategies and the values of inner nodes never go to DRAM.  Every address a pass reads
-// is fixed by the program, so each pass is cut into chunks (stream_chunks) that are loaded
+// is fixed by the program, so each pass is cut into chunks (stream_tables) that are loaded
 // into a per-lane ring in shared memory with cp.async one chunk ahead of the computation.
 // The arithmetic (regret matching, child order of every sum, the update) is that of k_hand,
 // so both schedules give the same bits.
@@ -922,11 +922,17 @@ __device__ __forceinline__ void load_rows(const double* __restrict__ base, size_
 
 // A program node, decoded.
 struct Op {
-  int n, row, type, player, A, deal, first_kid;
+  int node_off, row_off, type, player, A, deal, tmask, first_kid;
 };
 __device__ __forceinline__ Op decode(const ProgOp& o) {
-  return {o.node, o.row, (int)(o.code & 0xffu), (int)((o.code >> 8) & 0xffu), (int)((o.code >> 16) & 0xffu),
-          (int)(o.code >> 24), o.first_kid};
+  return {o.node_off,
+          o.row_off,
+          (int)(o.code & 3u),
+          (int)((o.code >> 2) & 1u),
+          (int)((o.code >> 3) & 63u),
+          (int)((o.code >> 9) & 0xffu),
+          (int)((o.code >> 17) & 0xffu),
+          o.first_kid};
 }
 
 // One lane's view of its subgame for the stream passes.
@@ -934,7 +940,8 @@ template <typename P>
 struct StreamLane {
   using V = typename P::V;
   const GameDev& G;
-  const ProgOp* prog;  // the program (shared memory when staged)
+  const ProgOp* prog;     // the program (shared memory when staged)
+  const uint32_t* units;  // this player's loads, bottom-up pass then top-down pass
   int p;
   bool valid;
   uint64_t hmask;
@@ -948,32 +955,22 @@ struct StreamLane {
   V* st;            // this lane's stack: slot s at st[s * 32]
 };
 
-// Issue the loads of chunk [k0, k1) of a pass into ring half `half` (one commit group).
-template <typename P, bool BACKWARD>
-__device__ __forceinline__ void stream_issue(const StreamLane<P>& L, int k0, int k1, int half) {
+// Issue loads [u0, u1) of a pass into ring half `half` (one commit group).
+template <typename P>
+__device__ __forceinline__ void stream_issue(const StreamLane<P>& L, const uint32_t* units, int u0, int u1,
+                                             int half) {
   using V = typename P::V;
-  const int N = L.G.n_nodes;
   uint64_t* ring = L.ring + (size_t)half * L.half * 32;
-  int u = 0;
-  for (int k = k0; k < k1; ++k) {
-    const Op nd = decode(L.prog[BACKWARD ? N - 1 - k : k]);
-    const int n = nd.n;
-    if (nd.type == kDecision && nd.player == L.p) {
-      const int A = nd.A;
-      const double* r = L.R + (size_t)nd.row * L.stride;
-      for (int a = 0; a < A; ++a) cp_async<8>(ring + (size_t)(u + a) * 32, r + (size_t)a * L.stride);
-      u += A;
-      if (BACKWARD) {
-        const double* s = L.S + (size_t)nd.row * L.stride;
-        for (int a = 0; a < A; ++a) cp_async<8>(ring + (size_t)(u + a) * 32, s + (size_t)a * L.stride);
-        u += A;
-        cp_async<(int)sizeof(V)>(ring + (size_t)u * 32, L.reach + (size_t)n * L.stride);
-        ++u;
-      }
-    } else if (BACKWARD && (nd.type == kFold || nd.type == kShowdown)) {
-      cp_async<(int)sizeof(V)>(ring + (size_t)u * 32, L.cfv + (size_t)n * L.stride);
-      ++u;
-    }
+  for (int u = u0; u < u1; ++u) {
+    const uint32_t d = units[u];
+    const uint32_t arr = d >> 30, off = d & 0x3fffffffu;
+    uint64_t* dst = ring + (size_t)(u - u0) * 32;
+    if (arr == kArrR)
+      cp_async<8>(dst, L.R + off);
+    else if (arr == kArrS)
+      cp_async<8>(dst, L.S + off);
+    else
+      cp_async<(int)sizeof(V)>(dst, (arr == kArrReach ? L.reach : L.cfv) + off);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -988,37 +985,51 @@ __device__ __forceinline__ typename P::V ring_value(const uint64_t* slot) {
   return *reinterpret_cast<const typename P::V*>(slot);
 }
 
-// Bottom-up pass over chunk [k0, k1) (program positions counted from its end).
+// Bottom-up pass over chunk [k0, k1) (program positions counted from its end).  A node's
+// children values come from the ring (terminal children, in child order) or from the stack
+// (inner children, child 0 on top).
 template <typename P>
 __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp,
                                                       const Discount& d, int variant) {
   using V = typename P::V;
-  const int N = L.G.n_nodes;
+  const int N = L.G.prog_len;
   const uint64_t* ring = L.ring + (size_t)half * L.half * 32;
   V* st = L.st;
   int u = 0;
   for (int k = k0; k < k1; ++k) {
     const Op nd = decode(L.prog[N - 1 - k]);
     const int A = nd.A;
-    if (nd.type == kFold || nd.type == kShowdown) {
-      st[sp * 32] = ring_value<P>(ring + (size_t)u * 32);
-      ++u;
-      ++sp;
-      continue;
-    }
     V val;
     if (nd.type == kChance) {  // children values carry the card probabilities
       typename P::Acc acc = P::acc0();
+      const bool term = nd.tmask & 1;  // all children terminal (after an all-in) or all inner
       for (int a = 0; a < A; ++a) {
-        const V x = st[(sp - 1 - a) * 32];
+        const V x = term ? ring_value<P>(ring + (size_t)(u++) * 32) : st[(--sp) * 32];
         if (!((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull)) P::acc(acc, x);
       }
       val = P::value(acc);
     } else if (nd.player != L.p) {
       typename P::Acc acc = P::acc0();
-      for (int a = 0; a < A; ++a) P::acc(acc, st[(sp - 1 - a) * 32]);
+      for (int a = 0; a < A; ++a) {
+        V x;
+        if ((nd.tmask >> a) & 1)
+          x = ring_value<P>(ring + (size_t)(u++) * 32);
+        else
+          x = st[(--sp) * 32];
+        P::acc(acc, x);
+      }
       val = P::value(acc);
     } else {
+      V c[kStreamMaxActions];
+#pragma unroll
+      for (int a = 0; a < kStreamMaxActions; ++a) {
+        if (a < A) {
+          if ((nd.tmask >> a) & 1)
+            c[a] = ring_value<P>(ring + (size_t)(u++) * 32);
+          else
+            c[a] = st[(--sp) * 32];
+        }
+      }
       const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
       const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
       const V pi = ring_value<P>(ring + (size_t)(u + 2 * A) * 32);
@@ -1031,32 +1042,31 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
       typename P::Acc acc = P::acc0();
 #pragma unroll
       for (int a = 0; a < kStreamMaxActions; ++a)
-        if (a < A) P::acc_mul(acc, sg[a], st[(sp - 1 - a) * 32]);
+        if (a < A) P::acc_mul(acc, sg[a], c[a]);
       val = P::value(acc);
 #pragma unroll
       for (int a = 0; a < kStreamMaxActions; ++a) {
         if (a < A) {
-          const V rr = P::sub(st[(sp - 1 - a) * 32], val);          // instantaneous regret
+          const V rr = P::sub(c[a], val);                          // instantaneous regret
           const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
           double x = Rv[a] + P::to_double(rr);
           if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
           if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
           const double sn = fma(Sr[(size_t)a * 32], d.dS, variant == 1 ? d.wS * contrib : contrib);
           if (L.valid) {
-            L.R[(size_t)(nd.row + a) * L.stride] = x;
-            L.S[(size_t)(nd.row + a) * L.stride] = sn;
+            L.R[(size_t)nd.row_off + (size_t)a * L.stride] = x;
+            L.S[(size_t)nd.row_off + (size_t)a * L.stride] = sn;
           }
         }
       }
     }
-    sp -= A;
-    st[sp * 32] = val;
-    ++sp;
+    st[(sp++) * 32] = val;
   }
 }
 
 // Top-down pass over chunk [k0, k1) with sigma = RM(R): records the reach at the player's
-// decision nodes and at the terminals.
+// decision nodes and, for the terminal children, at the terminals; pushes the reach of the
+// inner children (child 0 on top).
 template <typename P>
 __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp) {
   using V = typename P::V;
@@ -1065,15 +1075,11 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
   int u = 0;
   for (int k = k0; k < k1; ++k) {
     const Op nd = decode(L.prog[k]);
-    const int n = nd.n;
-    --sp;
-    V x = st[sp * 32];
+    V x = st[(--sp) * 32];
     if (nd.deal != kNoCard && ((L.hmask >> nd.deal) & 1ull)) x = P::zero();
     const int A = nd.A;
-    if (nd.type == kFold || nd.type == kShowdown) {
-      if (L.valid) L.reach[(size_t)n * L.stride] = x;
-    } else if (nd.type == kDecision && nd.player == L.p) {
-      if (L.valid) L.reach[(size_t)n * L.stride] = x;
+    if (nd.type == kDecision && nd.player == L.p) {
+      if (L.valid) L.reach[nd.node_off] = x;
       const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
       u += A;
       double Rv[kStreamMaxActions];
@@ -1082,29 +1088,50 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
       for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
       regret_match<P>(Rv, A, sg);
 #pragma unroll
-      for (int a = kStreamMaxActions - 1; a >= 0; --a)
-        if (a < A) st[(sp + A - 1 - a) * 32] = P::mul(x, sg[a]);  // child 0 on top
-      sp += A;
-    } else {  // opponent decision or chance: the player's reach passes through
-      for (int a = 0; a < A; ++a) st[(sp + a) * 32] = x;
-      sp += A;
+      for (int a = kStreamMaxActions - 1; a >= 0; --a) {
+        if (a < A) {
+          const V y = P::mul(x, sg[a]);
+          if ((nd.tmask >> a) & 1) {
+            if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
+          } else {
+            st[(sp++) * 32] = y;
+          }
+        }
+      }
+    } else if (nd.type == kChance) {  // the player's reach passes through to each card
+      if (nd.tmask & 1) {  // terminal children: their reach, zero where the hand holds the card
+        for (int a = 0; a < A; ++a) {
+          const V y = ((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull) ? P::zero() : x;
+          if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
+        }
+      } else {  // inner children apply their own card when they pop it
+        for (int a = 0; a < A; ++a) st[(sp++) * 32] = x;
+      }
+    } else {  // opponent decision: the player's reach passes through
+      for (int a = A - 1; a >= 0; --a) {
+        if ((nd.tmask >> a) & 1) {
+          if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = x;
+        } else {
+          st[(sp++) * 32] = x;
+        }
+      }
     }
   }
 }
 
-// One pass: chunk c + 1 loads while chunk c computes.
-template <typename P, bool BACKWARD, typename F>
-__device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int list, F compute) {
-  const int32_t* ch = L.G.chunks + L.G.chunk_off[list];
-  const int nch = L.G.chunk_count[list];
-  stream_issue<P, BACKWARD>(L, ch[0], ch[1], 0);
+// One pass (list q of the load tables): chunk c + 1 loads while chunk c computes.
+template <typename P, typename F>
+__device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int q, const uint32_t* units, F compute) {
+  const int32_t* ch = L.G.chunks + 2 * (size_t)L.G.chunk_off[q];  // (node, unit) pairs
+  const int nch = L.G.chunk_count[q];
+  stream_issue<P>(L, units, ch[1], ch[3], 0);
   for (int c = 0; c < nch; ++c) {
     if (c + 1 < nch)
-      stream_issue<P, BACKWARD>(L, ch[c + 1], ch[c + 2], (c + 1) & 1);
+      stream_issue<P>(L, units, ch[2 * c + 3], ch[2 * c + 5], (c + 1) & 1);
     else
       asm volatile("cp.async.commit_group;" ::: "memory");
     cp_async_wait_group<1>();  // chunk c has landed (each lane reads only its own column)
-    compute(ch[c], ch[c + 1], c & 1);
+    compute(ch[2 * c], ch[2 * c + 2], c & 1);
   }
   cp_async_wait_group<0>();
 }
@@ -1115,7 +1142,7 @@ template <typename P>
 __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const GameDev* __restrict__ games, const Work* __restrict__ work, int n_work, int player_mask, int advance,
     int* iter, unsigned* done, const Discount* __restrict__ disc_tab, int variant, int depth, int prog_nodes,
-    int half_units) {
+    int prog_units, int half_units) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char sms[];
   __shared__ Discount disc;
@@ -1130,16 +1157,22 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
   if (threadIdx.x == 0) disc = disc_tab[*iter];
   // shared memory: the program, then per warp a prefetch ring (2 halves of half_units
   // 8-byte units per lane) and a stack
+  const size_t tables = (size_t)prog_nodes * sizeof(ProgOp) + (size_t)prog_units * 4;  // multiple of 16
   ProgOp* sprog = reinterpret_cast<ProgOp*>(sms);
-  uint64_t* ring = reinterpret_cast<uint64_t*>(sms + (size_t)prog_nodes * sizeof(ProgOp)) +
-                   (size_t)warp * 2 * half_units * 32 + lane;
-  V* st = reinterpret_cast<V*>(sms + (size_t)prog_nodes * sizeof(ProgOp) +
-                               (size_t)kStreamWarps * 2 * half_units * 32 * 8) +
+  uint32_t* sunits = reinterpret_cast<uint32_t*>(sms + (size_t)prog_nodes * sizeof(ProgOp));
+  uint64_t* ring = reinterpret_cast<uint64_t*>(sms + tables) + (size_t)warp * 2 * half_units * 32 + lane;
+  V* st = reinterpret_cast<V*>(sms + tables + (size_t)kStreamWarps * 2 * half_units * 32 * 8) +
           (size_t)warp * depth * 32 + lane;
+  // this player's loads: the bottom-up pass's, then the top-down pass's
+  const uint32_t* gunits_b = G.units + G.unit_off[p];
+  const uint32_t* gunits_f = G.units + G.unit_off[2 + p];
+  const int nb = G.unit_count[p], nf = G.unit_count[2 + p];
   if (prog_nodes > 0) {  // static: staged while the previous launch finishes
     const int4* src = reinterpret_cast<const int4*>(G.prog);
     int4* dst = reinterpret_cast<int4*>(sprog);
-    for (int k = threadIdx.x; k < G.n_nodes; k += blockDim.x) dst[k] = __ldg(src + k);
+    for (int k = threadIdx.x; k < G.prog_len; k += blockDim.x) dst[k] = __ldg(src + k);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) sunits[k] = __ldg(gunits_b + k);
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) sunits[nb + k] = __ldg(gunits_f + k);
   }
   pdl_wait();  // the terminal values come from the launch just before this one
   pdl_trigger();
@@ -1149,19 +1182,22 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const bool valid = h < G.n_hands;
     const size_t stride = (size_t)G.hstride;
     const size_t plane = (size_t)p * G.n_nodes * stride + h;
-    const StreamLane<P> L{G, prog_nodes > 0 ? sprog : G.prog, p, valid, valid ? G.hand_mask[h] : 0ull, stride,
+    const bool staged = prog_nodes > 0;
+    const StreamLane<P> L{G, staged ? sprog : G.prog, staged ? sunits : gunits_b, p, valid,
+                          valid ? G.hand_mask[h] : 0ull, stride,
                           G.R + h, G.S + h, static_cast<V*>(G.reach) + plane, static_cast<V*>(G.cfv) + plane, ring,
                           half_units, st};
     const Discount d = disc;
     int sp = 0;
-    stream_pass<P, true>(L, p, [&](int k0, int k1, int half) {
+    stream_pass<P>(L, p, L.units, [&](int k0, int k1, int half) {
       stream_backward_chunk<P>(L, k0, k1, half, sp, d, variant);
     });
     if (valid) L.cfv[0] = st[0];  // root value (read-back)
     __threadfence_block();       // the new R rows are read back by this lane's own copies below
     st[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
     sp = 1;
-    stream_pass<P, false>(L, 2 + p, [&](int k0, int k1, int half) { stream_forward_chunk<P>(L, k0, k1, half, sp); });
+    stream_pass<P>(L, 2 + p, staged ? sunits + nb : gunits_f,
+                   [&](int k0, int k1, int half) { stream_forward_chunk<P>(L, k0, k1, half, sp); });
   }
 
   if (advance) {
@@ -1331,10 +1367,12 @@ template <typename P>
 static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   const int players = player_mask == 3 ? 2 : 1;
   const int grid = c.n_warp_work * players;
-  const size_t smem = stream_smem_size(c.stream_prog, c.stream_half, c.stream_depth, sizeof(typename P::V));
+  const size_t smem =
+      stream_smem_size(c.stream_prog, c.stream_units, c.stream_half, c.stream_depth, sizeof(typename P::V));
   const cudaError_t e = launch_kernel(k_stream_update<P>, grid, kStreamWarps * 32, smem, stream, c.pdl != 0,
                                       c.games, c.warp_work, c.n_warp_work, player_mask, advance, c.iter, c.done,
-                                      c.disc, c.variant, c.stream_depth, c.stream_prog, c.stream_half);
+                                      c.disc, c.variant, c.stream_depth, c.stream_prog, c.stream_units,
+                                      c.stream_half);
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_stream_update failed: %s\n", cudaGetErrorString(e));
     return -1;

@@ -64,13 +64,19 @@ struct alignas(16) NodeDev {
 };
 static_assert(sizeof(NodeDev) == 32, "NodeDev is 32 bytes");
 
-// One node of the stream schedule's program (pre-order), 16 bytes.
+// One node of the stream schedule's program (pre-order), 16 bytes.  Offsets are in
+// elements of a per-hand array (multiples of hstride).
 struct alignas(16) ProgOp {
-  int32_t node;
-  int32_t row;        // decision: first row; showdown: board table; otherwise -1
-  uint32_t code;      // type | player << 8 | n_kids << 16 | deal << 24
+  int32_t node_off;   // node * hstride
+  int32_t row_off;    // decision: first row * hstride; otherwise 0
+  uint32_t code;      // type (2 bits) | player << 2 | n_kids << 3 (6 bits) | deal << 9 (8 bits) |
+                      // terminal-children mask << 17 (bit a: child a is a fold or showdown;
+                      // chance nodes: bit 0, all children are)
   int32_t first_kid;
 };
+
+// One load of the stream schedule's prefetch: array << 30 | element offset.
+enum StreamArray : uint32_t { kArrR = 0, kArrS = 1, kArrReach = 2, kArrCfv = 3 };
 static_assert(sizeof(ProgOp) == 16, "ProgOp is 16 bytes");
 
 // Offsets (in uint16) of the terminal-table sections for H hands of k cards from a deck.
@@ -112,9 +118,12 @@ struct GameDev {
   const void* range_v;         // [2][hstride] normalised ranges, value type V
   const double* range64;       // [2][hstride]
   const uint16_t* term_tab;    // [n_boards][TermTab.len]
-  const ProgOp* prog;          // [n_nodes] the tree in depth-first pre-order (stream schedule)
-  const int32_t* chunks;       // load chunks of the stream schedule (see stream_chunks)
+  const ProgOp* prog;          // [prog_len] inner nodes in depth-first pre-order (stream schedule)
+  int prog_len;
+  const int32_t* chunks;       // load chunks of the stream schedule (see stream_tables)
   int chunk_off[4], chunk_count[4];
+  const uint32_t* units;       // loads of the stream schedule, in the order the passes use them
+  int unit_off[4], unit_count[4];
   // state
   double* R;
   double* S;
@@ -170,6 +179,7 @@ struct LaunchCtx {
   int stream_prog;             // nodes of the largest tree, if its program is staged in shared
                                // memory; 0 = read from global memory
   int stream_half;             // units per lane in each half of the stream prefetch ring
+  int stream_units;            // load descriptors staged per block (0 when the program is not)
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
@@ -183,10 +193,12 @@ int hand_kernel_smem_limit();
 // Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
-// Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes),
-// a prefetch ring of 2 x half 8-byte units and a stack of `depth` slots (es bytes) per lane.
-inline size_t stream_smem_size(int prog_nodes, int half, int depth, size_t es) {
-  return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)kStreamWarps * 32 * (2 * (size_t)half * 8 + (size_t)depth * es);
+// Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes)
+// and one player's load descriptors (prog_units), a prefetch ring of 2 x half 8-byte units
+// and a stack of `depth` slots (es bytes) per lane.
+inline size_t stream_smem_size(int prog_nodes, int prog_units, int half, int depth, size_t es) {
+  return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)prog_units * 4 +
+         (size_t)kStreamWarps * 32 * (2 * (size_t)half * 8 + (size_t)depth * es);
 }
 
 }  // namespace pcfr

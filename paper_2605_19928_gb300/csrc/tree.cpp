@@ -492,31 +492,45 @@ std::vector<int32_t> row_nodes(const HostGame& g) {
   return out;
 }
 
-std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions) {
-  std::vector<int32_t> pre;
-  pre.reserve(g.nodes.size());
+static bool is_terminal(const NodeDev& nd) { return nd.type == kFold || nd.type == kShowdown; }
+
+std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions, bool* ok) {
+  std::vector<int32_t> pre;  // inner nodes only
   std::vector<int32_t> todo{0};
+  bool fine = !is_terminal(g.nodes[0]);
   while (!todo.empty()) {
     const int n = todo.back();
     todo.pop_back();
-    pre.push_back(n);
     const NodeDev& nd = g.nodes[(size_t)n];
-    for (int a = nd.n_kids - 1; a >= 0; --a) todo.push_back(nd.first_kid + a);  // child 0 first
+    if (is_terminal(nd)) continue;
+    pre.push_back(n);
+    for (int a = nd.n_kids - 1; a >= 0; --a) {  // child 0 first
+      const NodeDev& kid = g.nodes[(size_t)(nd.first_kid + a)];
+      // a chance node's children are all terminal (after an all-in) or all inner
+      if (nd.type == kChance && is_terminal(kid) != is_terminal(g.nodes[(size_t)nd.first_kid])) fine = false;
+      todo.push_back(nd.first_kid + a);
+    }
   }
+  auto inner_kids = [&](int n) {
+    const NodeDev& nd = g.nodes[(size_t)n];
+    int c = 0;
+    for (int a = 0; a < nd.n_kids; ++a) c += !is_terminal(g.nodes[(size_t)(nd.first_kid + a)]);
+    return c;
+  };
   int sp = 1, most = 1, amax = 0;
-  for (int n : pre) {  // top-down: pop the node's reach, push its children's
-    sp += g.nodes[(size_t)n].n_kids - 1;
+  for (int n : pre) {  // top-down: pop the node's reach, push its inner children's
+    sp += inner_kids(n) - 1;
     most = std::max(most, sp);
     if (g.nodes[(size_t)n].type == kDecision) amax = std::max(amax, (int)g.nodes[(size_t)n].n_kids);
   }
   sp = 0;
-  for (size_t k = pre.size(); k-- > 0;) {  // bottom-up: pop the children's values, push the node's
-    sp += 1 - g.nodes[(size_t)pre[k]].n_kids;
-    most = std::max(most, sp + g.nodes[(size_t)pre[k]].n_kids - 1);
+  for (size_t k = pre.size(); k-- > 0;) {  // bottom-up: pop the inner children's values, push the node's
+    sp += 1 - inner_kids(pre[k]);
     most = std::max(most, sp);
   }
   *depth = most;
   *max_actions = amax;
+  *ok = fine;
   return pre;
 }
 
@@ -525,41 +539,67 @@ std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& p
   out.reserve(pre.size());
   for (int n : pre) {
     const NodeDev& nd = g.nodes[(size_t)n];
+    uint32_t tmask = 0;  // chance nodes: bit 0 when all children are terminal
+    for (int a = 0; a < nd.n_kids && a < (nd.type == kChance ? 1 : 8); ++a)
+      if (is_terminal(g.nodes[(size_t)(nd.first_kid + a)])) tmask |= 1u << a;
     ProgOp op;
-    op.node = n;
-    op.row = nd.row;
-    op.code = (uint32_t)nd.type | (uint32_t)nd.player << 8 | (uint32_t)nd.n_kids << 16 | (uint32_t)nd.deal << 24;
+    op.node_off = n * g.hstride;
+    op.row_off = nd.type == kDecision ? nd.row * g.hstride : 0;
+    op.code = (uint32_t)(nd.type & 3u) | (uint32_t)(nd.player & 1u) << 2 | (uint32_t)(nd.n_kids & 63u) << 3 |
+              (uint32_t)nd.deal << 9 | tmask << 17;
     op.first_kid = nd.first_kid;
     out.push_back(op);
   }
   return out;
 }
 
-std::vector<int32_t> stream_chunks(const HostGame& g, const std::vector<int32_t>& pre, int half, int off[4],
-                                   int count[4]) {
-  std::vector<int32_t> out;
+std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half,
+                                   std::vector<uint32_t>& units, int unit_off[4], int unit_count[4],
+                                   int chunk_off[4], int chunk_count[4]) {
+  std::vector<int32_t> chunks;
+  units.clear();
   const int N = (int)pre.size();
+  const uint32_t S = (uint32_t)g.hstride;
   for (int q = 0; q < 4; ++q) {
     const int p = q & 1;
     const bool backward = q < 2;
-    off[q] = (int)out.size();
-    out.push_back(0);
+    unit_off[q] = (int)units.size();
+    chunk_off[q] = (int)chunks.size() / 2;
     int used = 0;
     for (int k = 0; k < N; ++k) {
-      const NodeDev& nd = g.nodes[(size_t)pre[(size_t)(backward ? N - 1 - k : k)]];
-      int units = 0;
-      if (nd.type == kDecision && nd.player == p) units = backward ? 2 * nd.n_kids + 1 : nd.n_kids;
-      if (backward && (nd.type == kFold || nd.type == kShowdown)) units = 1;
-      if (used + units > half) {
-        out.push_back(k);
+      const int n = pre[(size_t)(backward ? N - 1 - k : k)];
+      const std::vector<uint32_t> mine = node_loads(g, n, p, backward, S);
+      if (k == 0 || used + (int)mine.size() > half) {
+        chunks.push_back(k);
+        chunks.push_back((int)units.size() - unit_off[q]);
         used = 0;
       }
-      used += units;
+      used += (int)mine.size();
+      units.insert(units.end(), mine.begin(), mine.end());
     }
-    count[q] = (int)out.size() - off[q];
-    out.push_back(N);
+    unit_count[q] = (int)units.size() - unit_off[q];
+    chunk_count[q] = (int)chunks.size() / 2 - chunk_off[q];
+    chunks.push_back(N);
+    chunks.push_back(unit_count[q]);
   }
-  return out;
+  return chunks;
+}
+
+std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S) {
+  std::vector<uint32_t> mine;
+  const NodeDev& nd = g.nodes[(size_t)n];
+  if (backward)  // values of the terminal children, in child order
+    for (int a = 0; a < nd.n_kids; ++a)
+      if (is_terminal(g.nodes[(size_t)(nd.first_kid + a)]))
+        mine.push_back(kArrCfv << 30 | (uint32_t)(nd.first_kid + a) * S);
+  if (nd.type == kDecision && nd.player == p) {
+    for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrR << 30 | (uint32_t)(nd.row + a) * S);
+    if (backward) {
+      for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrS << 30 | (uint32_t)(nd.row + a) * S);
+      mine.push_back(kArrReach << 30 | (uint32_t)n * S);
+    }
+  }
+  return mine;
 }
 
 }  // namespace pcfr

@@ -42,26 +42,34 @@ std::vector<int32_t> decision_nodes(const HostGame& g, int begin[3]);
 // Decision node owning each regret row.
 std::vector<int32_t> row_nodes(const HostGame& g);
 
-// Program of the one-warp-per-32-hands schedule: the nodes in depth-first pre-order
-// (children in their natural order).  Walked forwards it is a top-down order in which a
-// stack of reach values pops each node's reach and pushes its children's (child 0 on top);
-// walked backwards it is a bottom-up order in which a stack of values pushes each node's
-// value and pops its children's in the order 0, 1, ...  `depth` receives the deepest either
-// stack gets, `max_actions` the most actions at any decision node.
-std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions);
+// Program of the one-warp-per-32-hands schedule: the inner (decision and chance) nodes in
+// depth-first pre-order, children in their natural order; terminal nodes are handled by
+// their parents.  Walked forwards it is a top-down order in which a stack of reach values
+// pops each node's reach and pushes its inner children's (child 0 on top); walked backwards
+// it is a bottom-up order in which a stack of values pushes each node's value and pops its
+// inner children's in the order 0, 1, ...  `depth` receives the deepest either stack gets,
+// `max_actions` the most actions at a decision node, `ok` whether the tree suits the
+// schedule (its root is inner and chance nodes have no terminal children).
+std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions, bool* ok);
+
+// Loads of node n in a pass of the stream schedule for player p (StreamArray << 30 |
+// element offset, hstride S): bottom-up, the values of its terminal children and, at p's
+// decision nodes, R and S of each action and p's reach; top-down, R of each action at p's
+// decision nodes.
+std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S);
 
 // The program as the stream kernel reads it: one ProgOp per node in pre-order.
 std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& pre);
 
-// Load chunks of the stream schedule: the program cut into runs of consecutive nodes whose
-// rows fit half of a warp's prefetch ring (`half` 8-byte units per lane), so that one run
-// can load while the previous one computes.  Four lists, one after the other in the result:
-// the bottom-up pass of player 0 and of player 1 (units per node: 2A + 1 at the player's
-// decision nodes for R, S and the reach; 1 at terminals for the value) and the top-down pass
-// of player 0 and of player 1 (A at the player's decision nodes for R).  List q holds the
-// program positions where its chunks start, then the program length; off[q] is where it
-// begins in the result and count[q] its number of chunks.
-std::vector<int32_t> stream_chunks(const HostGame& g, const std::vector<int32_t>& pre, int half, int off[4],
-                                   int count[4]);
+// Load tables of the stream schedule, four passes: the bottom-up pass of player 0 and of
+// player 1 and the top-down pass of player 0 and of player 1 (node_loads).  `units` receives each pass's
+// loads in the order the pass uses them (StreamArray << 30 | element offset), unit_off[q] /
+// unit_count[q] where pass q's begin and how many; the result holds each pass's chunks --
+// runs of consecutive nodes whose loads fit `half` units -- as (first node position, first
+// unit) pairs followed by (program length, unit count), chunk_off[q] (in pairs) and
+// chunk_count[q] where pass q's begin and how many.
+std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half,
+                                   std::vector<uint32_t>& units, int unit_off[4], int unit_count[4],
+                                   int chunk_off[4], int chunk_count[4]);
 
 }  // namespace pcfr
