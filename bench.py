@@ -414,15 +414,18 @@ def run_ours(args):
 
     target = None
     if batch:
-        need = time_to_target(capi, tree, G, max_iters=ips, every=10, target_mbb=1.0)
-        got = sorted(x for x in need if x is not None)
-        pct = (lambda q: None if len(got) < G else got[min(G - 1, int(q * G))])
-        target = {"target_mbb_per_hand": 1.0, "reached": len(got), "of": G, "checked_every_iters": 10,
-                  "iters_p50": pct(0.50), "iters_p99": pct(0.99),
-                  "ms_p50": None if pct(0.50) is None else pct(0.50) * ms_per_iter,
-                  "ms_p99": None if pct(0.99) is None else pct(0.99) * ms_per_iter,
+        limit = 4 * ips
+        need = time_to_target(capi, tree, G, max_iters=limit, every=10, target_mbb=1.0)
+        ranked = sorted(x if x is not None else float("inf") for x in need)
+        pct = (lambda q: ranked[min(G - 1, int(q * G))])
+        fmt = (lambda x: None if x == float("inf") else x)
+        target = {"target_mbb_per_hand": 1.0, "reached": sum(x is not None for x in need), "of": G,
+                  "checked_every_iters": 10, "limit_iters": limit,
+                  "iters_p50": fmt(pct(0.50)), "iters_p99": fmt(pct(0.99)),
+                  "ms_p50": None if fmt(pct(0.50)) is None else pct(0.50) * ms_per_iter,
+                  "ms_p99": None if fmt(pct(0.99)) is None else pct(0.99) * ms_per_iter,
                   "note": "iterations of the whole batch (all subgames advance together) times the "
-                          "measured ms per batch iteration"}
+                          "measured ms per batch iteration; null = not reached within limit_iters"}
 
     # end to end through the C ABI with host buffers: inputs from pinned host memory,
     # create + solve + exploitability + read of each root's average strategy, every step

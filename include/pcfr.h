@@ -226,6 +226,16 @@ int cfr_stage_times(cfr_tree* tree, int n_iters, double* ms, int64_t* launches);
  * to device when the handle was created. */
 int cfr_counters(const cfr_tree* tree, int64_t* kernel_launches, int64_t* device_bytes, int64_t* h2d_bytes);
 
+/* One dense layer of the depth-limit leaf network (Section 3, depth-limited solving; the
+ * paper's Stage 5 evaluates the network on the GPU, Section 4.3), on the tensor cores:
+ * C = act(A B^T + bias).  All pointers are device memory: A [M][K] and B [N][K] BF16
+ * row-major (16-byte aligned), bias [N] FP32 or NULL, C [M][N] BF16 (out_f32 = 0) or FP32.
+ * act = 1 applies GELU (0.5 x (1 + erf(x / sqrt 2))), 0 none.  N must be a multiple of 128
+ * and K of 64 (CFR_EINVAL otherwise).  Asynchronous on `stream` (a cudaStream_t or NULL);
+ * *err (a device int) is set to 1 if a bounded device-side wait gave up. */
+int cfr_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
+                  int out_f32, int* err, void* stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void cfr_tree_destroy(cfr_tree* tree);
 

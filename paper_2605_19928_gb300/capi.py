@@ -30,7 +30,8 @@ CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
-           "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule")
+           "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule",
+           "cfr_gemm_bf16")
 
 
 class CfrError(RuntimeError):
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
         lib.cfr_reset.argtypes = [P]
         lib.cfr_exploitability_noalloc.argtypes = [P, pd, pd]
         lib.cfr_schedule.argtypes = [P]
+        lib.cfr_gemm_bf16.argtypes = [P, P, P, P, I, I, I, I, I, P, P]
         lib.cfr_tree_destroy.argtypes = [P]
         lib.cfr_tree_destroy.restype = None
         lib.cfr_last_error.restype = C.c_char_p
@@ -221,6 +223,18 @@ def cfr_iterate(tree, n_iters: int = 1):
 
 def cfr_sync(tree):
     _check(load().cfr_sync(tree))
+
+
+def cfr_gemm_bf16(A, B, bias, C, act: bool, err, stream=None):
+    """C = act(A B^T + bias) on the tensor cores; A [M, K] and B [N, K] bfloat16 CUDA tensors,
+    bias float32 [N] or None, C bfloat16 or float32 [M, N], err an int32 CUDA tensor."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert B.shape[1] == K and tuple(C.shape) == (M, N)
+    import torch
+    out_f32 = C.dtype == torch.float32
+    _check(load().cfr_gemm_bf16(A.data_ptr(), B.data_ptr(), None if bias is None else bias.data_ptr(), C.data_ptr(),
+                                M, N, K, int(bool(act)), int(out_f32), err.data_ptr(), _stream_arg(stream)))
 
 
 def cfr_schedule(tree) -> int:

@@ -772,6 +772,20 @@ int cfr_counters(const cfr_tree* t, int64_t* kernel_launches, int64_t* device_by
   return CFR_OK;
 }
 
+int cfr_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
+                  int out_f32, int* err, void* stream) {
+  if (!A || !B || !C || !err) return fail(CFR_EINVAL, "A, B, C and err are required");
+  int rc = check_device();
+  if (rc) return rc;
+  static const int configured = configure_gemm();
+  if (configured != 0) return fail(CFR_ECUDA, "GEMM kernel attribute setup failed");
+  const int r = launch_gemm_bf16(A, B, bias, C, M, N, K, act, out_f32, err, stream);
+  if (r == -2) return fail(CFR_EINVAL, "cfr_gemm_bf16: N must be a multiple of 128, K of 64, pointers 16-byte aligned");
+  if (r == -3) return fail(CFR_ECUDA, "cfr_gemm_bf16: no tensor-map encoder in the driver");
+  if (r != 0) return fail(CFR_ECUDA, "cfr_gemm_bf16: launch failed");
+  return CFR_OK;
+}
+
 void cfr_tree_destroy(cfr_tree* t) { delete t; }
 
 const char* cfr_last_error(void) { return g_last_error.c_str(); }

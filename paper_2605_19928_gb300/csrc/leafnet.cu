@@ -1,0 +1,278 @@
+// Dense layers of the depth-limit leaf network (Section 3, depth-limited solving; Stage 5,
+// Section 4.3): C = act(A B^T + bias) with A the [M][K] BF16 activations, B the [N][K] BF16
+// weights (both K-major), FP32 accumulation on the 5th-generation tensor cores.
+//
+// One CTA computes a 128 x 128 tile of C:
+//   * warp 0 allocates 128 TMEM columns (the FP32 accumulator: lane = row, column = col)
+//     and, from one lane, streams 128 x 64 tiles of A and B into a 4-stage ring of shared
+//     memory with TMA (128-byte swizzle, the layout the MMA descriptors below describe);
+//   * one lane of warp 1 issues tcgen05.mma (M 128, N 128, K 16 per instruction, four per
+//     64-wide stage) and commits each stage back to its "empty" barrier;
+//   * after the last commit, all four warps read their 32-lane quarter of the accumulator
+//     with tcgen05.ld, add the bias, apply GELU (hidden layers) and store BF16 or FP32.
+// Every mbarrier wait is bounded; a wait that gives up sets *err and the CTA stops issuing.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "pcfr_internal.h"
+
+namespace pcfr {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kTileBytes = kBM * kBK * 2;  // 16 KB, one A or one B stage
+constexpr int kGemmThreads = 128;
+constexpr long kGemmWaitLimit = 1l << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool bar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  for (long k = 0; k < kGemmWaitLimit; ++k)
+    if (bar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 64 BF16
+// (128 bytes), 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1,
+// layout type 2 (128-byte swizzle).  The tile starts 1024-byte aligned; the K offset within
+// the 128-byte row is added to the start address (32 bytes per MMA step of K = 16).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3fffu);   // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused with swizzle): 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 1024 B between 8-row groups
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N = kBN, M = kBM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ uint16_t to_bf16(float x) {  // round to nearest even (finite inputs)
+  uint32_t u = __float_as_uint(x);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                const float* __restrict__ bias, void* __restrict__ out, int M, int N, int K, int act, int out_f32,
+                int* err) {
+  extern __shared__ __align__(1024) unsigned char smg[];
+  // 1024-byte aligned stage buffers: A stages, then B stages
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smg) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sa = base;
+  unsigned char* sb = base + kStages * kTileBytes;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int kb_count = K / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&done, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    for (int kb = 0; kb < kb_count; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t round = (uint32_t)(kb / kStages);
+      if (!bar_wait(&empty[s], (round & 1u) ^ 1u)) {
+        failed = 1;
+        break;
+      }
+      bar_expect_tx(&full[s], 2 * kTileBytes);
+      tma_load_2d(sa + s * kTileBytes, &map_a, kb * kBK, m0, &full[s]);
+      tma_load_2d(sb + s * kTileBytes, &map_b, kb * kBK, n0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    for (int kb = 0; kb < kb_count; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t round = (uint32_t)(kb / kStages);
+      if (!bar_wait(&full[s], round & 1u)) {
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(sa + s * kTileBytes), b0 = smem_addr(sb + s * kTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        mma_bf16(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+    }
+    mma_commit(&done);  // every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
+  const bool ok = bar_wait(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok || failed) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else {
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < kBN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        const int col = n0 + c0;
+        float y[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          y[j] = __uint_as_float(v[j]) + (bias ? bias[col + j] : 0.f);
+          if (act) y[j] = gelu(y[j]);
+        }
+        if (out_f32) {
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)row * N + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+        } else {
+          uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + (size_t)row * N + col);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              w[e] = (uint32_t)to_bf16(y[8 * j + 2 * e]) | ((uint32_t)to_bf16(y[8 * j + 2 * e + 1]) << 16);
+            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// Row-major [rows][cols] BF16 matrix, 128 x 64 boxes with 128-byte swizzle.
+bool encode(CUtensorMap* map, const void* ptr, int rows, int cols) {
+  EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t gemm_smem_bytes() { return (size_t)2 * kStages * kTileBytes + 1024; }
+
+int configure_gemm() {
+  return cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes()) ==
+                 cudaSuccess
+             ? 0
+             : -1;
+}
+
+int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
+                     int out_f32, int* err, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || N % kBN || K % kBK) return -2;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) return -2;
+  CUtensorMap ma, mb;
+  if (!encode(&ma, A, M, K) || !encode(&mb, B, N, K)) return -3;
+  const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / kBN));
+  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(), (cudaStream_t)stream>>>(ma, mb, bias, C, M, N, K, act, out_f32,
+                                                                               err);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of k_gemm_bf16 failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
+  return 0;
+}
+
+}  // namespace pcfr

@@ -193,6 +193,12 @@ int hand_kernel_smem_limit();
 // Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
+// Dense layer of the leaf network (leafnet.cu): C[M][N] = act(A[M][K] B[N][K]^T + bias), BF16
+// A and B, FP32 accumulation, C in BF16 (out_f32 = 0) or FP32; N a multiple of 128, K of 64.
+// Returns 0, -1 (launch failed), -2 (bad shape or alignment), -3 (no tensor-map encoder).
+int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
+                     int out_f32, int* err, void* stream);
+int configure_gemm();
 // Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes)
 // and one player's load descriptors (prog_units), a prefetch ring of 2 x half 8-byte units
 // and a stack of `depth` slots (es bytes) per lane.
