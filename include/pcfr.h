@@ -43,7 +43,7 @@ extern "C" {
 
 enum { CFR_GAME_HOLDEM = 0, CFR_GAME_KUHN = 1, CFR_GAME_LEDUC = 2 };
 enum { CFR_VARIANT_CFR = 0, CFR_VARIANT_CFRPLUS = 1, CFR_VARIANT_DCFR = 2 };
-enum { CFR_NODE_DECISION = 0, CFR_NODE_FOLD = 1, CFR_NODE_SHOWDOWN = 2, CFR_NODE_CHANCE = 3 };
+enum { CFR_NODE_DECISION = 0, CFR_NODE_FOLD = 1, CFR_NODE_SHOWDOWN = 2, CFR_NODE_CHANCE = 3, CFR_NODE_LEAF = 4 };
 enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_CFV = 3 };
 
 /*
@@ -66,6 +66,10 @@ enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_
  *               x facing a call of d raises by d + x * (pot + d); sizes reaching the stack
  *               become all-in; duplicates are dropped.
  *   max_raises  bets plus raises allowed per street (the opening bet counts).
+ *   depth_limit 0: solve to the end of the game (exact).  1 (turn subgames): the tree stops
+ *               at the river card (Section 3, depth-limited solving): every chance node
+ *               with chips behind becomes a CFR_NODE_LEAF whose values the leaf network
+ *               gives (cfr_set_leaf_net); all-in run-outs stay exact.
  */
 typedef struct cfr_game_spec {
   int game;
@@ -81,6 +85,7 @@ typedef struct cfr_game_spec {
   int n_bet_sizes;
   const double* bet_sizes;
   int max_raises;
+  int depth_limit;
 } cfr_game_spec;
 
 /*
@@ -210,6 +215,9 @@ int cfr_sync(cfr_tree* tree);
  *   CFR_STAGE_AVG_REACH   average strategy and its forward reach, both players
  *   CFR_STAGE_BR_TERMINAL terminal values against the average strategy, both players
  *   CFR_STAGE_BR          best-response backward pass and FP64 root reduction, both players
+ *   CFR_STAGE_LEAF        depth-limit leaves (Stage 5): network inputs, the four dense layers
+ *                         and the leaf values (one launch sequence per player update, and
+ *                         one for both players in the exploitability pass)
  * Synchronises. */
 enum {
   CFR_STAGE_TERMINAL = 0,
@@ -217,7 +225,8 @@ enum {
   CFR_STAGE_AVG_REACH = 2,
   CFR_STAGE_BR_TERMINAL = 3,
   CFR_STAGE_BR = 4,
-  CFR_N_STAGES = 5
+  CFR_STAGE_LEAF = 5,
+  CFR_N_STAGES = 6
 };
 int cfr_stage_times(cfr_tree* tree, int n_iters, double* ms, int64_t* launches);
 
@@ -225,6 +234,36 @@ int cfr_stage_times(cfr_tree* tree, int n_iters, double* ms, int64_t* launches);
  * replays count every kernel they contain), device bytes allocated, and bytes copied host
  * to device when the handle was created. */
 int cfr_counters(const cfr_tree* tree, int64_t* kernel_launches, int64_t* device_bytes, int64_t* h2d_bytes);
+
+/* The depth-limit leaf network (Section 3, depth-limited solving; evaluated in one batch per
+ * player update, Stage 5, Section 4.3) of a handle whose trees have CFR_NODE_LEAF nodes.
+ * Four dense layers, BF16 weights W[k] row-major [out][in] and FP32 biases b[k]:
+ *   layer 1: 2752 -> 512, GELU     layer 2: 512 -> 512, GELU
+ *   layer 3: 512 -> 512, GELU      layer 4: 512 -> 2688
+ * Input (per leaf and river card r): both players' reach at the leaf over the 1326 two-card
+ * slots (slot of cards a < b: b (b - 1) / 2 + a), each normalised to sum 1 over the hands
+ * not holding r; a one-hot of the five board cards (offset 2652); pot / (pot + 2 stack) and
+ * stack / (pot + 2 stack) at the leaf (offsets 2704, 2705); zeros up to 2752.  Output:
+ * player 0's then player 1's value per unit pot over the slots (offsets 0 and 1326).  The
+ * value of hand h of player i at leaf n is pot(n) P(r) kappa sum over r not in h of
+ * output_i,r(h) times the opponent reach over hands sharing no card with h or r.  Host
+ * buffers, copied (synchronises).  Must be set before cfr_iterate on such a handle. */
+int cfr_set_leaf_net(cfr_tree* tree, const uint16_t* const W[4], const float* const b[4]);
+
+/* Evaluate the leaf network once on the current state (the reach the next player update
+ * would see; average != 0: under the average strategy, as the exploitability pass does)
+ * and store both players' leaf values (CFR_READ_CFV, or CFR_READ_BR_CFV with average), so
+ * that one evaluation can be inspected with cfr_read_leaf_rows.  Synchronises. */
+int cfr_eval_leaves(cfr_tree* tree, int average);
+
+/* Depth-limit leaves of a handle: *n_leaves their count (any out pointer may be NULL); for
+ * leaf 0 .. n_leaves-1 (leaf < 0: count only) its game, node and first network row.  A
+ * leaf's 48 rows follow the river cards not on its board in ascending order. */
+int cfr_leaf_info(const cfr_tree* tree, int leaf, int* n_leaves, int* game, int* node, int* row0);
+
+/* Read network rows of the last leaf evaluation into a host buffer (synchronises):
+ * what 0 = inputs (n_rows x 2752 BF16 as uint16), 1 = outputs (n_rows x 2688 FP32). */
+int cfr_read_leaf_rows(cfr_tree* tree, int what, int row0, int n_rows, void* out);
 
 /* One dense layer of the depth-limit leaf network (Section 3, depth-limited solving; the
  * paper's Stage 5 evaluates the network on the GPU, Section 4.3), on the tensor cores:

@@ -45,11 +45,11 @@
 #include <string.h>
 
 enum { G_HOLDEM = 0, G_KUHN = 1, G_LEDUC = 2 };
-enum { T_DEC = 0, T_FOLD = 1, T_SHOW = 2, T_CHANCE = 3 };
+enum { T_DEC = 0, T_FOLD = 1, T_SHOW = 2, T_CHANCE = 3, T_LEAF = 4 };
 enum { V_CFR = 0, V_CFRPLUS = 1, V_DCFR = 2 };
 
 typedef struct {
-  int type;        /* T_DEC, T_FOLD, T_SHOW, T_CHANCE */
+  int type;        /* T_DEC, T_FOLD, T_SHOW, T_CHANCE, T_LEAF */
   int player;      /* acting player (decision) or folding player (fold) */
   int parent;      /* -1 at the root */
   int paction;     /* index of this node among its parent's children */
@@ -61,6 +61,7 @@ typedef struct {
   int board[5];    /* public cards at this node */
   int deal;        /* card dealt by a chance parent, else -1 */
   int row;         /* decision nodes: first regret row */
+  double* leafy;   /* depth-limit leaves: network outputs [ncards][2][nh] (set from outside) */
 } Node;
 
 typedef struct Oracle {
@@ -79,6 +80,7 @@ typedef struct Oracle {
   double alpha, beta, gamma;
   int alternating;
   int nthreads;
+  int depth_limit;       /* 1: a river chance node with chips behind is a leaf */
 
   Node* nodes;
   int nn, ncap;
@@ -131,6 +133,8 @@ static int build_street_end(Oracle* o, int parent, int paction, int street, cons
                             const int* board, int deal) {
   if (street + 1 >= o->nstreets)
     return new_node(o, T_SHOW, -1, parent, paction, street, c, nboard, board, deal);
+  if (o->depth_limit && o->game == G_HOLDEM && !(c[0] >= o->cap || c[1] >= o->cap))
+    return new_node(o, T_LEAF, -1, parent, paction, street, c, nboard, board, deal);
   int id = new_node(o, T_CHANCE, -1, parent, paction, street, c, nboard, board, deal);
   int live[64], nlive = 0;
   for (int card = 0; card < o->deck; ++card) {
@@ -246,12 +250,29 @@ static double utility(const Oracle* o, const Node* n, int i, int hi, int ho) {
 
 static int hand_has(const Oracle* o, int h, int card) { return (int)((o->hmask[h] >> card) & 1u); }
 
+/* Depth-limit leaf (Section 3): the river card is dealt by chance, 1/K each of the K cards
+ * left given both hands, and the network's value per unit pot of player i's hand on the
+ * completed board stands for the rest of the game: u_i = sum_r (1/K) pot y_i^r(h_i). */
+static double leaf_utility(const Oracle* o, const Node* n, int i, int hi, int ho) {
+  if (!n->leafy) return 0.0;
+  uint64_t dead = o->hmask[hi] | o->hmask[ho];
+  uint64_t on = 0;
+  for (int k = 0; k < n->nboard; ++k) on |= 1ull << n->board[k];
+  double K = (double)(o->deck - n->nboard - 2 * o->hsize), pot = n->c[0] + n->c[1], u = 0.0;
+  for (int card = 0, r = 0; card < o->deck; ++card) {
+    if ((on >> card) & 1u) continue;
+    if (!((dead >> card) & 1u)) u += n->leafy[((size_t)r * 2 + (size_t)i) * o->nh + (size_t)hi];
+    ++r;
+  }
+  return u * pot / K;
+}
+
 /* ------------------------------------------------------------------ creation */
 
 Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* cards, const double* r0,
                     const double* r1, const int* strength, int nstr, double pot, double stack, int nsizes,
                     const double* sizes, int max_raises, int variant, double alpha, double beta, double gamma,
-                    int alternating, int nthreads) {
+                    int alternating, int nthreads, int depth_limit) {
   g_err[0] = 0;
   if (nh <= 0 || !cards || !r0 || !r1) {
     snprintf(g_err, sizeof g_err, "empty hand list or range");
@@ -267,6 +288,7 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
   o->alternating = alternating;
   o->nthreads = nthreads < 1 ? 1 : nthreads;
   o->max_raises = max_raises;
+  o->depth_limit = depth_limit;
   int start_board[5] = {0};
   int nb0 = 0;
   if (game == G_KUHN) {
@@ -352,7 +374,10 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
 
 void ocfr_destroy(Oracle* o) {
   if (!o) return;
-  for (int n = 0; n < o->nn; ++n) free(o->nodes[n].kids);
+  for (int n = 0; n < o->nn; ++n) {
+    free(o->nodes[n].kids);
+    free(o->nodes[n].leafy);
+  }
   free(o->nodes);
   free(o->cards); free(o->hmask); free(o->r[0]); free(o->r[1]); free(o->strength);
   free(o->R); free(o->S); free(o->sig); free(o->prof); free(o->rinst);
@@ -416,6 +441,8 @@ static double walk(const Walk* w, int node, const int hands[2], double pi0, doub
   double u;
   if (n->type == T_FOLD || n->type == T_SHOW) {
     u = utility(o, n, i, hands[i], hands[1 - i]);
+  } else if (n->type == T_LEAF) {
+    u = leaf_utility(o, n, i, hands[i], hands[1 - i]);
   } else if (n->type == T_CHANCE) {
     uint64_t dead = o->hmask[hands[0]] | o->hmask[hands[1]];
     for (int k = 0; k < n->nboard; ++k) dead |= 1ull << n->board[k];
@@ -622,11 +649,12 @@ static double br_rec(const BRWork* w, int node, int h) {
   const Node* n = &o->nodes[node];
   int i = w->i;
   double v = 0.0;
-  if (n->type == T_FOLD || n->type == T_SHOW) {
+  if (n->type == T_FOLD || n->type == T_SHOW || n->type == T_LEAF) {
     const unsigned char* cm = o->compat + (size_t)h * o->nh;
     const double* q = w->q + (size_t)node * o->nh;
     for (int ho = 0; ho < o->nh; ++ho)
-      if (cm[ho] && q[ho] != 0.0) v += q[ho] * utility(o, n, i, h, ho);
+      if (cm[ho] && q[ho] != 0.0)
+        v += q[ho] * (n->type == T_LEAF ? leaf_utility(o, n, i, h, ho) : utility(o, n, i, h, ho));
     v /= o->Z;
   } else if (n->type == T_CHANCE) {
     /* the card probability is inside the opponent-and-chance reach q below this node */
@@ -718,6 +746,42 @@ double ocfr_exploitability(Oracle* o, double br_out[2]) {
   double b1 = ocfr_best_response(o, 1, NULL, NULL);
   if (br_out) { br_out[0] = b0; br_out[1] = b1; }
   return 0.5 * (b0 + b1);
+}
+
+/* ------------------------------------------------------------------ depth-limit leaves */
+
+/* Player p's own reach at `node` for every hand: p's range times p's action probabilities
+ * on the path (kind 0: current strategy, regret matching of R; kind 1: average strategy),
+ * zero for hands holding a card dealt on the path. */
+int ocfr_node_reach(Oracle* o, int kind, int p, int node, double* out) {
+  if (node < 0 || node >= o->nn) return -1;
+  double* prof = (double*)malloc(sizeof(double) * (size_t)o->nrows * o->nh);
+  if (kind == 0) regret_match(o, o->R, prof);
+  else average_strategy(o, prof);
+  for (int h = 0; h < o->nh; ++h) out[h] = o->r[p][h];
+  int path[256], len = 0;
+  for (int n = node; n > 0 && len < 256; n = o->nodes[n].parent) path[len++] = n;
+  for (int k = len - 1; k >= 0; --k) {
+    const Node* child = &o->nodes[path[k]];
+    const Node* par = &o->nodes[child->parent];
+    for (int h = 0; h < o->nh; ++h) {
+      if (par->type == T_DEC && par->player == p) out[h] *= prof[(size_t)(par->row + child->paction) * o->nh + h];
+      if (child->deal >= 0 && hand_has(o, h, child->deal)) out[h] = 0.0;
+    }
+  }
+  free(prof);
+  return 0;
+}
+
+/* Network outputs at a leaf: y [K][2][nh], one block per river card not on the leaf's board
+ * (ascending), per player the value per unit pot of each hand. */
+int ocfr_set_leaf_values(Oracle* o, int node, const double* y) {
+  if (node < 0 || node >= o->nn || o->nodes[node].type != T_LEAF) return -1;
+  Node* n = &o->nodes[node];
+  const size_t K = (size_t)(o->deck - n->nboard);
+  if (!n->leafy) n->leafy = (double*)malloc(sizeof(double) * K * 2 * (size_t)o->nh);
+  memcpy(n->leafy, y, sizeof(double) * K * 2 * (size_t)o->nh);
+  return 0;
 }
 
 /* ------------------------------------------------------------------ accessors */

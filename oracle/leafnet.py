@@ -68,3 +68,39 @@ def forward(x, layers) -> np.ndarray:
         y = dense(h, bf16_round(w), b, act=not last)
         h = y if last else bf16_round(y)
     return h
+
+
+SLOTS = 1326
+IN_FEATURES = 2 * SLOTS + 52 + 2
+IN_PADDED = 2752
+
+
+def pair_slot(a: int, b: int) -> int:
+    """Slot of the two-card hand {a, b}: b (b - 1) / 2 + a for a < b (all 1326 pairs)."""
+    a, b = min(a, b), max(a, b)
+    return b * (b - 1) // 2 + a
+
+
+def leaf_input(reach, hands, board, r: int, feat) -> np.ndarray:
+    """FP64 network input at a leaf for river card r: reach[p] is player p's reach per hand
+    (hands [n][2]), normalised to sum 1 over the hands not holding r (uniform over them if
+    that sum is 0) and placed at each hand's slot; then a one-hot of board + r; then the two
+    pot / stack features; zero padding to IN_PADDED."""
+    x = np.zeros(IN_PADDED, np.float64)
+    live = np.array([r not in (int(a), int(b)) for a, b in hands])
+    slots = np.array([pair_slot(int(a), int(b)) for a, b in hands])
+    for p in range(2):
+        q = np.where(live, np.asarray(reach[p], dtype=np.float64), 0.0)
+        s = q.sum()
+        v = q / s if s > 0 else live / live.sum()
+        x[p * SLOTS + slots[live]] = v[live]
+    for c in list(board) + [r]:
+        x[2 * SLOTS + int(c)] = 1.0
+    x[2 * SLOTS + 52] = feat[0]
+    x[2 * SLOTS + 53] = feat[1]
+    return x
+
+
+def leaf_features(pot: float, behind: float):
+    """pot / (pot + 2 behind) and behind / (pot + 2 behind) at a leaf."""
+    return pot / (pot + 2 * behind), behind / (pot + 2 * behind)

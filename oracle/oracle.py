@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-T_DEC, T_FOLD, T_SHOW, T_CHANCE = 0, 1, 2, 3
+T_DEC, T_FOLD, T_SHOW, T_CHANCE, T_LEAF = 0, 1, 2, 3, 4
 VARIANTS = {"cfr": 0, "cfr+": 1, "dcfr": 2}
 
 
@@ -46,7 +46,7 @@ def _load():
         pi = C.POINTER(C.c_int)
         pd = C.POINTER(C.c_double)
         lib.ocfr_create.restype = P
-        lib.ocfr_create.argtypes = [I, I, pi, I, pi, pd, pd, pi, I, D, D, I, pd, I, I, D, D, D, I, I]
+        lib.ocfr_create.argtypes = [I, I, pi, I, pi, pd, pd, pi, I, D, D, I, pd, I, I, D, D, D, I, I, I]
         lib.ocfr_destroy.argtypes = [P]
         lib.ocfr_error.restype = C.c_char_p
         lib.ocfr_iterate.argtypes = [P, I]
@@ -75,6 +75,10 @@ def _load():
         lib.ocfr_set_node_state.argtypes = [P, I, pd, pd]
         lib.ocfr_set_node_state.restype = I
         lib.ocfr_set_iterations.argtypes = [P, I]
+        lib.ocfr_node_reach.argtypes = [P, I, I, I, pd]
+        lib.ocfr_node_reach.restype = I
+        lib.ocfr_set_leaf_values.argtypes = [P, I, pd]
+        lib.ocfr_set_leaf_values.restype = I
         _lib = lib
         return lib
 
@@ -113,7 +117,7 @@ class Oracle:
                                   _ptr(r0, C.c_double), _ptr(r1, C.c_double), _ptr(strength, C.c_int), nstr,
                                   float(spec.pot), float(spec.stack), len(spec.bet_sizes), _ptr(sizes, C.c_double),
                                   int(spec.max_raises), VARIANTS[variant], alpha, beta, gamma, int(alternating),
-                                  self.threads)
+                                  self.threads, int(getattr(spec, "depth_limit", 0)))
         if not self._h:
             raise ValueError("oracle: " + lib.ocfr_error().decode())
         self.n_nodes = lib.ocfr_n_nodes(self._h)
@@ -208,6 +212,21 @@ class Oracle:
 
     def set_iterations(self, t: int):
         self._lib.ocfr_set_iterations(self._h, int(t))
+
+    def node_reach(self, kind: str, p: int, n: int) -> np.ndarray:
+        """Player p's own reach at node n per hand, under the current ("current") or average
+        ("average") strategy."""
+        out = np.zeros(self.n_hands, np.float64)
+        if self._lib.ocfr_node_reach(self._h, {"current": 0, "average": 1}[kind], p, n, _ptr(out, C.c_double)) != 0:
+            raise ValueError(f"bad node {n}")
+        return out
+
+    def set_leaf_values(self, n: int, y):
+        """Network outputs at depth-limit leaf n: y [K][2][n_hands], K the river cards not on
+        the leaf's board in ascending order, values per unit pot."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if self._lib.ocfr_set_leaf_values(self._h, n, _ptr(y, C.c_double)) != 0:
+            raise ValueError(f"node {n} is not a leaf")
 
     def values_current(self, i: int):
         """Counterfactual values of player i under the current strategy (no update)."""

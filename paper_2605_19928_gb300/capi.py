@@ -19,19 +19,22 @@ LIB_PATH = os.path.join(_PKG, "libpcfr.so")
 CFR_OK, CFR_EINVAL, CFR_ENOMEM, CFR_ECUDA, CFR_ETIMEOUT, CFR_ESTATE = 0, -1, -2, -3, -4, -5
 CFR_GAME_HOLDEM, CFR_GAME_KUHN, CFR_GAME_LEDUC = 0, 1, 2
 CFR_VARIANT_CFR, CFR_VARIANT_CFRPLUS, CFR_VARIANT_DCFR = 0, 1, 2
-CFR_NODE_DECISION, CFR_NODE_FOLD, CFR_NODE_SHOWDOWN, CFR_NODE_CHANCE = 0, 1, 2, 3
+CFR_NODE_DECISION, CFR_NODE_FOLD, CFR_NODE_SHOWDOWN, CFR_NODE_CHANCE, CFR_NODE_LEAF = 0, 1, 2, 3, 4
+LEAF_SLOTS, LEAF_IN, LEAF_HIDDEN, LEAF_OUT, LEAF_CARDS = 1326, 2752, 512, 2688, 48
+LEAF_SHAPES = ((LEAF_HIDDEN, LEAF_IN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_OUT, LEAF_HIDDEN))
 CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV = 0, 1, 2, 3
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
 CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM = 0, 1, 2
 SCHEDULES = {"auto": CFR_SCHEDULE_AUTO, "level": CFR_SCHEDULE_LEVEL, "stream": CFR_SCHEDULE_STREAM}
 VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR}
-CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br")
+CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br", "leaf")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
            "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule",
-           "cfr_gemm_bf16")
+           "cfr_gemm_bf16", "cfr_set_leaf_net", "cfr_leaf_info", "cfr_read_leaf_rows",
+           "cfr_eval_leaves")
 
 
 class CfrError(RuntimeError):
@@ -45,7 +48,7 @@ class cfr_game_spec(C.Structure):
                 ("hands", C.POINTER(C.c_uint8)), ("range", C.POINTER(C.c_float) * 2),
                 ("strength", C.POINTER(C.c_int32)), ("n_strength_rows", C.c_int), ("pot", C.c_double),
                 ("stack", C.c_double), ("n_bet_sizes", C.c_int), ("bet_sizes", C.POINTER(C.c_double)),
-                ("max_raises", C.c_int)]
+                ("max_raises", C.c_int), ("depth_limit", C.c_int)]
 
 
 class cfr_solver_opts(C.Structure):
@@ -91,6 +94,10 @@ def load(path: str = LIB_PATH):
         lib.cfr_exploitability_noalloc.argtypes = [P, pd, pd]
         lib.cfr_schedule.argtypes = [P]
         lib.cfr_gemm_bf16.argtypes = [P, P, P, P, I, I, I, I, I, P, P]
+        lib.cfr_set_leaf_net.argtypes = [P, C.POINTER(P), C.POINTER(P)]
+        lib.cfr_leaf_info.argtypes = [P, I, pi, pi, pi, pi]
+        lib.cfr_read_leaf_rows.argtypes = [P, I, I, I, P]
+        lib.cfr_eval_leaves.argtypes = [P, I]
         lib.cfr_tree_destroy.argtypes = [P]
         lib.cfr_tree_destroy.restype = None
         lib.cfr_last_error.restype = C.c_char_p
@@ -169,6 +176,7 @@ def make_spec(g) -> tuple[cfr_game_spec, tuple]:
     s.n_bet_sizes = int(sizes.size)
     s.bet_sizes = sizes.ctypes.data_as(C.POINTER(C.c_double))
     s.max_raises = int(g.max_raises)
+    s.depth_limit = int(getattr(g, "depth_limit", 0))
     return s, (board, hands, r0, r1, strength, sizes)
 
 
@@ -235,6 +243,47 @@ def cfr_gemm_bf16(A, B, bias, C, act: bool, err, stream=None):
     out_f32 = C.dtype == torch.float32
     _check(load().cfr_gemm_bf16(A.data_ptr(), B.data_ptr(), None if bias is None else bias.data_ptr(), C.data_ptr(),
                                 M, N, K, int(bool(act)), int(out_f32), err.data_ptr(), _stream_arg(stream)))
+
+
+def cfr_set_leaf_net(tree, weights, biases):
+    """weights: 4 arrays (bfloat16 bit patterns as uint16, or float32 rounded to BF16 here)
+    of shapes LEAF_SHAPES; biases: 4 float32 arrays."""
+    Ws, bs = [], []
+    for k, (w, b) in enumerate(zip(weights, biases)):
+        w = np.asarray(w)
+        if w.dtype != np.uint16:
+            f = np.ascontiguousarray(w, dtype=np.float32).reshape(-1).view(np.uint32).astype(np.uint64)
+            w = (((f + 0x7FFF + ((f >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16).reshape(w.shape)
+        assert w.shape == LEAF_SHAPES[k], (k, w.shape)
+        Ws.append(np.ascontiguousarray(w))
+        bs.append(np.ascontiguousarray(b, dtype=np.float32).reshape(LEAF_SHAPES[k][0]))
+    Wp = (C.c_void_p * 4)(*[w.ctypes.data for w in Ws])
+    bp = (C.c_void_p * 4)(*[b.ctypes.data for b in bs])
+    _check(load().cfr_set_leaf_net(tree, Wp, bp))
+
+
+def cfr_eval_leaves(tree, average: bool = False):
+    _check(load().cfr_eval_leaves(tree, int(bool(average))))
+
+
+def cfr_leaf_info(tree):
+    """[(game, node, row0)] of every depth-limit leaf."""
+    lib = load()
+    n = C.c_int()
+    _check(lib.cfr_leaf_info(tree, -1, C.byref(n), None, None, None))
+    out = []
+    for k in range(n.value):
+        g, nd, r0 = C.c_int(), C.c_int(), C.c_int()
+        _check(lib.cfr_leaf_info(tree, k, None, C.byref(g), C.byref(nd), C.byref(r0)))
+        out.append((g.value, nd.value, r0.value))
+    return out
+
+
+def cfr_read_leaf_rows(tree, what: int, row0: int, n_rows: int) -> np.ndarray:
+    """what 0: network inputs (uint16 BF16 bits [n_rows, LEAF_IN]); 1: outputs (float32 [n_rows, LEAF_OUT])."""
+    out = np.empty((n_rows, LEAF_IN), np.uint16) if what == 0 else np.empty((n_rows, LEAF_OUT), np.float32)
+    _check(load().cfr_read_leaf_rows(tree, int(what), int(row0), int(n_rows), out.ctypes.data))
+    return out
 
 
 def cfr_schedule(tree) -> int:

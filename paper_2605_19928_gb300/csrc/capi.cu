@@ -63,6 +63,9 @@ struct cfr_tree {
   int64_t state_gen = 0;        // bumped whenever R or S may change
   int64_t avg_gen = -1;         // state_gen for which sigbar holds k_average_rows' output
   int64_t cur_gen = -1;         // state_gen for which sigma holds RM(R) (stream schedule)
+  LeafCtx leaf{};               // depth-limit leaves and their network (none: n_leaves = 0)
+  std::vector<LeafDev> leaf_host;
+  bool leaf_net_set = false;
   int64_t launches = 0;         // kernels launched (graph replays included)
   int64_t device_bytes = 0;
   int64_t h2d_bytes = 0;
@@ -175,6 +178,75 @@ int check_device() {
   if (prop.major != 10 || prop.minor != 3)
     return fail(CFR_ECUDA, "libpcfr needs a compute capability 10.3 (GB300) device, found " +
                                std::to_string(prop.major) + "." + std::to_string(prop.minor));
+  return CFR_OK;
+}
+
+int leaf_launches(const cfr_tree* t, int player_mask);
+
+// Depth-limit leaves of every game: their network rows, features and slot maps, and the
+// network's activation and weight buffers (the weights arrive with cfr_set_leaf_net).
+int setup_leaves(cfr_tree* t, const cfr_game_spec* specs, int n_games) {
+  LeafCtx& L = t->leaf;
+  L = LeafCtx{};
+  int hmax = 0;
+  for (int g = 0; g < n_games; ++g) {
+    hmax = std::max(hmax, t->host[g].hstride);
+    const HostGame& h = t->host[g];
+    const double cap = specs[g].pot / 2.0 + specs[g].stack;
+    for (int n : h.leaves) {
+      LeafDev lf{};
+      lf.game = g;
+      lf.node = n;
+      lf.row0 = (int)t->leaf_host.size() * kLeafCards;
+      const double pot = h.contrib[2 * (size_t)n] + h.contrib[2 * (size_t)n + 1];
+      const double behind = cap - h.contrib[2 * (size_t)n];
+      lf.feat[0] = (float)(pot / (pot + 2.0 * behind));
+      lf.feat[1] = (float)(behind / (pot + 2.0 * behind));
+      t->leaf_host.push_back(lf);
+    }
+  }
+  if (t->leaf_host.empty()) return CFR_OK;
+  L.n_leaves = (int)t->leaf_host.size();
+  L.hstride_max = hmax;
+  std::vector<int16_t> slot((size_t)n_games * hmax, 0), hand_at((size_t)n_games * kLeafSlots, -1);
+  for (int g = 0; g < n_games; ++g) {
+    const HostGame& h = t->host[g];
+    if (h.hand_size != 2) continue;
+    for (int k = 0; k < h.n_hands; ++k) {
+      int a = h.hand_cards[2 * (size_t)k], b = h.hand_cards[2 * (size_t)k + 1];
+      if (a > b) std::swap(a, b);
+      const int sl = b * (b - 1) / 2 + a;
+      slot[(size_t)g * hmax + k] = (int16_t)sl;
+      hand_at[(size_t)g * kLeafSlots + sl] = (int16_t)k;
+    }
+  }
+  const size_t rows = (size_t)L.n_leaves * kLeafCards;
+  LeafDev* ld;
+  int16_t *sd, *hd;
+  int rc;
+  if ((rc = upload(t, t->leaf_host, &ld)) || (rc = upload(t, slot, &sd)) || (rc = upload(t, hand_at, &hd))) return rc;
+  L.leaves = ld;
+  L.slot = sd;
+  L.hand_at = hd;
+  uint16_t *x, *h1, *h2, *h3;
+  float* y;
+  if ((rc = zeros(t, rows * kLeafIn, &x)) || (rc = zeros(t, rows * kLeafHidden, &h1)) ||
+      (rc = zeros(t, rows * kLeafHidden, &h2)) || (rc = zeros(t, rows * kLeafHidden, &h3)) ||
+      (rc = zeros(t, rows * kLeafOut, &y)))
+    return rc;
+  L.X = x; L.H1 = h1; L.H2 = h2; L.H3 = h3; L.Y = y;
+  const size_t wn[4] = {(size_t)kLeafHidden * kLeafIn, (size_t)kLeafHidden * kLeafHidden,
+                        (size_t)kLeafHidden * kLeafHidden, (size_t)kLeafOut * kLeafHidden};
+  const size_t bn[4] = {(size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafOut};
+  for (int k = 0; k < 4; ++k) {
+    uint16_t* w;
+    float* b;
+    if ((rc = zeros(t, wn[k], &w)) || (rc = zeros(t, bn[k], &b))) return rc;
+    L.W[k] = w;
+    L.b[k] = b;
+  }
+  static const int gemm_ok = configure_gemm();
+  if (gemm_ok != 0) return fail(CFR_ECUDA, "GEMM kernel attribute setup failed");
   return CFR_OK;
 }
 
@@ -421,7 +493,12 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_prog = stream_prog;
   c.stream_half = stream_half;
   c.stream_units = stream_units;
-  t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1);
+  if ((rc = setup_leaves(t, specs, n_games))) {
+    delete t;
+    return rc;
+  }
+  t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1) +
+                              (o.alternating ? leaf_launches(t, 1) + leaf_launches(t, 2) : leaf_launches(t, 3));
   t->launches += 1;
   if (launch_init(c, stream) != 0) {
     delete t;
@@ -436,15 +513,33 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   return CFR_OK;
 }
 
-// One iteration: alternating = terminal + update for player 0, then for player 1.
+// Depth-limit leaves (Stage 5): network inputs from both players' reach at the leaves, the
+// four dense layers, then the leaf values of player 0, player 1 or both (mask 1, 2, 3).
+// Launches 1 + 4 + (1 or 2) kernels; none without leaves.
+int enqueue_leaves(cfr_tree* t, int player_mask, int use_bar, cudaStream_t s) {
+  const LeafCtx& L = t->leaf;
+  if (L.n_leaves == 0) return 0;
+  const LaunchCtx& c = t->ctx;
+  if (launch_leaf_inputs(c, L, use_bar, s) || launch_leaf_net(c, L, s)) return -1;
+  for (int p = 0; p < 2; ++p)
+    if (((player_mask >> p) & 1) && launch_leaf_values(c, L, p, use_bar, s)) return -1;
+  return 0;
+}
+
+int leaf_launches(const cfr_tree* t, int player_mask) {
+  return t->leaf.n_leaves == 0 ? 0 : 5 + (player_mask == 3 ? 2 : 1);
+}
+
+// One iteration: alternating = terminal + update for player 0, then for player 1 (each
+// preceded by the leaf network when the tree has depth-limit leaves).
 int enqueue_iteration(cfr_tree* t, cudaStream_t s) {
   const LaunchCtx& c = t->ctx;
   if (t->opts.alternating) {
-    if (launch_terminal(c, 1, 0, s) || launch_update(c, 1, 0, s) || launch_terminal(c, 2, 0, s) ||
-        launch_update(c, 2, 1, s))
+    if (enqueue_leaves(t, 1, 0, s) || launch_terminal(c, 1, 0, s) || launch_update(c, 1, 0, s) ||
+        enqueue_leaves(t, 2, 0, s) || launch_terminal(c, 2, 0, s) || launch_update(c, 2, 1, s))
       return -1;
   } else {
-    if (launch_terminal(c, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
+    if (enqueue_leaves(t, 3, 0, s) || launch_terminal(c, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
   }
   return 0;
 }
@@ -505,6 +600,7 @@ int cfr_batch_create(const cfr_game_spec* specs, int n_games, const cfr_solver_o
 
 int cfr_iterate(cfr_tree* t, int n_iters) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (t->leaf.n_leaves > 0 && !t->leaf_net_set) return fail(CFR_ESTATE, "the tree has leaves: set the leaf network first");
   if (n_iters < 0) return fail(CFR_EINVAL, "n_iters < 0");
   if (n_iters == 0) return CFR_OK;
   int rc0 = ensure_discounts(t, (int64_t)t->iters_done + n_iters);
@@ -572,8 +668,8 @@ int cfr_exploitability_async(cfr_tree* t) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
     const LaunchCtx& c = t->ctx;
-    const int rc = launch_avg_reach(c, t->capture) || launch_terminal(c, 3, 1, t->capture) ||
-                   launch_br(c, t->capture);
+    const int rc = launch_avg_reach(c, t->capture) || enqueue_leaves(t, 3, 1, t->capture) ||
+                   launch_terminal(c, 3, 1, t->capture) || launch_br(c, t->capture);
     cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
     if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -583,7 +679,7 @@ int cfr_exploitability_async(cfr_tree* t) {
   }
   t->avg_gen = -1;  // the pass rewrites sigbar with its own normalisation
   CK(cudaGraphLaunch(t->expl_graph, t->stream));
-  t->launches += t->ctx.n_term_work > 0 ? 3 : 2;
+  t->launches += (t->ctx.n_term_work > 0 ? 3 : 2) + leaf_launches(t, 3);
   return CFR_OK;
 }
 
@@ -700,6 +796,7 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
 
 int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (t->leaf.n_leaves > 0 && !t->leaf_net_set) return fail(CFR_ESTATE, "the tree has leaves: set the leaf network first");
   if (!ms || n_iters < 0) return fail(CFR_EINVAL, "bad arguments");
   const int drc = ensure_discounts(t, (int64_t)t->iters_done + n_iters);
   if (drc) return drc;
@@ -722,13 +819,21 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   for (int it = 0; it < n_iters && !rc && err == cudaSuccess; ++it) {
     if (t->opts.alternating) {
       for (int p = 0; p < 2 && !rc && err == cudaSuccess; ++p) {
-        rc = launch_terminal(c, 1 << p, 0, s);
+        if (t->leaf.n_leaves > 0) {
+          rc = enqueue_leaves(t, 1 << p, 0, s);
+          if (!rc) err = mark(CFR_STAGE_LEAF);
+        }
+        if (!rc && err == cudaSuccess) rc = launch_terminal(c, 1 << p, 0, s);
         if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
         if (!rc && err == cudaSuccess) rc = launch_update(c, 1 << p, p == 1, s);
         if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
       }
     } else {
-      rc = launch_terminal(c, 3, 0, s);
+      if (t->leaf.n_leaves > 0) {
+        rc = enqueue_leaves(t, 3, 0, s);
+        if (!rc) err = mark(CFR_STAGE_LEAF);
+      }
+      if (!rc && err == cudaSuccess) rc = launch_terminal(c, 3, 0, s);
       if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
       if (!rc && err == cudaSuccess) rc = launch_update(c, 3, 1, s);
       if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
@@ -736,6 +841,10 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   }
   if (!rc && err == cudaSuccess) rc = launch_avg_reach(c, s);
   if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_AVG_REACH);
+  if (!rc && err == cudaSuccess && t->leaf.n_leaves > 0) {
+    rc = enqueue_leaves(t, 3, 1, s);
+    if (!rc) err = mark(CFR_STAGE_LEAF);
+  }
   if (!rc && err == cudaSuccess) rc = launch_terminal(c, 3, 1, s);
   if (!rc && err == cudaSuccess && c.n_term_work > 0) err = mark(CFR_STAGE_BR_TERMINAL);
   if (!rc && err == cudaSuccess) rc = launch_br(c, s);
@@ -769,6 +878,65 @@ int cfr_counters(const cfr_tree* t, int64_t* kernel_launches, int64_t* device_by
   if (kernel_launches) *kernel_launches = t->launches;
   if (device_bytes) *device_bytes = t->device_bytes;
   if (h2d_bytes) *h2d_bytes = t->h2d_bytes;
+  return CFR_OK;
+}
+
+int cfr_set_leaf_net(cfr_tree* t, const uint16_t* const W[4], const float* const b[4]) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (t->leaf.n_leaves == 0) return fail(CFR_ESTATE, "the tree has no depth-limit leaves");
+  if (!W || !b) return fail(CFR_EINVAL, "W and b are required");
+  const size_t wn[4] = {(size_t)kLeafHidden * kLeafIn, (size_t)kLeafHidden * kLeafHidden,
+                        (size_t)kLeafHidden * kLeafHidden, (size_t)kLeafOut * kLeafHidden};
+  const size_t bn[4] = {(size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafOut};
+  for (int k = 0; k < 4; ++k) {
+    if (!W[k] || !b[k]) return fail(CFR_EINVAL, "every layer needs weights and a bias");
+    CK(cudaMemcpyAsync(const_cast<void*>(t->leaf.W[k]), W[k], wn[k] * 2, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(const_cast<float*>(t->leaf.b[k]), b[k], bn[k] * 4, cudaMemcpyHostToDevice, t->stream));
+  }
+  CK(cudaStreamSynchronize(t->stream));
+  t->leaf_net_set = true;
+  return CFR_OK;
+}
+
+int cfr_eval_leaves(cfr_tree* t, int average) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (t->leaf.n_leaves == 0) return fail(CFR_ESTATE, "the tree has no depth-limit leaves");
+  if (!t->leaf_net_set) return fail(CFR_ESTATE, "set the leaf network first");
+  if (average) {
+    if (launch_avg_reach(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "average launch failed");
+    t->avg_gen = -1;
+  }
+  if (enqueue_leaves(t, 3, average ? 1 : 0, t->stream) != 0) return fail(CFR_ECUDA, "leaf launch failed");
+  t->launches += (average ? 1 : 0) + leaf_launches(t, 3);
+  return cfr_sync(t);
+}
+
+int cfr_leaf_info(const cfr_tree* t, int leaf, int* n_leaves, int* game, int* node, int* row0) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  if (n_leaves) *n_leaves = t->leaf.n_leaves;
+  if (leaf < 0) return CFR_OK;
+  if (leaf >= t->leaf.n_leaves) return fail(CFR_EINVAL, "leaf index out of range");
+  const LeafDev& lf = t->leaf_host[(size_t)leaf];
+  if (game) *game = lf.game;
+  if (node) *node = lf.node;
+  if (row0) *row0 = lf.row0;
+  return CFR_OK;
+}
+
+int cfr_read_leaf_rows(cfr_tree* t, int what, int row0, int n_rows, void* out) {
+  if (!t) return fail(CFR_EINVAL, "tree is NULL");
+  const int rows = t->leaf.n_leaves * kLeafCards;
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > rows || (!out && n_rows)) return fail(CFR_EINVAL, "bad row range");
+  if (what == 0) {
+    CK(cudaMemcpyAsync(out, static_cast<const uint16_t*>(t->leaf.X) + (size_t)row0 * kLeafIn,
+                       (size_t)n_rows * kLeafIn * 2, cudaMemcpyDeviceToHost, t->stream));
+  } else if (what == 1) {
+    CK(cudaMemcpyAsync(out, t->leaf.Y + (size_t)row0 * kLeafOut, (size_t)n_rows * kLeafOut * 4,
+                       cudaMemcpyDeviceToHost, t->stream));
+  } else {
+    return fail(CFR_EINVAL, "what must be 0 (inputs) or 1 (outputs)");
+  }
+  CK(cudaStreamSynchronize(t->stream));
   return CFR_OK;
 }
 
@@ -914,7 +1082,7 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
   cudaStream_t s = t->stream;
   CK(cudaMemsetAsync(scratch + kStaticPartialBytes + kStaticOutBytes, 0, (size_t)c.n_games * sizeof(unsigned), s));
   t->avg_gen = -1;
-  if (launch_avg_reach(c, s) || launch_terminal(c, 3, 1, s) || launch_br(c, s))
+  if (launch_avg_reach(c, s) || enqueue_leaves(t, 3, 1, s) || launch_terminal(c, 3, 1, s) || launch_br(c, s))
     return fail(CFR_ECUDA, "exploitability launch failed");
   k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);
   CK(cudaGetLastError());

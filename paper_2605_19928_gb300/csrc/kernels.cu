@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
       for (int idx = slot; idx < cnt; idx += nslots) {
         const int n = a0 + idx;
         const NodeDev nd = nodes[n];
-        if (nd.type == kFold || nd.type == kShowdown) continue;
+        if (is_end(nd.type)) continue;
         const int A = nd.n_kids, k0 = nd.first_kid;
         V val;
         if (MODE == kModeBR && nd.type == kDecision && nd.player == p) {

@@ -275,4 +275,191 @@ int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, i
   return 0;
 }
 
+// ------------------------------------------------------------------ leaf inputs and values
+//
+// Depth-limit leaves (Section 3: a network maps both players' normalised reach and the public
+// state to counterfactual values; Stage 5 evaluates all leaves in one batch, Section 4.3).
+// Each leaf is a river-card chance node; the network is evaluated once per river card r
+// that is not on the board, on the board completed by r.  The value of hand h of player i
+// at leaf n is then
+//     v_i(n, h) = payoff(n) kappa  sum_{r not in h}  y_i^r(h) M_r(h)
+// with payoff(n) = pot at n x P(river card) (1/44 given both hands), y_i^r(h) the network's
+// value per unit pot of h, and M_r(h) the opponent reach at n over hands sharing no card
+// with h or r (inclusion-exclusion as at fold nodes, with the river card removed).
+
+namespace {
+
+constexpr int kLeafThreads = 256;
+
+template <typename V>
+__device__ __forceinline__ float vf(const V& x);
+template <>
+__device__ __forceinline__ float vf<float>(const float& x) { return x; }
+template <>
+__device__ __forceinline__ float vf<float2>(const float2& x) { return x.x + x.y; }
+
+__device__ __forceinline__ float block_sum(float x, float* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  float t = 0.f;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];  // fixed order
+  return t;
+}
+
+// Slot of the two-card hand {a, b} (a != b): b (b - 1) / 2 + a with a < b.
+__device__ __forceinline__ int pair_slot(int a, int b) {
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  return b * (b - 1) / 2 + a;
+}
+
+// One block per network row (leaf, river card): writes the row of X.
+template <typename V>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __restrict__ games, LeafCtx L,
+                                                              int use_bar) {
+  __shared__ float red[kLeafThreads / 32];
+  const int row = blockIdx.x;
+  const int li = row / kLeafCards, ri = row - li * kLeafCards;
+  const LeafDev lf = L.leaves[li];
+  const GameDev& G = games[lf.game];
+  const NodeDev nd = G.nodes[lf.node];
+  // the ri-th card not on the board
+  int r = -1;
+  for (int c = 0, k = 0; c < 52; ++c)
+    if (!((nd.board >> c) & 1ull)) {
+      if (k == ri) {
+        r = c;
+        break;
+      }
+      ++k;
+    }
+  const size_t stride = (size_t)G.hstride;
+  const V* reach = static_cast<const V*>(use_bar ? G.reach_bar : G.reach);
+  const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
+  uint16_t* x = static_cast<uint16_t*>(L.X) + (size_t)row * kLeafIn;
+  for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) x[k] = 0;
+  float sum[2], cnt = 0.f;
+  for (int p = 0; p < 2; ++p) {
+    const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
+    float s = 0.f, n = 0.f;
+    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
+      if (!((G.hand_mask[h] >> r) & 1ull)) s += vf(q[h]), n += 1.f;
+    sum[p] = block_sum(s, red);
+    if (p == 0) cnt = block_sum(n, red);
+  }
+  __syncthreads();  // the zero fill is complete
+  for (int p = 0; p < 2; ++p) {
+    const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
+    // a player who never reaches the leaf: uniform over the hands (the values are then unused)
+    const float inv = sum[p] > 0.f ? 1.f / sum[p] : 0.f;
+    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
+      if (!((G.hand_mask[h] >> r) & 1ull)) {
+        const float v = sum[p] > 0.f ? vf(q[h]) * inv : 1.f / cnt;
+        x[p * kLeafSlots + slot[h]] = to_bf16(v);
+      }
+  }
+  if (threadIdx.x < 52) {
+    const bool on = ((nd.board >> threadIdx.x) & 1ull) || (int)threadIdx.x == r;
+    if (on) x[2 * kLeafSlots + threadIdx.x] = 0x3f80;  // 1.0
+  }
+  if (threadIdx.x == 0) {
+    x[2 * kLeafSlots + 52] = to_bf16(lf.feat[0]);
+    x[2 * kLeafSlots + 53] = to_bf16(lf.feat[1]);
+  }
+}
+
+// One block per leaf: the leaf values of player i.
+template <typename V>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_values(const GameDev* __restrict__ games, LeafCtx L,
+                                                              int i, int use_bar) {
+  __shared__ float C[52];
+  __shared__ float red[kLeafThreads / 32];
+  const LeafDev lf = L.leaves[blockIdx.x];
+  const GameDev& G = games[lf.game];
+  const NodeDev nd = G.nodes[lf.node];
+  const size_t stride = (size_t)G.hstride;
+  const V* q = static_cast<const V*>(use_bar ? G.reach_bar : G.reach) + ((size_t)(1 - i) * G.n_nodes + lf.node) * stride;
+  V* out = static_cast<V*>(use_bar ? G.cfv_br : G.cfv) + ((size_t)i * G.n_nodes + lf.node) * stride;
+  const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
+  const int16_t* hand_at = L.hand_at + (size_t)lf.game * kLeafSlots;
+  // opponent totals: T and C[c] = sum over hands holding c (one warp per card, fixed order)
+  float t = 0.f;
+  for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x) t += vf(q[h]);
+  const float T = block_sum(t, red);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < 52; c += kLeafThreads / 32) {
+    float s = 0.f;
+    for (int h = lane; h < G.n_hands; h += 32)
+      if ((G.hand_mask[h] >> c) & 1ull) s += vf(q[h]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) C[c] = s;
+  }
+  __syncthreads();
+  const float scale = (float)(G.payoff[lf.node] * G.kappa64);
+  for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x) {
+    const uint64_t hm = G.hand_mask[h];
+    int c1 = -1, c2 = -1;
+    for (int c = 0; c < 52; ++c)
+      if ((hm >> c) & 1ull) {
+        if (c1 < 0) c1 = c;
+        else c2 = c;
+      }
+    const float qh = vf(q[h]);
+    const int s = slot[h];
+    float acc = 0.f;
+    for (int c = 0, ri = 0; c < 52; ++c) {
+      if ((nd.board >> c) & 1ull) continue;
+      const int row = lf.row0 + ri++;
+      if ((hm >> c) & 1ull) continue;  // the hand holds the river card
+      const int h1 = hand_at[pair_slot(c1, c)], h2 = hand_at[pair_slot(c2, c)];
+      const float q1 = h1 >= 0 ? vf(q[h1]) : 0.f, q2 = h2 >= 0 ? vf(q[h2]) : 0.f;
+      const float M = T - C[c] - (C[c1] - q1) - (C[c2] - q2) + qh;
+      acc = fmaf(L.Y[(size_t)row * kLeafOut + i * kLeafSlots + s], M, acc);
+    }
+    const float v = ((nd.board & hm) ? 0.f : scale * acc);
+    if constexpr (sizeof(V) == 4)
+      out[h] = v;
+    else
+      out[h] = make_float2(v, 0.f);
+  }
+}
+
+}  // namespace
+
+int launch_leaf_inputs(const LaunchCtx& c, const LeafCtx& L, int use_bar, void* stream) {
+  if (L.n_leaves == 0) return 0;
+  const int rows = L.n_leaves * kLeafCards;
+  if (c.precision == kPrecisionSingle)
+    k_leaf_inputs<float><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+  else
+    k_leaf_inputs<float2><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_leaf_net(const LaunchCtx& c, const LeafCtx& L, void* stream) {
+  if (L.n_leaves == 0) return 0;
+  const int rows = L.n_leaves * kLeafCards;
+  if (launch_gemm_bf16(L.X, L.W[0], L.b[0], L.H1, rows, kLeafHidden, kLeafIn, 1, 0, c.err, stream) ||
+      launch_gemm_bf16(L.H1, L.W[1], L.b[1], L.H2, rows, kLeafHidden, kLeafHidden, 1, 0, c.err, stream) ||
+      launch_gemm_bf16(L.H2, L.W[2], L.b[2], L.H3, rows, kLeafHidden, kLeafHidden, 1, 0, c.err, stream) ||
+      launch_gemm_bf16(L.H3, L.W[3], L.b[3], L.Y, rows, kLeafOut, kLeafHidden, 0, 1, c.err, stream))
+    return -1;
+  return 0;
+}
+
+int launch_leaf_values(const LaunchCtx& c, const LeafCtx& L, int player, int use_bar, void* stream) {
+  if (L.n_leaves == 0) return 0;
+  if (c.precision == kPrecisionSingle)
+    k_leaf_values<float><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
+  else
+    k_leaf_values<float2><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace pcfr

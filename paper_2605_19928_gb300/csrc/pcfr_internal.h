@@ -32,7 +32,10 @@
 
 namespace pcfr {
 
-enum NodeType : uint8_t { kDecision = 0, kFold = 1, kShowdown = 2, kChance = 3 };
+enum NodeType : uint8_t { kDecision = 0, kFold = 1, kShowdown = 2, kChance = 3, kLeaf = 4 };
+// Fold, showdown and depth-limit leaf nodes: their values come from outside the per-hand
+// tree passes (terminal and leaf launches).
+__host__ __device__ inline bool is_end(int type) { return type == kFold || type == kShowdown || type == kLeaf; }
 
 constexpr int kMaxActions = 16;
 constexpr int kMaxDeck = 52;
@@ -199,6 +202,45 @@ int configure_kernels();  // once per process, before the first launch
 int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
                      int out_f32, int* err, void* stream);
 int configure_gemm();
+
+// ---- depth-limit leaf network (leafnet.cu)
+// Network input per (leaf, river card): both players' reach at the leaf over the 1326
+// two-card slots (each normalised to sum 1 over the hands not holding the river card), a
+// one-hot of the 5 board cards, then 2 pot / stack features; zero padding to kLeafIn.
+// Output: each player's value per unit pot over the 1326 slots; padding to kLeafOut.
+constexpr int kLeafSlots = 1326;
+constexpr int kLeafFeatures = 2 * kLeafSlots + 52 + 2;  // 2706
+constexpr int kLeafIn = 2752;                           // padded to a multiple of 64
+constexpr int kLeafHidden = 512;
+constexpr int kLeafOut = 2688;                          // 2 x 1326 padded to a multiple of 128
+constexpr int kLeafCards = 48;                          // river cards after 4 board cards
+
+struct LeafDev {      // one depth-limit leaf
+  int game, node;
+  int row0;           // first of its kLeafCards network rows (river cards ascending)
+  float feat[2];      // pot / (pot + 2 stack), stack / (pot + 2 stack) at the leaf
+};
+
+struct LeafCtx {
+  const LeafDev* leaves;   // device [n_leaves]
+  int n_leaves;
+  const int16_t* slot;     // per game [hstride]: slot of each hand (device, game-major)
+  const int16_t* hand_at;  // per game [kLeafSlots]: hand in each slot or -1
+  int hstride_max;
+  void* X;                 // [rows][kLeafIn] BF16
+  void* H1;                // [rows][kLeafHidden] BF16
+  void* H2;
+  void* H3;
+  float* Y;                // [rows][kLeafOut]
+  const void* W[4];        // BF16 [out][in]
+  const float* b[4];
+};
+
+// Leaf values of player i (use_bar: against the average strategy, into cfv_br) or, with
+// player -1, only the network (both players' inputs and the four layers).
+int launch_leaf_inputs(const LaunchCtx& c, const LeafCtx& L, int use_bar, void* stream);
+int launch_leaf_net(const LaunchCtx& c, const LeafCtx& L, void* stream);
+int launch_leaf_values(const LaunchCtx& c, const LeafCtx& L, int player, int use_bar, void* stream);
 // Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes)
 // and one player's load descriptors (prog_units), a prefetch ring of 2 x half 8-byte units
 // and a stack of `depth` slots (es bytes) per lane.

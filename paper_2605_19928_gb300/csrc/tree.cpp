@@ -237,6 +237,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
       g.n_hands = (int)g.hand_mask.size();
     }
     const int want_rows = spec.n_board == 5 ? 1 : 52;
+    if (spec.depth_limit != 0 && (spec.depth_limit != 1 || spec.n_board != 4)) {
+      err = "depth_limit 1 applies to turn subgames only";
+      return CFR_EINVAL;
+    }
     if (!spec.strength || spec.n_strength_rows != want_rows) {
       err = "strength must have 1 row (river) or 52 rows (turn)";
       return CFR_EINVAL;
@@ -303,6 +307,12 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     nd.level = (uint8_t)s.level;
     nd.board = board_bits(s);
     kids.clear();
+    // depth limit: a chance node with chips behind ends the tree; the leaf network values it
+    const bool all_in = std::max(s.c[0], s.c[1]) >= R.cap;
+    if (s.type == kChance && spec.depth_limit && spec.game == CFR_GAME_HOLDEM && !all_in) {
+      s.type = kLeaf;
+      nd.type = kLeaf;
+    }
     if (s.type == kDecision) decision_children(R, s, kids);
     else if (s.type == kChance) chance_children(R, s, kids);
     // Terminal payoffs carry the probability of the public cards dealt on their path, so
@@ -313,6 +323,7 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     double pay = 0.0;
     if (s.type == kFold) pay = s.c[s.player] * s.chance;
     if (s.type == kShowdown) pay = s.c[0] * s.chance;
+    if (s.type == kLeaf) pay = (s.c[0] + s.c[1]) * s.chance * per_card;  // pot x P(river card)
     nd.arow = -1;
     nd.aplayer = kNoCard;
     if (s.type == kChance)
@@ -368,8 +379,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
       g.nodes[n].aplayer = par.player;
     }
   }
-  for (int n = 0; n < N; ++n)
+  for (int n = 0; n < N; ++n) {
     if (g.nodes[n].type == kFold || g.nodes[n].type == kShowdown) g.terminals.push_back(n);
+    if (g.nodes[n].type == kLeaf) g.leaves.push_back(n);
+  }
 
   // ---- showdown tables, one per board the tree can show down on
   std::vector<std::vector<int>> strengths;  // [board table][hand]
@@ -492,7 +505,7 @@ std::vector<int32_t> row_nodes(const HostGame& g) {
   return out;
 }
 
-static bool is_terminal(const NodeDev& nd) { return nd.type == kFold || nd.type == kShowdown; }
+static bool is_terminal(const NodeDev& nd) { return is_end(nd.type); }
 
 std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions, bool* ok) {
   std::vector<int32_t> pre;  // inner nodes only

@@ -19,6 +19,7 @@ struct HostGame {
   int n_rows = 0;
   int row_begin[3] = {0, 0, 0};
   std::vector<int32_t> terminals;     // fold and showdown node ids
+  std::vector<int32_t> leaves;        // depth-limit leaf node ids
   // hands
   int n_hands = 0, hstride = 0;
   std::vector<uint8_t> hand_cards;    // [n_hands][2]

@@ -45,6 +45,7 @@ class GameSpec:
     bet_sizes: tuple = ()                 # pot fractions, ALL_IN for the all-in bet
     max_raises: int = 0                   # bets + raises allowed per street
     seeds: dict = field(default_factory=dict)
+    depth_limit: int = 0                  # 1: the turn tree stops at the river card (leaf network)
 
     @property
     def n_hands(self) -> int:

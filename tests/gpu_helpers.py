@@ -115,7 +115,7 @@ def stored_cfv(tree, g, info):
     every node's, the stream schedule the terminals' and the root's."""
     if capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL:
         return True
-    return g == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN)
+    return g == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN, capi.CFR_NODE_LEAF)
 
 
 def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, floor_frac=FLOOR):

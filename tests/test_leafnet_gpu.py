@@ -60,3 +60,124 @@ def test_shapes_are_checked():
     with pytest.raises(capi.CfrError) as e:
         capi.cfr_gemm_bf16(A, B, None, C, False, err)
     assert e.value.code == capi.CFR_EINVAL
+
+
+# ---------------------------------------------------------------- depth-limit leaves in the CFR iteration
+
+from gpu_helpers import compare_player, inject, node_map  # noqa: E402
+from paper_2605_19928_gb300 import synth  # noqa: E402
+
+
+def _leaf_spec(n_hands=40, seed=5, max_raises=2):
+    spec = synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, bet_sizes=(1.0, synth.ALL_IN),
+                              max_raises=max_raises)
+    spec.depth_limit = 1
+    return spec
+
+
+def _random_net(seed):
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for k, shape in enumerate(capi.LEAF_SHAPES):
+        w = rng.standard_normal(shape).astype(np.float32) * np.float32(2.0 / np.sqrt(shape[1]))
+        W.append(ln.bf16_round(w * (0.2 if k == 3 else 1.0)))
+        b.append(rng.standard_normal(shape[0]).astype(np.float32) * 0.05)
+    return W, b
+
+
+def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
+    """Check one evaluation's inputs and outputs against the oracle; load the GPU's outputs
+    into the oracle's leaves.  Returns the worst output error relative to the row maximum."""
+    g2o = {g: o for g, o, _ in mapping}
+    board = [int(c) for c in spec.board]
+    live = [c for c in range(52) if c not in board]
+    slots = np.array([ln.pair_slot(int(a), int(c)) for a, c in spec.hands])
+    worst = 0.0
+    for game, node, row0 in capi.cfr_leaf_info(tree):
+        o = g2o[node]
+        X = ln.bf16_from_bits(capi.cfr_read_leaf_rows(tree, 0, row0, 48))
+        Y = capi.cfr_read_leaf_rows(tree, 1, row0, 48)
+        if check_inputs:
+            reach = [orc.node_reach("current", p, o) for p in (0, 1)]
+            c = capi.cfr_node_info(tree, node)["contrib"]
+            feat = ln.leaf_features(c[0] + c[1], spec.pot / 2 + spec.stack - c[0])
+            for k, r in enumerate(live):
+                x = ln.leaf_input(reach, spec.hands, board, r, feat)
+                # the GPU rounds its FP32 input to BF16: one BF16 step of the exact value at most
+                assert np.all(np.abs(X[k] - x) <= np.abs(x) * 2.0 ** -8 + 1e-30), (node, r)
+        Yr = ln.forward(X, list(zip(W, b)))
+        scale = np.max(np.abs(Yr), axis=1, keepdims=True)
+        # hidden activations are rounded to BF16 on both sides; a rounding that falls the
+        # other way moves an output by about one BF16 step of that activation's share
+        err = np.max(np.abs(Y[:, :ln.SLOTS * 2] - Yr[:, :ln.SLOTS * 2]) / scale)
+        assert err <= 3e-2, (node, err)
+        worst = max(worst, float(err))
+        y = np.stack([Y[:, :ln.SLOTS][:, slots], Y[:, ln.SLOTS:2 * ln.SLOTS][:, slots]], axis=1)
+        orc.set_leaf_values(o, y.astype(np.float64))
+    return worst
+
+
+@pytest.mark.parametrize("schedule", ["level", "stream"])
+def test_leaf_inputs_outputs_and_values_match_oracle(schedule):
+    from oracle.oracle import Oracle
+    spec = _leaf_spec()
+    W, b = _random_net(1)
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", schedule=schedule))
+    try:
+        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_iterate(tree, 3)
+        capi.cfr_eval_leaves(tree)
+        orc = Oracle(spec, variant="dcfr")
+        mapping = node_map(tree, orc)
+        inject(tree, orc, mapping)
+        print("output error", _leaf_rows(tree, orc, spec, mapping, W, b))
+        for i in (0, 1):
+            orc.values_current(i)
+            for g, o, info in mapping:
+                if info["type"] == capi.CFR_NODE_LEAF:
+                    got = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=i)
+                    want = orc.cfv(i, o)
+                    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)) + 1e-9 * spec.pot, (i, g)
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("schedule,variant", [("level", "dcfr"), ("stream", "dcfr"), ("level", "cfr+")])
+def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant):
+    from oracle.oracle import Oracle
+    spec = _leaf_spec(n_hands=32, seed=9)
+    W, b = _random_net(2)
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, schedule=schedule))
+    try:
+        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_iterate(tree, 2)
+        orc = Oracle(spec, variant=variant)
+        mapping = node_map(tree, orc)
+        for t in range(3, 6):
+            inject(tree, orc, mapping)
+            capi.cfr_eval_leaves(tree)  # the evaluation player 0's update is about to see
+            _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=False)
+            capi.cfr_iterate(tree, 1)
+            orc.update_player(0, t)
+            compare_player(tree, orc, mapping, 0)
+            inject(tree, orc, mapping, player=0)
+            _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=False)  # player 1's evaluation
+            orc.update_player(1, t)
+            compare_player(tree, orc, mapping, 1)
+            orc.set_iterations(t)
+        e, _ = capi.cfr_exploitability(tree)
+        assert np.isfinite(e[0])
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_leaf_handles_need_a_network():
+    spec = _leaf_spec(n_hands=20)
+    tree = capi.cfr_tree_create(spec)
+    try:
+        with pytest.raises(capi.CfrError) as e:
+            capi.cfr_iterate(tree, 1)
+        assert e.value.code == capi.CFR_ESTATE
+        assert len(capi.cfr_leaf_info(tree)) > 0
+    finally:
+        capi.cfr_tree_destroy(tree)

@@ -65,3 +65,83 @@ def test_forward_rounds_hidden_activations():
     h = ln.bf16_round(ln.gelu(ln.bf16_round(x).astype(np.float64) @ ln.bf16_round(l1[0]).T.astype(np.float64) + l1[1]))
     want = h.astype(np.float64) @ ln.bf16_round(l2[0]).T.astype(np.float64) + l2[1]
     assert np.allclose(ln.forward(x, [l1, l2]), want, atol=1e-12)
+
+
+# ---------------------------------------------------------------- depth-limit leaves in the oracle
+
+def _turn(n_hands=12, seed=5, **kw):
+    from paper_2605_19928_gb300 import synth
+    kw.setdefault("bet_sizes", (1.0, synth.ALL_IN))
+    kw.setdefault("max_raises", 1)
+    return synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
+
+
+def test_leaves_replace_the_river_chance_nodes_with_chips_behind(oracle_mod):
+    exact = _turn()
+    limited = _turn()
+    limited.depth_limit = 1
+    oe, ol = oracle_mod.Oracle(exact, threads=1), oracle_mod.Oracle(limited, threads=1)
+    ne, nl = oe.nodes(), ol.nodes()
+    chance_with_chips = [n for n in ne if n["type"] == oracle_mod.T_CHANCE and max(n["contrib"]) < exact.pot / 2 + exact.stack]
+    leaves = [n for n in nl if n["type"] == oracle_mod.T_LEAF]
+    assert len(leaves) == len(chance_with_chips) > 0
+    assert sorted(n["contrib"] for n in leaves) == sorted(n["contrib"] for n in chance_with_chips)
+    # all-in run-outs stay exact: the limited tree keeps those chance nodes and their showdowns
+    allin = sum(1 for n in ne if n["type"] == oracle_mod.T_CHANCE) - len(chance_with_chips)
+    assert sum(1 for n in nl if n["type"] == oracle_mod.T_CHANCE) == allin
+
+
+def test_constant_leaf_values_give_that_share_of_the_pot(oracle_mod):
+    spec = _turn(max_raises=0)  # check / check: the turn ends at one leaf
+    spec.depth_limit = 1
+    o = oracle_mod.Oracle(spec, threads=1)
+    leaves = [k for k, n in enumerate(o.nodes()) if n["type"] == oracle_mod.T_LEAF]
+    assert len(leaves) == 1
+    y = np.zeros((48, 2, spec.n_hands))
+    y[:, 0, :], y[:, 1, :] = 0.25, -0.1
+    o.set_leaf_values(leaves[0], y)
+    o.load_profile("current")
+    v = o.profile_value()
+    assert v[0] == pytest.approx(0.25 * spec.pot, rel=1e-12)
+    assert v[1] == pytest.approx(-0.1 * spec.pot, rel=1e-12)
+
+
+def test_leaf_values_depend_on_the_cards_left(oracle_mod):
+    """Values that depend on the river card only: a hand's leaf value is pot / 44 times the
+    sum over the river cards neither hand holds, weighted by the opponent reach."""
+    spec = _turn(n_hands=9, max_raises=0)
+    spec.depth_limit = 1
+    o = oracle_mod.Oracle(spec, threads=1)
+    leaf = [k for k, n in enumerate(o.nodes()) if n["type"] == oracle_mod.T_LEAF][0]
+    live = [c for c in range(52) if c not in set(int(b) for b in spec.board)]
+    f = np.linspace(-1.0, 1.0, 48)
+    y = np.zeros((48, 2, spec.n_hands))
+    y[:, 0, :] = f[:, None]
+    o.set_leaf_values(leaf, y)
+    o.values_current(0)
+    got = o.cfv(0, leaf)
+    r = spec.ranges.astype(np.float64)
+    r = r / r.sum(axis=1, keepdims=True)
+    hands = [set(int(c) for c in h) for h in spec.hands]
+    Z = sum(r[0, a] * r[1, b] for a in range(9) for b in range(9) if not hands[a] & hands[b])
+    for h in range(9):
+        want = 0.0
+        for o_ in range(9):
+            if hands[h] & hands[o_]:
+                continue
+            u = sum(f[k] for k, c in enumerate(live) if c not in hands[h] | hands[o_]) * spec.pot / 44
+            want += r[1, o_] / Z * u
+        assert got[h] == pytest.approx(want, rel=1e-12, abs=1e-15)
+
+
+def test_leaf_input_row_layout():
+    hands = np.array([[0, 1], [2, 5], [1, 7]])
+    x = ln.leaf_input([np.array([1.0, 3.0, 0.0]), np.array([0.0, 0.0, 2.0])], hands, [10, 20, 30, 40], 5,
+                      ln.leaf_features(100.0, 50.0))
+    # river card 5 removes hand [2, 5]: player 0's reach renormalises over the others
+    assert x[ln.pair_slot(0, 1)] == 1.0 and x[ln.pair_slot(2, 5)] == 0.0
+    assert x[ln.SLOTS + ln.pair_slot(1, 7)] == 1.0
+    assert ln.pair_slot(0, 1) == 0 and ln.pair_slot(50, 51) == 1325
+    assert [k - 2 * ln.SLOTS for k in np.flatnonzero(x[2 * ln.SLOTS:2 * ln.SLOTS + 52]) + 2 * ln.SLOTS] == [5, 10, 20, 30, 40]
+    assert x[2 * ln.SLOTS + 52] == pytest.approx(0.5) and x[2 * ln.SLOTS + 53] == pytest.approx(0.25)
+    assert x.shape == (2752,) and not x[2 * ln.SLOTS + 54:].any()
