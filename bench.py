@@ -42,8 +42,9 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["river", "batch"], default="river",
-                    help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle")
+    ap.add_argument("--workload", choices=["river", "batch", "leaf"], default="river",
+                    help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle; "
+                         "leaf: depth-limited turn subgame with the BF16 leaf network, against the exact turn")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--iters-per-step", type=int, default=None, help="default 1000 (river) or 500 (batch)")
     ap.add_argument("--precision", choices=["pairs", "single"], default="pairs")
@@ -200,32 +201,45 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak(sustained: bool = False):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        if key in d:
+            return float(d[key]), "measured " + key
+    return (1700.0 if sustained else 1900.0), "fallback"
+
+
 def tree_shape(capi, tree, game: int = 0):
     n_nodes, n_hands, _ = capi.cfr_tree_info(tree, game)
     rows = [0, 0]
-    terminals = 0
+    ends = 0
     for n in range(n_nodes):
         info = capi.cfr_node_info(tree, n, game)
         if info["type"] == capi.CFR_NODE_DECISION:
             rows[info["player"]] += info["n_actions"]
-        elif info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN):
-            terminals += 1
-    return {"nodes": n_nodes, "hands": n_hands, "rows": rows, "terminals": terminals}
+        elif info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN, capi.CFR_NODE_LEAF):
+            ends += 1
+    return {"nodes": n_nodes, "hands": n_hands, "rows": rows, "terminals": ends}
 
 
 def algorithmic_bytes(shape, stage: str, value_bytes: int) -> float:
-    """Bytes one launch must move, for one player's launch (the mean of the two players').
-
-    update:   per (decision row of the player, hand): R and S read + write (32 B), strategy
-              read + write (2 V); per (node, hand): reach read + write and value write (3 V);
-              per (terminal, hand): terminal value read (V).
-    terminal: per (terminal, hand): opponent reach read and value write (2 V)."""
+    """Algorithmic bytes of one launch, from the per-unit figures of the traversal:
+    per (decision row, hand) and iteration R and S read + written (32 B) and the strategy
+    written once and read by the two traversals (3 V); per (node, hand) and traversal the
+    reach written + read and the value written + read (4 V).  With V = 4 (FP32 values) that
+    is 44 B per row-hand and 32 B per node-hand per iteration.  An update launch (one
+    player) owns its player's rows and one traversal's inner nodes, a terminal launch one
+    traversal's terminal nodes; the figures are the mean over the two players' launches."""
     H, V = shape["hands"], value_bytes
     rows = 0.5 * (shape["rows"][0] + shape["rows"][1])
+    inner = shape["nodes"] - shape["terminals"]
     if stage == "update":
-        return H * (rows * (32 + 2 * V) + shape["nodes"] * 3 * V + shape["terminals"] * V)
+        return H * (rows * (32 + 3 * V) + inner * 4 * V)
     if stage == "terminal":
-        return H * shape["terminals"] * 2 * V
+        return H * shape["terminals"] * 4 * V
     raise ValueError(stage)
 
 
@@ -507,10 +521,190 @@ def cpu_baseline(specs, seconds, batch):
                       f"batch ({total:.1f} s); value = 1 / mean seconds per subgame iteration"}
 
 
+def node_paths(capi, tree, game: int = 0) -> dict:
+    """Action path from the root (tuple of child indices) -> node id."""
+    n_nodes = capi.cfr_tree_info(tree, game)[0]
+    paths = {0: ()}
+    for n in range(1, n_nodes):
+        info = capi.cfr_node_info(tree, n, game)
+        paths[n] = paths[info["parent"]] + (info["action"],)
+    return {p: n for n, p in paths.items()}
+
+
+def gemm_throughput(capi, torch, device, M=16384, reps=20):
+    """TFLOP/s of the leaf network's layer shapes on the tensor cores (inputs in HBM)."""
+    out = {}
+    for name, (N, K) in (("layer1", (512, 2752)), ("layer4", (2688, 512))):
+        A = torch.randn(M, K, device=device).to(torch.bfloat16)
+        B = (torch.randn(N, K, device=device) / K ** 0.5).to(torch.bfloat16)
+        bias = torch.zeros(N, device=device)
+        C = torch.empty(M, N, device=device, dtype=torch.bfloat16)
+        err = torch.zeros(1, dtype=torch.int32, device=device)
+        for _ in range(3):
+            capi.cfr_gemm_bf16(A, B, bias, C, True, err)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        s.record()
+        for _ in range(reps):
+            capi.cfr_gemm_bf16(A, B, bias, C, True, err)
+        e.record()
+        torch.cuda.synchronize(device)
+        ms = s.elapsed_time(e) / reps
+        out[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
+                     "wait_errors": int(err.item())}
+    return out
+
+
+def run_leaf(args):
+    """Depth-limited turn subgame with the learned leaf network vs the exact turn subgame."""
+    import numpy as np
+    import torch
+
+    from paper_2605_19928_gb300 import capi, leafnet_train, synth
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device: the CUDA path has no CPU fallback"}))
+        return 2
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = dist_init(world, True)
+    capi.load()
+    capi.use_torch_allocator()
+    stream = torch.cuda.current_stream(device)
+    kw = dict(seed=0 + 1000 * rank, range_seed=1 + 1000 * rank)
+    spec_leaf = synth.ranked_turn_subgame(depth_limit=1, **kw)
+    spec_exact = synth.ranked_turn_subgame(depth_limit=0, **kw)
+    opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, precision=args.precision)
+    W, b = leafnet_train.load_weights()
+    meta = np.load(os.path.join(ROOT, "paper_2605_19928_gb300", "leafnet_weights.npz"))["meta"]
+    L = capi.cfr_tree_create(spec_leaf, opts, stream=stream.cuda_stream)
+    E = capi.cfr_tree_create(spec_exact, opts, stream=stream.cuda_stream)
+    capi.cfr_set_leaf_net(L, W, b)
+    ips = args.iters_per_step
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def timed(tree, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            capi.cfr_reset(tree)
+            capi.cfr_iterate(tree, ips)
+            capi.cfr_exploitability_async(tree)
+        torch.cuda.synchronize(device)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            st[k].record(stream)
+            capi.cfr_reset(tree)
+            capi.cfr_iterate(tree, ips)
+            capi.cfr_exploitability_async(tree)
+            en[k].record(stream)
+        torch.cuda.synchronize(device)
+        return sum(a.elapsed_time(c) for a, c in zip(st, en)) / 1000.0
+
+    launches0 = capi.cfr_counters(L)["kernel_launches"]
+    clocks = ClockSampler(device.index)
+    barrier(dist, device)
+    clocks.start()
+    t_leaf = timed(L, args.steps, args.warmup)
+    clock_info = clocks.stop()
+    gpu_launches = capi.cfr_counters(L)["kernel_launches"] - launches0
+    value, t_max = aggregate(args.steps * ips, t_leaf, world, dist, device)
+    e_leaf_own, _ = capi.cfr_exploitability_result(L)
+    t_exact = timed(E, max(1, args.steps // 4), 1)
+    e_exact, _ = capi.cfr_exploitability_result(E)
+    exact_ips = max(1, args.steps // 4) * ips / t_exact
+    # the learned turn strategy in the exact game: E's river play, L's turn play
+    pe, pl = node_paths(capi, E), node_paths(capi, L)
+    for path, nl in pl.items():
+        if capi.cfr_node_info(L, nl)["type"] == capi.CFR_NODE_DECISION:
+            capi.cfr_write_values(E, capi.CFR_READ_AVG_SUM, pe[path], capi.cfr_read_values(L, capi.CFR_READ_AVG_SUM, nl))
+    e_hybrid, _ = capi.cfr_exploitability(E)
+    # the network against exact river solving at every leaf: give the depth-limited handle
+    # the exact handle's turn strategy, evaluate the network there, and compare with the
+    # values the exact handle's next player-0 traversal finds at the same river-card nodes
+    snap = {}
+    for path, nl in pl.items():
+        if capi.cfr_node_info(L, nl)["type"] == capi.CFR_NODE_DECISION:
+            snap[path] = capi.cfr_read_values(E, capi.CFR_READ_REGRET, pe[path])
+    for path, nl in pl.items():
+        if path in snap:
+            capi.cfr_write_values(L, capi.CFR_READ_REGRET, nl, snap[path])
+    capi.cfr_eval_leaves(L)
+    capi.cfr_iterate(E, 1)
+    rel, abs_err = [], 0.0
+    for _, nl, _ in capi.cfr_leaf_info(L):
+        path = [p for p, n in pl.items() if n == nl][0]
+        v_net = capi.cfr_read_values(L, capi.CFR_READ_CFV, nl, player=0)
+        v_ex = capi.cfr_read_values(E, capi.CFR_READ_CFV, pe[path], player=0)
+        rel.append(float(np.abs(v_net - v_ex).sum() / max(np.abs(v_ex).sum(), 1e-30)))
+        abs_err += float(np.abs(v_net - v_ex).sum())
+    leaf_check = {"relative_l1_mean": float(np.mean(rel)), "relative_l1_max": float(np.max(rel)),
+                  "leaves": len(rel),
+                  "note": "player 0's leaf values from the network vs from the exact river subtrees, same turn "
+                          "strategy (the exact solve's current one); sum over hands of |difference| / sum |exact|"}
+    # per-stage times of the learned form (launch by launch)
+    capi.cfr_reset(L)
+    stages = capi.cfr_stage_times(L, min(ips, 100))
+    leaves = capi.cfr_leaf_info(L)
+    rows = len(leaves) * capi.LEAF_CARDS
+    flops = 2.0 * rows * (capi.LEAF_IN * capi.LEAF_HIDDEN + 2 * capi.LEAF_HIDDEN ** 2 + capi.LEAF_HIDDEN * capi.LEAF_OUT)
+    gemm = gemm_throughput(capi, torch, device)
+    peak, peak_kind = bf16_peak()
+    best = max(gemm.values(), key=lambda g: g["tflops"])
+    roofline = {"bound": "tensor", "kernel": "k_gemm_bf16 (leaf network layers, M = 16384 rows)",
+                "achieved": best["tflops"], "peak": peak, "unit": "TFLOP/s", "frac": best["tflops"] / peak,
+                "peak_source": peak_kind, "traffic": None, "layers": gemm,
+                "leaf_stage": {"rows_per_evaluation": rows, "flops_per_evaluation": flops,
+                               "ms": stages["leaf"][0],
+                               "tflops_incl_input_and_value_kernels": flops / (stages["leaf"][0] * 1e-3) / 1e12},
+                "stage_ms": {k: v[0] for k, v in stages.items()}}
+    mbb = lambda e: 1000.0 * float(e) / BB_CHIPS
+    n_exact = capi.cfr_tree_info(E)[0]
+    capi.cfr_tree_destroy(L)
+    capi.cfr_tree_destroy(E)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
+                "ms_per_iter": 1000.0 * t_max / (args.steps * ips), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": ("f32x2" if args.precision == "pairs" else "f32") + " values, f64 R/S, bf16 network",
+                "data": "synthetic (rank-based showdowns; network trained on 200k self-generated river solves)",
+                "config": {"workload": "depth-limited turn subgame, leaf network at the river card",
+                           "board_cards": 4, "hands": spec_leaf.n_hands, "leaves": len(leaves),
+                           "network": "2752-512-512-512-2688 BF16, GELU", "pot": spec_leaf.pot,
+                           "stack": spec_leaf.stack, "bet_sizes": "0.5,1.0 pot,all-in", "max_raises": 3,
+                           "variant": "DCFR(1.5,0,2) alternating", "iters_per_step": ips,
+                           "step": "reset + iterations + exploitability (network leaves)",
+                           "l2": "flushed between steps (256 MB write, outside the timed events)",
+                           "seeds": spec_leaf.seeds},
+                "exact_form": {"iter_per_s": exact_ips, "ms_per_iter": 1000.0 / exact_ips, "nodes": n_exact,
+                               "exploitability_mbb": mbb(e_exact[0])},
+                "learned_form": {"exploitability_in_exact_game_mbb": mbb(e_hybrid[0]),
+                                 "exploitability_with_network_leaves_mbb": mbb(e_leaf_own[0]),
+                                 "gap_to_exact_mbb": mbb(e_hybrid[0]) - mbb(e_exact[0]),
+                                 "note": "turn strategy of the depth-limited solve, river play of the exact "
+                                         "solve, best responses in the exact game"},
+                "leaf_values_vs_exact_river": leaf_check,
+                "network": {"training_solves": int(meta[0]), "solve_iters": int(meta[1]), "epochs": int(meta[2]),
+                            "median_solve_exploitability_mbb": float(meta[4]),
+                            "validation_mean_abs_error_pot": float(meta[5])},
+                "speedup_vs_exact": value / exact_ips,
+                "roofline": roofline, "cpu_baseline": None, "e2e": None, "gpu_launches": int(gpu_launches),
+                "clocks": clock_info}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.iters_per_step is None:
-        args.iters_per_step = 500 if args.workload == "batch" else 1000
+        args.iters_per_step = {"batch": 500, "leaf": 300}.get(args.workload, 1000)
+    if args.workload == "leaf" and args.impl == "ours":
+        return run_leaf(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -201,6 +201,13 @@ int cfr_node_info(const cfr_tree* tree, int game, int node, int* type, int* play
  *     call, [n_hands]. */
 int cfr_read_values(cfr_tree* tree, int game, int what, int player, int node, double* out, size_t out_len);
 
+/* Overwrite a decision node's cumulative regrets (CFR_READ_REGRET) or average-strategy sums
+ * (CFR_READ_AVG_SUM) from a host buffer of [n_actions][n_hands] doubles (synchronises).
+ * For tests and for evaluating a strategy found elsewhere: after writing R the current
+ * strategy (regret matching, Eq. rm) and both players' reach are recomputed at once; the
+ * average strategy follows S at the next exploitability or cfr_strategy call. */
+int cfr_write_values(cfr_tree* tree, int game, int what, int node, const double* in, size_t in_len);
+
 /* Block until all work queued on the handle's stream has finished. */
 int cfr_sync(cfr_tree* tree);
 

@@ -34,7 +34,7 @@ EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iter
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
            "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule",
            "cfr_gemm_bf16", "cfr_set_leaf_net", "cfr_leaf_info", "cfr_read_leaf_rows",
-           "cfr_eval_leaves")
+           "cfr_eval_leaves", "cfr_write_values")
 
 
 class CfrError(RuntimeError):
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         lib.cfr_leaf_info.argtypes = [P, I, pi, pi, pi, pi]
         lib.cfr_read_leaf_rows.argtypes = [P, I, I, I, P]
         lib.cfr_eval_leaves.argtypes = [P, I]
+        lib.cfr_write_values.argtypes = [P, I, I, I, pd, S]
         lib.cfr_tree_destroy.argtypes = [P]
         lib.cfr_tree_destroy.restype = None
         lib.cfr_last_error.restype = C.c_char_p
@@ -360,6 +361,11 @@ def cfr_read_values(tree, what: int, node: int, player: int = 0, game: int = 0) 
     _check(load().cfr_read_values(tree, game, what, player, node, out.ctypes.data_as(C.POINTER(C.c_double)),
                                   out.size))
     return out
+
+
+def cfr_write_values(tree, what: int, node: int, values, game: int = 0):
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    _check(load().cfr_write_values(tree, game, int(what), int(node), v.ctypes.data_as(C.POINTER(C.c_double)), v.size))
 
 
 def cfr_stage_times(tree, n_iters: int = 1) -> dict:

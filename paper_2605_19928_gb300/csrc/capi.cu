@@ -794,6 +794,28 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
   return fail(CFR_EINVAL, "unknown read kind");
 }
 
+int cfr_write_values(cfr_tree* t, int game, int what, int node, const double* in, size_t in_len) {
+  int rc = check_game(t, game);
+  if (rc) return rc;
+  const HostGame& h = t->host[game];
+  const GameDev& d = t->dev[game];
+  if (node < 0 || node >= (int)h.nodes.size() || h.nodes[node].type != kDecision)
+    return fail(CFR_EINVAL, "node is not a decision node");
+  if (what != CFR_READ_REGRET && what != CFR_READ_AVG_SUM) return fail(CFR_EINVAL, "what must be REGRET or AVG_SUM");
+  const NodeDev& nd = h.nodes[node];
+  const size_t H = (size_t)h.n_hands, S = (size_t)h.hstride;
+  if (!in || in_len < (size_t)nd.n_kids * H) return fail(CFR_EINVAL, "input buffer too small");
+  double* dst = (what == CFR_READ_REGRET ? d.R : d.S) + (size_t)nd.row * S;
+  CK(cudaMemcpy2DAsync(dst, S * 8, in, H * 8, H * 8, nd.n_kids, cudaMemcpyHostToDevice, t->stream));
+  // new regrets: the current strategy and both players' reach follow them at once
+  if (what == CFR_READ_REGRET && launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "strategy launch failed");
+  if (what == CFR_READ_REGRET) t->launches += 1;
+  CK(cudaStreamSynchronize(t->stream));
+  t->state_gen += 1;
+  t->avg_gen = -1;
+  return CFR_OK;
+}
+
 int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   if (t->leaf.n_leaves > 0 && !t->leaf_net_set) return fail(CFR_ESTATE, "the tree has leaves: set the leaf network first");

@@ -150,3 +150,147 @@ def batch_rivers(n: int = 256, seed: int = 0, n_hands: int | None = None) -> lis
         g.name = f"river_batch_{k}"
         out.append(g)
     return out
+
+
+# ---------------------------------------------------------------- rank-based showdown strengths
+
+def rank_strength(board, hands) -> np.ndarray:
+    """Showdown strength of each two-card hand on a 5-card board, from the rules of poker:
+    the category of the best five of the seven cards (high card, pair, two pair, three of a
+    kind, straight, flush, full house, four of a kind, straight flush), then the ranks that
+    break ties within it.  Deterministic in the cards, so a network can learn it; returned
+    as dense int32 ranks (equal strength, equal rank)."""
+    board = np.asarray(board, dtype=np.int64)
+    hands = np.asarray(hands, dtype=np.int64)
+    n = hands.shape[0]
+    cards = np.concatenate([hands, np.broadcast_to(board, (n, 5))], axis=1)  # [n, 7]
+    rank, suit = cards // 4, cards % 4
+    cnt = np.zeros((n, 13), np.int64)
+    np.add.at(cnt, (np.arange(n)[:, None], rank), 1)
+    scnt = np.zeros((n, 4), np.int64)
+    np.add.at(scnt, (np.arange(n)[:, None], suit), 1)
+
+    def straight_top(present):  # present [n, 13] bool -> highest straight top rank or -1
+        p = np.concatenate([present[:, 12:13], present], axis=1)  # ace plays low
+        top = np.full(n, -1)
+        for hi in range(4, 14):
+            ok = p[:, hi - 4:hi + 1].all(axis=1)
+            top = np.where(ok, hi - 1, top)
+        return top
+
+    st = straight_top(cnt > 0)
+    fsuit = np.argmax(scnt, axis=1)
+    flush = scnt.max(axis=1) >= 5
+    fpres = np.zeros((n, 13), bool)
+    for k in range(7):
+        m = suit[:, k] == fsuit
+        fpres[np.arange(n)[m], rank[m, k]] = True
+    sft = np.where(flush, straight_top(fpres), -1)
+    ranks = np.arange(13)[None, :]
+
+    def best(mask):  # highest rank where mask holds, else -1
+        return np.where(mask.any(axis=1), 12 - np.argmax(mask[:, ::-1], axis=1), -1)
+
+    def top(mask, k):  # the k highest ranks where mask holds (-1 where fewer)
+        out, m = [], mask.copy()
+        for _ in range(k):
+            r = best(m)
+            out.append(r)
+            m = m & (ranks != r[:, None])
+        return out
+
+    quad = best(cnt == 4)
+    trip = best(cnt >= 3)
+    pair1 = best((cnt >= 2) & (ranks != trip[:, None]))
+    pair2 = best((cnt >= 2) & (ranks != pair1[:, None]) & (ranks != trip[:, None]))
+    quads = quad >= 0
+    full = (trip >= 0) & (pair1 >= 0)
+    trips = (trip >= 0) & ~full
+    twop = (trip < 0) & (pair2 >= 0)
+    pair = (trip < 0) & (pair1 >= 0) & (pair2 < 0)
+    cat = np.zeros(n, np.int64)
+    cat = np.where(pair, 1, cat)
+    cat = np.where(twop, 2, cat)
+    cat = np.where(trips, 3, cat)
+    cat = np.where(st >= 0, 4, cat)
+    cat = np.where(flush, 5, cat)
+    cat = np.where(full, 6, cat)
+    cat = np.where(quads, 7, cat)
+    cat = np.where(sft >= 0, 8, cat)
+    # tie-break: the ranks of the five cards that play, most significant first
+    seen = cnt >= 1
+    sel = {0: top(cnt == 1, 5),
+           1: [pair1] + top(cnt == 1, 3),
+           2: [pair1, pair2, best(seen & (ranks != pair1[:, None]) & (ranks != pair2[:, None]))],
+           3: [trip] + top(cnt == 1, 2),
+           4: [st],
+           6: [trip, pair1],
+           7: [quad, best(seen & (ranks != quad[:, None]))],
+           8: [sft]}
+    fr = np.where(fpres, np.arange(13)[None, :], -1)
+    fr = -np.sort(-fr, axis=1)[:, :5]
+    sel[5] = [fr[:, k] for k in range(5)]
+    tb = np.zeros(n, np.int64)
+    for c, seq in sel.items():
+        v = np.zeros(n, np.int64)
+        for k in range(5):
+            v = v * 16 + (np.maximum(seq[k], 0) if k < len(seq) else 0)
+        tb = np.where(cat == c, v, tb)
+    score = cat * (16 ** 5) + tb
+    _, dense = np.unique(score, return_inverse=True)
+    return dense.astype(np.int32)
+
+
+def ranked_turn_subgame(n_hands: int | None = None, seed: int = 0, range_seed: int = 1, pot: float = 100.0,
+                        stack: float = 400.0, bet_sizes=(0.5, 1.0, ALL_IN), max_raises: int = 3,
+                        depth_limit: int = 0) -> GameSpec:
+    """A turn subgame like turn_subgame, with showdown strengths from rank_strength on each
+    completed board (rows of board cards are unused and zero)."""
+    g = turn_subgame(n_hands=n_hands, seed=seed, range_seed=range_seed, pot=pot, stack=stack,
+                     bet_sizes=bet_sizes, max_raises=max_raises)
+    strength = np.zeros((DECK, g.n_hands), np.int32)
+    for c in range(DECK):
+        if c in set(int(b) for b in g.board):
+            continue
+        live = ~np.any(g.hands == c, axis=1)
+        s = np.zeros(g.n_hands, np.int32)
+        s[live] = rank_strength(np.concatenate([g.board, [c]]), g.hands[live])
+        strength[c] = s
+    g.strength = strength
+    g.name = "turn_ranked"
+    g.depth_limit = depth_limit
+    return g
+
+
+def leaf_training_rivers(n: int, seed: int = 0, pot_range=(100.0, 900.0), behind_range=(50.0, 500.0),
+                         bet_sizes=(0.5, 1.0, ALL_IN), max_raises: int = 3) -> list[GameSpec]:
+    """River subgames for training the leaf network: seeded boards, rank_strength showdowns,
+    pots and chips behind spanning those of turn leaves, and ranges shaped like those that
+    reach a leaf after betting.  Each player's range is, with equal odds, Dirichlet(1);
+    tilted towards strong or weak hands, exp(b z) with z the hand's strength percentile in
+    [-1, 1] and b uniform in [-6, 6]; or polarised, exp(b |z|) with b in [0, 6] -- each
+    times Dirichlet(1) noise and thinned by a random keep-probability."""
+    rng = np.random.default_rng(20_000 + seed)
+    out = []
+    for k in range(n):
+        board = np.sort(rng.choice(DECK, size=5, replace=False)).astype(np.int32)
+        combos = all_combos(board)
+        strength = rank_strength(board, combos)
+        z = 2.0 * (np.argsort(np.argsort(strength, kind="stable"), kind="stable") / max(1, len(strength) - 1)) - 1.0
+        ranges = rng.exponential(1.0, size=(2, combos.shape[0]))
+        for p in range(2):
+            kind = int(rng.integers(0, 3))
+            if kind == 1:
+                ranges[p] *= np.exp(rng.uniform(-6.0, 6.0) * z)
+            elif kind == 2:
+                ranges[p] *= np.exp(rng.uniform(0.0, 6.0) * np.abs(z))
+        keep = rng.random((2, combos.shape[0])) < rng.uniform(0.3, 1.0, size=(2, 1))
+        ranges = ranges * keep
+        ranges[ranges.sum(axis=1) == 0] = 1.0
+        ranges = (ranges / ranges.sum(axis=1, keepdims=True)).astype(np.float32)
+        pot = float(rng.uniform(*pot_range))
+        behind = float(rng.uniform(*behind_range))
+        out.append(GameSpec(GAME_HOLDEM, f"leaf_river_{k}", board, combos, ranges, strength[None, :].copy(), pot,
+                            behind, tuple(float(x) for x in bet_sizes), max_raises,
+                            {"leaf_river": 20_000 + seed, "k": k}))
+    return out

@@ -1,0 +1,45 @@
+"""Input generators: the rank-based showdown evaluator against hand-worked poker cases, and
+the generators' shapes."""
+import numpy as np
+
+from paper_2605_19928_gb300 import synth
+
+
+def card(rank, suit):
+    return 4 * rank + suit
+
+
+def test_rank_strength_orders_categories():
+    # board: A K Q of suit 0, 5 of suit 1, 4 of suit 2 (ranks 0..12 = deuce..ace)
+    board = [card(12, 0), card(11, 0), card(10, 0), card(3, 1), card(2, 2)]
+    hands = np.array([[card(9, 0), card(8, 0)],    # J T suited: straight flush to the ace
+                      [card(9, 1), card(8, 2)],    # J T: straight to the ace
+                      [card(12, 1), card(12, 2)],  # A A: three of a kind
+                      [card(1, 0), card(0, 0)],    # 3 2 of suit 0: flush, A K Q 3 2
+                      [card(3, 0), card(2, 0)],    # 5 4 of suit 0: flush, A K Q 5 4
+                      [card(0, 1), card(1, 2)],    # 2 3: straight to the five (ace low)
+                      [card(6, 1), card(7, 2)]])   # 8 9: ace high
+    s = synth.rank_strength(board, hands)
+    order = list(np.argsort(s))
+    assert order == [6, 2, 5, 1, 3, 4, 0]
+
+
+def test_rank_strength_ties_and_kickers():
+    board = [card(12, 0), card(12, 1), card(7, 2), card(5, 3), card(2, 0)]
+    hands = np.array([[card(11, 2), card(3, 1)],   # A A K: pair of aces, king kicker
+                      [card(11, 3), card(4, 1)],   # same five cards (A A K 9 7): tie
+                      [card(10, 2), card(3, 3)],   # A A Q
+                      [card(7, 0), card(3, 2)]])   # two pair, aces and nines
+    s = synth.rank_strength(board, hands)
+    assert s[0] == s[1] and s[2] < s[0] < s[3]
+
+
+def test_training_rivers_are_seeded_and_valid():
+    a = synth.leaf_training_rivers(3, seed=4)
+    b = synth.leaf_training_rivers(3, seed=4)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.board, y.board) and np.array_equal(x.ranges, y.ranges)
+        assert x.hands.shape == (1081, 2) and np.allclose(x.ranges.sum(axis=1), 1.0, atol=1e-5)
+        assert 100.0 <= x.pot <= 900.0 and 50.0 <= x.stack <= 500.0
+    t = synth.ranked_turn_subgame(n_hands=30, depth_limit=1)
+    assert t.depth_limit == 1 and t.strength.shape == (52, 30)
