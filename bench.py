@@ -42,7 +42,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["river", "batch", "leaf"], default="river",
+    ap.add_argument("--workload", choices=["river", "batch", "leaf", "gemm"], default="river",
                     help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle; "
                          "leaf: depth-limited turn subgame with the BF16 leaf network, against the exact turn")
     ap.add_argument("--batch-size", type=int, default=256)
@@ -555,6 +555,21 @@ def gemm_throughput(capi, torch, device, M=16384, reps=20):
     return out
 
 
+def run_gemm(args):
+    """Only the leaf network's dense layers on the tensor cores (for profiling)."""
+    import torch
+
+    from paper_2605_19928_gb300 import capi
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    capi.load()
+    g = gemm_throughput(capi, torch, device, reps=max(1, args.steps))
+    peak, kind = bf16_peak()
+    print(json.dumps({"workload": "leaf network layers, M = 16384 rows", "layers": g, "peak_tflops": peak,
+                      "peak_source": kind}))
+    return 0
+
+
 def run_leaf(args):
     """Depth-limited turn subgame with the learned leaf network vs the exact turn subgame."""
     import numpy as np
@@ -705,6 +720,8 @@ def main(argv=None):
         args.iters_per_step = {"batch": 500, "leaf": 300}.get(args.workload, 1000)
     if args.workload == "leaf" and args.impl == "ours":
         return run_leaf(args)
+    if args.workload == "gemm" and args.impl == "ours":
+        return run_gemm(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -42,9 +42,9 @@ extern "C" {
 #define CFR_ESTATE (-5)   /* call not valid in the handle's current state */
 
 enum { CFR_GAME_HOLDEM = 0, CFR_GAME_KUHN = 1, CFR_GAME_LEDUC = 2 };
-enum { CFR_VARIANT_CFR = 0, CFR_VARIANT_CFRPLUS = 1, CFR_VARIANT_DCFR = 2 };
+enum { CFR_VARIANT_CFR = 0, CFR_VARIANT_CFRPLUS = 1, CFR_VARIANT_DCFR = 2, CFR_VARIANT_PCFRPLUS = 3 };
 enum { CFR_NODE_DECISION = 0, CFR_NODE_FOLD = 1, CFR_NODE_SHOWDOWN = 2, CFR_NODE_CHANCE = 3, CFR_NODE_LEAF = 4 };
-enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_CFV = 3 };
+enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_CFV = 3, CFR_READ_PREDICTION = 4 };
 
 /*
  * One subgame (Section 5, "Game": heads-up poker solved to the end of a betting round).
@@ -93,6 +93,9 @@ typedef struct cfr_game_spec {
  * algorithms"; the paper's default is DCFR): at iteration t, R <- R + r then positive
  * regrets are scaled by t^alpha/(t^alpha+1) and the rest by t^beta/(t^beta+1);
  * S <- S * (t/(t+1))^gamma + pi_i * sigma.  CFR+: R <- max(R + r, 0), S <- S + t pi_i sigma.
+ * Predictive CFR+ (the paper's second variant, Section 5, after Farina et al.): R <-
+ * max(R + r, 0), the prediction M <- r (the instantaneous regret just seen), the strategy
+ * is regret matching of R + M, S <- S + t^2 pi_i sigma.
  * alternating != 0 updates player 0 then player 1 (with player 0's new strategy) each
  * iteration; 0 updates both from the same strategy.
  * chunk_hands: hands per CUDA block in the per-hand passes (0 = automatic; otherwise a
@@ -193,16 +196,18 @@ int cfr_node_info(const cfr_tree* tree, int game, int node, int* type, int* play
                   int* action_in_parent, int* deal_card, double* contrib);
 
 /* Read solver state into a host buffer of doubles (synchronises):
- *   CFR_READ_REGRET, CFR_READ_AVG_SUM: a decision node's cumulative regrets R or average-
- *     strategy sums S, [n_actions][n_hands] (player is ignored);
+ *   CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_PREDICTION: a decision node's cumulative
+ *     regrets R, average-strategy sums S or Predictive CFR+ prediction M,
+ *     [n_actions][n_hands] (player is ignored);
  *   CFR_READ_CFV: player's counterfactual values at `node` from that player's last
  *     traversal, [n_hands];
  *   CFR_READ_BR_CFV: player's best-response values at `node` from the last exploitability
  *     call, [n_hands]. */
 int cfr_read_values(cfr_tree* tree, int game, int what, int player, int node, double* out, size_t out_len);
 
-/* Overwrite a decision node's cumulative regrets (CFR_READ_REGRET) or average-strategy sums
- * (CFR_READ_AVG_SUM) from a host buffer of [n_actions][n_hands] doubles (synchronises).
+/* Overwrite a decision node's cumulative regrets (CFR_READ_REGRET), average-strategy sums
+ * (CFR_READ_AVG_SUM) or Predictive CFR+ prediction (CFR_READ_PREDICTION) from a host buffer
+ * of [n_actions][n_hands] doubles (synchronises).
  * For tests and for evaluating a strategy found elsewhere: after writing R the current
  * strategy (regret matching, Eq. rm) and both players' reach are recomputed at once; the
  * average strategy follows S at the next exploitability or cfr_strategy call. */

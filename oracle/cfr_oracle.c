@@ -46,7 +46,7 @@
 
 enum { G_HOLDEM = 0, G_KUHN = 1, G_LEDUC = 2 };
 enum { T_DEC = 0, T_FOLD = 1, T_SHOW = 2, T_CHANCE = 3, T_LEAF = 4 };
-enum { V_CFR = 0, V_CFRPLUS = 1, V_DCFR = 2 };
+enum { V_CFR = 0, V_CFRPLUS = 1, V_DCFR = 2, V_PCFRPLUS = 3 };
 
 typedef struct {
   int type;        /* T_DEC, T_FOLD, T_SHOW, T_CHANCE, T_LEAF */
@@ -86,6 +86,7 @@ typedef struct Oracle {
   int nn, ncap;
   int nrows;
   double *R, *S, *sig, *prof, *rinst;
+  double* M;             /* Predictive CFR+: the prediction (last instantaneous regret) */
   double* cfv[2];        /* [nn][nh], counterfactual values of the last traversal of player i */
   unsigned char* compat; /* [nh][nh] 1 if the two hands share no card */
   double Z;
@@ -367,6 +368,7 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
   o->sig = (double*)calloc(cells, sizeof(double));
   o->prof = (double*)calloc(cells, sizeof(double));
   o->rinst = (double*)calloc(cells, sizeof(double));
+  o->M = (double*)calloc(cells, sizeof(double));
   o->cfv[0] = (double*)calloc((size_t)o->nn * nh, sizeof(double));
   o->cfv[1] = (double*)calloc((size_t)o->nn * nh, sizeof(double));
   return o;
@@ -380,26 +382,31 @@ void ocfr_destroy(Oracle* o) {
   }
   free(o->nodes);
   free(o->cards); free(o->hmask); free(o->r[0]); free(o->r[1]); free(o->strength);
-  free(o->R); free(o->S); free(o->sig); free(o->prof); free(o->rinst);
+  free(o->R); free(o->S); free(o->sig); free(o->prof); free(o->rinst); free(o->M);
   free(o->cfv[0]); free(o->cfv[1]); free(o->compat);
   free(o);
 }
 
 /* ------------------------------------------------------------------ regret matching, Eq. (rm) */
 
+/* Regret matching (Eq. rm) of R; Predictive CFR+ matches R + M, the regrets plus the
+ * prediction of the next instantaneous regret. */
 static void regret_match(const Oracle* o, const double* R, double* out) {
+  const int pred = o->variant == V_PCFRPLUS;
   for (int n = 0; n < o->nn; ++n) {
     const Node* nd = &o->nodes[n];
     if (nd->type != T_DEC) continue;
     for (int h = 0; h < o->nh; ++h) {
       double pos = 0.0;
       for (int a = 0; a < nd->nkids; ++a) {
-        double x = R[(size_t)(nd->row + a) * o->nh + h];
+        size_t cell = (size_t)(nd->row + a) * o->nh + h;
+        double x = R[cell] + (pred ? o->M[cell] : 0.0);
         if (x > 0.0) pos += x;
       }
       for (int a = 0; a < nd->nkids; ++a) {
-        double x = R[(size_t)(nd->row + a) * o->nh + h];
-        out[(size_t)(nd->row + a) * o->nh + h] = pos > 0.0 ? (x > 0.0 ? x : 0.0) / pos : 1.0 / nd->nkids;
+        size_t cell = (size_t)(nd->row + a) * o->nh + h;
+        double x = R[cell] + (pred ? o->M[cell] : 0.0);
+        out[cell] = pos > 0.0 ? (x > 0.0 ? x : 0.0) / pos : 1.0 / nd->nkids;
       }
     }
   }
@@ -543,6 +550,8 @@ static void update_player(Oracle* o, int i, int t) {
     dS = pow((double)t / (double)(t + 1), o->gamma);
   } else if (o->variant == V_CFRPLUS) {
     wS = (double)t;
+  } else if (o->variant == V_PCFRPLUS) {
+    wS = (double)t * (double)t;  /* quadratic averaging */
   }
   for (int n = 0; n < o->nn; ++n) {
     const Node* nd = &o->nodes[n];
@@ -552,8 +561,9 @@ static void update_player(Oracle* o, int i, int t) {
         size_t cell = (size_t)(nd->row + a) * o->nh + h;
         double x = o->R[cell] + o->rinst[cell];
         if (o->variant == V_DCFR) x *= x > 0.0 ? dpos : dneg;
-        if (o->variant == V_CFRPLUS && x < 0.0) x = 0.0;
+        if ((o->variant == V_CFRPLUS || o->variant == V_PCFRPLUS) && x < 0.0) x = 0.0;
         o->R[cell] = x;
+        if (o->variant == V_PCFRPLUS) o->M[cell] = o->rinst[cell];  /* predict the next regret */
         o->S[cell] *= dS;
       }
   }
@@ -608,6 +618,14 @@ int ocfr_set_node_state(Oracle* o, int node, const double* R, const double* S) {
 }
 
 void ocfr_set_iterations(Oracle* o, int t) { o->t = t; }
+
+/* Overwrite a decision node's Predictive CFR+ prediction ([nkids][nh]). */
+int ocfr_set_node_pred(Oracle* o, int node, const double* M) {
+  if (node < 0 || node >= o->nn || o->nodes[node].type != T_DEC) return -1;
+  const Node* nd = &o->nodes[node];
+  memcpy(o->M + (size_t)nd->row * o->nh, M, sizeof(double) * (size_t)nd->nkids * o->nh);
+  return 0;
+}
 
 /* ------------------------------------------------------------------ profiles and best response */
 
@@ -811,6 +829,7 @@ int ocfr_get_node(Oracle* o, int what, int node, double* out) {
   size_t off = (size_t)nd->row * o->nh, len = (size_t)nd->nkids * o->nh;
   if (what == 0) memcpy(out, o->R + off, sizeof(double) * len);
   else if (what == 1) memcpy(out, o->S + off, sizeof(double) * len);
+  else if (what == 4) memcpy(out, o->M + off, sizeof(double) * len);
   else if (what == 2) {
     regret_match(o, o->R, o->sig);
     memcpy(out, o->sig + off, sizeof(double) * len);

@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 T_DEC, T_FOLD, T_SHOW, T_CHANCE, T_LEAF = 0, 1, 2, 3, 4
-VARIANTS = {"cfr": 0, "cfr+": 1, "dcfr": 2}
+VARIANTS = {"cfr": 0, "cfr+": 1, "dcfr": 2, "pcfr+": 3}
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +75,8 @@ def _load():
         lib.ocfr_set_node_state.argtypes = [P, I, pd, pd]
         lib.ocfr_set_node_state.restype = I
         lib.ocfr_set_iterations.argtypes = [P, I]
+        lib.ocfr_set_node_pred.argtypes = [P, I, pd]
+        lib.ocfr_set_node_pred.restype = I
         lib.ocfr_node_reach.argtypes = [P, I, I, I, pd]
         lib.ocfr_node_reach.restype = I
         lib.ocfr_set_leaf_values.argtypes = [P, I, pd]
@@ -113,6 +115,7 @@ class Oracle:
             threads = os.cpu_count() or 1
         self.threads = int(threads)
         self._keep = (cards, r0, r1, board, strength, sizes)
+        self.variant = variant
         self._h = lib.ocfr_create(spec.game, int(board.size), _ptr(board, C.c_int), nh, _ptr(cards, C.c_int),
                                   _ptr(r0, C.c_double), _ptr(r1, C.c_double), _ptr(strength, C.c_int), nstr,
                                   float(spec.pot), float(spec.stack), len(spec.bet_sizes), _ptr(sizes, C.c_double),
@@ -186,6 +189,15 @@ class Oracle:
 
     def strategy(self, n: int) -> np.ndarray:
         return self._node_rows(2, n)
+
+    def prediction(self, n: int) -> np.ndarray:
+        """Predictive CFR+: the prediction M (last instantaneous regret) at node n."""
+        return self._node_rows(4, n)
+
+    def set_node_pred(self, n: int, M):
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        if self._lib.ocfr_set_node_pred(self._h, n, _ptr(M, C.c_double)) != 0:
+            raise ValueError(f"node {n} is not a decision node")
 
     def profile(self, n: int) -> np.ndarray:
         return self._node_rows(3, n)

@@ -18,16 +18,17 @@ LIB_PATH = os.path.join(_PKG, "libpcfr.so")
 
 CFR_OK, CFR_EINVAL, CFR_ENOMEM, CFR_ECUDA, CFR_ETIMEOUT, CFR_ESTATE = 0, -1, -2, -3, -4, -5
 CFR_GAME_HOLDEM, CFR_GAME_KUHN, CFR_GAME_LEDUC = 0, 1, 2
-CFR_VARIANT_CFR, CFR_VARIANT_CFRPLUS, CFR_VARIANT_DCFR = 0, 1, 2
+CFR_VARIANT_CFR, CFR_VARIANT_CFRPLUS, CFR_VARIANT_DCFR, CFR_VARIANT_PCFRPLUS = 0, 1, 2, 3
 CFR_NODE_DECISION, CFR_NODE_FOLD, CFR_NODE_SHOWDOWN, CFR_NODE_CHANCE, CFR_NODE_LEAF = 0, 1, 2, 3, 4
 LEAF_SLOTS, LEAF_IN, LEAF_HIDDEN, LEAF_OUT, LEAF_CARDS = 1326, 2752, 512, 2688, 48
 LEAF_SHAPES = ((LEAF_HIDDEN, LEAF_IN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_OUT, LEAF_HIDDEN))
-CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV = 0, 1, 2, 3
+CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV, CFR_READ_PREDICTION = 0, 1, 2, 3, 4
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
 CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM = 0, 1, 2
 SCHEDULES = {"auto": CFR_SCHEDULE_AUTO, "level": CFR_SCHEDULE_LEVEL, "stream": CFR_SCHEDULE_STREAM}
-VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR}
+VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR,
+            "pcfr+": CFR_VARIANT_PCFRPLUS}
 CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br", "leaf")
 EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iterate", "cfr_strategy",
            "cfr_exploitability", "cfr_tree_info", "cfr_node_info", "cfr_read_values", "cfr_sync",
@@ -356,7 +357,7 @@ def cfr_reset(tree):
 def cfr_read_values(tree, what: int, node: int, player: int = 0, game: int = 0) -> np.ndarray:
     info = cfr_node_info(tree, node, game)
     nh = cfr_tree_info(tree, game)[1]
-    shape = (info["n_actions"], nh) if what in (CFR_READ_REGRET, CFR_READ_AVG_SUM) else (nh,)
+    shape = (info["n_actions"], nh) if what in (CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_PREDICTION) else (nh,)
     out = np.zeros(shape, np.float64)
     _check(load().cfr_read_values(tree, game, what, player, node, out.ctypes.data_as(C.POINTER(C.c_double)),
                                   out.size))

@@ -147,6 +147,8 @@ std::vector<Discount> discount_table(const cfr_solver_opts& o, int capacity) {
       x.dS = std::pow(t / (t + 1.0), o.gamma);
     } else if (o.variant == CFR_VARIANT_CFRPLUS) {
       x.wS = t;
+    } else if (o.variant == CFR_VARIANT_PCFRPLUS) {
+      x.wS = t * t;  // quadratic averaging
     }
     d[(size_t)k] = x;
   }
@@ -257,7 +259,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if (!specs || n_games <= 0) return fail(CFR_EINVAL, "no game given");
   cfr_solver_opts o{CFR_VARIANT_DCFR, 1.5, 0.0, 2.0, 1, 0, CFR_PRECISION_PAIRS, CFR_SCHEDULE_AUTO};
   if (opts) o = *opts;
-  if (o.variant < 0 || o.variant > 2) return fail(CFR_EINVAL, "unknown CFR variant");
+  if (o.variant < 0 || o.variant > 3) return fail(CFR_EINVAL, "unknown CFR variant");
   if (o.precision != CFR_PRECISION_PAIRS && o.precision != CFR_PRECISION_SINGLE)
     return fail(CFR_EINVAL, "unknown precision");
   const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
@@ -324,7 +326,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     max_prog = std::max(max_prog, (int)programs[g].size());
     for (int n : programs[g])
       for (int p = 0; p < 2; ++p)
-        max_loads = std::max(max_loads, (int)node_loads(t->host[g], n, p, true, (uint32_t)t->host[g].hstride).size());
+        max_loads = std::max(max_loads, (int)node_loads(t->host[g], n, p, true, (uint32_t)t->host[g].hstride,
+                                                        o.variant == CFR_VARIANT_PCFRPLUS).size());
   }
   const int stream_prog = max_prog * (int)sizeof(ProgOp) <= 64 * 1024 ? max_prog : 0;
   const int stream_half = std::max(kStreamHalfMin, max_loads);
@@ -335,10 +338,11 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   int stream_units_max = 0;
   for (int g = 0; g < n_games; ++g) {
     std::array<int, 16>& m = table_meta[g];
-    chunk_lists[g] = stream_tables(t->host[g], programs[g], stream_half, unit_lists[g], &m[0], &m[4], &m[8], &m[12]);
+    chunk_lists[g] = stream_tables(t->host[g], programs[g], stream_half, o.variant == CFR_VARIANT_PCFRPLUS,
+                                   unit_lists[g], &m[0], &m[4], &m[8], &m[12]);
     for (int p = 0; p < 2; ++p) stream_units_max = std::max(stream_units_max, m[4 + p] + m[4 + 2 + p]);
     const size_t span = std::max(t->host[g].nodes.size(), (size_t)t->host[g].n_rows) * (size_t)t->host[g].hstride;
-    stream_ok = stream_ok && span < (1u << 30);
+    stream_ok = stream_ok && span < (1u << kArrShift);
   }
   stream_units_max = (stream_units_max + 3) / 4 * 4;  // keeps the ring 16-byte aligned
   const int stream_units = stream_prog ? stream_units_max : 0;
@@ -415,6 +419,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     if ((rc = zeros(t, rows, &d.R)) || (rc = zeros(t, rows, &d.S)) || (rc = zeros(t, rows * vf, &sig)) ||
         (rc = zeros(t, rows * vf, &sigb)) || (rc = zeros(t, cells * vf, &rch)) || (rc = zeros(t, cells * vf, &rchb)) ||
         (rc = zeros(t, cells * vf, &cf)) || (rc = zeros(t, cells * vf, &cfb)) ||
+        (o.variant == CFR_VARIANT_PCFRPLUS && (rc = zeros(t, rows, &d.M))) ||
         (rc = zeros(t, (size_t)2 * d.n_chunks, &d.br_partial)) || (rc = zeros(t, 2, &d.br_out)) ||
         (rc = zeros(t, 1, &d.br_done))) {
       delete t;
@@ -716,6 +721,7 @@ int cfr_reset(cfr_tree* t) {
     const size_t rows = (size_t)d.n_rows * d.hstride * sizeof(double);
     CK(cudaMemsetAsync(d.R, 0, rows, t->stream));
     CK(cudaMemsetAsync(d.S, 0, rows, t->stream));
+    if (d.M) CK(cudaMemsetAsync(d.M, 0, rows, t->stream));
   }
   CK(cudaMemsetAsync(t->d_iter, 0, sizeof(int), t->stream));
   t->state_gen += 1;
@@ -769,11 +775,12 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
   const NodeDev& nd = h.nodes[node];
   const int H = h.n_hands;
   const size_t S = (size_t)h.hstride;
-  if (what == CFR_READ_REGRET || what == CFR_READ_AVG_SUM) {
+  if (what == CFR_READ_REGRET || what == CFR_READ_AVG_SUM || what == CFR_READ_PREDICTION) {
     if (nd.type != kDecision) return fail(CFR_EINVAL, "node is not a decision node");
+    if (what == CFR_READ_PREDICTION && !d.M) return fail(CFR_EINVAL, "only Predictive CFR+ keeps a prediction");
     const size_t need = (size_t)nd.n_kids * H;
     if (out_len < need) return fail(CFR_EINVAL, "output buffer too small");
-    const double* src = (what == CFR_READ_REGRET ? d.R : d.S) + (size_t)nd.row * S;
+    const double* src = (what == CFR_READ_REGRET ? d.R : what == CFR_READ_AVG_SUM ? d.S : d.M) + (size_t)nd.row * S;
     CK(cudaMemcpy2DAsync(out, (size_t)H * 8, src, S * 8, (size_t)H * 8, nd.n_kids, cudaMemcpyDeviceToHost,
                          t->stream));
     CK(cudaStreamSynchronize(t->stream));
@@ -801,15 +808,17 @@ int cfr_write_values(cfr_tree* t, int game, int what, int node, const double* in
   const GameDev& d = t->dev[game];
   if (node < 0 || node >= (int)h.nodes.size() || h.nodes[node].type != kDecision)
     return fail(CFR_EINVAL, "node is not a decision node");
-  if (what != CFR_READ_REGRET && what != CFR_READ_AVG_SUM) return fail(CFR_EINVAL, "what must be REGRET or AVG_SUM");
+  if (what != CFR_READ_REGRET && what != CFR_READ_AVG_SUM && what != CFR_READ_PREDICTION)
+    return fail(CFR_EINVAL, "what must be REGRET, AVG_SUM or PREDICTION");
+  if (what == CFR_READ_PREDICTION && !d.M) return fail(CFR_EINVAL, "only Predictive CFR+ keeps a prediction");
   const NodeDev& nd = h.nodes[node];
   const size_t H = (size_t)h.n_hands, S = (size_t)h.hstride;
   if (!in || in_len < (size_t)nd.n_kids * H) return fail(CFR_EINVAL, "input buffer too small");
-  double* dst = (what == CFR_READ_REGRET ? d.R : d.S) + (size_t)nd.row * S;
+  double* dst = (what == CFR_READ_REGRET ? d.R : what == CFR_READ_AVG_SUM ? d.S : d.M) + (size_t)nd.row * S;
   CK(cudaMemcpy2DAsync(dst, S * 8, in, H * 8, H * 8, nd.n_kids, cudaMemcpyHostToDevice, t->stream));
   // new regrets: the current strategy and both players' reach follow them at once
-  if (what == CFR_READ_REGRET && launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "strategy launch failed");
-  if (what == CFR_READ_REGRET) t->launches += 1;
+  if (what != CFR_READ_AVG_SUM && launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "strategy launch failed");
+  if (what != CFR_READ_AVG_SUM) t->launches += 1;
   CK(cudaStreamSynchronize(t->stream));
   t->state_gen += 1;
   t->avg_gen = -1;

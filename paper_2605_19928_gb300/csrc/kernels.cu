@@ -786,16 +786,20 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
         const NodeDev nd = nodes[n];
         const V rr = P::sub(v[nd.first_kid + (rb + r - nd.row)], v[n]);  // instantaneous regret
         const double contrib = P::to_double(P::mul(rch[n], sg[r]));     // pi_i(I) sigma(I, a)
-        x = Rc[r] + P::to_double(rr);
+        const double rd = P::to_double(rr);
+        x = Rc[r] + rd;
         if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
-        if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
-        const double sn = fma(Sc[r], d.dS, variant == 1 ? d.wS * contrib : contrib);  // wS = 1 unless CFR+
+        if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;  // CFR+, Predictive CFR+
+        const double sn = fma(Sc[r], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
         if (valid) {
           gR[(size_t)r * stride] = x;
           gS[(size_t)r * stride] = sn;
+          if (variant == 3) G.M[(size_t)(rb + r) * stride + h] = rd;  // the prediction of the next regret
         }
+        if (variant == 3) x += rd;  // Predictive CFR+ matches R + M
       } else {
         x = MODE == kModeInit ? Rc[r] : Sc[r];
+        if (MODE == kModeInit && G.M) x += valid ? G.M[(size_t)(rb + r) * stride + h] : 0.0;
       }
       if (wr) sg[r] = __double_as_longlong(x) > 0 ? P::of_double(x) : P::zero();
     }
@@ -948,6 +952,7 @@ struct StreamLane {
   size_t stride;
   double* R;        // column h of R
   double* S;
+  double* M;        // column h of the Predictive CFR+ prediction (null otherwise)
   V* reach;         // column h of player p's reach plane
   V* cfv;           // column h of player p's value plane
   uint64_t* ring;   // this lane's prefetch ring: unit u of half k at ring[(k * half + u) * 32]
@@ -963,12 +968,14 @@ __device__ __forceinline__ void stream_issue(const StreamLane<P>& L, const uint3
   uint64_t* ring = L.ring + (size_t)half * L.half * 32;
   for (int u = u0; u < u1; ++u) {
     const uint32_t d = units[u];
-    const uint32_t arr = d >> 30, off = d & 0x3fffffffu;
+    const uint32_t arr = d >> kArrShift, off = d & kArrOffMask;
     uint64_t* dst = ring + (size_t)(u - u0) * 32;
     if (arr == kArrR)
       cp_async<8>(dst, L.R + off);
     else if (arr == kArrS)
       cp_async<8>(dst, L.S + off);
+    else if (arr == kArrM)
+      cp_async<8>(dst, L.M + off);
     else
       cp_async<(int)sizeof(V)>(dst, (arr == kArrReach ? L.reach : L.cfv) + off);
   }
@@ -1030,15 +1037,23 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
             c[a] = st[(--sp) * 32];
         }
       }
+      const bool pred = L.M != nullptr;  // Predictive CFR+: R, M, S, reach
       const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-      const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
-      const V pi = ring_value<P>(ring + (size_t)(u + 2 * A) * 32);
-      u += 2 * A + 1;
+      const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
+      const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + (pred ? 2 : 1) * A) * 32);
+      const V pi = ring_value<P>(ring + (size_t)(u + (pred ? 3 : 2) * A) * 32);
+      u += (pred ? 3 : 2) * A + 1;
       double Rv[kStreamMaxActions];
       V sg[kStreamMaxActions];
+      {
+        double Rm[kStreamMaxActions];
 #pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
-      regret_match<P>(Rv, A, sg);
+        for (int a = 0; a < kStreamMaxActions; ++a) {
+          Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+          Rm[a] = Rv[a] + (pred && a < A ? Mr[(size_t)a * 32] : 0.0);
+        }
+        regret_match<P>(Rm, A, sg);
+      }
       typename P::Acc acc = P::acc0();
 #pragma unroll
       for (int a = 0; a < kStreamMaxActions; ++a)
@@ -1049,13 +1064,15 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
         if (a < A) {
           const V rr = P::sub(c[a], val);                          // instantaneous regret
           const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
-          double x = Rv[a] + P::to_double(rr);
+          const double rd = P::to_double(rr);
+          double x = Rv[a] + rd;
           if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
-          if (variant == 1 && __double_as_longlong(x) < 0) x = 0.0;
-          const double sn = fma(Sr[(size_t)a * 32], d.dS, variant == 1 ? d.wS * contrib : contrib);
+          if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;
+          const double sn = fma(Sr[(size_t)a * 32], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
           if (L.valid) {
             L.R[(size_t)nd.row_off + (size_t)a * L.stride] = x;
             L.S[(size_t)nd.row_off + (size_t)a * L.stride] = sn;
+            if (pred) L.M[(size_t)nd.row_off + (size_t)a * L.stride] = rd;
           }
         }
       }
@@ -1080,12 +1097,15 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
     const int A = nd.A;
     if (nd.type == kDecision && nd.player == L.p) {
       if (L.valid) L.reach[nd.node_off] = x;
+      const bool pred = L.M != nullptr;  // Predictive CFR+: R then M
       const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-      u += A;
+      const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
+      u += (pred ? 2 : 1) * A;
       double Rv[kStreamMaxActions];
       V sg[kStreamMaxActions];
 #pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+      for (int a = 0; a < kStreamMaxActions; ++a)
+        Rv[a] = a < A ? Rr[(size_t)a * 32] + (pred ? Mr[(size_t)a * 32] : 0.0) : 0.0;
       regret_match<P>(Rv, A, sg);
 #pragma unroll
       for (int a = kStreamMaxActions - 1; a >= 0; --a) {
@@ -1185,8 +1205,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const bool staged = prog_nodes > 0;
     const StreamLane<P> L{G, staged ? sprog : G.prog, staged ? sunits : gunits_b, p, valid,
                           valid ? G.hand_mask[h] : 0ull, stride,
-                          G.R + h, G.S + h, static_cast<V*>(G.reach) + plane, static_cast<V*>(G.cfv) + plane, ring,
-                          half_units, st};
+                          G.R + h, G.S + h, G.M ? G.M + h : nullptr, static_cast<V*>(G.reach) + plane,
+                          static_cast<V*>(G.cfv) + plane, ring, half_units, st};
     const Discount d = disc;
     int sp = 0;
     stream_pass<P>(L, p, L.units, [&](int k0, int k1, int half) {
@@ -1231,6 +1251,12 @@ __global__ void k_current_rows(const GameDev* __restrict__ games, int n_games) {
       double Rv[kStreamMaxActions];
       V sg[kStreamMaxActions];
       load_rows(G.R + (size_t)nd.row * stride + h, stride, nd.n_kids, Rv);
+      if (G.M) {  // Predictive CFR+: regret matching of R + M
+        double Mv[kStreamMaxActions];
+        load_rows(G.M + (size_t)nd.row * stride + h, stride, nd.n_kids, Mv);
+#pragma unroll
+        for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] += Mv[a];
+      }
       regret_match<P>(Rv, nd.n_kids, sg);
 #pragma unroll
       for (int a = 0; a < kStreamMaxActions; ++a)

@@ -78,8 +78,9 @@ struct alignas(16) ProgOp {
   int32_t first_kid;
 };
 
-// One load of the stream schedule's prefetch: array << 30 | element offset.
-enum StreamArray : uint32_t { kArrR = 0, kArrS = 1, kArrReach = 2, kArrCfv = 3 };
+// One load of the stream schedule's prefetch: array << kArrShift | element offset.
+enum StreamArray : uint32_t { kArrR = 0, kArrS = 1, kArrReach = 2, kArrCfv = 3, kArrM = 4 };
+constexpr uint32_t kArrShift = 29, kArrOffMask = (1u << 29) - 1u;
 static_assert(sizeof(ProgOp) == 16, "ProgOp is 16 bytes");
 
 // Offsets (in uint16) of the terminal-table sections for H hands of k cards from a deck.
@@ -130,6 +131,7 @@ struct GameDev {
   // state
   double* R;
   double* S;
+  double* M;                   // Predictive CFR+ prediction [n_rows][hstride] (else null)
   void* sigma;
   void* sigbar;
   void* reach;

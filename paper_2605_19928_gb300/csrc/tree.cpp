@@ -566,7 +566,7 @@ std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& p
   return out;
 }
 
-std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half,
+std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half, bool pred,
                                    std::vector<uint32_t>& units, int unit_off[4], int unit_count[4],
                                    int chunk_off[4], int chunk_count[4]) {
   std::vector<int32_t> chunks;
@@ -581,7 +581,7 @@ std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>
     int used = 0;
     for (int k = 0; k < N; ++k) {
       const int n = pre[(size_t)(backward ? N - 1 - k : k)];
-      const std::vector<uint32_t> mine = node_loads(g, n, p, backward, S);
+      const std::vector<uint32_t> mine = node_loads(g, n, p, backward, S, pred);
       if (k == 0 || used + (int)mine.size() > half) {
         chunks.push_back(k);
         chunks.push_back((int)units.size() - unit_off[q]);
@@ -598,18 +598,20 @@ std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>
   return chunks;
 }
 
-std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S) {
+std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S, bool pred) {
   std::vector<uint32_t> mine;
   const NodeDev& nd = g.nodes[(size_t)n];
   if (backward)  // values of the terminal children, in child order
     for (int a = 0; a < nd.n_kids; ++a)
       if (is_terminal(g.nodes[(size_t)(nd.first_kid + a)]))
-        mine.push_back(kArrCfv << 30 | (uint32_t)(nd.first_kid + a) * S);
+        mine.push_back(kArrCfv << kArrShift | (uint32_t)(nd.first_kid + a) * S);
   if (nd.type == kDecision && nd.player == p) {
-    for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrR << 30 | (uint32_t)(nd.row + a) * S);
+    for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrR << kArrShift | (uint32_t)(nd.row + a) * S);
+    if (pred)
+      for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrM << kArrShift | (uint32_t)(nd.row + a) * S);
     if (backward) {
-      for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrS << 30 | (uint32_t)(nd.row + a) * S);
-      mine.push_back(kArrReach << 30 | (uint32_t)n * S);
+      for (int a = 0; a < nd.n_kids; ++a) mine.push_back(kArrS << kArrShift | (uint32_t)(nd.row + a) * S);
+      mine.push_back(kArrReach << kArrShift | (uint32_t)n * S);
     }
   }
   return mine;

@@ -53,23 +53,23 @@ std::vector<int32_t> row_nodes(const HostGame& g);
 // schedule (its root is inner and chance nodes have no terminal children).
 std::vector<int32_t> dfs_program(const HostGame& g, int* depth, int* max_actions, bool* ok);
 
-// Loads of node n in a pass of the stream schedule for player p (StreamArray << 30 |
+// Loads of node n in a pass of the stream schedule for player p (StreamArray << kArrShift |
 // element offset, hstride S): bottom-up, the values of its terminal children and, at p's
-// decision nodes, R and S of each action and p's reach; top-down, R of each action at p's
-// decision nodes.
-std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S);
+// decision nodes, R of each action (then the Predictive CFR+ prediction M with pred), S of
+// each action and p's reach; top-down, R (and M) of each action at p's decision nodes.
+std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward, uint32_t S, bool pred);
 
 // The program as the stream kernel reads it: one ProgOp per node in pre-order.
 std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& pre);
 
 // Load tables of the stream schedule, four passes: the bottom-up pass of player 0 and of
 // player 1 and the top-down pass of player 0 and of player 1 (node_loads).  `units` receives each pass's
-// loads in the order the pass uses them (StreamArray << 30 | element offset), unit_off[q] /
+// loads in the order the pass uses them (StreamArray << kArrShift | element offset), unit_off[q] /
 // unit_count[q] where pass q's begin and how many; the result holds each pass's chunks --
 // runs of consecutive nodes whose loads fit `half` units -- as (first node position, first
 // unit) pairs followed by (program length, unit count), chunk_off[q] (in pairs) and
 // chunk_count[q] where pass q's begin and how many.
-std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half,
+std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half, bool pred,
                                    std::vector<uint32_t>& units, int unit_off[4], int unit_count[4],
                                    int chunk_off[4], int chunk_count[4]);
 

@@ -240,15 +240,23 @@ def profile_value(g, prof, i=0):
 
 
 def run_cfr(g, iterations, variant="cfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True):
-    """CFR by definition: regrets from profile deviations, then the variant update."""
-    R, S = {}, {}
+    """CFR by definition: regrets from profile deviations, then the variant update.
+    Predictive CFR+ ("pcfr+") plays regret matching on R + M with M the last instantaneous
+    regret, keeps R non-negative and weighs the average by t^2."""
+    R, S, M = {}, {}, {}
+
+    def strategy():
+        if variant != "pcfr+":
+            return regret_matching(R)
+        return regret_matching({k: [R[k][a] + M.get(k, [0.0] * len(R[k]))[a] for a in range(len(R[k]))] for k in R})
+
     for t in range(1, iterations + 1):
         ta, tb = t ** alpha, t ** beta
         dpos, dneg, dS = ta / (ta + 1.0), tb / (tb + 1.0), (t / (t + 1.0)) ** gamma
         players = [0, 1]
-        snap = regret_matching(R) if not alternating else None
+        snap = strategy() if not alternating else None
         for i in players:
-            prof = regret_matching(R) if alternating else snap
+            prof = strategy() if alternating else snap
             reg, _ = regrets_and_values(g, prof, i)
             reach = own_reach(g, prof, i)
             for key, r in reg.items():
@@ -258,15 +266,17 @@ def run_cfr(g, iterations, variant="cfr", alpha=1.5, beta=0.0, gamma=2.0, altern
                     x = old[a] + r[a]
                     if variant == "dcfr":
                         x *= dpos if x > 0 else dneg
-                    if variant == "cfr+":
+                    if variant in ("cfr+", "pcfr+"):
                         x = max(x, 0.0)
                     new.append(x)
                 R[key] = new
+                if variant == "pcfr+":
+                    M[key] = list(r)
             for key, pi in reach.items():
                 n = len(reg[key])
                 sig = prof.probs(key, n)
                 old = S.get(key, [0.0] * n)
-                wS = float(t) if variant == "cfr+" else 1.0
+                wS = {"cfr+": float(t), "pcfr+": float(t) * t}.get(variant, 1.0)
                 S[key] = [(old[a] * (dS if variant == "dcfr" else 1.0)) + wS * pi * sig[a] for a in range(n)]
     return R, S
 

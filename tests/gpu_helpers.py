@@ -103,11 +103,14 @@ def compare_state(tree, oracle, mapping, game=0, check_cfv=True, check_strategy=
 
 
 def inject(tree, oracle, mapping, game=0, player=None):
-    """Load the GPU's R and S (all decision nodes, or one player's) into the oracle."""
+    """Load the GPU's R and S (and the Predictive CFR+ prediction) of all decision nodes, or
+    of one player's, into the oracle."""
     for g, o, info in mapping:
         if info["type"] == capi.CFR_NODE_DECISION and (player is None or info["player"] == player):
             oracle.set_node_state(o, capi.cfr_read_values(tree, capi.CFR_READ_REGRET, g, game=game),
                                   capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, g, game=game))
+            if oracle.variant == "pcfr+":
+                oracle.set_node_pred(o, capi.cfr_read_values(tree, capi.CFR_READ_PREDICTION, g, game=game))
 
 
 def stored_cfv(tree, g, info):
@@ -129,6 +132,9 @@ def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, f
             S_g = capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, g, game=game)
             worst["R"] = max(worst["R"], close(R_g, oracle.regrets(o), rtol, floor=floor, what=f"R node {g}"))
             worst["S"] = max(worst["S"], close(S_g, oracle.avg_sums(o), rtol, what=f"S node {g}"))
+            if oracle.variant == "pcfr+":
+                M_g = capi.cfr_read_values(tree, capi.CFR_READ_PREDICTION, g, game=game)
+                close(M_g, oracle.prediction(o), rtol, floor=floor, what=f"prediction node {g}")
         if not stored_cfv(tree, g, info):
             continue
         v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=player, game=game)

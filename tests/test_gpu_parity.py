@@ -48,9 +48,9 @@ def leduc_random(seed=11):
 # differently (with few hands, or uniform deals, such ties appear within a few iterations
 # and send two correct runs down different paths).
 CASES = {
-    "kuhn": (kuhn_random, ["cfr", "cfr+", "dcfr"], False),
-    "leduc": (leduc_random, ["cfr", "cfr+", "dcfr"], False),
-    "river_203": (lambda: river(203), ["dcfr", "cfr+"], True),        # 26 blocks, ragged tail
+    "kuhn": (kuhn_random, ["cfr", "cfr+", "dcfr", "pcfr+"], False),
+    "leduc": (leduc_random, ["cfr", "cfr+", "dcfr", "pcfr+"], False),
+    "river_203": (lambda: river(203), ["dcfr", "cfr+", "pcfr+"], True),        # 26 blocks, ragged tail
     "river_64_r4": (lambda: river(64, seed=9, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
                     ["dcfr"], False),
     "turn_40": (lambda: turn(40), ["dcfr"], False),
@@ -116,7 +116,8 @@ def test_first_ten_iterations_match_oracle(case, variant):
 
 @pytest.mark.parametrize("game,variant,iters,bound", [
     ("kuhn", "cfr", 1000, 2e-3), ("kuhn", "cfr+", 1000, 1e-3),
-    ("leduc", "cfr", 1000, 0.02), ("leduc", "cfr+", 1000, 2e-3), ("leduc", "dcfr", 1000, 2e-3)])
+    ("leduc", "cfr", 1000, 0.02), ("leduc", "cfr+", 1000, 2e-3), ("leduc", "dcfr", 1000, 2e-3),
+    ("leduc", "pcfr+", 1000, 2e-3)])
 def test_uniform_kuhn_and_leduc_converge_like_the_oracle(game, variant, iters, bound):
     """Config: Leduc (936 infosets) and Kuhn with uniform deals, 1000 iterations, FP32 GPU vs
     FP64 oracle.  Exact ties make the trajectories differ, so compare what is unique: both
@@ -239,7 +240,7 @@ def test_invalid_specs_are_rejected():
 # the oracle exactly like the level schedule, and with the level schedule bit for bit.
 
 STREAM_CASES = [("kuhn", "cfr"), ("leduc", "cfr+"), ("river_203", "dcfr"), ("turn_40", "dcfr"),
-                ("river_64_r4", "dcfr")]
+                ("river_64_r4", "dcfr"), ("leduc", "pcfr+"), ("river_203", "pcfr+")]
 
 
 @pytest.mark.parametrize("case,variant", STREAM_CASES)
@@ -256,7 +257,7 @@ def test_stream_schedule_simultaneous_updates_match_oracle():
     run_pair(river(97, seed=21), "dcfr", iters=5, alternating=False, schedule="stream")
 
 
-def _state(tree, n_games):
+def _state(tree, n_games, with_pred=False):
     out = []
     for game in range(n_games):
         n_nodes = capi.cfr_tree_info(tree, game)[0]
@@ -265,6 +266,8 @@ def _state(tree, n_games):
             if info["type"] == capi.CFR_NODE_DECISION:
                 out.append(capi.cfr_read_values(tree, capi.CFR_READ_REGRET, n, game=game))
                 out.append(capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, n, game=game))
+                if with_pred:
+                    out.append(capi.cfr_read_values(tree, capi.CFR_READ_PREDICTION, n, game=game))
                 out.append(capi.cfr_strategy(tree, n, average=False, game=game))
                 out.append(capi.cfr_strategy(tree, n, average=True, game=game))
             if n == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN):
@@ -274,7 +277,7 @@ def _state(tree, n_games):
 
 
 @pytest.mark.parametrize("precision", ["pairs", "single"])
-@pytest.mark.parametrize("variant,alternating", [("dcfr", True), ("cfr+", True), ("cfr", False)])
+@pytest.mark.parametrize("variant,alternating", [("dcfr", True), ("cfr+", True), ("cfr", False), ("pcfr+", True)])
 def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alternating):
     specs = [river(203, seed=51), river(64, seed=52, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
              leduc_random(seed=53), turn(40, seed=54), kuhn_random(seed=55)]
@@ -285,7 +288,7 @@ def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alter
         try:
             assert capi.cfr_schedule(tree) == capi.SCHEDULES[schedule]
             capi.cfr_iterate(tree, 7)
-            states.append(_state(tree, len(specs)))
+            states.append(_state(tree, len(specs), with_pred=variant == "pcfr+"))
             expl.append(capi.cfr_exploitability(tree, len(specs)))
         finally:
             capi.cfr_tree_destroy(tree)

@@ -246,7 +246,8 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("variant,alternating", [("cfr", True), ("cfr+", True), ("dcfr", True), ("dcfr", False)])
+@pytest.mark.parametrize("variant,alternating", [("cfr", True), ("cfr+", True), ("dcfr", True), ("dcfr", False),
+                                               ("pcfr+", True), ("pcfr+", False)])
 def test_two_iterations_match_definitions(oracle_mod, case, variant, alternating):
     spec = CASES[case]()
     if case in ("kuhn", "leduc"):
@@ -255,8 +256,9 @@ def test_two_iterations_match_definitions(oracle_mod, case, variant, alternating
     o = oracle_mod.Oracle(spec, variant=variant, alternating=alternating, threads=2)
     g = bf_game(spec)
     hmap = history_map(o, g)
-    o.iterate(2)
-    R, S = bf.run_cfr(g, 2, variant=variant, alternating=alternating)
+    n_it = 3 if variant == "pcfr+" else 2  # the prediction first steers iteration 2
+    o.iterate(n_it)
+    R, S = bf.run_cfr(g, n_it, variant=variant, alternating=alternating)
     assert compare_state(o, g, hmap, R, S) > 0
 
 
@@ -326,7 +328,7 @@ def test_cfr_plus_regrets_never_negative(oracle_mod):
             assert (o.regrets(n) >= 0).all()
 
 
-@pytest.mark.parametrize("variant", ["cfr", "cfr+", "dcfr"])
+@pytest.mark.parametrize("variant", ["cfr", "cfr+", "dcfr", "pcfr+"])
 def test_leduc_exploitability_falls_to_zero(oracle_mod, variant):
     o = oracle_mod.Oracle(synth.leduc(), variant=variant, threads=1)
     seen = []
@@ -336,7 +338,7 @@ def test_leduc_exploitability_falls_to_zero(oracle_mod, variant):
         assert e >= -1e-15
         seen.append(e)
     assert seen[0] > seen[1] > seen[2]
-    assert seen[2] < {"cfr": 0.02, "cfr+": 0.002, "dcfr": 0.002}[variant]
+    assert seen[2] < {"cfr": 0.02, "cfr+": 0.002, "dcfr": 0.002, "pcfr+": 0.002}[variant]
 
 
 def test_thread_count_does_not_change_results(oracle_mod):
