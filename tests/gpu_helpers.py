@@ -92,8 +92,10 @@ def compare_state(tree, oracle, mapping, game=0, check_cfv=True, check_strategy=
             worst["R"] = max(worst["R"], close(R_g, R_o, floor=floor, what=f"R node {g}"))
             worst["S"] = max(worst["S"], close(S_g, S_o, what=f"S node {g}"))
             if check_strategy:
+                # Predictive CFR+ plays regret matching of R + M (regrets plus prediction)
+                R_m = R_o + oracle.prediction(o) if oracle.variant == "pcfr+" else R_o
                 sig = capi.cfr_strategy(tree, g, average=False, game=game)
-                worst["sigma"] = max(worst["sigma"], compare_strategies(sig, R_o, what=f"sigma node {g}"))
+                worst["sigma"] = max(worst["sigma"], compare_strategies(sig, R_m, what=f"sigma node {g}"))
         if check_cfv and stored_cfv(tree, g, info):
             for i in (0, 1):
                 v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=i, game=game)
