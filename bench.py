@@ -42,9 +42,11 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["river", "batch", "leaf", "gemm"], default="river",
+    ap.add_argument("--workload", choices=["river", "batch", "leaf", "flop", "gemm"], default="river",
                     help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle; "
-                         "leaf: depth-limited turn subgame with the BF16 leaf network, against the exact turn")
+                         "leaf: depth-limited turn subgame with the BF16 leaf network, against the exact turn; "
+                         "flop: depth-limited flop subgame (leaves at the river card), against the exact flop; "
+                         "gemm: the leaf network's dense layers alone")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--iters-per-step", type=int, default=None, help="default 1000 (river) or 500 (batch)")
     ap.add_argument("--precision", choices=["pairs", "single"], default="pairs")
@@ -571,7 +573,8 @@ def run_gemm(args):
 
 
 def run_leaf(args):
-    """Depth-limited turn subgame with the learned leaf network vs the exact turn subgame."""
+    """Depth-limited subgame with the learned leaf network vs the exact subgame: the turn
+    (workload leaf) or the flop (workload flop, turn card dealt by chance inside the tree)."""
     import numpy as np
     import torch
 
@@ -588,8 +591,10 @@ def run_leaf(args):
     capi.use_torch_allocator()
     stream = torch.cuda.current_stream(device)
     kw = dict(seed=0 + 1000 * rank, range_seed=1 + 1000 * rank)
-    spec_leaf = synth.ranked_turn_subgame(depth_limit=1, **kw)
-    spec_exact = synth.ranked_turn_subgame(depth_limit=0, **kw)
+    flop = args.workload == "flop"
+    make = synth.ranked_flop_subgame if flop else synth.ranked_turn_subgame
+    spec_leaf = make(depth_limit=1, **kw)
+    spec_exact = make(depth_limit=0, **kw)
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, precision=args.precision)
     W, b = leafnet_train.load_weights()
     meta = np.load(os.path.join(ROOT, "paper_2605_19928_gb300", "leafnet_weights.npz"))["meta"]
@@ -627,9 +632,10 @@ def run_leaf(args):
     gpu_launches = capi.cfr_counters(L)["kernel_launches"] - launches0
     value, t_max = aggregate(args.steps * ips, t_leaf, world, dist, device)
     e_leaf_own, _ = capi.cfr_exploitability_result(L)
-    t_exact = timed(E, max(1, args.steps // 4), 1)
+    exact_steps = 1 if flop else max(1, args.steps // 4)
+    t_exact = timed(E, exact_steps, 1)
     e_exact, _ = capi.cfr_exploitability_result(E)
-    exact_ips = max(1, args.steps // 4) * ips / t_exact
+    exact_ips = exact_steps * ips / t_exact
     # the learned turn strategy in the exact game: E's river play, L's turn play
     pe, pl = node_paths(capi, E), node_paths(capi, L)
     for path, nl in pl.items():
@@ -649,8 +655,9 @@ def run_leaf(args):
     capi.cfr_eval_leaves(L)
     capi.cfr_iterate(E, 1)
     rel, abs_err = [], 0.0
+    lp = {n: p for p, n in pl.items()}
     for _, nl, _ in capi.cfr_leaf_info(L):
-        path = [p for p, n in pl.items() if n == nl][0]
+        path = lp[nl]
         v_net = capi.cfr_read_values(L, capi.CFR_READ_CFV, nl, player=0)
         v_ex = capi.cfr_read_values(E, capi.CFR_READ_CFV, pe[path], player=0)
         rel.append(float(np.abs(v_net - v_ex).sum() / max(np.abs(v_ex).sum(), 1e-30)))
@@ -685,11 +692,18 @@ def run_leaf(args):
                 "ms_per_iter": 1000.0 * t_max / (args.steps * ips), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": ("f32x2" if args.precision == "pairs" else "f32") + " values, f64 R/S, bf16 network",
-                "data": "synthetic (rank-based showdowns; network trained on 200k self-generated river solves)",
-                "config": {"workload": "depth-limited turn subgame, leaf network at the river card",
-                           "board_cards": 4, "hands": spec_leaf.n_hands, "leaves": len(leaves),
+                "data": "synthetic (rank-based showdowns; network trained on %dk self-generated river solves)"
+                        % (int(meta[0]) // 1000),
+                "config": {"workload": ("depth-limited flop subgame (turn card by chance), leaf network at the "
+                                        "river card" if flop else
+                                        "depth-limited turn subgame, leaf network at the river card"),
+                           "board_cards": len(spec_leaf.board), "hands": spec_leaf.n_hands, "leaves": len(leaves),
+                           "nodes": capi.cfr_tree_info(L)[0],
                            "network": "2752-512-512-512-2688 BF16, GELU", "pot": spec_leaf.pot,
-                           "stack": spec_leaf.stack, "bet_sizes": "0.5,1.0 pot,all-in", "max_raises": 3,
+                           "stack": spec_leaf.stack,
+                           "bet_sizes": ",".join("all-in" if x <= 0 else "%g" % x for x in spec_leaf.bet_sizes)
+                                        + " (pot fractions)",
+                           "max_raises": spec_leaf.max_raises,
                            "variant": "DCFR(1.5,0,2) alternating", "iters_per_step": ips,
                            "step": "reset + iterations + exploitability (network leaves)",
                            "l2": "flushed between steps (256 MB write, outside the timed events)",
@@ -698,9 +712,12 @@ def run_leaf(args):
                                "exploitability_mbb": mbb(e_exact[0])},
                 "learned_form": {"exploitability_in_exact_game_mbb": mbb(e_hybrid[0]),
                                  "exploitability_with_network_leaves_mbb": mbb(e_leaf_own[0]),
+                                 "note_network_leaves": "best responses with the network's values at the "
+                                                        "leaves; the two players' outputs are not zero-sum, "
+                                                        "so this can fall below 0",
                                  "gap_to_exact_mbb": mbb(e_hybrid[0]) - mbb(e_exact[0]),
-                                 "note": "turn strategy of the depth-limited solve, river play of the exact "
-                                         "solve, best responses in the exact game"},
+                                 "note": "strategy of the depth-limited solve above the leaves, river play of "
+                                         "the exact solve, best responses in the exact game"},
                 "leaf_values_vs_exact_river": leaf_check,
                 "network": {"training_solves": int(meta[0]), "solve_iters": int(meta[1]), "epochs": int(meta[2]),
                             "median_solve_exploitability_mbb": float(meta[4]),
@@ -717,8 +734,8 @@ def run_leaf(args):
 def main(argv=None):
     args = parse_args(argv)
     if args.iters_per_step is None:
-        args.iters_per_step = {"batch": 500, "leaf": 300}.get(args.workload, 1000)
-    if args.workload == "leaf" and args.impl == "ours":
+        args.iters_per_step = {"batch": 500, "leaf": 300, "flop": 300}.get(args.workload, 1000)
+    if args.workload in ("leaf", "flop") and args.impl == "ours":
         return run_leaf(args)
     if args.workload == "gemm" and args.impl == "ours":
         return run_gemm(args)

@@ -48,8 +48,10 @@ enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_
 
 /*
  * One subgame (Section 5, "Game": heads-up poker solved to the end of a betting round).
- *   game        CFR_GAME_HOLDEM: a hold'em turn (n_board 4: turn betting, a chance node over
- *               the river card, river betting) or river (n_board 5) subgame;
+ *   game        CFR_GAME_HOLDEM: a hold'em flop (n_board 3: flop betting, a chance node
+ *               over the turn card, turn betting, a chance node over the river card, river
+ *               betting), turn (n_board 4: from the turn betting on) or river (n_board 5)
+ *               subgame;
  *               CFR_GAME_KUHN / CFR_GAME_LEDUC: the full games (board, hands, strength,
  *               pot, stack and bet sizes are ignored; range may be NULL for uniform).
  *   board       [n_board] card ids 0..51 (card = 4 * rank + suit), distinct.
@@ -59,17 +61,19 @@ enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_
  *   range[p]    [n_hands] player p's reach at the root, >= 0, not all zero; normalised
  *               internally to sum 1.  NULL = uniform.
  *   strength    showdown strength, higher wins, equal splits: [1][n_hands] for a river
- *               subgame, [52][n_hands] for a turn subgame (row = river card; rows of board
- *               cards are ignored).
+ *               subgame, [52][n_hands] for a turn subgame (row = river card) and
+ *               [52 * 52][n_hands] for a flop subgame (row = turn card * 52 + river card);
+ *               rows of impossible boards are ignored.
  *   pot, stack  chips in the pot (each player has put in pot / 2) and behind each player.
  *   bet_sizes   [n_bet_sizes] bet sizes as pot fractions; a size <= 0 means all-in.  A size
  *               x facing a call of d raises by d + x * (pot + d); sizes reaching the stack
  *               become all-in; duplicates are dropped.
  *   max_raises  bets plus raises allowed per street (the opening bet counts).
- *   depth_limit 0: solve to the end of the game (exact).  1 (turn subgames): the tree stops
- *               at the river card (Section 3, depth-limited solving): every chance node
- *               with chips behind becomes a CFR_NODE_LEAF whose values the leaf network
- *               gives (cfr_set_leaf_net); all-in run-outs stay exact.
+ *   depth_limit 0: solve to the end of the game (exact).  1 (flop and turn subgames): the
+ *               tree stops at the river card (Section 3, depth-limited solving): every
+ *               chance node that deals the river card with chips behind becomes a
+ *               CFR_NODE_LEAF whose values the leaf network gives (cfr_set_leaf_net); the
+ *               flop's turn card stays a chance node and all-in run-outs stay exact.
  */
 typedef struct cfr_game_spec {
   int game;

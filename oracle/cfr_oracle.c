@@ -33,6 +33,10 @@
  *   - DCFR at iteration t: R <- R + r, then R is multiplied by t^a/(t^a+1) where positive and
  *     by t^b/(t^b+1) elsewhere; S <- S * (t/(t+1))^g + pi_i * sigma;
  *   - CFR+: R <- max(R + r, 0), S <- S + t * pi_i * sigma;
+ *   - Predictive CFR+ (evaluated beside DCFR in Section 5): R <- max(R + r, 0), the
+ *     prediction M <- r, the strategy is regret matching of R + M, S <- S + t^2 pi_i sigma;
+ *   - hold'em subgames start on the flop, turn or river; with a depth limit the tree ends
+ *     where the river card is to come (a leaf), unless a player is all-in;
  *   - a bet of fraction x facing a call of d raises by d + x * (pot + d); sizes reaching the
  *     stack become all-in and duplicate sizes are dropped; "max raises" counts the opening
  *     bet; player 0 acts first on every street.
@@ -134,7 +138,8 @@ static int build_street_end(Oracle* o, int parent, int paction, int street, cons
                             const int* board, int deal) {
   if (street + 1 >= o->nstreets)
     return new_node(o, T_SHOW, -1, parent, paction, street, c, nboard, board, deal);
-  if (o->depth_limit && o->game == G_HOLDEM && !(c[0] >= o->cap || c[1] >= o->cap))
+  /* the depth limit ends the tree where the river card is to come, unless nobody can bet */
+  if (o->depth_limit && o->game == G_HOLDEM && street + 2 == o->nstreets && !(c[0] >= o->cap || c[1] >= o->cap))
     return new_node(o, T_LEAF, -1, parent, paction, street, c, nboard, board, deal);
   int id = new_node(o, T_CHANCE, -1, parent, paction, street, c, nboard, board, deal);
   int live[64], nlive = 0;
@@ -237,7 +242,8 @@ static int strength_at(const Oracle* o, const Node* n, int h) {
     int rank = o->cards[h] / 2, brank = n->board[0] / 2;
     return rank == brank ? 10 + rank : rank;
   }
-  int row = o->nstr == 1 ? 0 : n->board[4];
+  /* row of the completed board: 0 (river), the river card (turn), turn x 52 + river (flop) */
+  int row = o->nstr == 1 ? 0 : o->nstr == 52 ? n->board[4] : n->board[3] * 52 + n->board[4];
   return o->strength[(size_t)row * (size_t)o->nh + (size_t)h];
 }
 
@@ -300,7 +306,8 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
     o->deck = 52; o->hsize = 2;
     if (nboard == 5) o->nstreets = 1;
     else if (nboard == 4) o->nstreets = 2;
-    else { snprintf(g_err, sizeof g_err, "hold'em subgames start on the turn or river"); free(o); return NULL; }
+    else if (nboard == 3) o->nstreets = 3;
+    else { snprintf(g_err, sizeof g_err, "hold'em subgames start on the flop, turn or river"); free(o); return NULL; }
     nb0 = nboard;
     for (int k = 0; k < nboard; ++k) start_board[k] = board[k];
     o->pot = pot;
@@ -311,7 +318,7 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
     o->strength = (int*)malloc(sizeof(int) * (size_t)nstr * (size_t)nh);
     memcpy(o->strength, strength, sizeof(int) * (size_t)nstr * (size_t)nh);
     o->nstr = nstr;
-    if (!((nboard == 5 && nstr == 1) || (nboard == 4 && nstr == 52))) {
+    if (!((nboard == 5 && nstr == 1) || (nboard == 4 && nstr == 52) || (nboard == 3 && nstr == 52 * 52))) {
       snprintf(g_err, sizeof g_err, "strength rows do not match the board");
       free(o);
       return NULL;

@@ -83,11 +83,13 @@ def pair_slot(a: int, b: int) -> int:
 
 def leaf_input(reach, hands, board, r: int, feat) -> np.ndarray:
     """FP64 network input at a leaf for river card r: reach[p] is player p's reach per hand
-    (hands [n][2]), normalised to sum 1 over the hands not holding r (uniform over them if
-    that sum is 0) and placed at each hand's slot; then a one-hot of board + r; then the two
-    pot / stack features; zero padding to IN_PADDED."""
+    (hands [n][2]), normalised to sum 1 over the live hands -- those holding neither r nor a
+    card of the leaf's board (uniform over them if that sum is 0) -- and placed at each
+    hand's slot; then a one-hot of board + r; then the two pot / stack features; zero
+    padding to IN_PADDED."""
     x = np.zeros(IN_PADDED, np.float64)
-    live = np.array([r not in (int(a), int(b)) for a, b in hands])
+    dead = set(int(c) for c in board) | {int(r)}
+    live = np.array([not ({int(a), int(b)} & dead) for a, b in hands])
     slots = np.array([pair_slot(int(a), int(b)) for a, b in hands])
     for p in range(2):
         q = np.where(live, np.asarray(reach[p], dtype=np.float64), 0.0)

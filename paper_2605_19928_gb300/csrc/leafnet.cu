@@ -344,12 +344,14 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __r
   const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
   uint16_t* x = static_cast<uint16_t*>(L.X) + (size_t)row * kLeafIn;
   for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) x[k] = 0;
+  // live hands hold neither a card of the leaf's board (the flop's turn card) nor r
+  const uint64_t dead = nd.board | (1ull << r);
   float sum[2], cnt = 0.f;
   for (int p = 0; p < 2; ++p) {
     const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
     float s = 0.f, n = 0.f;
     for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
-      if (!((G.hand_mask[h] >> r) & 1ull)) s += vf(q[h]), n += 1.f;
+      if (!(G.hand_mask[h] & dead)) s += vf(q[h]), n += 1.f;
     sum[p] = block_sum(s, red);
     if (p == 0) cnt = block_sum(n, red);
   }
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __r
     // a player who never reaches the leaf: uniform over the hands (the values are then unused)
     const float inv = sum[p] > 0.f ? 1.f / sum[p] : 0.f;
     for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
-      if (!((G.hand_mask[h] >> r) & 1ull)) {
+      if (!(G.hand_mask[h] & dead)) {
         const float v = sum[p] > 0.f ? vf(q[h]) * inv : 1.f / cnt;
         x[p * kLeafSlots + slot[h]] = to_bf16(v);
       }

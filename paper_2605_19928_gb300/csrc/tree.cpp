@@ -164,15 +164,15 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
   } else if (spec.game == CFR_GAME_HOLDEM) {
     g.deck = 52;
     g.hand_size = 2;
-    if (spec.n_board != 4 && spec.n_board != 5) {
-      err = "hold'em subgames start on the turn (4 board cards) or the river (5)";
+    if (spec.n_board < 3 || spec.n_board > 5) {
+      err = "hold'em subgames start on the flop (3 board cards), the turn (4) or the river (5)";
       return CFR_EINVAL;
     }
     if (!spec.board) {
       err = "board is NULL";
       return CFR_EINVAL;
     }
-    g.n_streets = spec.n_board == 5 ? 1 : 2;
+    g.n_streets = 6 - spec.n_board;  // river 1, turn 2, flop 3
     uint64_t bm = 0;
     for (int k = 0; k < spec.n_board; ++k) {
       const int c = spec.board[k];
@@ -236,13 +236,13 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
         }
       g.n_hands = (int)g.hand_mask.size();
     }
-    const int want_rows = spec.n_board == 5 ? 1 : 52;
-    if (spec.depth_limit != 0 && (spec.depth_limit != 1 || spec.n_board != 4)) {
-      err = "depth_limit 1 applies to turn subgames only";
+    const int want_rows = spec.n_board == 5 ? 1 : spec.n_board == 4 ? 52 : 52 * 52;
+    if (spec.depth_limit != 0 && (spec.depth_limit != 1 || spec.n_board == 5)) {
+      err = "depth_limit 1 applies to flop and turn subgames only";
       return CFR_EINVAL;
     }
     if (!spec.strength || spec.n_strength_rows != want_rows) {
-      err = "strength must have 1 row (river) or 52 rows (turn)";
+      err = "strength must have 1 row (river), 52 rows (turn) or 52 x 52 rows (flop)";
       return CFR_EINVAL;
     }
   } else {
@@ -307,9 +307,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     nd.level = (uint8_t)s.level;
     nd.board = board_bits(s);
     kids.clear();
-    // depth limit: a chance node with chips behind ends the tree; the leaf network values it
+    // depth limit: the chance node that deals the river card ends the tree when a player has
+    // chips behind; the leaf network values it
     const bool all_in = std::max(s.c[0], s.c[1]) >= R.cap;
-    if (s.type == kChance && spec.depth_limit && spec.game == CFR_GAME_HOLDEM && !all_in) {
+    if (s.type == kChance && spec.depth_limit && spec.game == CFR_GAME_HOLDEM && s.nboard == 4 && !all_in) {
       s.type = kLeaf;
       nd.type = kLeaf;
     }
@@ -329,9 +330,12 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     if (s.type == kChance)
       for (Pending& kp : kids) kp.chance = s.chance * per_card;
     if (s.type == kShowdown) {
-      // showdown board table: 0 for boards fixed at the root, else by the last dealt card
+      // showdown strength row (numbered into tables below): 0 for boards fixed at the root,
+      // else the dealt cards (Leduc: the public card; turn: the river card; flop: turn x 52 +
+      // river)
       if (spec.game == CFR_GAME_LEDUC) nd.row = s.board[0];
       else if (spec.game == CFR_GAME_HOLDEM && g.n_streets == 2) nd.row = s.board[4];
+      else if (spec.game == CFR_GAME_HOLDEM && g.n_streets == 3) nd.row = s.board[3] * 52 + s.board[4];
       else nd.row = 0;
     }
     if (s.type == kDecision ? kids.size() > (size_t)kMaxActions : kids.size() > (size_t)kMaxDeck) {
@@ -384,22 +388,23 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     if (g.nodes[n].type == kLeaf) g.leaves.push_back(n);
   }
 
-  // ---- showdown tables, one per board the tree can show down on
-  std::vector<std::vector<int>> strengths;  // [board table][hand]
-  if (spec.game == CFR_GAME_KUHN) {
-    strengths.assign(1, std::vector<int>(H));
-    for (int h = 0; h < H; ++h) strengths[0][h] = h;
-  } else if (spec.game == CFR_GAME_LEDUC) {
-    strengths.assign(6, std::vector<int>(H));
-    for (int b = 0; b < 6; ++b)
-      for (int h = 0; h < H; ++h) strengths[b][h] = (h / 2 == b / 2) ? 10 + h / 2 : h / 2;
-  } else if (g.n_streets == 1) {
-    strengths.assign(1, std::vector<int>(spec.strength, spec.strength + H));
-  } else {
-    strengths.assign(52, std::vector<int>(H));
-    for (int r = 0; r < 52; ++r)
-      for (int h = 0; h < H; ++h) strengths[r][h] = spec.strength[(size_t)r * H + h];
-  }
+  // ---- showdown tables, one per board the tree shows down on (table 0 also serves the
+  // fold terminals, which only read its card lists)
+  std::vector<int> keys;
+  for (const NodeDev& nd : g.nodes)
+    if (nd.type == kShowdown) keys.push_back(nd.row);
+  if (keys.empty()) keys.push_back(0);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  for (NodeDev& nd : g.nodes)
+    if (nd.type == kShowdown) nd.row = (int)(std::lower_bound(keys.begin(), keys.end(), nd.row) - keys.begin());
+  std::vector<std::vector<int>> strengths(keys.size(), std::vector<int>(H));  // [board table][hand]
+  for (size_t b = 0; b < keys.size(); ++b)
+    for (int h = 0; h < H; ++h) {
+      if (spec.game == CFR_GAME_KUHN) strengths[b][h] = h;
+      else if (spec.game == CFR_GAME_LEDUC) strengths[b][h] = (h / 2 == keys[b] / 2) ? 10 + h / 2 : h / 2;
+      else strengths[b][h] = spec.strength[(size_t)keys[b] * H + h];
+    }
   const int B = (int)strengths.size();
   const int k = g.hand_size;
   g.n_boards = B;

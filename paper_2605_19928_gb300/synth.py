@@ -39,13 +39,14 @@ class GameSpec:
     board: np.ndarray                     # int32 [n_board] public cards (hold'em only)
     hands: np.ndarray                     # uint8 [n_hands, hand_size] private cards
     ranges: np.ndarray                    # float32 [2, n_hands], >= 0 (normalised by the solvers)
-    strength: np.ndarray | None = None    # int32 [rows, n_hands]; 1 row (river) or 52 (turn, by river card)
+    strength: np.ndarray | None = None    # int32 [rows, n_hands]; 1 row (river), 52 (turn, by river
+                                          # card) or 52 x 52 (flop, turn card x 52 + river card)
     pot: float = 0.0                      # chips in the pot; each player has put in pot / 2
     stack: float = 0.0                    # chips behind for each player
     bet_sizes: tuple = ()                 # pot fractions, ALL_IN for the all-in bet
     max_raises: int = 0                   # bets + raises allowed per street
     seeds: dict = field(default_factory=dict)
-    depth_limit: int = 0                  # 1: the turn tree stops at the river card (leaf network)
+    depth_limit: int = 0                  # 1: the tree stops where the river card is to come (leaf network)
 
     @property
     def n_hands(self) -> int:
@@ -107,6 +108,33 @@ def turn_subgame(n_hands: int | None = None, seed: int = 0, range_seed: int = 1,
     return GameSpec(GAME_HOLDEM, "turn", board, combos, ranges, np.ascontiguousarray(strength), pot, stack,
                     tuple(float(x) for x in bet_sizes), max_raises,
                     {"board_strength": seed, "ranges": range_seed})
+
+
+def flop_subgame(n_hands: int | None = None, seed: int = 0, range_seed: int = 1,
+                 pot: float = 100.0, stack: float = 150.0,
+                 bet_sizes=(0.33, 0.75, 1.25, ALL_IN), max_raises: int = 4, depth_limit: int = 0) -> GameSpec:
+    """Flop subgame: 3 seeded board cards; the turn and river cards are dealt by chance.
+
+    Strength row t * 52 + r holds every hand's showdown strength on the board completed by
+    turn t and river r, one uniform draw in [0, 2000) per hand and unordered pair {t, r}
+    (rows of the pairs that meet the board or repeat a card are unused and left at zero).
+    """
+    rng = np.random.default_rng(seed)
+    board = np.sort(rng.choice(DECK, size=3, replace=False)).astype(np.int32)
+    combos = all_combos(board)
+    strength = np.zeros((DECK * DECK, combos.shape[0]), np.int32)
+    live = [c for c in range(DECK) if c not in set(int(b) for b in board)]
+    for a, b in combinations(live, 2):
+        s = rng.integers(0, 2000, size=combos.shape[0]).astype(np.int32)
+        strength[a * DECK + b] = s
+        strength[b * DECK + a] = s
+    if n_hands is not None and n_hands < combos.shape[0]:
+        keep = np.sort(np.random.default_rng(seed + 7919).choice(combos.shape[0], size=n_hands, replace=False))
+        combos, strength = combos[keep], strength[:, keep]
+    ranges = _dirichlet_ranges(np.random.default_rng(range_seed), combos.shape[0])
+    return GameSpec(GAME_HOLDEM, "flop", board, combos, ranges, np.ascontiguousarray(strength), pot, stack,
+                    tuple(float(x) for x in bet_sizes), max_raises,
+                    {"board_strength": seed, "ranges": range_seed}, depth_limit)
 
 
 def kuhn() -> GameSpec:
@@ -258,6 +286,27 @@ def ranked_turn_subgame(n_hands: int | None = None, seed: int = 0, range_seed: i
         strength[c] = s
     g.strength = strength
     g.name = "turn_ranked"
+    g.depth_limit = depth_limit
+    return g
+
+
+def ranked_flop_subgame(n_hands: int | None = None, seed: int = 0, range_seed: int = 1, pot: float = 100.0,
+                        stack: float = 150.0, bet_sizes=(0.33, 0.75, 1.25, ALL_IN), max_raises: int = 4,
+                        depth_limit: int = 0) -> GameSpec:
+    """A flop subgame like flop_subgame, with showdown strengths from rank_strength on each
+    completed board."""
+    g = flop_subgame(n_hands=n_hands, seed=seed, range_seed=range_seed, pot=pot, stack=stack,
+                     bet_sizes=bet_sizes, max_raises=max_raises)
+    strength = np.zeros((DECK * DECK, g.n_hands), np.int32)
+    live = [c for c in range(DECK) if c not in set(int(b) for b in g.board)]
+    for a, b in combinations(live, 2):
+        ok = ~np.any((g.hands == a) | (g.hands == b), axis=1)
+        s = np.zeros(g.n_hands, np.int32)
+        s[ok] = rank_strength(np.concatenate([g.board, [a, b]]), g.hands[ok])
+        strength[a * DECK + b] = s
+        strength[b * DECK + a] = s
+    g.strength = strength
+    g.name = "flop_ranked"
     g.depth_limit = depth_limit
     return g
 

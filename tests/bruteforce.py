@@ -22,7 +22,7 @@ KUHN, LEDUC, HOLDEM = "kuhn", "leduc", "holdem"
 
 
 class Game:
-    """Heads-up poker subgame: Kuhn, Leduc, or a hold'em turn/river subgame."""
+    """Heads-up poker subgame: Kuhn, Leduc, or a hold'em flop/turn/river subgame."""
 
     def __init__(self, kind, hands=None, ranges=None, board=(), strength=None, pot=2.0, stack=0.0,
                  sizes=(), max_raises=1):
@@ -35,7 +35,7 @@ class Game:
             self.bets, self.max_raises, self.base = [2.0, 4.0], 2, 1.0
         else:
             self.deck, self.hands = 52, [tuple(int(c) for c in h) for h in hands]
-            self.n_streets = 1 if len(board) == 5 else 2
+            self.n_streets = 6 - len(board)  # river 1, turn 2, flop 3
             self.bets, self.max_raises, self.base = None, max_raises, pot / 2.0
             self.cap = pot / 2.0 + stack
             self.sizes = list(sizes)
@@ -107,7 +107,12 @@ class Game:
         if self.kind == LEDUC:
             r, br = self.hands[h][0] // 2, board[0] // 2
             return 10 + r if r == br else r
-        row = 0 if len(self.board0) == 5 else board[4]
+        if len(self.board0) == 5:
+            row = 0
+        elif len(self.board0) == 4:
+            row = board[4]
+        else:
+            row = board[3] * 52 + board[4]
         return int(self.strength[row][h])
 
     def utility(self, hands, hist, i):

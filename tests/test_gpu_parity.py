@@ -29,6 +29,12 @@ def turn(n_hands, seed=5, **kw):
     return synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
 
 
+def flop(n_hands, seed=5, **kw):
+    kw.setdefault("bet_sizes", (synth.ALL_IN,))
+    kw.setdefault("max_raises", 1)
+    return synth.flop_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
+
+
 def kuhn_random(seed=7):
     g = synth.kuhn()
     g.ranges[:] = synth.random_ranges(3, seed)
@@ -217,6 +223,14 @@ def test_average_strategy_readback():
                 compare_strategies(cur, orc.regrets(o), what=f"current strategy node {g}")
     finally:
         capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("schedule", ["level", "stream"])
+def test_flop_matches_oracle_from_the_same_state(schedule):
+    """Three streets: turn and river cards by chance, 2352 showdown boards, all-in run-outs
+    from the flop and from the turn (31k nodes)."""
+    worst = run_pair(flop(12), "dcfr", iters=3, forced=True, schedule=schedule)
+    print("flop", schedule, worst)
 
 
 def test_invalid_specs_are_rejected():

@@ -68,11 +68,26 @@ from gpu_helpers import compare_player, inject, node_map  # noqa: E402
 from paper_2605_19928_gb300 import synth  # noqa: E402
 
 
-def _leaf_spec(n_hands=40, seed=5, max_raises=2):
-    spec = synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, bet_sizes=(1.0, synth.ALL_IN),
-                              max_raises=max_raises)
+def _leaf_spec(n_hands=40, seed=5, max_raises=2, street="turn"):
+    if street == "flop":  # all-in the only bet: 49 turn cards, one leaf below each
+        spec = synth.flop_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, bet_sizes=(synth.ALL_IN,),
+                                  max_raises=1)
+    else:
+        spec = synth.turn_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1,
+                                  bet_sizes=(1.0, synth.ALL_IN), max_raises=max_raises)
     spec.depth_limit = 1
     return spec
+
+
+def _node_board(orc, spec, o):
+    """The board at oracle node o: the subgame's cards and those dealt on the way."""
+    info = orc.nodes()
+    dealt = []
+    while o > 0:
+        if info[o]["deal"] >= 0:
+            dealt.append(info[o]["deal"])
+        o = info[o]["parent"]
+    return [int(c) for c in spec.board] + dealt[::-1]
 
 
 def _random_net(seed):
@@ -89,12 +104,13 @@ def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
     """Check one evaluation's inputs and outputs against the oracle; load the GPU's outputs
     into the oracle's leaves.  Returns the worst output error relative to the row maximum."""
     g2o = {g: o for g, o, _ in mapping}
-    board = [int(c) for c in spec.board]
-    live = [c for c in range(52) if c not in board]
     slots = np.array([ln.pair_slot(int(a), int(c)) for a, c in spec.hands])
     worst = 0.0
     for game, node, row0 in capi.cfr_leaf_info(tree):
         o = g2o[node]
+        board = _node_board(orc, spec, o)
+        live = [c for c in range(52) if c not in board]
+        assert len(board) == 4 and len(live) == 48
         X = ln.bf16_from_bits(capi.cfr_read_leaf_rows(tree, 0, row0, 48))
         Y = capi.cfr_read_leaf_rows(tree, 1, row0, 48)
         if check_inputs:
@@ -117,10 +133,11 @@ def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
     return worst
 
 
-@pytest.mark.parametrize("schedule", ["level", "stream"])
-def test_leaf_inputs_outputs_and_values_match_oracle(schedule):
+@pytest.mark.parametrize("schedule,street", [("level", "turn"), ("stream", "turn"), ("level", "flop"),
+                                             ("stream", "flop")])
+def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
     from oracle.oracle import Oracle
-    spec = _leaf_spec()
+    spec = _leaf_spec(n_hands=24, street="flop") if street == "flop" else _leaf_spec()
     W, b = _random_net(1)
     tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", schedule=schedule))
     try:
@@ -142,10 +159,11 @@ def test_leaf_inputs_outputs_and_values_match_oracle(schedule):
         capi.cfr_tree_destroy(tree)
 
 
-@pytest.mark.parametrize("schedule,variant", [("level", "dcfr"), ("stream", "dcfr"), ("level", "cfr+")])
-def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant):
+@pytest.mark.parametrize("schedule,variant,street", [("level", "dcfr", "turn"), ("stream", "dcfr", "turn"),
+                                                     ("level", "cfr+", "turn"), ("level", "dcfr", "flop")])
+def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant, street):
     from oracle.oracle import Oracle
-    spec = _leaf_spec(n_hands=32, seed=9)
+    spec = _leaf_spec(n_hands=32, seed=9, street=street)
     W, b = _random_net(2)
     tree = capi.cfr_tree_create(spec, capi.make_opts(variant, schedule=schedule))
     try:
@@ -179,5 +197,38 @@ def test_leaf_handles_need_a_network():
             capi.cfr_iterate(tree, 1)
         assert e.value.code == capi.CFR_ESTATE
         assert len(capi.cfr_leaf_info(tree)) > 0
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def test_full_size_flop_with_network_leaves():
+    """The flop workload at full size (1176 hands, leaves below every turn card): sampled
+    network rows against the FP64 forward pass of the same inputs, and input rows that are
+    normalised ranges over the hands live on the leaf's board."""
+    from paper_2605_19928_gb300 import leafnet_train
+    spec = synth.ranked_flop_subgame(depth_limit=1)
+    W, b = leafnet_train.load_weights()
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision="single"))
+    try:
+        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_iterate(tree, 20)
+        e, br = capi.cfr_exploitability(tree)
+        assert np.isfinite(e[0]) and np.isfinite(br).all()
+        leaves = capi.cfr_leaf_info(tree)
+        assert len(leaves) > 1000
+        capi.cfr_eval_leaves(tree)
+        rng = np.random.default_rng(0)
+        for k in rng.choice(len(leaves), size=3, replace=False):
+            _, node, row0 = leaves[int(k)]
+            X = ln.bf16_from_bits(capi.cfr_read_leaf_rows(tree, 0, row0, 48))
+            Y = capi.cfr_read_leaf_rows(tree, 1, row0, 48)
+            on = X[:, 2 * ln.SLOTS:2 * ln.SLOTS + 52]
+            assert np.all(on.sum(axis=1) == 5)
+            for p in (0, 1):
+                tot = X[:, p * ln.SLOTS:(p + 1) * ln.SLOTS].astype(np.float64).sum(axis=1)
+                assert np.all(np.abs(tot - 1.0) <= 0.01), (node, p)
+            Yr = ln.forward(X, list(zip([ln.bf16_from_bits(w) for w in W], b)))  # W: BF16 bit patterns
+            scale = np.max(np.abs(Yr), axis=1, keepdims=True)
+            assert np.max(np.abs(Y[:, :2 * ln.SLOTS] - Yr[:, :2 * ln.SLOTS]) / scale) <= 3e-2
     finally:
         capi.cfr_tree_destroy(tree)

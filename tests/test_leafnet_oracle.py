@@ -134,6 +134,47 @@ def test_leaf_values_depend_on_the_cards_left(oracle_mod):
         assert got[h] == pytest.approx(want, rel=1e-12, abs=1e-15)
 
 
+def _flop(n_hands=10, seed=4, **kw):
+    from paper_2605_19928_gb300 import synth
+    kw.setdefault("bet_sizes", (1.0, synth.ALL_IN))
+    kw.setdefault("max_raises", 1)
+    return synth.flop_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, **kw)
+
+
+def test_flop_leaves_sit_where_the_river_card_is_to_come(oracle_mod):
+    """On the flop the depth limit ends the tree after the turn betting: the turn-card chance
+    nodes stay, the river-card chance nodes with chips behind become leaves."""
+    exact, limited = _flop(), _flop()
+    limited.depth_limit = 1
+    oe, ol = oracle_mod.Oracle(exact, threads=1), oracle_mod.Oracle(limited, threads=1)
+    ne, nl = oe.nodes(), ol.nodes()
+    cap = exact.pot / 2 + exact.stack
+    chance = [n for n in ne if n["type"] == oracle_mod.T_CHANCE]
+    river_with_chips = [n for n in chance if n["n_board"] == 4 and max(n["contrib"]) < cap]
+    leaves = [n for n in nl if n["type"] == oracle_mod.T_LEAF]
+    assert len(leaves) == len(river_with_chips) > 0
+    assert all(n["n_board"] == 4 for n in leaves)
+    turn_chance = [n for n in nl if n["type"] == oracle_mod.T_CHANCE and n["n_board"] == 3]
+    assert len(turn_chance) == sum(1 for n in chance if n["n_board"] == 3) > 0
+    assert all(n["n_actions"] == 49 for n in turn_chance)
+
+
+def test_flop_constant_leaf_values_give_that_share_of_the_pot(oracle_mod):
+    spec = _flop(max_raises=0)  # check / check on the flop and on each turn: 49 leaves
+    spec.depth_limit = 1
+    o = oracle_mod.Oracle(spec, threads=1)
+    leaves = [k for k, n in enumerate(o.nodes()) if n["type"] == oracle_mod.T_LEAF]
+    assert len(leaves) == 49
+    y = np.zeros((48, 2, spec.n_hands))
+    y[:, 0, :], y[:, 1, :] = 0.25, -0.1
+    for leaf in leaves:
+        o.set_leaf_values(leaf, y)
+    o.load_profile("current")
+    v = o.profile_value()
+    assert v[0] == pytest.approx(0.25 * spec.pot, rel=1e-12)
+    assert v[1] == pytest.approx(-0.1 * spec.pot, rel=1e-12)
+
+
 def test_leaf_input_row_layout():
     hands = np.array([[0, 1], [2, 5], [1, 7]])
     x = ln.leaf_input([np.array([1.0, 3.0, 0.0]), np.array([0.0, 0.0, 2.0])], hands, [10, 20, 30, 40], 5,

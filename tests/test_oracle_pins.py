@@ -99,6 +99,12 @@ def small_turn(n_hands=6, seed=5):
                               max_raises=1)
 
 
+def small_flop(n_hands=4, seed=3):
+    """Flop subgame small enough to enumerate: all-in the only bet, one per street."""
+    return synth.flop_subgame(n_hands=n_hands, seed=seed, range_seed=seed + 1, bet_sizes=(synth.ALL_IN,),
+                              max_raises=1)
+
+
 # ---------------------------------------------------------------- trees and counts
 
 def test_kuhn_tree(oracle_mod):
@@ -123,7 +129,7 @@ def test_leduc_tree_has_936_infosets(oracle_mod):
 
 
 @pytest.mark.parametrize("make", [lambda: small_river(), lambda: small_river(max_raises=4),
-                                  lambda: small_turn()])
+                                  lambda: small_turn(), lambda: small_flop()])
 def test_holdem_trees_agree_with_rules_engine(oracle_mod, make):
     spec = make()
     o = oracle_mod.Oracle(spec, threads=1)
@@ -259,6 +265,18 @@ def test_two_iterations_match_definitions(oracle_mod, case, variant, alternating
     n_it = 3 if variant == "pcfr+" else 2  # the prediction first steers iteration 2
     o.iterate(n_it)
     R, S = bf.run_cfr(g, n_it, variant=variant, alternating=alternating)
+    assert compare_state(o, g, hmap, R, S) > 0
+
+
+def test_flop_two_iterations_match_definitions(oracle_mod):
+    """Three streets: the turn and river cards dealt by chance (1/45 then 1/44 given both
+    hands), showdown strengths by completed board."""
+    spec = small_flop()
+    o = oracle_mod.Oracle(spec, variant="dcfr", threads=2)
+    g = bf_game(spec)
+    hmap = history_map(o, g)
+    o.iterate(2)
+    R, S = bf.run_cfr(g, 2, variant="dcfr")
     assert compare_state(o, g, hmap, R, S) > 0
 
 
