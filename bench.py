@@ -49,7 +49,9 @@ def parse_args(argv=None):
                          "gemm: the leaf network's dense layers alone")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--iters-per-step", type=int, default=None, help="default 1000 (river) or 500 (batch)")
-    ap.add_argument("--precision", choices=["pairs", "single"], default="pairs")
+    ap.add_argument("--precision", choices=["pairs", "single"], default=None,
+                    help="values as FP32 pairs or plain FP32 (R and S are FP64 either way); default pairs for "
+                         "the single river, FP32 for the batch and the depth-limited workloads")
     ap.add_argument("--chunk-hands", type=int, default=0)
     ap.add_argument("--schedule", choices=["auto", "level", "stream"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
@@ -684,6 +686,10 @@ def run_leaf(args):
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
     mbb = lambda e: 1000.0 * float(e) / BB_CHIPS
     n_exact = capi.cfr_tree_info(E)[0]
+    n_leaf_nodes = capi.cfr_tree_info(L)[0]
+    sched = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream",
+             capi.CFR_SCHEDULE_WIDE: "wide"}
+    schedules = {"learned": sched[capi.cfr_schedule(L)], "exact": sched[capi.cfr_schedule(E)]}
     capi.cfr_tree_destroy(L)
     capi.cfr_tree_destroy(E)
     if rank == 0:
@@ -698,7 +704,7 @@ def run_leaf(args):
                                         "river card" if flop else
                                         "depth-limited turn subgame, leaf network at the river card"),
                            "board_cards": len(spec_leaf.board), "hands": spec_leaf.n_hands, "leaves": len(leaves),
-                           "nodes": capi.cfr_tree_info(L)[0],
+                           "nodes": n_leaf_nodes, "schedules": schedules,
                            "network": "2752-512-512-512-2688 BF16, GELU", "pot": spec_leaf.pot,
                            "stack": spec_leaf.stack,
                            "bet_sizes": ",".join("all-in" if x <= 0 else "%g" % x for x in spec_leaf.bet_sizes)
@@ -735,6 +741,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.iters_per_step is None:
         args.iters_per_step = {"batch": 500, "leaf": 300, "flop": 300}.get(args.workload, 1000)
+    if args.precision is None:
+        args.precision = "pairs" if args.workload == "river" else "single"
     if args.workload in ("leaf", "flop") and args.impl == "ours":
         return run_leaf(args)
     if args.workload == "gemm" and args.impl == "ours":

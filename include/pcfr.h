@@ -113,11 +113,15 @@ typedef struct cfr_game_spec {
  * walks the tree level by level (lowest latency for one subgame).  CFR_SCHEDULE_STREAM: one
  * warp per 32 hands walks a depth-first program of its tree with no block barriers and no
  * inner-node state in DRAM (highest throughput for batches; needs at most 8 actions per
- * decision node).  CFR_SCHEDULE_AUTO (0) picks STREAM when the handle has at least 1216
- * such warps (8 per SM) and every tree allows it, else LEVEL.
+ * decision node).  CFR_SCHEDULE_WIDE: every pass (update, initial strategy, average, best
+ * response) is one launch per tree level over all of that level's (node, hand) pairs, one
+ * thread each (for one tree too large for a block to stage in shared memory: exact turns
+ * and flops; one subgame per handle, at most 8 actions per decision node).
+ * CFR_SCHEDULE_AUTO (0) picks STREAM when the handle has at least 1216 such warps (8 per
+ * SM) and every tree allows it, WIDE for one subgame too large to stage, else LEVEL.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
-enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2 };
+enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2, CFR_SCHEDULE_WIDE = 3 };
 typedef struct cfr_solver_opts {
   int variant;
   double alpha;
@@ -185,8 +189,8 @@ int cfr_exploitability_noalloc(cfr_tree* tree, double* expl, double* br);
  * (asynchronous, on the handle's stream). */
 int cfr_reset(cfr_tree* tree);
 
-/* The update schedule the handle uses (CFR_SCHEDULE_LEVEL or CFR_SCHEDULE_STREAM), or a
- * negative status. */
+/* The schedule the handle uses (CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM or
+ * CFR_SCHEDULE_WIDE), or a negative status. */
 int cfr_schedule(const cfr_tree* tree);
 
 /* Sizes of one subgame and the number of iterations done.  Any out pointer may be NULL. */
@@ -222,9 +226,11 @@ int cfr_sync(cfr_tree* tree);
 
 /* Per-stage device time, after the paper's per-stage breakdown (Section 5, Table 3).
  * Runs n_iters iterations (advancing the solve exactly like cfr_iterate) launch by launch
- * instead of as a graph, with CUDA events around every kernel, then one exploitability
- * pass the same way.  ms[k] receives the mean device time of one launch of stage k and
- * launches[k] (may be NULL) the number of launches timed; both have CFR_N_STAGES entries.
+ * instead of as a graph, with CUDA events around every stage, then one exploitability
+ * pass the same way.  ms[k] receives the mean device time of one occurrence of stage k
+ * (one launch; a sequence of launches for the leaf stage and under CFR_SCHEDULE_WIDE) and
+ * launches[k] (may be NULL) the number of occurrences timed; both have CFR_N_STAGES
+ * entries.
  *   CFR_STAGE_TERMINAL    fold and showdown values of one player (Stages 2-4)
  *   CFR_STAGE_UPDATE      backward values, regret and average update, new strategy and
  *                         forward reach of one player (Stages 6-7, then 1-2)

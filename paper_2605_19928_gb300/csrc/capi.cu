@@ -48,6 +48,8 @@ struct cfr_tree {
   Work* d_term_work = nullptr;
   Work* d_term_runs = nullptr;
   Work* d_warp_work = nullptr;
+  int32_t* d_wide_inner = nullptr;  // wide schedule: inner node ids, level by level
+  std::vector<int> wide_ls, wide_inner_off;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
   int* d_err = nullptr;
@@ -184,6 +186,7 @@ int check_device() {
 }
 
 int leaf_launches(const cfr_tree* t, int player_mask);
+int pass_launches(const cfr_tree* t, int which, int player_mask, int advance);
 
 // Depth-limit leaves of every game: their network rows, features and slot maps, and the
 // network's activation and weight buffers (the weights arrive with cfr_set_leaf_net).
@@ -265,7 +268,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
   if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
     return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
-  if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_STREAM) return fail(CFR_EINVAL, "unknown schedule");
+  if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_WIDE) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
   static int configured = configure_kernels();
@@ -309,7 +312,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   // Update schedule: one warp per 32 hands when the handle has enough of them to fill the
   // GPU (8 warps per SM) and every tree fits the warp's registers and stack.
   std::vector<std::vector<int32_t>> programs(n_games);
-  int stream_depth = 1, stream_warps = 0;
+  int stream_depth = 1, stream_warps = 0, actions_max = 0;
   bool stream_ok = true;
   for (int g = 0; g < n_games; ++g) {
     int depth = 0, amax = 0;
@@ -317,6 +320,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     programs[g] = dfs_program(t->host[g], &depth, &amax, &fits);
     stream_ok = stream_ok && fits;
     stream_depth = std::max(stream_depth, depth);
+    actions_max = std::max(actions_max, amax);
     stream_ok = stream_ok && amax <= kStreamMaxActions;
     stream_warps += (t->host[g].n_hands + 31) / 32;
   }
@@ -357,6 +361,35 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     schedule = kScheduleStream;
   } else if (o.schedule == CFR_SCHEDULE_AUTO && stream_ok && stream_warps >= 8 * 152) {
     schedule = kScheduleStream;
+  }
+  // Wide schedule: one subgame whose tree a block cannot stage (the per-hand pass would walk
+  // it from global memory a few nodes at a time).
+  const bool wide_ok = n_games == 1 && actions_max <= kStreamMaxActions;
+  if (o.schedule == CFR_SCHEDULE_WIDE) {
+    if (!wide_ok) {
+      delete t;
+      return fail(CFR_EINVAL, "the wide schedule takes one subgame with at most " +
+                                  std::to_string(kStreamMaxActions) + " actions per decision node");
+    }
+    schedule = kScheduleWide;
+  } else if (o.schedule == CFR_SCHEDULE_AUTO && schedule == kScheduleLevel && wide_ok && !all_fit) {
+    schedule = kScheduleWide;
+  }
+  if (schedule == kScheduleWide) {  // per level: the node range, and the inner nodes
+    const HostGame& h = t->host[0];
+    const int L = (int)h.level_start.size() - 1;
+    t->wide_ls.assign(h.level_start.begin(), h.level_start.end());
+    t->wide_inner_off.assign(1, 0);
+    std::vector<int32_t> inner;
+    for (int l = 0; l < L; ++l) {
+      for (int n = h.level_start[l]; n < h.level_start[l + 1]; ++n)
+        if (!is_end(h.nodes[(size_t)n].type)) inner.push_back(n);
+      t->wide_inner_off.push_back((int)inner.size());
+    }
+    if ((rc = upload(t, inner, &t->d_wide_inner))) {
+      delete t;
+      return rc;
+    }
   }
 
   std::vector<Work> chunk_work, term_work, warp_work;
@@ -498,13 +531,31 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_prog = stream_prog;
   c.stream_half = stream_half;
   c.stream_units = stream_units;
+  if (schedule == kScheduleWide) {
+    const HostGame& h = t->host[0];
+    c.wide_levels = (int)t->wide_ls.size() - 1;
+    c.wide_ls = t->wide_ls.data();
+    c.wide_inner_off = t->wide_inner_off.data();
+    c.wide_inner = t->d_wide_inner;
+    c.wide_stride = h.hstride;
+    int dmax = 0;
+    for (int p = 0; p < 2; ++p) {
+      int cnt = 0;
+      for (const NodeDev& nd : h.nodes) cnt += nd.type == kDecision && nd.player == p;
+      dmax = std::max(dmax, cnt);
+    }
+    c.wide_max_dec = dmax;
+  }
   if ((rc = setup_leaves(t, specs, n_games))) {
     delete t;
     return rc;
   }
-  t->launches_per_iteration = (o.alternating ? 2 : 1) * (c.n_term_work > 0 ? 2 : 1) +
-                              (o.alternating ? leaf_launches(t, 1) + leaf_launches(t, 2) : leaf_launches(t, 3));
-  t->launches += 1;
+  t->launches_per_iteration =
+      (o.alternating ? pass_launches(t, kModeUpdate, 1, 0) + pass_launches(t, kModeUpdate, 2, 1)
+                     : pass_launches(t, kModeUpdate, 3, 1)) +
+      (c.n_term_work > 0 ? (o.alternating ? 2 : 1) : 0) +
+      (o.alternating ? leaf_launches(t, 1) + leaf_launches(t, 2) : leaf_launches(t, 3));
+  t->launches += pass_launches(t, kModeInit, 3, 0);
   if (launch_init(c, stream) != 0) {
     delete t;
     return fail(CFR_ECUDA, "initial strategy launch failed");
@@ -533,6 +584,12 @@ int enqueue_leaves(cfr_tree* t, int player_mask, int use_bar, cudaStream_t s) {
 
 int leaf_launches(const cfr_tree* t, int player_mask) {
   return t->leaf.n_leaves == 0 ? 0 : 5 + (player_mask == 3 ? 2 : 1);
+}
+
+// Kernels one pass launches: one, or one per level under the wide schedule.
+int pass_launches(const cfr_tree* t, int which, int player_mask, int advance) {
+  if (t->ctx.schedule != kScheduleWide) return 1;
+  return wide_launch_count(t->ctx, which, player_mask, advance);
 }
 
 // One iteration: alternating = terminal + update for player 0, then for player 1 (each
@@ -684,7 +741,8 @@ int cfr_exploitability_async(cfr_tree* t) {
   }
   t->avg_gen = -1;  // the pass rewrites sigbar with its own normalisation
   CK(cudaGraphLaunch(t->expl_graph, t->stream));
-  t->launches += (t->ctx.n_term_work > 0 ? 3 : 2) + leaf_launches(t, 3);
+  t->launches += (t->ctx.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) +
+                 pass_launches(t, kModeBR, 3, 0) + leaf_launches(t, 3);
   return CFR_OK;
 }
 
@@ -726,14 +784,16 @@ int cfr_reset(cfr_tree* t) {
   CK(cudaMemsetAsync(t->d_iter, 0, sizeof(int), t->stream));
   t->state_gen += 1;
   if (launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "initial strategy launch failed");
-  t->launches += 1;
+  t->launches += pass_launches(t, kModeInit, 3, 0);
   t->iters_done = 0;
   return CFR_OK;
 }
 
 int cfr_schedule(const cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
-  return t->ctx.schedule == kScheduleStream ? CFR_SCHEDULE_STREAM : CFR_SCHEDULE_LEVEL;
+  return t->ctx.schedule == kScheduleStream ? CFR_SCHEDULE_STREAM
+         : t->ctx.schedule == kScheduleWide ? CFR_SCHEDULE_WIDE
+                                            : CFR_SCHEDULE_LEVEL;
 }
 
 int cfr_tree_info(const cfr_tree* t, int game, int* n_nodes, int* n_hands, int* iters_done) {
@@ -818,7 +878,7 @@ int cfr_write_values(cfr_tree* t, int game, int what, int node, const double* in
   CK(cudaMemcpy2DAsync(dst, S * 8, in, H * 8, H * 8, nd.n_kids, cudaMemcpyHostToDevice, t->stream));
   // new regrets: the current strategy and both players' reach follow them at once
   if (what != CFR_READ_AVG_SUM && launch_init(t->ctx, t->stream) != 0) return fail(CFR_ECUDA, "strategy launch failed");
-  if (what != CFR_READ_AVG_SUM) t->launches += 1;
+  if (what != CFR_READ_AVG_SUM) t->launches += pass_launches(t, kModeInit, 3, 0);
   CK(cudaStreamSynchronize(t->stream));
   t->state_gen += 1;
   t->avg_gen = -1;
@@ -894,13 +954,12 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
   if (err != cudaSuccess) return cuda_fail(err, "cudaEventRecord");
   if (serr != cudaSuccess) return cuda_fail(serr, "cudaStreamSynchronize");
   t->iters_done += n_iters;
-  int64_t total = 0;
   for (int k = 0; k < CFR_N_STAGES; ++k) {
     ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;
     if (launches) launches[k] = cnt[k];
-    total += cnt[k];
   }
-  t->launches += total;
+  t->launches += (int64_t)n_iters * t->launches_per_iteration + (c.n_term_work > 0 ? 1 : 0) +
+                 pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) + leaf_launches(t, 3);
   return CFR_OK;
 }
 
@@ -938,7 +997,7 @@ int cfr_eval_leaves(cfr_tree* t, int average) {
     t->avg_gen = -1;
   }
   if (enqueue_leaves(t, 3, average ? 1 : 0, t->stream) != 0) return fail(CFR_ECUDA, "leaf launch failed");
-  t->launches += (average ? 1 : 0) + leaf_launches(t, 3);
+  t->launches += (average ? pass_launches(t, kModeAvg, 3, 0) : 0) + leaf_launches(t, 3);
   return cfr_sync(t);
 }
 
@@ -1117,7 +1176,7 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
     return fail(CFR_ECUDA, "exploitability launch failed");
   k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);
   CK(cudaGetLastError());
-  t->launches += c.n_term_work > 0 ? 4 : 3;
+  t->launches += (c.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) + 1;
   CK(cudaMemcpyAsync(br, scratch + kStaticPartialBytes, (size_t)c.n_games * 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

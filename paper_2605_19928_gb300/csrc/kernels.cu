@@ -33,7 +33,6 @@ namespace pcfr {
 constexpr int kHandThreads = 256;
 constexpr int kTermThreads = 512;
 
-enum HandMode { kModeInit = 0, kModeUpdate = 1, kModeAvg = 2, kModeBR = 3 };
 
 // ------------------------------------------------------------------ double-float arithmetic
 //
@@ -1048,9 +1047,11 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
       {
         double Rm[kStreamMaxActions];
 #pragma unroll
-        for (int a = 0; a < kStreamMaxActions; ++a) {
-          Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
-          Rm[a] = Rv[a] + (pred && a < A ? Mr[(size_t)a * 32] : 0.0);
+        for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = Rm[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+        if (pred) {  // Predictive CFR+ matches R + M (no FP64 add for the other variants)
+#pragma unroll
+          for (int a = 0; a < kStreamMaxActions; ++a)
+            if (a < A) Rm[a] = Rv[a] + Mr[(size_t)a * 32];
         }
         regret_match<P>(Rm, A, sg);
       }
@@ -1104,8 +1105,12 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
       double Rv[kStreamMaxActions];
       V sg[kStreamMaxActions];
 #pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a)
-        Rv[a] = a < A ? Rr[(size_t)a * 32] + (pred ? Mr[(size_t)a * 32] : 0.0) : 0.0;
+      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
+      if (pred) {  // Predictive CFR+ matches R + M
+#pragma unroll
+        for (int a = 0; a < kStreamMaxActions; ++a)
+          if (a < A) Rv[a] += Mr[(size_t)a * 32];
+      }
       regret_match<P>(Rv, A, sg);
 #pragma unroll
       for (int a = kStreamMaxActions - 1; a >= 0; --a) {
@@ -1287,6 +1292,198 @@ __global__ void k_average_rows(const GameDev* __restrict__ games, int n_games) {
   }
 }
 
+// ------------------------------------------------------------------ wide schedule
+//
+// For one tree too large to stage in shared memory, each pass of the per-hand kernel
+// becomes one launch per level in which every thread owns one (node, hand) pair: the hand
+// index is the fastest-moving coordinate, so each warp reads and writes 32 consecutive
+// entries of a row, and a level of n nodes runs n x hstride threads at once instead of
+// stepping through its nodes in a few blocks.  The arithmetic per (node, hand) -- the order
+// of every sum over children, regret matching, the Stage 7 update -- is the per-hand
+// kernel's, so the schedules agree bit for bit.
+
+constexpr int kWideThreads = 256;
+
+// Bottom-up step at the inner nodes of one level (Stage 6, Eq. backward) for player p =
+// blockIdx.y when both players are in the launch.  kModeUpdate: at p's decision nodes also
+// the regrets, the Stage 7 update of R and S and the new strategy RM(R') (Eq. rm);
+// kModeBR: the best-response value max_a v(child a) at p's decision nodes.
+template <int MODE, typename P>
+__global__ void __launch_bounds__(kWideThreads) k_wide_back(const GameDev* __restrict__ games,
+                                                            const int32_t* __restrict__ inner, int cnt,
+                                                            int player_mask, const int* __restrict__ iter,
+                                                            const Discount* __restrict__ disc_tab, int variant) {
+  using V = typename P::V;
+  pdl_wait();
+  pdl_trigger();
+  const GameDev& G = games[0];
+  const int p = player_mask == 3 ? (int)blockIdx.y : (player_mask == 1 ? 0 : 1);
+  const size_t S = (size_t)G.hstride;
+  const size_t e = (size_t)blockIdx.x * kWideThreads + threadIdx.x;
+  if (e >= (size_t)cnt * S) return;
+  const int n = inner[e / S], h = (int)(e % S);
+  if (h >= G.n_hands) return;
+  const NodeDev nd = G.nodes[n];
+  const size_t N = (size_t)G.n_nodes;
+  V* v = static_cast<V*>(MODE == kModeBR ? G.cfv_br : G.cfv) + (size_t)p * N * S + h;
+  const int A = nd.n_kids, k0 = nd.first_kid;
+  V val;
+  if (MODE == kModeBR && nd.type == kDecision && nd.player == p) {
+    val = v[(size_t)k0 * S];
+    for (int a = 1; a < A; ++a) val = P::vmax(val, v[(size_t)(k0 + a) * S]);
+    v[(size_t)n * S] = val;
+    return;
+  }
+  if (nd.type == kChance) {
+    // children values already carry the card probabilities; cards in the hand are out
+    const uint64_t hmask = G.hand_mask[h];
+    typename P::Acc acc = P::acc0();
+    for (int a = 0; a < A; ++a)
+      if (!((hmask >> G.nodes[k0 + a].deal) & 1ull)) P::acc(acc, v[(size_t)(k0 + a) * S]);
+    v[(size_t)n * S] = P::value(acc);
+    return;
+  }
+  if (nd.player != p || MODE == kModeBR) {
+    typename P::Acc acc = P::acc0();
+    for (int a = 0; a < A; ++a) P::acc(acc, v[(size_t)(k0 + a) * S]);
+    v[(size_t)n * S] = P::value(acc);
+    return;
+  }
+  // p's decision node: value under the current strategy, then the Stage 7 update
+  V* sgp = static_cast<V*>(G.sigma) + (size_t)nd.row * S + h;
+  V c[kStreamMaxActions], sg[kStreamMaxActions];
+  typename P::Acc acc = P::acc0();
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a)
+    if (a < A) {
+      c[a] = v[(size_t)(k0 + a) * S];
+      sg[a] = sgp[(size_t)a * S];
+      P::acc_mul(acc, sg[a], c[a]);
+    }
+  val = P::value(acc);
+  v[(size_t)n * S] = val;
+  const Discount d = disc_tab[*iter];
+  const V pi = static_cast<const V*>(G.reach)[((size_t)p * N + n) * S + h];
+  double* Rp = G.R + (size_t)nd.row * S + h;
+  double* Sp = G.S + (size_t)nd.row * S + h;
+  double* Mp = variant == 3 ? G.M + (size_t)nd.row * S + h : nullptr;
+  double Rm[kStreamMaxActions];
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a) {
+    Rm[a] = 0.0;
+    if (a < A) {
+      const V rr = P::sub(c[a], val);                          // instantaneous regret
+      const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
+      const double rd = P::to_double(rr);
+      double x = Rp[(size_t)a * S] + rd;
+      if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+      if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;  // CFR+, Predictive CFR+
+      const double sn = fma(Sp[(size_t)a * S], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
+      Rp[(size_t)a * S] = x;
+      Sp[(size_t)a * S] = sn;
+      Rm[a] = x;
+      if (variant == 3) {
+        Mp[(size_t)a * S] = rd;  // the prediction of the next regret
+        Rm[a] = x + rd;          // Predictive CFR+ matches R + M
+      }
+    }
+  }
+  V sn[kStreamMaxActions];
+  regret_match<P>(Rm, A, sn);
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a)
+    if (a < A) sgp[(size_t)a * S] = sn[a];
+}
+
+// Strategy rows of player p (blockIdx.y when both): RM(R) (+ M for Predictive CFR+) into
+// sigma (avg = 0), or the average S / sum S into sigbar (avg = 1), as the per-hand kernel
+// computes them: positive parts in the value type, their sum in action order.
+template <typename P>
+__global__ void __launch_bounds__(kWideThreads) k_wide_rows(const GameDev* __restrict__ games, int player_mask,
+                                                            int avg) {
+  using V = typename P::V;
+  pdl_wait();
+  pdl_trigger();
+  const GameDev& G = games[0];
+  const int p = player_mask == 3 ? (int)blockIdx.y : (player_mask == 1 ? 0 : 1);
+  const size_t S = (size_t)G.hstride;
+  const int db = G.dec_begin[p], ndec = G.dec_begin[p + 1] - db;
+  const size_t e = (size_t)blockIdx.x * kWideThreads + threadIdx.x;
+  if (e >= (size_t)ndec * S) return;
+  const int h = (int)(e % S);
+  if (h >= G.n_hands) return;
+  const NodeDev nd = G.nodes[G.dec_nodes[db + (int)(e / S)]];
+  double x[kStreamMaxActions];
+  load_rows((avg ? G.S : G.R) + (size_t)nd.row * S + h, S, nd.n_kids, x);
+  if (!avg && G.M) {
+    double m[kStreamMaxActions];
+    load_rows(G.M + (size_t)nd.row * S + h, S, nd.n_kids, m);
+#pragma unroll
+    for (int a = 0; a < kStreamMaxActions; ++a) x[a] += m[a];
+  }
+  V sg[kStreamMaxActions];
+  regret_match<P>(x, nd.n_kids, sg);
+  V* out = static_cast<V*>(avg ? G.sigbar : G.sigma) + (size_t)nd.row * S + h;
+#pragma unroll
+  for (int a = 0; a < kStreamMaxActions; ++a)
+    if (a < nd.n_kids) out[(size_t)a * S] = sg[a];
+}
+
+// Top-down step at every node of one level -- the contiguous ids a0 .. a0 + cnt -- (Stages
+// 1-2): p's reach is the parent's times p's probability of the action, and zero for hands
+// holding a dealt card.  Level 0 (the root) takes p's range.
+template <typename P>
+__global__ void __launch_bounds__(kWideThreads) k_wide_fwd(const GameDev* __restrict__ games, int a0, int cnt,
+                                                           int player_mask, int avg) {
+  using V = typename P::V;
+  pdl_wait();
+  pdl_trigger();
+  const GameDev& G = games[0];
+  const int p = player_mask == 3 ? (int)blockIdx.y : (player_mask == 1 ? 0 : 1);
+  const size_t S = (size_t)G.hstride;
+  const size_t e = (size_t)blockIdx.x * kWideThreads + threadIdx.x;
+  if (e >= (size_t)cnt * S) return;
+  const int n = a0 + (int)(e / S), h = (int)(e % S);
+  if (h >= G.n_hands) return;
+  V* rch = static_cast<V*>(avg ? G.reach_bar : G.reach) + (size_t)p * G.n_nodes * S + h;
+  if (n == 0) {
+    rch[0] = static_cast<const V*>(G.range_v)[(size_t)p * S + h];
+    return;
+  }
+  const NodeDev nd = G.nodes[n];
+  V x = rch[(size_t)nd.parent * S];
+  if (nd.aplayer == p) x = P::mul(x, static_cast<const V*>(avg ? G.sigbar : G.sigma)[(size_t)nd.arow * S + h]);
+  if (nd.deal != kNoCard && ((G.hand_mask[h] >> nd.deal) & 1ull)) x = P::zero();
+  rch[(size_t)n * S] = x;
+}
+
+// FP64 root sums of the best response, one block per player: sum_h r_p(h) v*_p(root, h),
+// each thread over a fixed stride of hands, then a fixed-order tree in shared memory.
+template <typename P>
+__global__ void __launch_bounds__(kWideThreads) k_wide_root(const GameDev* __restrict__ games) {
+  __shared__ double red[kWideThreads];
+  pdl_wait();
+  const GameDev& G = games[0];
+  const int p = blockIdx.x;
+  const size_t S = (size_t)G.hstride;
+  using V = typename P::V;
+  const V* v = static_cast<const V*>(G.cfv_br) + (size_t)p * G.n_nodes * S;
+  double x = 0.0;
+  for (int h = threadIdx.x; h < G.n_hands; h += kWideThreads) x += G.range64[(size_t)p * S + h] * P::to_double(v[h]);
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int o = kWideThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) G.br_out[p] = red[0];
+}
+
+__global__ void k_wide_advance(int* iter) {
+  pdl_wait();
+  *iter += 1;
+}
+
 // ------------------------------------------------------------------ launchers
 
 static int check_launch(const char* what) {
@@ -1388,7 +1585,104 @@ static int launch_hand(const LaunchCtx& c, int player_mask, int advance, void* s
                                          : launch_hand_p<MODE, Pairs>(c, player_mask, advance, stream, pdl);
 }
 
-int launch_init(const LaunchCtx& c, void* stream) { return launch_hand<kModeInit>(c, 3, 0, stream, false); }
+// ---- wide schedule: a pass is a sequence of per-level launches (host loop over levels)
+
+static unsigned wide_blocks(size_t items) { return (unsigned)((items + kWideThreads - 1) / kWideThreads); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_wide(void (*kernel)(KArgs...), unsigned blocks, int players, void* stream, bool pdl,
+                               Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, (unsigned)players);
+  cfg.blockDim = dim3(kWideThreads);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <int MODE, typename P>
+static cudaError_t wide_backward(const LaunchCtx& c, int player_mask, void* stream) {
+  const int players = player_mask == 3 ? 2 : 1;
+  const size_t S = (size_t)c.wide_stride;
+  for (int l = c.wide_levels - 1; l >= 0; --l) {
+    const int cnt = c.wide_inner_off[l + 1] - c.wide_inner_off[l];
+    if (cnt == 0) continue;
+    const cudaError_t e =
+        launch_wide(k_wide_back<MODE, P>, wide_blocks((size_t)cnt * S), players, stream, c.pdl != 0, c.games,
+                    c.wide_inner + c.wide_inner_off[l], cnt, player_mask, c.iter, c.disc, c.variant);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename P>
+static cudaError_t wide_forward(const LaunchCtx& c, int player_mask, int avg, int first_level, void* stream) {
+  const int players = player_mask == 3 ? 2 : 1;
+  const size_t S = (size_t)c.wide_stride;
+  for (int l = first_level; l < c.wide_levels; ++l) {
+    const int a0 = c.wide_ls[l], cnt = c.wide_ls[l + 1] - a0;
+    if (cnt == 0) continue;
+    const cudaError_t e = launch_wide(k_wide_fwd<P>, wide_blocks((size_t)cnt * S), players, stream, c.pdl != 0,
+                                      c.games, a0, cnt, player_mask, avg);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename P>
+static cudaError_t wide_rows(const LaunchCtx& c, int avg, void* stream) {
+  // rows of both players: the larger player's decision-node count sizes the grid
+  return launch_wide(k_wide_rows<P>, wide_blocks((size_t)c.wide_max_dec * c.wide_stride), 2, stream, c.pdl != 0,
+                     c.games, 3, avg);
+}
+
+template <typename P>
+static int wide_pass(const LaunchCtx& c, int which, int player_mask, int advance, void* stream) {
+  cudaError_t e = cudaSuccess;
+  if (which == kModeUpdate) {
+    e = wide_backward<kModeUpdate, P>(c, player_mask, stream);
+    if (e == cudaSuccess) e = wide_forward<P>(c, player_mask, 0, 1, stream);
+    if (e == cudaSuccess && advance) e = launch_wide(k_wide_advance, 1, 1, stream, c.pdl != 0, c.iter);
+  } else if (which == kModeInit || which == kModeAvg) {
+    const int avg = which == kModeAvg;
+    e = wide_rows<P>(c, avg, stream);
+    if (e == cudaSuccess) e = wide_forward<P>(c, 3, avg, 0, stream);
+  } else {  // kModeBR
+    e = wide_backward<kModeBR, P>(c, 3, stream);
+    if (e == cudaSuccess) e = launch_wide(k_wide_root<P>, 2, 1, stream, c.pdl != 0, c.games);
+  }
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of a wide-schedule kernel failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
+  return check_launch("wide schedule");
+}
+
+static int launch_wide_pass(const LaunchCtx& c, int which, int player_mask, int advance, void* stream) {
+  return c.precision == kPrecisionSingle ? wide_pass<Single>(c, which, player_mask, advance, stream)
+                                         : wide_pass<Pairs>(c, which, player_mask, advance, stream);
+}
+
+int wide_launch_count(const LaunchCtx& c, int which, int player_mask, int advance) {
+  int back = 0, fwd = 0;
+  for (int l = 0; l < c.wide_levels; ++l) {
+    back += c.wide_inner_off[l + 1] > c.wide_inner_off[l];
+    fwd += c.wide_ls[l + 1] > c.wide_ls[l];
+  }
+  (void)player_mask;
+  if (which == kModeUpdate) return back + (fwd - 1) + (advance ? 1 : 0);
+  if (which == kModeInit || which == kModeAvg) return 1 + fwd;
+  return back + 1;
+}
+
+int launch_init(const LaunchCtx& c, void* stream) {
+  if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeInit, 3, 0, stream);
+  return launch_hand<kModeInit>(c, 3, 0, stream, false);
+}
 template <typename P>
 static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   const int players = player_mask == 3 ? 2 : 1;
@@ -1407,6 +1701,7 @@ static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, voi
 }
 
 int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream) {
+  if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeUpdate, player_mask, advance, stream);
   if (c.schedule == kScheduleStream)
     return c.precision == kPrecisionSingle ? launch_stream_p<Single>(c, player_mask, advance, stream)
                                            : launch_stream_p<Pairs>(c, player_mask, advance, stream);
@@ -1420,8 +1715,14 @@ int launch_current_rows(const LaunchCtx& c, void* stream) {
     k_current_rows<Pairs><<<152, 256, 0, (cudaStream_t)stream>>>(c.games, c.n_games);
   return check_launch("k_current_rows");
 }
-int launch_avg_reach(const LaunchCtx& c, void* stream) { return launch_hand<kModeAvg>(c, 3, 0, stream, false); }
-int launch_br(const LaunchCtx& c, void* stream) { return launch_hand<kModeBR>(c, 3, 0, stream, c.pdl != 0); }
+int launch_avg_reach(const LaunchCtx& c, void* stream) {
+  if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeAvg, 3, 0, stream);
+  return launch_hand<kModeAvg>(c, 3, 0, stream, false);
+}
+int launch_br(const LaunchCtx& c, void* stream) {
+  if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeBR, 3, 0, stream);
+  return launch_hand<kModeBR>(c, 3, 0, stream, c.pdl != 0);
+}
 
 int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stream) {
   if (c.n_term_runs == 0) return 0;

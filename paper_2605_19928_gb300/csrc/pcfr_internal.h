@@ -43,8 +43,13 @@ constexpr uint8_t kNoCard = 255;
 constexpr int kPrecisionPairs = 0;   // values as double-float FP32 pairs
 constexpr int kPrecisionSingle = 1;  // values as FP32
 constexpr int kDiscountCapacity = 1 << 16;  // iterations covered by one discount table
+// Passes of the per-hand kernel (and of the wide schedule).
+enum HandMode { kModeInit = 0, kModeUpdate = 1, kModeAvg = 2, kModeBR = 3 };
+
 constexpr int kScheduleLevel = 1;   // per-hand passes: one block per chunk of hands, level by level
 constexpr int kScheduleStream = 2;  // update pass: one warp per 32 hands walks a depth-first program
+constexpr int kScheduleWide = 3;    // one large tree: every pass is a launch per level over all of
+                                    // that level's (node, hand) pairs
 constexpr int kStreamMaxActions = 8;  // actions at a decision node the stream schedule holds in registers
 constexpr int kStreamHalfMin = 12;   // 8-byte units per lane in each half of a warp's prefetch ring,
                                       // at least (or the most one node needs, 2 A + 1)
@@ -176,7 +181,7 @@ struct LaunchCtx {
   int variant;
   int precision;               // kPrecisionPairs or kPrecisionSingle
   int pdl;                     // chain launches with programmatic dependent launch
-  int schedule;                // kScheduleLevel or kScheduleStream (update launches)
+  int schedule;                // kScheduleLevel, kScheduleStream (update launches) or kScheduleWide
   const Work* warp_work;       // device [n_warp_work]: (game, first group of 32 hands) of each
                                // block of the stream schedule, largest trees first
   int n_warp_work;
@@ -185,6 +190,14 @@ struct LaunchCtx {
                                // memory; 0 = read from global memory
   int stream_half;             // units per lane in each half of the stream prefetch ring
   int stream_units;            // load descriptors staged per block (0 when the program is not)
+  // wide schedule (one game): level l holds nodes [wide_ls[l], wide_ls[l + 1]); its inner
+  // nodes are wide_inner[wide_inner_off[l] .. wide_inner_off[l + 1])
+  int wide_levels;             // number of levels
+  const int* wide_ls;          // host [wide_levels + 1]
+  const int* wide_inner_off;   // host [wide_levels + 1]
+  const int32_t* wide_inner;   // device: inner node ids, level by level
+  int wide_stride;             // hstride of the game
+  int wide_max_dec;            // decision nodes of the player who has more
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
@@ -194,6 +207,9 @@ int launch_current_rows(const LaunchCtx& c, void* stream);  // sigma = RM(R), ev
 int launch_avg_reach(const LaunchCtx& c, void* stream);
 int launch_br(const LaunchCtx& c, void* stream);
 int launch_average_rows(const LaunchCtx& c, void* stream);
+// Kernels one pass of the wide schedule launches (which: kModeInit, kModeUpdate, kModeAvg or
+// kModeBR, as the per-hand kernel's modes).
+int wide_launch_count(const LaunchCtx& c, int which, int player_mask, int advance);
 int hand_kernel_smem_limit();
 // Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);

@@ -225,7 +225,7 @@ def test_average_strategy_readback():
         capi.cfr_tree_destroy(tree)
 
 
-@pytest.mark.parametrize("schedule", ["level", "stream"])
+@pytest.mark.parametrize("schedule", ["level", "stream", "wide"])
 def test_flop_matches_oracle_from_the_same_state(schedule):
     """Three streets: turn and river cards by chance, 2352 showdown boards, all-in run-outs
     from the flop and from the turn (31k nodes)."""
@@ -271,6 +271,28 @@ def test_stream_schedule_simultaneous_updates_match_oracle():
     run_pair(river(97, seed=21), "dcfr", iters=5, alternating=False, schedule="stream")
 
 
+# ---------------------------------------------------------------- wide schedule
+# One launch per level over every (node, hand) pair of the level (large single trees); the
+# same arithmetic as the level schedule.
+
+WIDE_CASES = [("kuhn", "cfr"), ("leduc", "cfr+"), ("river_203", "dcfr"), ("turn_40", "dcfr"),
+              ("river_64_r4", "dcfr"), ("river_203", "pcfr+")]
+
+
+@pytest.mark.parametrize("case,variant", WIDE_CASES)
+def test_wide_schedule_matches_oracle_from_the_same_state(case, variant):
+    worst = run_pair(CASES[case][0](), variant, forced=True, schedule="wide")
+    print(case, variant, "wide forced", worst)
+
+
+def test_wide_schedule_first_ten_iterations_match_oracle():
+    run_pair(river(203), "dcfr", forced=False, schedule="wide")
+
+
+def test_wide_schedule_simultaneous_updates_match_oracle():
+    run_pair(river(97, seed=21), "dcfr", iters=5, alternating=False, schedule="wide")
+
+
 def _state(tree, n_games, with_pred=False):
     out = []
     for game in range(n_games):
@@ -312,6 +334,28 @@ def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alter
     assert np.array_equal(expl[0][0], expl[1][0]) and np.array_equal(expl[0][1], expl[1][1])
 
 
+@pytest.mark.parametrize("precision", ["pairs", "single"])
+@pytest.mark.parametrize("variant,alternating", [("dcfr", True), ("cfr+", True), ("cfr", False), ("pcfr+", True)])
+def test_wide_and_level_schedules_give_the_same_bits(precision, variant, alternating):
+    """Same state bits; the exploitability differs only in the order of its FP64 root sum."""
+    for spec in (river(203, seed=51), turn(40, seed=54), leduc_random(seed=53), kuhn_random(seed=55)):
+        states, expl = [], []
+        for schedule in ("level", "wide"):
+            tree = capi.cfr_tree_create(spec, capi.make_opts(variant, alternating=alternating, precision=precision,
+                                                             schedule=schedule))
+            try:
+                assert capi.cfr_schedule(tree) == capi.SCHEDULES[schedule]
+                capi.cfr_iterate(tree, 7)
+                states.append(_state(tree, 1, with_pred=variant == "pcfr+"))
+                expl.append(capi.cfr_exploitability(tree))
+            finally:
+                capi.cfr_tree_destroy(tree)
+        assert len(states[0]) == len(states[1])
+        for a, b in zip(*states):
+            assert np.array_equal(a, b)
+        np.testing.assert_allclose(expl[0][1], expl[1][1], rtol=1e-12, atol=1e-12 * spec.pot)
+
+
 def test_schedule_selection():
     tree = capi.cfr_tree_create(river(203))
     try:
@@ -335,6 +379,23 @@ def test_schedule_selection():
         assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL
     finally:
         capi.cfr_tree_destroy(tree)
+    with pytest.raises(capi.CfrError) as e:  # the wide form takes at most 8 actions too
+        capi.cfr_tree_create(wide, capi.make_opts(schedule="wide"))
+    assert e.value.code == capi.CFR_EINVAL
+    # one tree too large for a block to stage (31k nodes): the wide form; two of them: level
+    tree = capi.cfr_tree_create(flop(12))
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_WIDE
+    finally:
+        capi.cfr_tree_destroy(tree)
+    tree = capi.cfr_batch_create([flop(12), flop(12, seed=6)])
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_LEVEL
+    finally:
+        capi.cfr_tree_destroy(tree)
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_batch_create([river(30, seed=5), river(30, seed=6)], capi.make_opts(schedule="wide"))
+    assert e.value.code == capi.CFR_EINVAL
 
 
 # ---------------------------------------------------------------- FP32 values
@@ -345,7 +406,8 @@ def test_schedule_selection():
 # rounding decides near-ties between actions differently from FP64.
 
 @pytest.mark.parametrize("case,variant,schedule", [("river_203", "dcfr", "level"), ("river_203", "dcfr", "stream"),
-                                                   ("turn_40", "dcfr", "stream"), ("leduc", "cfr+", "stream")])
+                                                   ("turn_40", "dcfr", "stream"), ("leduc", "cfr+", "stream"),
+                                                   ("turn_40", "dcfr", "wide")])
 def test_single_precision_error_against_oracle(case, variant, schedule):
     from oracle.oracle import Oracle
     spec = CASES[case][0]()
@@ -369,7 +431,7 @@ def test_terminal_runs_match_one_node_blocks():
     """Large handles evaluate up to four terminal nodes per block; small ones one.  The same
     subgames solved in one large handle and one handle each must agree bit for bit."""
     specs = [river(64, seed=70 + k, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4) for k in range(40)]
-    big = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="single", schedule="level"))
+    big = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="pairs", schedule="level"))
     try:
         n_term = sum(1 for g in range(len(specs)) for n in range(capi.cfr_tree_info(big, g)[0])
                      if capi.cfr_node_info(big, n, g)["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN))
@@ -377,7 +439,7 @@ def test_terminal_runs_match_one_node_blocks():
         capi.cfr_iterate(big, 3)
         e_big, _ = capi.cfr_exploitability(big, len(specs))
         for g in (0, 17, 39):
-            one = capi.cfr_tree_create(specs[g], capi.make_opts("dcfr", precision="single", schedule="level"))
+            one = capi.cfr_tree_create(specs[g], capi.make_opts("dcfr", precision="pairs", schedule="level"))
             try:
                 capi.cfr_iterate(one, 3)
                 e_one, _ = capi.cfr_exploitability(one)
@@ -394,5 +456,29 @@ def test_terminal_runs_match_one_node_blocks():
                                                   capi.cfr_read_values(big, capi.CFR_READ_CFV, n, player=i, game=g))
             finally:
                 capi.cfr_tree_destroy(one)
+    finally:
+        capi.cfr_tree_destroy(big)
+
+
+@pytest.mark.parametrize("schedule", ["level", "stream"])
+def test_fp32_terminal_runs_match_oracle(schedule):
+    """A batch whose terminal nodes fill the GPU (runs of four nodes per block) with FP32
+    values: each subgame against the oracle from the GPU's own state, and its
+    exploitability."""
+    from oracle.oracle import Oracle
+    specs = [river(64, seed=70 + k, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4) for k in range(40)]
+    big = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="single", schedule=schedule))
+    try:
+        capi.cfr_iterate(big, 2)
+        for g in (0, 39):
+            orc = Oracle(specs[g], variant="dcfr")
+            mapping = node_map(big, orc, game=g)
+            for t in range(3, 5):
+                forced_step(big, orc, mapping, t, game=g, rtol=1e-5, floor_frac=1e-8)
+            inject(big, orc, mapping, game=g)
+            e_g, _ = capi.cfr_exploitability(big, len(specs))
+            assert e_g[g] == pytest.approx(orc.exploitability()[0], rel=1e-4, abs=1e-7 * specs[g].pot)
+            capi.cfr_reset(big)
+            capi.cfr_iterate(big, 2)
     finally:
         capi.cfr_tree_destroy(big)

@@ -133,8 +133,8 @@ def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
     return worst
 
 
-@pytest.mark.parametrize("schedule,street", [("level", "turn"), ("stream", "turn"), ("level", "flop"),
-                                             ("stream", "flop")])
+@pytest.mark.parametrize("schedule,street", [("level", "turn"), ("stream", "turn"), ("wide", "turn"),
+                                             ("level", "flop"), ("stream", "flop"), ("wide", "flop")])
 def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
     from oracle.oracle import Oracle
     spec = _leaf_spec(n_hands=24, street="flop") if street == "flop" else _leaf_spec()
@@ -160,7 +160,8 @@ def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
 
 
 @pytest.mark.parametrize("schedule,variant,street", [("level", "dcfr", "turn"), ("stream", "dcfr", "turn"),
-                                                     ("level", "cfr+", "turn"), ("level", "dcfr", "flop")])
+                                                     ("level", "cfr+", "turn"), ("level", "dcfr", "flop"),
+                                                     ("wide", "dcfr", "flop"), ("wide", "pcfr+", "turn")])
 def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant, street):
     from oracle.oracle import Oracle
     spec = _leaf_spec(n_hands=32, seed=9, street=street)
