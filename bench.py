@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch: keep the automatic layout instead of running the launch-tiling autotuner")
     return ap.parse_args(argv)
 
 
@@ -369,6 +371,13 @@ def run_ours(args):
     G = len(specs)
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
                           precision=args.precision, schedule=args.schedule)
+    tuned = None
+    if batch and not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0:
+        # launch tiling (schedule, hands per block, terminal nodes per block), outside the timed region
+        opts, ms_tuned = capi.cfr_autotune(specs, opts, iters=20, stream=stream.cuda_stream)
+        names = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream", capi.CFR_SCHEDULE_WIDE: "wide"}
+        tuned = {"schedule": names[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
+                 "ms_per_iter_while_tuning": ms_tuned}
 
     def create(sp):
         if batch:
@@ -483,6 +492,8 @@ def run_ours(args):
     if rank == 0:
         if batch:
             config = {**batch_config(args, specs, shapes), "schedule": schedule}
+            if tuned is not None:
+                config["autotune"] = tuned
             e_mbb = sorted(1000.0 * float(x) / BB_CHIPS for x in expl)
             quality = {"exploitability_mbb_median": e_mbb[G // 2], "exploitability_mbb_max": e_mbb[-1],
                        "time_to_1mbb": target}
@@ -698,8 +709,9 @@ def run_leaf(args):
                 "ms_per_iter": 1000.0 * t_max / (args.steps * ips), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": ("f32x2" if args.precision == "pairs" else "f32") + " values, f64 R/S, bf16 network",
-                "data": "synthetic (rank-based showdowns; network trained on %dk self-generated river solves)"
-                        % (int(meta[0]) // 1000),
+                "data": "synthetic (rank-based showdowns; network trained on %dk self-generated river solves%s)"
+                        % (int(meta[0]) // 1000, " and the river-card nodes of %d exact turn solves" % int(meta[6])
+                           if len(meta) > 6 and meta[6] > 0 else ""),
                 "config": {"workload": ("depth-limited flop subgame (turn card by chance), leaf network at the "
                                         "river card" if flop else
                                         "depth-limited turn subgame, leaf network at the river card"),
@@ -727,7 +739,9 @@ def run_leaf(args):
                 "leaf_values_vs_exact_river": leaf_check,
                 "network": {"training_solves": int(meta[0]), "solve_iters": int(meta[1]), "epochs": int(meta[2]),
                             "median_solve_exploitability_mbb": float(meta[4]),
-                            "validation_mean_abs_error_pot": float(meta[5])},
+                            "validation_mean_abs_error_pot": float(meta[5]),
+                            "turn_solves": int(meta[6]) if len(meta) > 6 else 0,
+                            "turn_leaf_examples": int(meta[7]) if len(meta) > 7 else 0},
                 "speedup_vs_exact": value / exact_ips,
                 "roofline": roofline, "cpu_baseline": None, "e2e": None, "gpu_launches": int(gpu_launches),
                 "clocks": clock_info}

@@ -44,7 +44,14 @@ extern "C" {
 enum { CFR_GAME_HOLDEM = 0, CFR_GAME_KUHN = 1, CFR_GAME_LEDUC = 2 };
 enum { CFR_VARIANT_CFR = 0, CFR_VARIANT_CFRPLUS = 1, CFR_VARIANT_DCFR = 2, CFR_VARIANT_PCFRPLUS = 3 };
 enum { CFR_NODE_DECISION = 0, CFR_NODE_FOLD = 1, CFR_NODE_SHOWDOWN = 2, CFR_NODE_CHANCE = 3, CFR_NODE_LEAF = 4 };
-enum { CFR_READ_REGRET = 0, CFR_READ_AVG_SUM = 1, CFR_READ_CFV = 2, CFR_READ_BR_CFV = 3, CFR_READ_PREDICTION = 4 };
+enum {
+  CFR_READ_REGRET = 0,
+  CFR_READ_AVG_SUM = 1,
+  CFR_READ_CFV = 2,
+  CFR_READ_BR_CFV = 3,
+  CFR_READ_PREDICTION = 4,
+  CFR_READ_AVG_REACH = 5
+};
 
 /*
  * One subgame (Section 5, "Game": heads-up poker solved to the end of a betting round).
@@ -119,6 +126,9 @@ typedef struct cfr_game_spec {
  * and flops; one subgame per handle, at most 8 actions per decision node).
  * CFR_SCHEDULE_AUTO (0) picks STREAM when the handle has at least 1216 such warps (8 per
  * SM) and every tree allows it, WIDE for one subgame too large to stage, else LEVEL.
+ * term_nodes: fold and showdown nodes per CUDA block of the terminal launch (nodes of one
+ * board; 0 = automatic: one while the nodes do not fill the GPU eight times over, up to
+ * four when they do; otherwise 1 to 4).  Results are the same bits for every value.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
 enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2, CFR_SCHEDULE_WIDE = 3 };
@@ -131,6 +141,7 @@ typedef struct cfr_solver_opts {
   int chunk_hands;
   int precision;
   int schedule;
+  int term_nodes;
 } cfr_solver_opts;
 
 typedef struct cfr_tree cfr_tree;
@@ -189,6 +200,20 @@ int cfr_exploitability_noalloc(cfr_tree* tree, double* expl, double* br);
  * (asynchronous, on the handle's stream). */
 int cfr_reset(cfr_tree* tree);
 
+/* Autotuner of the launch tiling (batched serving): builds the subgames under each
+ * candidate layout -- the level schedule with 4, 8, 16 and 32 hands per block, the stream
+ * schedule (32 hands per warp), the wide schedule (one subgame), then 1, 2 or 4 terminal
+ * nodes per block for the fastest -- times `iters` iterations of each after two warm-up
+ * iterations (CUDA events on `stream`, depth-limit leaves evaluated with an all-zero
+ * network), and writes the fastest options to *best (opts with schedule, chunk_hands and
+ * term_nodes set; term_nodes stays 0 when the automatic count was fastest) and its mean
+ * device time per iteration to *ms_per_iter (may be NULL).
+ * Every candidate gives the same results bit for bit, so only time decides.  Handles are
+ * created and destroyed one at a time (device memory of one handle at most).  Errors as
+ * for cfr_batch_create; CFR_EINVAL when iters < 1.  Synchronises. */
+int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream, int iters,
+                 cfr_solver_opts* best, double* ms_per_iter);
+
 /* The schedule the handle uses (CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM or
  * CFR_SCHEDULE_WIDE), or a negative status. */
 int cfr_schedule(const cfr_tree* tree);
@@ -210,7 +235,10 @@ int cfr_node_info(const cfr_tree* tree, int game, int node, int* type, int* play
  *   CFR_READ_CFV: player's counterfactual values at `node` from that player's last
  *     traversal, [n_hands];
  *   CFR_READ_BR_CFV: player's best-response values at `node` from the last exploitability
- *     call, [n_hands]. */
+ *     call, [n_hands];
+ *   CFR_READ_AVG_REACH: player's own reach at `node` under the average strategy (root range
+ *     times the player's average action probabilities on the path, zero for hands holding a
+ *     dealt card) from the last exploitability call, [n_hands]. */
 int cfr_read_values(cfr_tree* tree, int game, int what, int player, int node, double* out, size_t out_len);
 
 /* Overwrite a decision node's cumulative regrets (CFR_READ_REGRET), average-strategy sums
@@ -269,7 +297,11 @@ int cfr_counters(const cfr_tree* tree, int64_t* kernel_launches, int64_t* device
  * player 0's then player 1's value per unit pot over the slots (offsets 0 and 1326).  The
  * value of hand h of player i at leaf n is pot(n) P(r) kappa sum over r not in h of
  * output_i,r(h) times the opponent reach over hands sharing no card with h or r.  Host
- * buffers, copied (synchronises).  Must be set before cfr_iterate on such a handle. */
+ * buffers, copied (synchronises).  Must be set before cfr_iterate on such a handle.  When
+ * all subgames of the handle share one hand list, the library stores layer 1's range
+ * columns and layer 4's rows permuted to that list's order (the network is the same
+ * function; its kernels then read and write hand-ordered rows); the rows
+ * cfr_read_leaf_rows returns are in slot order either way. */
 int cfr_set_leaf_net(cfr_tree* tree, const uint16_t* const W[4], const float* const b[4]);
 
 /* Evaluate the leaf network once on the current state (the reach the next player update
@@ -284,7 +316,8 @@ int cfr_eval_leaves(cfr_tree* tree, int average);
 int cfr_leaf_info(const cfr_tree* tree, int leaf, int* n_leaves, int* game, int* node, int* row0);
 
 /* Read network rows of the last leaf evaluation into a host buffer (synchronises):
- * what 0 = inputs (n_rows x 2752 BF16 as uint16), 1 = outputs (n_rows x 2688 FP32). */
+ * what 0 = inputs (n_rows x 2752 BF16 as uint16), 1 = outputs (n_rows x 2688 FP32), in
+ * the slot layout cfr_set_leaf_net describes. */
 int cfr_read_leaf_rows(cfr_tree* tree, int what, int row0, int n_rows, void* out);
 
 /* One dense layer of the depth-limit leaf network (Section 3, depth-limited solving; the

@@ -23,6 +23,7 @@ CFR_NODE_DECISION, CFR_NODE_FOLD, CFR_NODE_SHOWDOWN, CFR_NODE_CHANCE, CFR_NODE_L
 LEAF_SLOTS, LEAF_IN, LEAF_HIDDEN, LEAF_OUT, LEAF_CARDS = 1326, 2752, 512, 2688, 48
 LEAF_SHAPES = ((LEAF_HIDDEN, LEAF_IN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_HIDDEN, LEAF_HIDDEN), (LEAF_OUT, LEAF_HIDDEN))
 CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV, CFR_READ_PREDICTION = 0, 1, 2, 3, 4
+CFR_READ_AVG_REACH = 5
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
 CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM, CFR_SCHEDULE_WIDE = 0, 1, 2, 3
@@ -36,7 +37,7 @@ EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iter
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
            "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule",
            "cfr_gemm_bf16", "cfr_set_leaf_net", "cfr_leaf_info", "cfr_read_leaf_rows",
-           "cfr_eval_leaves", "cfr_write_values")
+           "cfr_eval_leaves", "cfr_write_values", "cfr_autotune")
 
 
 class CfrError(RuntimeError):
@@ -55,7 +56,8 @@ class cfr_game_spec(C.Structure):
 
 class cfr_solver_opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("alternating", C.c_int), ("chunk_hands", C.c_int), ("precision", C.c_int), ("schedule", C.c_int)]
+                ("alternating", C.c_int), ("chunk_hands", C.c_int), ("precision", C.c_int), ("schedule", C.c_int),
+                ("term_nodes", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -80,6 +82,8 @@ def load(path: str = LIB_PATH):
         lib.cfr_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
         lib.cfr_tree_create.argtypes = [C.POINTER(cfr_game_spec), C.POINTER(cfr_solver_opts), P, C.POINTER(P)]
         lib.cfr_batch_create.argtypes = [C.POINTER(cfr_game_spec), I, C.POINTER(cfr_solver_opts), P, C.POINTER(P)]
+        lib.cfr_autotune.argtypes = [C.POINTER(cfr_game_spec), I, C.POINTER(cfr_solver_opts), P, I,
+                                     C.POINTER(cfr_solver_opts), C.POINTER(C.c_double)]
         lib.cfr_iterate.argtypes = [P, I]
         lib.cfr_strategy.argtypes = [P, I, I, I, C.POINTER(C.c_float), S]
         lib.cfr_exploitability.argtypes = [P, pd, pd]
@@ -184,11 +188,11 @@ def make_spec(g) -> tuple[cfr_game_spec, tuple]:
 
 
 def make_opts(variant="dcfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True, chunk_hands=0,
-              precision="pairs", schedule="auto") -> cfr_solver_opts:
+              precision="pairs", schedule="auto", term_nodes=0) -> cfr_solver_opts:
     return cfr_solver_opts(VARIANTS[variant] if isinstance(variant, str) else int(variant), alpha, beta, gamma,
                            int(alternating), int(chunk_hands),
                            PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                           SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule))
+                           SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule), int(term_nodes))
 
 
 def _stream_arg(stream):
@@ -226,6 +230,21 @@ def cfr_batch_create(specs, opts: cfr_solver_opts | None = None, stream=None) ->
                                 C.byref(out)))
     del keep
     return out
+
+
+def cfr_autotune(specs, opts: cfr_solver_opts | None = None, iters: int = 20, stream=None):
+    """(best options, ms per iteration) of the launch-tiling autotuner over these subgames."""
+    lib = load()
+    arr = (cfr_game_spec * len(specs))()
+    keep = []
+    for k, g in enumerate(specs):
+        arr[k], kk = make_spec(g)
+        keep.append(kk)
+    best, ms = cfr_solver_opts(), C.c_double()
+    _check(lib.cfr_autotune(arr, len(specs), C.byref(opts if opts else make_opts()), _stream_arg(stream), int(iters),
+                            C.byref(best), C.byref(ms)))
+    del keep
+    return best, float(ms.value)
 
 
 def cfr_iterate(tree, n_iters: int = 1):

@@ -67,6 +67,7 @@ struct cfr_tree {
   int64_t cur_gen = -1;         // state_gen for which sigma holds RM(R) (stream schedule)
   LeafCtx leaf{};               // depth-limit leaves and their network (none: n_leaves = 0)
   std::vector<LeafDev> leaf_host;
+  std::vector<int> leaf_col;    // network column of each card-pair slot (hand order, or the slot)
   bool leaf_net_set = false;
   int64_t launches = 0;         // kernels launched (graph replays included)
   int64_t device_bytes = 0;
@@ -213,6 +214,27 @@ int setup_leaves(cfr_tree* t, const cfr_game_spec* specs, int n_games) {
   if (t->leaf_host.empty()) return CFR_OK;
   L.n_leaves = (int)t->leaf_host.size();
   L.hstride_max = hmax;
+  // one hand list for all games: inputs and outputs in hand order (column of slot s)
+  bool same = t->host[0].hand_size == 2;
+  for (int g = 1; g < n_games && same; ++g) same = t->host[g].hand_cards == t->host[0].hand_cards;
+  L.hand_order = same ? 1 : 0;
+  t->leaf_col.assign(kLeafSlots, -1);
+  if (same) {
+    const HostGame& h0 = t->host[0];
+    std::vector<char> used(kLeafSlots, 0);
+    for (int k = 0; k < h0.n_hands; ++k) {
+      int a = h0.hand_cards[2 * (size_t)k], b = h0.hand_cards[2 * (size_t)k + 1];
+      if (a > b) std::swap(a, b);
+      const int sl = b * (b - 1) / 2 + a;
+      t->leaf_col[sl] = k;
+      used[sl] = 1;
+    }
+    int next = h0.n_hands;
+    for (int sl = 0; sl < kLeafSlots; ++sl)
+      if (!used[sl]) t->leaf_col[sl] = next++;
+  } else {
+    for (int sl = 0; sl < kLeafSlots; ++sl) t->leaf_col[sl] = sl;
+  }
   std::vector<int16_t> slot((size_t)n_games * hmax, 0), hand_at((size_t)n_games * kLeafSlots, -1);
   for (int g = 0; g < n_games; ++g) {
     const HostGame& h = t->host[g];
@@ -268,6 +290,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
   if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
     return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
+  if (o.term_nodes < 0 || o.term_nodes > 4) return fail(CFR_EINVAL, "term_nodes must be 0 to 4");
   if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_WIDE) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
@@ -471,7 +494,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   // up to four per block (same game and board table) when they do
   std::vector<Work> term_runs;
   {
-    const int per = std::max(1, std::min(4, (int)term_work.size() / (152 * 8)));
+    const int per = o.term_nodes ? o.term_nodes : std::max(1, std::min(4, (int)term_work.size() / (152 * 8)));
     size_t a = 0;
     while (a < term_work.size()) {
       const Work w = term_work[a];
@@ -846,13 +869,13 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
     CK(cudaStreamSynchronize(t->stream));
     return CFR_OK;
   }
-  if (what == CFR_READ_CFV || what == CFR_READ_BR_CFV) {
+  if (what == CFR_READ_CFV || what == CFR_READ_BR_CFV || what == CFR_READ_AVG_REACH) {
     if (player < 0 || player > 1) return fail(CFR_EINVAL, "player must be 0 or 1");
     if (out_len < (size_t)H) return fail(CFR_EINVAL, "output buffer too small");
     const size_t vf = t->opts.precision == CFR_PRECISION_SINGLE ? 1 : 2;
     std::vector<float> tmp((size_t)H * vf);
-    const float* src = static_cast<const float*>(what == CFR_READ_CFV ? d.cfv : d.cfv_br) +
-                       ((size_t)player * h.nodes.size() + node) * S * vf;
+    const void* arr = what == CFR_READ_CFV ? d.cfv : what == CFR_READ_BR_CFV ? d.cfv_br : d.reach_bar;
+    const float* src = static_cast<const float*>(arr) + ((size_t)player * h.nodes.size() + node) * S * vf;
     CK(cudaMemcpyAsync(tmp.data(), src, (size_t)H * 4 * vf, cudaMemcpyDeviceToHost, t->stream));
     CK(cudaStreamSynchronize(t->stream));
     for (int k = 0; k < H; ++k) out[k] = vf == 1 ? (double)tmp[k] : (double)tmp[2 * k] + (double)tmp[2 * k + 1];
@@ -978,10 +1001,35 @@ int cfr_set_leaf_net(cfr_tree* t, const uint16_t* const W[4], const float* const
   const size_t wn[4] = {(size_t)kLeafHidden * kLeafIn, (size_t)kLeafHidden * kLeafHidden,
                         (size_t)kLeafHidden * kLeafHidden, (size_t)kLeafOut * kLeafHidden};
   const size_t bn[4] = {(size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafHidden, (size_t)kLeafOut};
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 4; ++k)
     if (!W[k] || !b[k]) return fail(CFR_EINVAL, "every layer needs weights and a bias");
-    CK(cudaMemcpyAsync(const_cast<void*>(t->leaf.W[k]), W[k], wn[k] * 2, cudaMemcpyHostToDevice, t->stream));
-    CK(cudaMemcpyAsync(const_cast<float*>(t->leaf.b[k]), b[k], bn[k] * 4, cudaMemcpyHostToDevice, t->stream));
+  // the range inputs (columns of layer 1) and value outputs (rows of layer 4) move to the
+  // handle's column order
+  const std::vector<int>& col = t->leaf_col;
+  std::vector<uint16_t> w0(wn[0]), w3(wn[3]);
+  std::vector<float> b3(bn[3]);
+  for (int r = 0; r < kLeafHidden; ++r) {
+    const uint16_t* src = W[0] + (size_t)r * kLeafIn;
+    uint16_t* dst = w0.data() + (size_t)r * kLeafIn;
+    for (int c = 2 * kLeafSlots; c < kLeafIn; ++c) dst[c] = src[c];
+    for (int p = 0; p < 2; ++p)
+      for (int sl = 0; sl < kLeafSlots; ++sl) dst[p * kLeafSlots + col[sl]] = src[p * kLeafSlots + sl];
+  }
+  for (int r = 2 * kLeafSlots; r < kLeafOut; ++r) {
+    for (int c = 0; c < kLeafHidden; ++c) w3[(size_t)r * kLeafHidden + c] = W[3][(size_t)r * kLeafHidden + c];
+    b3[r] = b[3][r];
+  }
+  for (int p = 0; p < 2; ++p)
+    for (int sl = 0; sl < kLeafSlots; ++sl) {
+      const int ro = p * kLeafSlots + col[sl], ri = p * kLeafSlots + sl;
+      for (int c = 0; c < kLeafHidden; ++c) w3[(size_t)ro * kLeafHidden + c] = W[3][(size_t)ri * kLeafHidden + c];
+      b3[ro] = b[3][ri];
+    }
+  const void* wsrc[4] = {w0.data(), W[1], W[2], w3.data()};
+  const float* bsrc[4] = {b[0], b[1], b[2], b3.data()};
+  for (int k = 0; k < 4; ++k) {
+    CK(cudaMemcpyAsync(const_cast<void*>(t->leaf.W[k]), wsrc[k], wn[k] * 2, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(const_cast<float*>(t->leaf.b[k]), bsrc[k], bn[k] * 4, cudaMemcpyHostToDevice, t->stream));
   }
   CK(cudaStreamSynchronize(t->stream));
   t->leaf_net_set = true;
@@ -1017,16 +1065,25 @@ int cfr_read_leaf_rows(cfr_tree* t, int what, int row0, int n_rows, void* out) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   const int rows = t->leaf.n_leaves * kLeafCards;
   if (row0 < 0 || n_rows < 0 || row0 + n_rows > rows || (!out && n_rows)) return fail(CFR_EINVAL, "bad row range");
-  if (what == 0) {
-    CK(cudaMemcpyAsync(out, static_cast<const uint16_t*>(t->leaf.X) + (size_t)row0 * kLeafIn,
-                       (size_t)n_rows * kLeafIn * 2, cudaMemcpyDeviceToHost, t->stream));
-  } else if (what == 1) {
-    CK(cudaMemcpyAsync(out, t->leaf.Y + (size_t)row0 * kLeafOut, (size_t)n_rows * kLeafOut * 4,
-                       cudaMemcpyDeviceToHost, t->stream));
-  } else {
-    return fail(CFR_EINVAL, "what must be 0 (inputs) or 1 (outputs)");
-  }
+  if (what != 0 && what != 1) return fail(CFR_EINVAL, "what must be 0 (inputs) or 1 (outputs)");
+  const size_t width = what == 0 ? kLeafIn : kLeafOut, es = what == 0 ? 2 : 4;
+  std::vector<unsigned char> raw((size_t)n_rows * width * es);
+  const unsigned char* src = what == 0 ? static_cast<const unsigned char*>(t->leaf.X)
+                                       : reinterpret_cast<const unsigned char*>(t->leaf.Y);
+  if (n_rows)
+    CK(cudaMemcpyAsync(raw.data(), src + (size_t)row0 * width * es, raw.size(), cudaMemcpyDeviceToHost, t->stream));
   CK(cudaStreamSynchronize(t->stream));
+  // back to slot order: the range / value block of each player moves from column col[s] to s
+  unsigned char* o = static_cast<unsigned char*>(out);
+  const std::vector<int>& col = t->leaf_col;
+  for (int r = 0; r < n_rows; ++r) {
+    const unsigned char* in_row = raw.data() + (size_t)r * width * es;
+    unsigned char* out_row = o + (size_t)r * width * es;
+    memcpy(out_row + 2 * kLeafSlots * es, in_row + 2 * kLeafSlots * es, (width - 2 * kLeafSlots) * es);
+    for (int p = 0; p < 2; ++p)
+      for (int sl = 0; sl < kLeafSlots; ++sl)
+        memcpy(out_row + (size_t)(p * kLeafSlots + sl) * es, in_row + (size_t)(p * kLeafSlots + col[sl]) * es, es);
+  }
   return CFR_OK;
 }
 
@@ -1045,6 +1102,72 @@ int cfr_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int 
 }
 
 void cfr_tree_destroy(cfr_tree* t) { delete t; }
+
+int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream, int iters,
+                 cfr_solver_opts* best, double* ms_per_iter) {
+  if (!specs || n_games < 1 || !opts || !best) return fail(CFR_EINVAL, "specs, opts and best are required");
+  if (iters < 1) return fail(CFR_EINVAL, "iters must be at least 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // time one candidate; +inf when the layout does not apply (e.g. a tree the stream form refuses)
+  auto trial = [&](const cfr_solver_opts& o, double* ms) -> int {
+    *ms = INFINITY;
+    cfr_tree* t = nullptr;
+    int rc = create_impl(specs, n_games, &o, stream, &t);
+    // the level schedule takes every valid handle: its refusal is the caller's error
+    if (rc == CFR_EINVAL && o.schedule != CFR_SCHEDULE_LEVEL) return CFR_OK;
+    if (rc) return rc;
+    t->leaf_net_set = true;  // leaves, if any, run with the all-zero network the handle starts with
+    rc = cfr_iterate(t, 2);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaEventRecord(e0, s);
+    if (!rc && e == cudaSuccess) rc = cfr_iterate(t, iters);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float m = 0.f;
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&m, e0, e1);
+    if (!rc && e == cudaSuccess) rc = check_device_flag(t);
+    delete t;
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    *ms = (double)m / iters;
+    return CFR_OK;
+  };
+  cfr_solver_opts cand = *opts, top = *opts;
+  double top_ms = INFINITY, ms = 0.0;
+  int rc = CFR_OK;
+  cand.term_nodes = 0;
+  const int chunks[4] = {4, 8, 16, 32};
+  for (int k = 0; k < 4 && !rc; ++k) {  // level schedule, hands per block
+    cand.schedule = CFR_SCHEDULE_LEVEL;
+    cand.chunk_hands = chunks[k];
+    rc = trial(cand, &ms);
+    if (!rc && ms < top_ms) top_ms = ms, top = cand;
+  }
+  for (int sch : {CFR_SCHEDULE_STREAM, CFR_SCHEDULE_WIDE}) {
+    if (rc || (sch == CFR_SCHEDULE_WIDE && n_games != 1)) continue;
+    cand.schedule = sch;
+    cand.chunk_hands = 0;
+    rc = trial(cand, &ms);
+    if (!rc && ms < top_ms) top_ms = ms, top = cand;
+  }
+  cand = top;
+  for (int tn : {1, 2, 4}) {  // terminal nodes per block, for the fastest layout
+    if (rc) break;
+    cand.term_nodes = tn;
+    rc = trial(cand, &ms);
+    if (!rc && ms < top_ms) top_ms = ms, top = cand;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (!(top_ms < INFINITY)) return fail(CFR_EINVAL, "no layout applies to these subgames");
+  *best = top;
+  if (ms_per_iter) *ms_per_iter = top_ms;
+  return CFR_OK;
+}
 
 const char* cfr_last_error(void) { return g_last_error.c_str(); }
 

@@ -1309,7 +1309,7 @@ constexpr int kWideThreads = 256;
 // the regrets, the Stage 7 update of R and S and the new strategy RM(R') (Eq. rm);
 // kModeBR: the best-response value max_a v(child a) at p's decision nodes.
 template <int MODE, typename P>
-__global__ void __launch_bounds__(kWideThreads) k_wide_back(const GameDev* __restrict__ games,
+__global__ void __launch_bounds__(kWideThreads, 4) k_wide_back(const GameDev* __restrict__ games,
                                                             const int32_t* __restrict__ inner, int cnt,
                                                             int player_mask, const int* __restrict__ iter,
                                                             const Discount* __restrict__ disc_tab, int variant) {

@@ -2,9 +2,10 @@
 // Section 4.3): C = act(A B^T + bias) with A the [M][K] BF16 activations, B the [N][K] BF16
 // weights (both K-major), FP32 accumulation on the 5th-generation tensor cores.
 //
-// One CTA computes a 128 x 128 tile of C:
+// One CTA computes a 128 x 128 tile of C, two CTAs per SM (one's epilogue overlaps the
+// other's main loop):
 //   * warp 0 allocates 128 TMEM columns (the FP32 accumulator: lane = row, column = col)
-//     and, from one lane, streams 128 x 64 tiles of A and B into a 4-stage ring of shared
+//     and, from one lane, streams 128 x 64 tiles of A and B into a 3-stage ring of shared
 //     memory with TMA (128-byte swizzle, the layout the MMA descriptors below describe);
 //   * one lane of warp 1 issues tcgen05.mma (M 128, N 128, K 16 per instruction, four per
 //     64-wide stage) and commits each stage back to its "empty" barrier;
@@ -23,7 +24,7 @@ namespace pcfr {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;  // 97 KB: two CTAs per SM
 constexpr int kTileBytes = kBM * kBK * 2;  // 16 KB, one A or one B stage
 constexpr int kGemmThreads = 128;
 constexpr long kGemmWaitLimit = 1l << 22;
@@ -99,7 +100,7 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {  // round to nearest even
   return (uint16_t)(u >> 16);
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kGemmThreads, 2)
     k_gemm_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const float* __restrict__ bias, void* __restrict__ out, int M, int N, int K, int act, int out_f32,
                 int* err) {
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __r
     for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
       if (!(G.hand_mask[h] & dead)) {
         const float v = sum[p] > 0.f ? vf(q[h]) * inv : 1.f / cnt;
-        x[p * kLeafSlots + slot[h]] = to_bf16(v);
+        x[p * kLeafSlots + (L.hand_order ? h : slot[h])] = to_bf16(v);
       }
   }
   if (threadIdx.x < 52) {
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_values(const GameDev* __r
       const int h1 = hand_at[pair_slot(c1, c)], h2 = hand_at[pair_slot(c2, c)];
       const float q1 = h1 >= 0 ? vf(q[h1]) : 0.f, q2 = h2 >= 0 ? vf(q[h2]) : 0.f;
       const float M = T - C[c] - (C[c1] - q1) - (C[c2] - q2) + qh;
-      acc = fmaf(L.Y[(size_t)row * kLeafOut + i * kLeafSlots + s], M, acc);
+      acc = fmaf(L.Y[(size_t)row * kLeafOut + i * kLeafSlots + (L.hand_order ? h : s)], M, acc);
     }
     const float v = ((nd.board & hm) ? 0.f : scale * acc);
     if constexpr (sizeof(V) == 4)

@@ -252,6 +252,11 @@ struct LeafCtx {
   float* Y;                // [rows][kLeafOut]
   const void* W[4];        // BF16 [out][in]
   const float* b[4];
+  int hand_order;          // 1: every game has the same hand list, and the network's range
+                           // inputs and value outputs are laid out in that list's order
+                           // (hand h at column h of each player's 1326) -- the first and last
+                           // layers' weights are permuted to match -- so the leaf kernels
+                           // read and write them coalesced; 0: slot order
 };
 
 // Leaf values of player i (use_bar: against the average strategy, into cfv_br) or, with

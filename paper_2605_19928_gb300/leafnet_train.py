@@ -9,7 +9,11 @@ showdowns, thinned Dirichlet ranges, pots and chips behind spanning those of tur
 example per subgame: the input row the leaf kernels build (both ranges over the 1326 card
 slots, the 5-card board one-hot, the pot / stack features) and, per player and hand, the
 best-response value against the solution divided by pot x (opponent reach sharing no card)
-x kappa, i.e. the value per unit pot that the leaf kernels multiply back.
+x kappa, i.e. the value per unit pot that the leaf kernels multiply back.  With
+--turn-solves, exact turn subgames (synth.leaf_training_turns) are solved too and every
+river-card node below a leaf position gives one more example with the ranges the turn's
+solution brings there (turn_leaf_examples): the states the network meets in depth-limited
+solves.
 
 Training is offline model fitting with PyTorch autograd (Adam, Huber loss on the slots of
 hands that exist); the serving path is the library's own kernels (cfr_set_leaf_net).  The
@@ -104,6 +108,87 @@ def generate(n: int, iters: int, seed: int, log=print):
     return bf16(X), Y, Mk, float(np.median(expl))
 
 
+def turn_leaf_examples(spec, tree):
+    """Examples at the river-card nodes of a solved exact turn subgame: below every river
+    chance node with chips behind (where a depth-limited solve puts a leaf), the input row
+    the leaf kernels build from both players' reach under the average strategy, and per
+    player and hand the best-response value against it, per unit pot (divided by pot x
+    kappa / 44 x the opponent reach sharing no card with the hand)."""
+    n_nodes = capi.cfr_tree_info(tree)[0]
+    infos = [capi.cfr_node_info(tree, n) for n in range(n_nodes)]
+    kids = {}
+    for n in range(1, n_nodes):
+        kids.setdefault(infos[n]["parent"], []).append(n)
+    hands = spec.hands.astype(np.int64)
+    sl = slot_of(hands)
+    r = spec.ranges.astype(np.float64)
+    r = r / r.sum(axis=1, keepdims=True)
+    cm = np.zeros((hands.shape[0], 52), np.float64)
+    cm[np.arange(hands.shape[0])[:, None], hands] = 1.0
+
+    def blocker_free(q):  # opponent reach sharing no card with each hand
+        C = cm.T @ q
+        return q.sum() - C[hands[:, 0]] - C[hands[:, 1]] + q
+
+    Z = float(np.dot(r[0], blocker_free(r[1])))
+    cap = spec.pot / 2 + spec.stack
+    xs, ys, ms = [], [], []
+    for n, info in enumerate(infos):
+        if info["type"] != capi.CFR_NODE_CHANCE or max(info["contrib"]) >= cap:
+            continue
+        pot, behind = info["contrib"][0] + info["contrib"][1], cap - info["contrib"][0]
+        for kid in kids.get(n, []):
+            card = infos[kid]["deal"]
+            q = [capi.cfr_read_values(tree, capi.CFR_READ_AVG_REACH, kid, player=p) for p in (0, 1)]
+            if min(q[0].sum(), q[1].sum()) <= 0.0:
+                continue
+            v = [capi.cfr_read_values(tree, capi.CFR_READ_BR_CFV, kid, player=i) for i in (0, 1)]
+            x = np.zeros(IN, np.float32)
+            for p in (0, 1):
+                x[p * SLOTS + sl] = q[p] / q[p].sum()
+            x[2 * SLOTS + spec.board] = 1.0
+            x[2 * SLOTS + card] = 1.0
+            x[2 * SLOTS + 52] = pot / (pot + 2 * behind)
+            x[2 * SLOTS + 53] = behind / (pot + 2 * behind)
+            live = ~np.any(hands == card, axis=1)
+            y = np.zeros(OUT, np.float32)
+            m = np.zeros(OUT, np.float32)
+            for i in (0, 1):
+                M = blocker_free(q[1 - i])
+                ok = live & (M > 1e-12 * q[1 - i].sum())
+                val = np.zeros(hands.shape[0])
+                val[ok] = v[i][ok] * Z * 44.0 / (pot * M[ok])
+                y[i * SLOTS + sl] = val
+                m[i * SLOTS + sl] = ok
+            xs.append(x)
+            ys.append(y)
+            ms.append(m)
+    return xs, ys, ms
+
+
+def generate_turns(n_solves: int, iters: int, seed: int, log=print):
+    """Leaf examples from n_solves exact turn solves (DCFR, FP32 values, `iters` iterations)."""
+    opts = capi.make_opts("dcfr", precision="single")
+    X, Y, Mk, expl = [], [], [], []
+    t0 = time.time()
+    for k, spec in enumerate(synth.leaf_training_turns(n_solves, seed=seed)):
+        tree = capi.cfr_tree_create(spec, opts)
+        try:
+            capi.cfr_iterate(tree, iters)
+            e, _ = capi.cfr_exploitability(tree)
+            expl.append(1000.0 * float(e[0]) / 100.0)
+            xs, ys, ms = turn_leaf_examples(spec, tree)
+            X += xs
+            Y += ys
+            Mk += ms
+        finally:
+            capi.cfr_tree_destroy(tree)
+        if (k + 1) % 25 == 0:
+            log(f"  {k + 1} turn solves, {len(X)} leaf examples, {time.time() - t0:.0f} s, "
+                f"median exploitability {np.median(expl):.3f} mbb")
+    return bf16(np.array(X, np.float32)), np.array(Y, np.float32), np.array(Mk, np.float32), float(np.median(expl))
+
+
 def train(X, Y, Mk, epochs: int, seed: int, log=print):
     import torch
     torch.manual_seed(seed)
@@ -147,7 +232,9 @@ def train(X, Y, Mk, epochs: int, seed: int, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--samples", type=int, default=100_000)
+    ap.add_argument("--samples", type=int, default=100_000, help="river solves (one example each)")
+    ap.add_argument("--turn-solves", type=int, default=0,
+                    help="exact turn solves whose river-card nodes give leaf examples (many each)")
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--seed", type=int, default=0)
@@ -160,11 +247,23 @@ def main(argv=None):
     X, Y, Mk, med = generate(args.samples, args.iters, args.seed)
     t1 = time.time()
     print(f"generated {args.samples} river solves in {t1 - t0:.0f} s (median exploitability {med:.3f} mbb/hand)")
+    n_turn = 0
+    if args.turn_solves > 0:
+        Xt, Yt, Mt, med_t = generate_turns(args.turn_solves, args.iters, args.seed)
+        n_turn = Xt.shape[0]
+        print(f"generated {n_turn} leaf examples from {args.turn_solves} turn solves in {time.time() - t1:.0f} s "
+              f"(median exploitability {med_t:.3f} mbb/hand)")
+        # interleave so that the validation slice (the first 5 %) holds both kinds
+        X, Y, Mk = (np.concatenate([a, b]) for a, b in ((X, Xt), (Y, Yt), (Mk, Mt)))
+        order = np.random.default_rng(args.seed).permutation(X.shape[0])
+        X, Y, Mk = X[order], Y[order], Mk[order]
+        t1 = time.time()
     Wbits, b, mae = train(X, Y, Mk, args.epochs, args.seed)
     t2 = time.time()
     print(f"trained in {t2 - t1:.0f} s, validation mean |error| {mae:.4f} of the pot")
     np.savez_compressed(args.out, **{f"W{k}": w for k, w in enumerate(Wbits)}, **{f"b{k}": x for k, x in enumerate(b)},
-                        meta=np.array([args.samples, args.iters, args.epochs, args.seed, med, mae], np.float64))
+                        meta=np.array([args.samples, args.iters, args.epochs, args.seed, med, mae, args.turn_solves,
+                                       n_turn], np.float64))
     torch.cuda.synchronize()
     print("wrote", args.out)
 

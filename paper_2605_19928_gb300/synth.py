@@ -343,3 +343,45 @@ def leaf_training_rivers(n: int, seed: int = 0, pot_range=(100.0, 900.0), behind
                             behind, tuple(float(x) for x in bet_sizes), max_raises,
                             {"leaf_river": 20_000 + seed, "k": k}))
     return out
+
+
+def leaf_training_turns(n: int, seed: int = 0) -> list[GameSpec]:
+    """Exact turn subgames whose solutions give leaf-network examples at the river card
+    (the states a depth-limited solve meets at its leaves): seeded 4-card boards with
+    rank_strength showdowns on every river, Dirichlet(1) or strength-tilted ranges, pot
+    100-400 with 100-600 behind, and a turn bet tree drawn from the sizes of the
+    benchmark trees ({0.33, 0.5, 0.75, 1.0, 1.25} pot, 1-3 of them, plus all-in; 2-3
+    bets/raises)."""
+    rng = np.random.default_rng(40_000 + seed)
+    menu = np.array([0.33, 0.5, 0.75, 1.0, 1.25])
+    out = []
+    for k in range(n):
+        board = np.sort(rng.choice(DECK, size=4, replace=False)).astype(np.int32)
+        combos = all_combos(board)
+        strength = np.zeros((DECK, combos.shape[0]), np.int32)
+        for c in range(DECK):
+            if c in set(int(b) for b in board):
+                continue
+            live = ~np.any(combos == c, axis=1)
+            strength[c, live] = rank_strength(np.concatenate([board, [c]]), combos[live])
+        # tilt by the mean strength percentile over the river cards
+        pct = np.zeros(combos.shape[0])
+        for c in range(DECK):
+            if c in set(int(b) for b in board):
+                continue
+            live = ~np.any(combos == c, axis=1)
+            srt = np.argsort(np.argsort(strength[c, live], kind="stable"), kind="stable")
+            pct[live] += srt / max(1, live.sum() - 1)
+        z = 2.0 * pct / (DECK - 4) - 1.0
+        ranges = rng.exponential(1.0, size=(2, combos.shape[0]))
+        for p in range(2):
+            if rng.random() < 0.5:
+                ranges[p] *= np.exp(rng.uniform(-3.0, 3.0) * z)
+        ranges = (ranges / ranges.sum(axis=1, keepdims=True)).astype(np.float32)
+        n_sizes = int(rng.integers(1, 4))
+        sizes = tuple(sorted(float(x) for x in rng.choice(menu, size=n_sizes, replace=False))) + (ALL_IN,)
+        pot = float(rng.uniform(100.0, 400.0))
+        behind = float(rng.uniform(100.0, 600.0))
+        out.append(GameSpec(GAME_HOLDEM, f"leaf_turn_{k}", board, combos, ranges, strength, pot, behind, sizes,
+                            int(rng.integers(2, 4)), {"leaf_turn": 40_000 + seed, "k": k}))
+    return out

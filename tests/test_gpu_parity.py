@@ -482,3 +482,68 @@ def test_fp32_terminal_runs_match_oracle(schedule):
             capi.cfr_iterate(big, 2)
     finally:
         capi.cfr_tree_destroy(big)
+
+
+def test_autotune_picks_a_layout_with_the_same_results():
+    """The launch-tiling autotuner times every layout and returns the fastest; every layout
+    gives the same bits, so the tuned handle's state equals the default one's."""
+    specs = [river(96, seed=80 + k, max_raises=2) for k in range(12)]
+    base = capi.make_opts("dcfr", precision="single")
+    best, ms = capi.cfr_autotune(specs, base, iters=3)
+    assert ms > 0
+    assert best.schedule in (capi.CFR_SCHEDULE_LEVEL, capi.CFR_SCHEDULE_STREAM)
+    assert best.term_nodes in (0, 1, 2, 4) and best.variant == base.variant and best.precision == base.precision
+    states = []
+    for o in (base, best):
+        tree = capi.cfr_batch_create(specs, o)
+        try:
+            capi.cfr_iterate(tree, 5)
+            states.append(_state(tree, len(specs)))
+        finally:
+            capi.cfr_tree_destroy(tree)
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_autotune(specs, base, iters=0)
+    assert e.value.code == capi.CFR_EINVAL
+
+
+@pytest.mark.parametrize("schedule", ["level", "stream", "wide"])
+def test_fp32_strategy_is_regret_matching_rounded_to_nearest(schedule):
+    """FP32 values: the strategy the GPU derives from FP64 regrets is IEEE arithmetic on the
+    regrets rounded to FP32 (nearest, ties to even): positive parts, their sum in action
+    order, one FP32 reciprocal and products (Eq. rm).  The regrets cover 60 binades, values
+    exactly halfway between two floats (both parities of the last mantissa bit) and values
+    one FP64 step either side of those midpoints."""
+    spec = river(30, seed=5)
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision="single", schedule=schedule))
+    try:
+        info = capi.cfr_node_info(tree, 0)
+        A, H = info["n_actions"], spec.n_hands
+        assert A >= 3
+        rng = np.random.default_rng(17)
+        R = np.exp(rng.uniform(-69.0, 69.0, size=(A, H))) * rng.choice([-1.0, 1.0], size=(A, H), p=[0.3, 0.7])
+        f = rng.uniform(0.5, 4.0, size=(A, H)).astype(np.float32)
+        mid = f.astype(np.float64) + np.spacing(f).astype(np.float64) / 2  # exactly halfway
+        cols = np.arange(H) % 4
+        R = np.where(cols == 1, mid, R)
+        R = np.where(cols == 2, np.nextafter(mid, np.inf), R)
+        R = np.where(cols == 3, np.nextafter(mid, -np.inf), R)
+        capi.cfr_write_values(tree, capi.CFR_READ_REGRET, 0, R)
+        got = capi.cfr_strategy(tree, 0)
+        x = np.where(R > 0, R, 0.0).astype(np.float32)  # round to nearest even
+        want = np.empty((A, H), np.float32)
+        for h in range(H):
+            pos = x[:, h] > 0
+            if pos.sum() == 1:
+                want[:, h] = pos.astype(np.float32)
+            elif pos.sum() == 0:
+                want[:, h] = np.float32(1) / np.float32(A)
+            else:
+                tot = np.float32(0)
+                for a in range(A):
+                    tot = np.float32(tot + x[a, h])
+                want[:, h] = x[:, h] * (np.float32(1) / tot)
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    finally:
+        capi.cfr_tree_destroy(tree)
