@@ -959,24 +959,35 @@ struct StreamLane {
   V* st;            // this lane's stack: slot s at st[s * 32]
 };
 
-// Issue loads [u0, u1) of a pass into ring half `half` (one commit group).
+// Issue loads [u0, u1) of a pass into ring half `half` (one commit group).  A unit is the
+// warp's 32-hand segment of one row: 256 bytes of FP64 (or pair) values, 128 of FP32 ones,
+// landing at 256-byte slot u - u0 of the ring half.  The warp's lanes split the units into
+// 16-byte pieces (16 per 256-byte unit, 8 per 128-byte one), so one copy instruction moves
+// pieces of two units.
 template <typename P>
 __device__ __forceinline__ void stream_issue(const StreamLane<P>& L, const uint32_t* units, int u0, int u1,
                                              int half) {
   using V = typename P::V;
-  uint64_t* ring = L.ring + (size_t)half * L.half * 32;
-  for (int u = u0; u < u1; ++u) {
+  const int lane = threadIdx.x & 31;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(L.ring - lane + (size_t)half * L.half * 32);
+  const int pieces = (u1 - u0) * 16;
+  for (int k = lane; k < pieces; k += 32) {
+    const int u = u0 + (k >> 4), part = k & 15;
     const uint32_t d = units[u];
     const uint32_t arr = d >> kArrShift, off = d & kArrOffMask;
-    uint64_t* dst = ring + (size_t)(u - u0) * 32;
+    // the row's segment starts at the warp's first hand: the lane's column pointer minus its lane
+    const void* src;
     if (arr == kArrR)
-      cp_async<8>(dst, L.R + off);
+      src = L.R - lane + off + 2 * part;
     else if (arr == kArrS)
-      cp_async<8>(dst, L.S + off);
+      src = L.S - lane + off + 2 * part;
     else if (arr == kArrM)
-      cp_async<8>(dst, L.M + off);
+      src = L.M - lane + off + 2 * part;
+    else if (part * 16 >= 32 * (int)sizeof(V))  // FP32 rows fill half a slot
+      continue;
     else
-      cp_async<(int)sizeof(V)>(dst, (arr == kArrReach ? L.reach : L.cfv) + off);
+      src = reinterpret_cast<const unsigned char*>((arr == kArrReach ? L.reach : L.cfv) - lane + off) + part * 16;
+    cp_async<16>(ring + (size_t)(u - u0) * 256 + (size_t)part * 16, src);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -986,9 +997,17 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// This lane's value in a ring unit (slot: the lane's 8-byte entry of the unit): 8-byte
+// values sit at entry `lane`, FP32 values packed at float `lane` of the unit.
 template <typename P>
 __device__ __forceinline__ typename P::V ring_value(const uint64_t* slot) {
-  return *reinterpret_cast<const typename P::V*>(slot);
+  using V = typename P::V;
+  if constexpr (sizeof(V) == 4) {
+    const int lane = threadIdx.x & 31;
+    return reinterpret_cast<const V*>(slot - lane)[lane];
+  } else {
+    return *reinterpret_cast<const V*>(slot);
+  }
 }
 
 // Bottom-up pass over chunk [k0, k1) (program positions counted from its end).  A node's
@@ -1155,7 +1174,8 @@ __device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int q, const
       stream_issue<P>(L, units, ch[2 * c + 3], ch[2 * c + 5], (c + 1) & 1);
     else
       asm volatile("cp.async.commit_group;" ::: "memory");
-    cp_async_wait_group<1>();  // chunk c has landed (each lane reads only its own column)
+    cp_async_wait_group<1>();  // chunk c has landed: this lane's pieces
+    __syncwarp();              // and the other lanes' (each lane reads its own column of every piece)
     compute(ch[2 * c], ch[2 * c + 2], c & 1);
   }
   cp_async_wait_group<0>();
@@ -1218,7 +1238,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
       stream_backward_chunk<P>(L, k0, k1, half, sp, d, variant);
     });
     if (valid) L.cfv[0] = st[0];  // root value (read-back)
-    __threadfence_block();       // the new R rows are read back by this lane's own copies below
+    __threadfence_block();       // the new R rows are read back by the warp's copies below
+    __syncwarp();
     st[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
     sp = 1;
     stream_pass<P>(L, 2 + p, staged ? sunits + nb : gunits_f,
