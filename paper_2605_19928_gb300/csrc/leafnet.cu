@@ -320,104 +320,60 @@ __device__ __forceinline__ int pair_slot(int a, int b) {
   return b * (b - 1) / 2 + a;
 }
 
-// One block per leaf: writes the leaf's 48 rows of X (one per river card r not on the
-// leaf's board).  Both players' reach at the leaf is staged once; each player's total T and
-// per-card sums C[c] (one warp per card, fixed order) give every row's normaliser at once:
-// the reach of the hands live for r -- holding neither r nor a board card, whose reach is
-// zero below the deal anyway -- sums to T - C[r].  Counts of live hands (the uniform input
-// of a player who never reaches the leaf) come the same way.
+// One block per network row (leaf, river card): writes the row of X.
 template <typename V>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __restrict__ games, LeafCtx L,
                                                               int use_bar) {
-  __shared__ float qsm[2][kLeafSlots + 2];
-  __shared__ float C[2][52], T[2];
-  __shared__ int K[52], n_free;
   __shared__ float red[kLeafThreads / 32];
-  const LeafDev lf = L.leaves[blockIdx.x];
+  const int row = blockIdx.x;
+  const int li = row / kLeafCards, ri = row - li * kLeafCards;
+  const LeafDev lf = L.leaves[li];
   const GameDev& G = games[lf.game];
   const NodeDev nd = G.nodes[lf.node];
-  const int H = G.n_hands, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the ri-th card not on the board
+  int r = -1;
+  for (int c = 0, k = 0; c < 52; ++c)
+    if (!((nd.board >> c) & 1ull)) {
+      if (k == ri) {
+        r = c;
+        break;
+      }
+      ++k;
+    }
   const size_t stride = (size_t)G.hstride;
   const V* reach = static_cast<const V*>(use_bar ? G.reach_bar : G.reach);
+  const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
+  uint16_t* x = static_cast<uint16_t*>(L.X) + (size_t)row * kLeafIn;
+  for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) x[k] = 0;
+  // live hands hold neither a card of the leaf's board (the flop's turn card) nor r
+  const uint64_t dead = nd.board | (1ull << r);
+  float sum[2], cnt = 0.f;
   for (int p = 0; p < 2; ++p) {
     const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
-    float s = 0.f;
-    for (int h = threadIdx.x; h < H; h += blockDim.x) {
-      const float x = vf(q[h]);
-      qsm[p][h] = x;
-      s += x;
-    }
-    const float t = block_sum(s, red);
-    if (threadIdx.x == 0) T[p] = t;
+    float s = 0.f, n = 0.f;
+    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
+      if (!(G.hand_mask[h] & dead)) s += vf(q[h]), n += 1.f;
+    sum[p] = block_sum(s, red);
+    if (p == 0) cnt = block_sum(n, red);
   }
-  {
-    int nf = 0;
-    for (int h = threadIdx.x; h < H; h += blockDim.x) nf += (G.hand_mask[h] & nd.board) ? 0 : 1;
-    const float f = block_sum((float)nf, red);
-    if (threadIdx.x == 0) n_free = (int)f;
+  __syncthreads();  // the zero fill is complete
+  for (int p = 0; p < 2; ++p) {
+    const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
+    // a player who never reaches the leaf: uniform over the hands (the values are then unused)
+    const float inv = sum[p] > 0.f ? 1.f / sum[p] : 0.f;
+    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
+      if (!(G.hand_mask[h] & dead)) {
+        const float v = sum[p] > 0.f ? vf(q[h]) * inv : 1.f / cnt;
+        x[p * kLeafSlots + (L.hand_order ? h : slot[h])] = to_bf16(v);
+      }
   }
-  __syncthreads();  // qsm
-  for (int c = warp; c < 52; c += kLeafThreads / 32) {
-    float s0 = 0.f, s1 = 0.f;
-    int k = 0;
-    for (int h = lane; h < H; h += 32) {
-      const uint64_t hm = G.hand_mask[h];
-      if ((hm >> c) & 1ull) {
-        s0 += qsm[0][h];
-        s1 += qsm[1][h];
-        k += (hm & nd.board) ? 0 : 1;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      k += __shfl_xor_sync(0xffffffffu, k, o);
-    }
-    if (lane == 0) C[0][c] = s0, C[1][c] = s1, K[c] = k;
+  if (threadIdx.x < 52) {
+    const bool on = ((nd.board >> threadIdx.x) & 1ull) || (int)threadIdx.x == r;
+    if (on) x[2 * kLeafSlots + threadIdx.x] = 0x3f80;  // 1.0
   }
-  __syncthreads();
-  const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
-  for (int c = 0, ri = 0; c < 52; ++c) {
-    if ((nd.board >> c) & 1ull) continue;
-    const int row = lf.row0 + ri++;
-    uint16_t* x = static_cast<uint16_t*>(L.X) + (size_t)row * kLeafIn;
-    const uint64_t dead = nd.board | (1ull << c);
-    const float cnt = (float)(n_free - K[c]);
-    float sr[2], inv[2];
-    for (int p = 0; p < 2; ++p) {
-      sr[p] = T[p] - C[p][c];
-      inv[p] = sr[p] > 0.f ? 1.f / sr[p] : 0.f;
-    }
-    if (L.hand_order) {  // one pass over the row: hand h at column h of each player's block
-      for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) {
-        uint16_t v = 0;
-        if (k < 2 * kLeafSlots) {
-          const int p = k >= kLeafSlots, h = k - p * kLeafSlots;
-          if (h < H && !(G.hand_mask[h] & dead)) v = to_bf16(sr[p] > 0.f ? qsm[p][h] * inv[p] : 1.f / cnt);
-        } else if (k < 2 * kLeafSlots + 52) {
-          const int b = k - 2 * kLeafSlots;
-          v = (((nd.board >> b) & 1ull) || b == c) ? 0x3f80 : 0;  // 1.0
-        } else if (k == 2 * kLeafSlots + 52 || k == 2 * kLeafSlots + 53) {
-          v = to_bf16(lf.feat[k - 2 * kLeafSlots - 52]);
-        }
-        x[k] = v;
-      }
-    } else {  // slot order: zero the row, then scatter
-      for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) x[k] = 0;
-      __syncthreads();
-      for (int p = 0; p < 2; ++p)
-        for (int h = threadIdx.x; h < H; h += blockDim.x)
-          if (!(G.hand_mask[h] & dead))
-            x[p * kLeafSlots + slot[h]] = to_bf16(sr[p] > 0.f ? qsm[p][h] * inv[p] : 1.f / cnt);
-      if (threadIdx.x < 52) {
-        const bool on = ((nd.board >> threadIdx.x) & 1ull) || (int)threadIdx.x == c;
-        if (on) x[2 * kLeafSlots + threadIdx.x] = 0x3f80;  // 1.0
-      }
-      if (threadIdx.x == 0) {
-        x[2 * kLeafSlots + 52] = to_bf16(lf.feat[0]);
-        x[2 * kLeafSlots + 53] = to_bf16(lf.feat[1]);
-      }
-    }
+  if (threadIdx.x == 0) {
+    x[2 * kLeafSlots + 52] = to_bf16(lf.feat[0]);
+    x[2 * kLeafSlots + 53] = to_bf16(lf.feat[1]);
   }
 }
 
@@ -481,10 +437,11 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_values(const GameDev* __r
 
 int launch_leaf_inputs(const LaunchCtx& c, const LeafCtx& L, int use_bar, void* stream) {
   if (L.n_leaves == 0) return 0;
+  const int rows = L.n_leaves * kLeafCards;
   if (c.precision == kPrecisionSingle)
-    k_leaf_inputs<float><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+    k_leaf_inputs<float><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
   else
-    k_leaf_inputs<float2><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+    k_leaf_inputs<float2><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
