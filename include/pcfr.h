@@ -128,7 +128,7 @@ typedef struct cfr_game_spec {
  * SM) and every tree allows it, WIDE for one subgame too large to stage, else LEVEL.
  * term_nodes: fold and showdown nodes per CUDA block of the terminal launch (nodes of one
  * board; 0 = automatic: one while the nodes do not fill the GPU eight times over, up to
- * four when they do; otherwise 1 to 4).  Results are the same bits for every value.
+ * eight when they do; otherwise 1 to 8).  Results are the same bits for every value.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
 enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2, CFR_SCHEDULE_WIDE = 3 };
@@ -202,8 +202,8 @@ int cfr_reset(cfr_tree* tree);
 
 /* Autotuner of the launch tiling (batched serving): builds the subgames under each
  * candidate layout -- the level schedule with 4, 8, 16 and 32 hands per block, the stream
- * schedule (32 hands per warp), the wide schedule (one subgame), then 1, 2 or 4 terminal
- * nodes per block for the fastest -- times `iters` iterations of each after two warm-up
+ * schedule (32 hands per warp), the wide schedule (one subgame), then 1, 2, 4 or 8
+ * terminal nodes per block for the fastest -- times `iters` iterations of each after two warm-up
  * iterations (CUDA events on `stream`, depth-limit leaves evaluated with an all-zero
  * network), and writes the fastest options to *best (opts with schedule, chunk_hands and
  * term_nodes set; term_nodes stays 0 when the automatic count was fastest) and its mean

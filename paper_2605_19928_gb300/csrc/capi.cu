@@ -290,7 +290,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   const size_t es = o.precision == CFR_PRECISION_SINGLE ? 4 : 8;
   if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
     return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
-  if (o.term_nodes < 0 || o.term_nodes > 4) return fail(CFR_EINVAL, "term_nodes must be 0 to 4");
+  if (o.term_nodes < 0 || o.term_nodes > 8) return fail(CFR_EINVAL, "term_nodes must be 0 to 8");
   if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_WIDE) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
@@ -491,10 +491,10 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     for (int n : term) term_work.push_back({g, n});
   }
   // terminal runs: one node per block while the nodes do not fill the GPU many times over,
-  // up to four per block (same game and board table) when they do
+  // up to eight per block (same game and board table) when they do
   std::vector<Work> term_runs;
   {
-    const int per = o.term_nodes ? o.term_nodes : std::max(1, std::min(4, (int)term_work.size() / (152 * 8)));
+    const int per = o.term_nodes ? o.term_nodes : std::max(1, std::min(8, (int)term_work.size() / (152 * 8)));
     size_t a = 0;
     while (a < term_work.size()) {
       const Work w = term_work[a];
@@ -1154,7 +1154,7 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
     if (!rc && ms < top_ms) top_ms = ms, top = cand;
   }
   cand = top;
-  for (int tn : {1, 2, 4}) {  // terminal nodes per block, for the fastest layout
+  for (int tn : {1, 2, 4, 8}) {  // terminal nodes per block, for the fastest layout
     if (rc) break;
     cand.term_nodes = tn;
     rc = trial(cand, &ms);

@@ -510,7 +510,7 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
   }
 }
 
-// Terminal values (Stages 2-4).  One block per (player, run): a run is up to four fold or
+// Terminal values (Stages 2-4).  One block per (player, run): a run is up to eight fold or
 // showdown nodes of one game that read the same board table, which is staged once by a
 // bulk (TMA) copy; the opponent reach rows of the run's nodes arrive by bulk copies into
 // two alternating buffers, each node's row landing while the node before it computes.

@@ -428,7 +428,7 @@ def test_single_precision_error_against_oracle(case, variant, schedule):
 
 
 def test_terminal_runs_match_one_node_blocks():
-    """Large handles evaluate up to four terminal nodes per block; small ones one.  The same
+    """Large handles evaluate up to eight terminal nodes per block; small ones one.  The same
     subgames solved in one large handle and one handle each must agree bit for bit."""
     specs = [river(64, seed=70 + k, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4) for k in range(40)]
     big = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="pairs", schedule="level"))
@@ -492,7 +492,7 @@ def test_autotune_picks_a_layout_with_the_same_results():
     best, ms = capi.cfr_autotune(specs, base, iters=3)
     assert ms > 0
     assert best.schedule in (capi.CFR_SCHEDULE_LEVEL, capi.CFR_SCHEDULE_STREAM)
-    assert best.term_nodes in (0, 1, 2, 4) and best.variant == base.variant and best.precision == base.precision
+    assert best.term_nodes in (0, 1, 2, 4, 8) and best.variant == base.variant and best.precision == base.precision
     states = []
     for o in (base, best):
         tree = capi.cfr_batch_create(specs, o)
