@@ -84,3 +84,10 @@ def test_bad_options_are_rejected_before_any_device_call(lib):
     assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL
     bad = capi.make_opts(schedule=5)
     assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL
+    for tn in (-1, 9):  # terminal nodes per block: 0 (automatic) to 8
+        bad = capi.make_opts(term_nodes=tn)
+        assert lib.cfr_tree_create(C.byref(s), C.byref(bad), None, C.byref(out)) == capi.CFR_EINVAL
+    best, ms = capi.cfr_solver_opts(), C.c_double()
+    good = capi.make_opts()
+    assert lib.cfr_autotune(C.byref(s), 1, C.byref(good), None, 0, C.byref(best), C.byref(ms)) == capi.CFR_EINVAL
+    assert lib.cfr_autotune(None, 1, C.byref(good), None, 5, C.byref(best), C.byref(ms)) == capi.CFR_EINVAL
