@@ -49,7 +49,9 @@ struct cfr_tree {
   Work* d_term_runs = nullptr;
   Work* d_warp_work = nullptr;
   int32_t* d_wide_inner = nullptr;  // wide schedule: inner node ids, level by level
-  std::vector<int> wide_ls, wide_inner_off;
+  int32_t* d_wide_fwd = nullptr;    // wide schedule: nodes whose reach is stored, level by level
+  int32_t* d_term_src = nullptr;    // reach source of each terminal work entry
+  std::vector<int> wide_inner_off, wide_fwd_off;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
   int* d_err = nullptr;
@@ -398,18 +400,21 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   } else if (o.schedule == CFR_SCHEDULE_AUTO && schedule == kScheduleLevel && wide_ok && !all_fit) {
     schedule = kScheduleWide;
   }
-  if (schedule == kScheduleWide) {  // per level: the node range, and the inner nodes
+  if (schedule == kScheduleWide) {  // per level: the inner nodes, and the nodes whose reach is stored
     const HostGame& h = t->host[0];
     const int L = (int)h.level_start.size() - 1;
-    t->wide_ls.assign(h.level_start.begin(), h.level_start.end());
     t->wide_inner_off.assign(1, 0);
-    std::vector<int32_t> inner;
+    t->wide_fwd_off.assign(1, 0);
+    std::vector<int32_t> inner, fwd;
     for (int l = 0; l < L; ++l) {
-      for (int n = h.level_start[l]; n < h.level_start[l + 1]; ++n)
+      for (int n = h.level_start[l]; n < h.level_start[l + 1]; ++n) {
         if (!is_end(h.nodes[(size_t)n].type)) inner.push_back(n);
+        if (h.reach_src[(size_t)n] == n) fwd.push_back(n);
+      }
       t->wide_inner_off.push_back((int)inner.size());
+      t->wide_fwd_off.push_back((int)fwd.size());
     }
-    if ((rc = upload(t, inner, &t->d_wide_inner))) {
+    if ((rc = upload(t, inner, &t->d_wide_inner)) || (rc = upload(t, fwd, &t->d_wide_fwd))) {
       delete t;
       return rc;
     }
@@ -490,6 +495,9 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     std::stable_sort(term.begin(), term.end(), [&](int a, int b2) { return table(a) < table(b2); });
     for (int n : term) term_work.push_back({g, n});
   }
+  std::vector<int32_t> term_src(term_work.size());
+  for (size_t k = 0; k < term_work.size(); ++k)
+    term_src[k] = t->host[term_work[k].game].reach_src[(size_t)term_work[k].unit];
   // terminal runs: one node per block while the nodes do not fill the GPU many times over,
   // up to eight per block (same game and board table) when they do
   std::vector<Work> term_runs;
@@ -521,6 +529,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     for (int u = 0; u < (t->host[g].n_hands + 31) / 32; u += kStreamWarps) warp_work.push_back({g, u});
   if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
       (rc = upload(t, term_work, &t->d_term_work)) || (rc = upload(t, warp_work, &t->d_warp_work)) ||
+      (rc = upload(t, term_src, &t->d_term_src)) ||
       (rc = upload(t, term_runs, &t->d_term_runs)) ||
       (rc = zeros(t, 1, &t->d_iter)) ||
       (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) ||
@@ -534,6 +543,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.chunk_work = t->d_chunk_work;
   c.n_chunk_work = (int)chunk_work.size();
   c.term_work = t->d_term_work;
+  c.term_src = t->d_term_src;
   c.n_term_work = (int)term_work.size();
   c.term_runs = t->d_term_runs;
   c.n_term_runs = (int)term_runs.size();
@@ -556,10 +566,11 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_units = stream_units;
   if (schedule == kScheduleWide) {
     const HostGame& h = t->host[0];
-    c.wide_levels = (int)t->wide_ls.size() - 1;
-    c.wide_ls = t->wide_ls.data();
+    c.wide_levels = (int)t->wide_inner_off.size() - 1;
     c.wide_inner_off = t->wide_inner_off.data();
     c.wide_inner = t->d_wide_inner;
+    c.wide_fwd_off = t->wide_fwd_off.data();
+    c.wide_fwd = t->d_wide_fwd;
     c.wide_stride = h.hstride;
     int dmax = 0;
     for (int p = 0; p < 2; ++p) {
@@ -875,10 +886,15 @@ int cfr_read_values(cfr_tree* t, int game, int what, int player, int node, doubl
     const size_t vf = t->opts.precision == CFR_PRECISION_SINGLE ? 1 : 2;
     std::vector<float> tmp((size_t)H * vf);
     const void* arr = what == CFR_READ_CFV ? d.cfv : what == CFR_READ_BR_CFV ? d.cfv_br : d.reach_bar;
-    const float* src = static_cast<const float*>(arr) + ((size_t)player * h.nodes.size() + node) * S * vf;
+    // a run-out node's reach is its source's with the hands holding a dealt card zeroed
+    const int at = what == CFR_READ_AVG_REACH ? h.reach_src[(size_t)node] : node;
+    const float* src = static_cast<const float*>(arr) + ((size_t)player * h.nodes.size() + at) * S * vf;
     CK(cudaMemcpyAsync(tmp.data(), src, (size_t)H * 4 * vf, cudaMemcpyDeviceToHost, t->stream));
     CK(cudaStreamSynchronize(t->stream));
     for (int k = 0; k < H; ++k) out[k] = vf == 1 ? (double)tmp[k] : (double)tmp[2 * k] + (double)tmp[2 * k + 1];
+    if (at != node)
+      for (int k = 0; k < H; ++k)
+        if (h.hand_mask[(size_t)k] & nd.board) out[k] = 0.0;
     return CFR_OK;
   }
   return fail(CFR_EINVAL, "unknown read kind");

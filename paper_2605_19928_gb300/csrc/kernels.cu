@@ -513,13 +513,16 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
 // Terminal values (Stages 2-4).  One block per (player, run): a run is up to eight fold or
 // showdown nodes of one game that read the same board table, which is staged once by a
 // bulk (TMA) copy; the opponent reach rows of the run's nodes arrive by bulk copies into
-// two alternating buffers, each node's row landing while the node before it computes.
+// two alternating buffers, each node's row landing while the node before it computes.  A
+// showdown below an all-in run-out reads the run-out's reach row (src) and zeroes the hands
+// holding a dealt card itself (nobody acts below the run-out, so that is its reach).
 // Every wait is bounded: on a timeout the block sets *err, lets its copies drain and leaves.
 // RUNS = false is the one-node form (latency: all registers it wants); RUNS = true fits four
 // blocks per SM for handles whose terminal nodes fill the GPU many times over.
 template <typename P, bool RUNS>
 __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const GameDev* __restrict__ games,
                                                             const Work* __restrict__ work,
+                                                            const int32_t* __restrict__ src,
                                                             const Work* __restrict__ runs, int n_runs,
                                                             int player_mask, int use_bar, int* err) {
   using V = typename P::V;
@@ -568,10 +571,10 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
   pdl_wait();  // the reach rows come from the launch just before this one
   pdl_trigger();
   if (threadIdx.x == 0) {
-    bulk_copy_g2s(qbuf, qsrc + (size_t)work[first].unit * stride, q_bytes, &bar[0]);
+    bulk_copy_g2s(qbuf, qsrc + (size_t)src[first] * stride, q_bytes, &bar[0]);
     if (RUNS && count > 1) {
       mbar_arrive_expect_tx(&bar[1], q_bytes);
-      bulk_copy_g2s(qbuf + stride, qsrc + (size_t)work[first + 1].unit * stride, q_bytes, &bar[1]);
+      bulk_copy_g2s(qbuf + stride, qsrc + (size_t)src[first + 1] * stride, q_bytes, &bar[1]);
     }
   }
   for (int j = 0; j < count; ++j) {
@@ -590,12 +593,18 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
       __syncthreads();
       return;
     }
+    if (src[first + j] != n) {  // below an all-in run-out: the run-out's reach, without the
+      V* qb = qbuf + (size_t)(j & 1) * stride;  // hands holding a card dealt on the way
+      for (int h = threadIdx.x; h < H; h += blockDim.x)
+        if (G.hand_mask[h] & nd.board) qb[h] = P::zero();
+      __syncthreads();
+    }
     terminal_values<P>(G, nd, i, u64, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc, dst + (size_t)n * stride);
     if (!RUNS) break;
     __syncthreads();  // buffer j & 1 and the scan arrays are free again
     if (threadIdx.x == 0 && j + 2 < count) {
       mbar_arrive_expect_tx(&bar[j & 1], q_bytes);
-      bulk_copy_g2s(qbuf + (size_t)(j & 1) * stride, qsrc + (size_t)work[first + j + 2].unit * stride, q_bytes,
+      bulk_copy_g2s(qbuf + (size_t)(j & 1) * stride, qsrc + (size_t)src[first + j + 2] * stride, q_bytes,
                     &bar[j & 1]);
     }
   }
@@ -1137,8 +1146,8 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
 }
 
 // Top-down pass over chunk [k0, k1) with sigma = RM(R): records the reach at the player's
-// decision nodes and, for the terminal children, at the terminals; pushes the reach of the
-// inner children (child 0 on top).
+// decision nodes, at chance nodes and, for the terminal children, at the terminals; pushes
+// the reach of the inner children (child 0 on top).
 template <typename P>
 __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp) {
   using V = typename P::V;
@@ -1178,6 +1187,7 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
         }
       }
     } else if (nd.type == kChance) {  // the player's reach passes through to each card
+      if (L.valid) L.reach[nd.node_off] = x;  // read by the showdowns of an all-in run-out
       if (nd.tmask & 1) {  // terminal children: their reach, zero where the hand holds the card
         for (int a = 0; a < A; ++a) {
           const V y = ((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull) ? P::zero() : x;
@@ -1485,11 +1495,12 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_rows(const GameDev* __res
     if (a < nd.n_kids) out[(size_t)a * S] = sg[a];
 }
 
-// Top-down step at every node of one level -- the contiguous ids a0 .. a0 + cnt -- (Stages
+// Top-down step at the nodes of one level whose reach is stored (list[0 .. cnt)) (Stages
 // 1-2): p's reach is the parent's times p's probability of the action, and zero for hands
 // holding a dealt card.  Level 0 (the root) takes p's range.
 template <typename P>
-__global__ void __launch_bounds__(kWideThreads) k_wide_fwd(const GameDev* __restrict__ games, int a0, int cnt,
+__global__ void __launch_bounds__(kWideThreads) k_wide_fwd(const GameDev* __restrict__ games,
+                                                           const int32_t* __restrict__ list, int cnt,
                                                            int player_mask, int avg) {
   using V = typename P::V;
   pdl_wait();
@@ -1499,7 +1510,7 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_fwd(const GameDev* __rest
   const size_t S = (size_t)G.hstride;
   const size_t e = (size_t)blockIdx.x * kWideThreads + threadIdx.x;
   if (e >= (size_t)cnt * S) return;
-  const int n = a0 + (int)(e / S), h = (int)(e % S);
+  const int n = list[e / S], h = (int)(e % S);
   if (h >= G.n_hands) return;
   V* rch = static_cast<V*>(avg ? G.reach_bar : G.reach) + (size_t)p * G.n_nodes * S + h;
   if (n == 0) {
@@ -1680,10 +1691,10 @@ static cudaError_t wide_forward(const LaunchCtx& c, int player_mask, int avg, in
   const int players = player_mask == 3 ? 2 : 1;
   const size_t S = (size_t)c.wide_stride;
   for (int l = first_level; l < c.wide_levels; ++l) {
-    const int a0 = c.wide_ls[l], cnt = c.wide_ls[l + 1] - a0;
+    const int a0 = c.wide_fwd_off[l], cnt = c.wide_fwd_off[l + 1] - a0;
     if (cnt == 0) continue;
     const cudaError_t e = launch_wide(k_wide_fwd<P>, wide_blocks((size_t)cnt * S), players, stream, c.pdl != 0,
-                                      c.games, a0, cnt, player_mask, avg);
+                                      c.games, c.wide_fwd + a0, cnt, player_mask, avg);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1727,7 +1738,7 @@ int wide_launch_count(const LaunchCtx& c, int which, int player_mask, int advanc
   int back = 0, fwd = 0;
   for (int l = 0; l < c.wide_levels; ++l) {
     back += c.wide_inner_off[l + 1] > c.wide_inner_off[l];
-    fwd += c.wide_ls[l + 1] > c.wide_ls[l];
+    fwd += c.wide_fwd_off[l + 1] > c.wide_fwd_off[l];
   }
   (void)player_mask;
   if (which == kModeUpdate) return back + (fwd - 1) + (advance ? 1 : 0);
@@ -1789,14 +1800,14 @@ int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stre
   const bool runs = c.n_term_runs < c.n_term_work;
   if (c.precision == kPrecisionSingle)
     e = runs ? launch_kernel(k_terminal<Single, true>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
-                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
+                             c.term_work, c.term_src, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
              : launch_kernel(k_terminal<Single, false>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
-                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
+                             c.term_work, c.term_src, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
   else
     e = runs ? launch_kernel(k_terminal<Pairs, true>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
-                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
+                             c.term_work, c.term_src, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err)
              : launch_kernel(k_terminal<Pairs, false>, grid, kTermThreads, c.smem_term, stream, pdl, c.games,
-                             c.term_work, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
+                             c.term_work, c.term_src, c.term_runs, c.n_term_runs, player_mask, use_bar, c.err);
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_terminal failed: %s\n", cudaGetErrorString(e));
     return -1;

@@ -171,6 +171,8 @@ struct LaunchCtx {
   const Work* term_runs;       // device [n_term_runs]: (first entry of term_work, count), the
                                // terminal nodes one block evaluates
   int n_term_runs;
+  const int32_t* term_src;     // device [n_term_work]: node whose reach rows stand for each
+                               // terminal's (HostGame::reach_src)
   int* iter;                   // device: iterations completed
   unsigned* done;              // device: block arrival counter
   int* err;                    // device: nonzero after a bounded wait gave up
@@ -190,12 +192,14 @@ struct LaunchCtx {
                                // memory; 0 = read from global memory
   int stream_half;             // units per lane in each half of the stream prefetch ring
   int stream_units;            // load descriptors staged per block (0 when the program is not)
-  // wide schedule (one game): level l holds nodes [wide_ls[l], wide_ls[l + 1]); its inner
-  // nodes are wide_inner[wide_inner_off[l] .. wide_inner_off[l + 1])
+  // wide schedule (one game): level l's inner nodes are wide_inner[wide_inner_off[l] ..
+  // wide_inner_off[l + 1]), the nodes whose reach is stored wide_fwd[wide_fwd_off[l] ..
+  // wide_fwd_off[l + 1]) (all but the run-out nodes that read their source's reach)
   int wide_levels;             // number of levels
-  const int* wide_ls;          // host [wide_levels + 1]
   const int* wide_inner_off;   // host [wide_levels + 1]
   const int32_t* wide_inner;   // device: inner node ids, level by level
+  const int* wide_fwd_off;     // host [wide_levels + 1]
+  const int32_t* wide_fwd;     // device: node ids, level by level
   int wide_stride;             // hstride of the game
   int wide_max_dec;            // decision nodes of the player who has more
 };

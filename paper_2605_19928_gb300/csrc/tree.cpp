@@ -387,6 +387,14 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     if (g.nodes[n].type == kFold || g.nodes[n].type == kShowdown) g.terminals.push_back(n);
     if (g.nodes[n].type == kLeaf) g.leaves.push_back(n);
   }
+  // reach sources (level order: a parent's source is known before its children's)
+  g.reach_src.resize(N);
+  for (int n = 0; n < N; ++n) {
+    const NodeDev& nd = g.nodes[n];
+    const bool below_chance = nd.parent >= 0 && g.nodes[nd.parent].type == kChance;
+    const bool passes = nd.type == kChance || nd.type == kShowdown || nd.type == kFold;
+    g.reach_src[n] = below_chance && passes ? g.reach_src[nd.parent] : n;
+  }
 
   // ---- showdown tables, one per board the tree shows down on (table 0 also serves the
   // fold terminals, which only read its card lists)

@@ -20,6 +20,10 @@ struct HostGame {
   int row_begin[3] = {0, 0, 0};
   std::vector<int32_t> terminals;     // fold and showdown node ids
   std::vector<int32_t> leaves;        // depth-limit leaf node ids
+  // node whose reach equals this node's up to zeroing hands that hold a dealt card: the
+  // top chance node of an all-in run-out for the run-out's inner chance nodes and
+  // showdowns (nobody acts below it), the node itself otherwise
+  std::vector<int32_t> reach_src;
   // hands
   int n_hands = 0, hstride = 0;
   std::vector<uint8_t> hand_cards;    // [n_hands][2]
