@@ -504,7 +504,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "subgame iter/s" if batch else "iter/s",
                 "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
-                "ms_per_iter": ms_per_iter, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step_std": float(np.std(step_ms)), "ms_per_iter": ms_per_iter,
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32x2 values, f64 R/S" if args.precision == "pairs" else
                 "f32 values, f64 R/S", "data": "synthetic", "config": config, **quality,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
@@ -519,9 +520,13 @@ def cpu_baseline(specs, seconds, batch):
     """The oracle as it stands on the host cores, on a bounded sample of the workload."""
     if not batch:
         r = oracle_sample(specs[0], seconds)
+        one = oracle_sample(specs[0], seconds / 3, threads=1)  # the same oracle on one core
         return {"value": r["iters"] / r["seconds"], "unit": "iter/s", "cores": r["threads"], "kind": "oracle",
                 "sample": f"{r['iters']} DCFR iterations of the same 1081-hand river subgame plus one "
-                          f"exploitability pass ({r['seconds']:.1f} s, FP64, walks every history)"}
+                          f"exploitability pass ({r['seconds']:.1f} s, FP64, walks every history)",
+                "single_thread": {"value": one["iters"] / one["seconds"], "unit": "iter/s", "cores": 1,
+                                  "sample": f"{one['iters']} iterations plus one exploitability pass "
+                                            f"({one['seconds']:.1f} s)"}}
     picks = sorted(set(int(k * len(specs) / 4) for k in range(4)))
     sec_per_iter, iters, total, threads = [], 0, 0.0, 1
     for g in picks:
