@@ -12,8 +12,12 @@ timed steps (L2 flushed between steps with a 256 MB write, outside the timed eve
 Under torchrun each rank solves its own subgame (seeds offset by rank) with no
 collective: weak scaling, value = all ranks' iterations / the slowest rank's time.
 
-`--impl reference` times the FP64 CPU oracle (the reference for this build) on the same
-workload instead, on the host cores.
+`--impl reference` times the FP64 CPU oracle (the paper publishes no code, so the oracle is
+the reference implementation) on the same workload instead, on the host cores.
+
+Other workloads (`--workload`): `batch` (256 uneven river subgames in one handle, the
+launch tiling autotuned first), `leaf` and `flop` (depth-limited turn and flop subgames
+with the BF16 leaf network, against the exact subgames), `gemm` (the network's layers).
 """
 from __future__ import annotations
 
