@@ -6,9 +6,11 @@
  * (arxiv 2605.19928).  The iteration follows the paper's seven-stage pipeline (Section 4.1,
  * Table 1): regret matching (Section 3, Eq. rm), forward reach (Section 4.2, Stages 1-2),
  * blocker-corrected opponent reach at fold terminals (Stage 3), rank-sorted showdown values
- * (Stage 4), depth-limit chance leaves (Stage 5, exact form), backward counterfactual values
- * (Section 4.4, Stage 6, Eq. backward) and the regret / average-strategy update (Stage 7)
- * for vanilla CFR, CFR+ and DCFR (Section 2).  Exploitability uses a best-response pass.
+ * (Stage 4), depth-limit leaves (Stage 5: exact chance nodes, or the BF16 leaf network on
+ * the tensor cores), backward counterfactual values (Section 4.4, Stage 6, Eq. backward)
+ * and the regret / average-strategy update (Stage 7) for vanilla CFR, CFR+, DCFR (Section
+ * 2) and Predictive CFR+ (Section 5).  Exploitability uses a best-response pass.  One
+ * handle holds one subgame or a batch of them (batched serving).
  *
  * Conventions
  *   - Every function returns CFR_OK (0) or a negative CFR_E* code; cfr_last_error()
