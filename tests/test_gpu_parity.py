@@ -547,3 +547,27 @@ def test_fp32_strategy_is_regret_matching_rounded_to_nearest(schedule):
         assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
     finally:
         capi.cfr_tree_destroy(tree)
+
+
+def test_full_size_batch_sampled_subgames_match_oracle():
+    """The benchmarked batch itself (256 uneven 1081-hand rivers, FP32 values, the stream
+    schedule the bench's autotuner picks, terminal runs): two sampled subgames against the
+    oracle from the GPU's own state for one iteration, and their exploitability."""
+    from oracle.oracle import Oracle
+    specs = synth.batch_rivers(256, seed=0)
+    tree = capi.cfr_batch_create(specs, capi.make_opts("dcfr", precision="single", schedule="stream"))
+    try:
+        assert capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_STREAM
+        capi.cfr_iterate(tree, 3)
+        for g in (0, 255):
+            orc = Oracle(specs[g], variant="dcfr")
+            mapping = node_map(tree, orc, game=g)
+            w = forced_step(tree, orc, mapping, 4, game=g, rtol=1e-5, floor_frac=1e-8)
+            print("batch subgame", g, w)
+            inject(tree, orc, mapping, game=g)
+            e_g, _ = capi.cfr_exploitability(tree, len(specs))
+            assert e_g[g] == pytest.approx(orc.exploitability()[0], rel=1e-4, abs=1e-7 * specs[g].pot)
+            capi.cfr_reset(tree)
+            capi.cfr_iterate(tree, 3)
+    finally:
+        capi.cfr_tree_destroy(tree)
