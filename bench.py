@@ -444,6 +444,10 @@ def run_ours(args):
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
 
     target = None
+    if not batch:  # the single subgame: iterations (and device time) to 1 mbb/hand
+        need = time_to_target(capi, tree, 1, max_iters=ips, every=10, target_mbb=1.0)[0]
+        target = {"target_mbb_per_hand": 1.0, "checked_every_iters": 10, "iters": need,
+                  "ms": None if need is None else need * ms_per_iter}
     if batch:
         limit = 4 * ips
         need = time_to_target(capi, tree, G, max_iters=limit, every=10, target_mbb=1.0)
@@ -503,7 +507,7 @@ def run_ours(args):
                        "time_to_1mbb": target}
         else:
             config = {**workload_config(args, specs[0], shapes[0]["nodes"]), "schedule": schedule}
-            quality = {"exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS,
+            quality = {"exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS, "time_to_1mbb": target,
                        "exploitability_pct_pot": 100.0 * float(expl[0]) / specs[0].pot}
         line = {"metric": METRIC, "value": value, "unit": "subgame iter/s" if batch else "iter/s",
                 "n_gpus": world, "steps": args.steps,
