@@ -338,6 +338,22 @@ def test_zero_sum(oracle_mod, case):
         assert abs(v[0] + v[1]) <= 1e-12 * max(1.0, spec.pot)
 
 
+def test_leduc_average_strategy_reaches_the_game_value(oracle_mod):
+    """CFR+ on Leduc: the average profile's value for player 0 approaches the game value
+    quoted in tests/golden/leduc_value.txt, within its exploitability plus the quote's
+    rounding."""
+    with open(os.path.join(GOLDEN, "leduc_value.txt")) as f:
+        want = float([ln.split()[1] for ln in f if ln.startswith("game_value_player0")][0])
+    o = oracle_mod.Oracle(synth.leduc(), variant="cfr+", threads=4)
+    o.iterate(2000)
+    o.load_profile("average")
+    v = o.profile_value()
+    e = o.exploitability()[0]
+    assert e < 2e-4
+    assert abs(v[0] - want) <= e + 5e-5
+    assert v[0] + v[1] == pytest.approx(0.0, abs=1e-12)
+
+
 def test_cfr_plus_regrets_never_negative(oracle_mod):
     o = oracle_mod.Oracle(synth.leduc(), variant="cfr+", threads=1)
     o.iterate(20)
