@@ -43,3 +43,31 @@ def test_training_rivers_are_seeded_and_valid():
         assert 100.0 <= x.pot <= 900.0 and 50.0 <= x.stack <= 500.0
     t = synth.ranked_turn_subgame(n_hands=30, depth_limit=1)
     assert t.depth_limit == 1 and t.strength.shape == (52, 30)
+
+
+def test_flop_strength_rows_depend_only_on_the_completed_board():
+    g = synth.flop_subgame(n_hands=40, seed=2)
+    assert g.board.shape == (3,) and g.hands.shape == (40, 2) and g.strength.shape == (52 * 52, 40)
+    on = set(int(c) for c in g.board)
+    live = [c for c in range(52) if c not in on]
+    for t, r in [(live[0], live[5]), (live[10], live[3]), (live[20], live[44])]:
+        assert np.array_equal(g.strength[t * 52 + r], g.strength[r * 52 + t])  # same five cards
+    assert not g.strength[live[0] * 52 + live[0]].any()          # a card cannot come twice
+    assert not g.strength[int(g.board[0]) * 52 + live[1]].any()  # nor a board card
+    r = synth.ranked_flop_subgame(n_hands=25, seed=6)
+    t, v = live[1], live[7]
+    ok = ~np.any((r.hands == t) | (r.hands == v), axis=1)
+    want = synth.rank_strength(np.concatenate([r.board, [t, v]]), r.hands[ok])
+    # the same order as the evaluator on the completed board (dense ranks may differ by offset)
+    assert np.array_equal(np.argsort(r.strength[t * 52 + v][ok], kind="stable"), np.argsort(want, kind="stable"))
+
+
+def test_training_turns_are_seeded_and_valid():
+    a = synth.leaf_training_turns(2, seed=3)
+    b = synth.leaf_training_turns(2, seed=3)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.board, y.board) and np.array_equal(x.ranges, y.ranges)
+        assert x.board.shape == (4,) and x.hands.shape == (1128, 2) and x.strength.shape == (52, 1128)
+        assert np.allclose(x.ranges.sum(axis=1), 1.0, atol=1e-5)
+        assert 100.0 <= x.pot <= 400.0 and 100.0 <= x.stack <= 600.0
+        assert x.bet_sizes[-1] == synth.ALL_IN and 2 <= x.max_raises <= 3
