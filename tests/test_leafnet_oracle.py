@@ -175,6 +175,51 @@ def test_flop_constant_leaf_values_give_that_share_of_the_pot(oracle_mod):
     assert v[1] == pytest.approx(-0.1 * spec.pot, rel=1e-12)
 
 
+def test_flop_leaf_values_weigh_turn_and_river_cards(oracle_mod):
+    """Check-down flop to the leaves below each turn card, with outputs that depend on the
+    turn and river cards: player 0's value is the mean, over the deals, of the mean over
+    the 45 turn cards neither hand holds of the mean over the 44 river cards left of pot x
+    output -- the chance weights 1/45 and 1/44 of the two dealt cards."""
+    spec = _flop(n_hands=8, max_raises=0)
+    spec.depth_limit = 1
+    o = oracle_mod.Oracle(spec, threads=1)
+    nodes = o.nodes()
+    board = set(int(b) for b in spec.board)
+    f = np.sin(np.arange(52 * 52, dtype=np.float64)).reshape(52, 52)  # output for (turn, river)
+    for k, n in enumerate(nodes):
+        if n["type"] != oracle_mod.T_LEAF:
+            continue
+        t = n["deal"] if n["deal"] >= 0 else nodes[n["parent"]]["deal"]
+        while t < 0:  # the turn card is dealt above the leaf
+            n = nodes[n["parent"]]
+            t = n["deal"]
+        rivers = [c for c in range(52) if c not in board and c != t]
+        y = np.zeros((48, 2, spec.n_hands))
+        y[:, 0, :] = f[t, rivers][:, None]
+        o.set_leaf_values(k, y)
+    o.load_profile("current")
+    got = o.profile_value()[0]
+    r = spec.ranges.astype(np.float64)
+    r = r / r.sum(axis=1, keepdims=True)
+    hands = [set(int(c) for c in h) for h in spec.hands]
+    Z, acc = 0.0, 0.0
+    for a in range(spec.n_hands):
+        for b in range(spec.n_hands):
+            if hands[a] & hands[b]:
+                continue
+            w = r[0, a] * r[1, b]
+            dead = board | hands[a] | hands[b]
+            turns = [c for c in range(52) if c not in dead]
+            u = 0.0
+            for t in turns:
+                rivers = [c for c in range(52) if c not in dead and c != t]
+                u += np.mean([spec.pot * f[t, c] for c in rivers])
+            Z += w
+            acc += w * u / len(turns)
+    assert len(turns) == 45 and len(rivers) == 44
+    assert got == pytest.approx(acc / Z, rel=1e-12, abs=1e-13)
+
+
 def test_leaf_input_row_layout():
     hands = np.array([[0, 1], [2, 5], [1, 7]])
     x = ln.leaf_input([np.array([1.0, 3.0, 0.0]), np.array([0.0, 0.0, 2.0])], hands, [10, 20, 30, 40], 5,
