@@ -604,7 +604,7 @@ def run_leaf(args):
     import numpy as np
     import torch
 
-    from paper_2605_19928_gb300 import capi, leafnet_train, synth
+    from paper_2605_19928_gb300 import capi, leafnet_train, serve, synth
 
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
@@ -658,6 +658,9 @@ def run_leaf(args):
     gpu_launches = capi.cfr_counters(L)["kernel_launches"] - launches0
     value, t_max = aggregate(args.steps * ips, t_leaf, world, dist, device)
     e_leaf_own, _ = capi.cfr_exploitability_result(L)
+    # the served form: the network judged on 64 of its own leaf rows against exact river
+    # solves of their continuations, falling back to the exact subgame above the tolerance
+    judge = serve.judge_leaves(L, spec_leaf, n_rows=64, iters=300, seed=rank, stream=stream.cuda_stream)
     exact_steps = 1 if flop else max(1, args.steps // 4)
     t_exact = timed(E, exact_steps, 1)
     e_exact, _ = capi.cfr_exploitability_result(E)
@@ -709,6 +712,19 @@ def run_leaf(args):
                                "tflops_incl_input_and_value_kernels": flops / (stages["leaf"][0] * 1e-3) / 1e12},
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
     mbb = lambda e: 1000.0 * float(e) / BB_CHIPS
+    learned_ok = judge.rows > 0 and judge.reach_weighted_error <= serve.DEFAULT_TOL
+    ms_leaf_step, ms_exact_step = 1000.0 * t_leaf / args.steps, 1000.0 * t_exact / exact_steps
+    served = {"form": "learned" if learned_ok else "exact (fallback)", "tol_pot": serve.DEFAULT_TOL,
+              "judge": {"rows": judge.rows, "candidates": judge.candidates,
+                        "mean_abs_error_pot": judge.mean_abs_error,
+                        "reach_weighted_error_pot": judge.reach_weighted_error,
+                        "max_row_error_pot": judge.max_row_error,
+                        "continuation_exploitability_mbb": judge.continuation_exploitability_mbb,
+                        "ms": judge.ms, "continuation_iters": 300},
+              "exploitability_in_exact_game_mbb": mbb(e_hybrid[0]) if learned_ok else mbb(e_exact[0]),
+              "ms_per_solve": ms_leaf_step + judge.ms + (0.0 if learned_ok else ms_exact_step),
+              "note": "one solve = the depth-limited solve (one step), the judge (host wall time, "
+                      "continuation solves included) and, after a fallback, the exact solve (one step)"}
     n_exact = capi.cfr_tree_info(E)[0]
     n_leaf_nodes = capi.cfr_tree_info(L)[0]
     sched = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream",
@@ -750,6 +766,7 @@ def run_leaf(args):
                                  "note": "strategy of the depth-limited solve above the leaves, river play of "
                                          "the exact solve, best responses in the exact game"},
                 "leaf_values_vs_exact_river": leaf_check,
+                "served": served,
                 "network": {"training_solves": int(meta[0]), "solve_iters": int(meta[1]), "epochs": int(meta[2]),
                             "median_solve_exploitability_mbb": float(meta[4]),
                             "validation_mean_abs_error_pot": float(meta[5]),

@@ -1,0 +1,102 @@
+"""Host logic of the served depth-limited solve (learned leaves judged against exact
+continuation solves, Section 3): continuation specs, leaf boards, row order and the error
+statistic.  No GPU: the tree walk runs on a fake public tree."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2605_19928_gb300 import capi, serve, synth
+
+
+def test_river_cards_follow_the_leaf_rows():
+    board = [3, 17, 30, 44]
+    cards = serve.river_cards(board)
+    assert len(cards) == capi.LEAF_CARDS
+    assert cards == sorted(cards) and not set(cards) & set(board)
+
+
+def test_turn_continuation_is_the_river_subgame_below_the_card():
+    spec = synth.ranked_turn_subgame(n_hands=150, seed=3, range_seed=4, depth_limit=1)
+    rng = np.random.default_rng(0)
+    reach = rng.random((2, spec.n_hands))
+    r = serve.river_cards(spec.board)[11]
+    cont = serve.continuation_spec(spec, spec.board, r, reach, pot=160.0, behind=320.0)
+    full = sorted([int(c) for c in spec.board] + [r])
+    assert cont.board.tolist() == full and cont.depth_limit == 0
+    live = ~np.any(spec.hands == r, axis=1)
+    assert cont.n_hands == int(live.sum())
+    assert not np.isin(cont.hands, full).any()
+    np.testing.assert_array_equal(cont.hands, spec.hands[live])
+    # strengths from the rules of poker on the completed board, computed afresh
+    np.testing.assert_array_equal(cont.strength[0], synth.rank_strength(full, cont.hands))
+    for p in (0, 1):
+        want = reach[p][live] / reach[p][live].sum()
+        np.testing.assert_allclose(cont.ranges[p], want, rtol=1e-6)
+    assert (cont.pot, cont.stack) == (160.0, 320.0)
+    assert cont.bet_sizes == spec.bet_sizes and cont.max_raises == spec.max_raises
+
+
+def test_flop_continuation_uses_the_turn_and_river_row():
+    spec = synth.ranked_flop_subgame(n_hands=60, seed=5, range_seed=6, depth_limit=1)
+    t = serve.river_cards(spec.board)[7]
+    board = [int(c) for c in spec.board] + [t]
+    r = serve.river_cards(board)[30]
+    reach = np.ones((2, spec.n_hands))
+    cont = serve.continuation_spec(spec, board, r, reach, pot=200.0, behind=50.0)
+    full = sorted(board + [r])
+    np.testing.assert_array_equal(cont.strength[0], synth.rank_strength(full, cont.hands))
+    assert not np.isin(cont.hands, full).any()
+
+
+def test_continuation_without_reach_is_skipped():
+    spec = synth.ranked_turn_subgame(n_hands=80, seed=1, range_seed=2, depth_limit=1)
+    reach = np.ones((2, spec.n_hands))
+    r = serve.river_cards(spec.board)[0]
+    reach[1][~np.any(spec.hands == r, axis=1)] = 0.0  # player 1 only holds hands with card r
+    assert serve.continuation_spec(spec, spec.board, r, reach, 100.0, 100.0) is None
+
+
+def test_strength_row_rejects_other_boards():
+    spec = synth.ranked_turn_subgame(n_hands=40, seed=1, range_seed=2)
+    with pytest.raises(ValueError):
+        serve.strength_row(spec, list(spec.board))
+
+
+def test_row_errors_by_hand():
+    hands = np.array([[0, 1], [2, 5]], np.uint8)
+    sl = [1 * 0 // 2 + 0, 5 * 4 // 2 + 2]  # slot b (b - 1) / 2 + a
+    y_net = np.zeros(2 * serve.SLOTS + 36, np.float32)
+    y_ex = np.zeros_like(y_net)
+    mask = np.zeros_like(y_net)
+    y_net[sl[0]], y_ex[sl[0]], mask[sl[0]] = 0.5, 0.25, 1.0             # player 0, hand 0
+    y_net[sl[1]], y_ex[sl[1]], mask[sl[1]] = -1.0, -1.0, 1.0            # player 0, hand 1
+    y_net[serve.SLOTS + sl[1]], y_ex[serve.SLOTS + sl[1]] = 3.0, 1.0    # player 1, hand 1: masked
+    y_net[serve.SLOTS + sl[0]], y_ex[serve.SLOTS + sl[0]], mask[serve.SLOTS + sl[0]] = 0.0, 0.1, 1.0
+    ranges = np.array([[0.75, 0.25], [0.4, 0.6]])
+    tot, weighted, cnt = serve.row_errors(y_net, y_ex, mask, ranges, hands)
+    assert cnt == 3
+    assert tot == pytest.approx(0.25 + 0.0 + 0.1, rel=1e-6)
+    assert weighted == pytest.approx(0.5 * (0.75 * 0.25 + 0.4 * 0.1), rel=1e-6)
+
+
+def test_leaf_board_collects_the_dealt_cards(monkeypatch):
+    # root decision 0 -> chance 1 -> (turn card 9) 2 -> decision 3 -> leaf 4
+    nodes = {0: (capi.CFR_NODE_DECISION, -1, -1), 1: (capi.CFR_NODE_CHANCE, 0, -1),
+             2: (capi.CFR_NODE_DECISION, 1, 9), 3: (capi.CFR_NODE_DECISION, 2, -1),
+             4: (capi.CFR_NODE_LEAF, 3, -1)}
+
+    def fake_info(tree, node, game=0):
+        t, parent, deal = nodes[node]
+        return {"type": t, "parent": parent, "deal": deal}
+
+    monkeypatch.setattr(serve.capi, "cfr_node_info", fake_info)
+    spec = synth.flop_subgame(n_hands=10, seed=2, range_seed=3)
+    assert serve.leaf_board(None, 4, spec) == [int(c) for c in spec.board] + [9]
+    assert serve.leaf_board(None, 1, spec) == [int(c) for c in spec.board]
+
+
+def test_solve_depth_limited_wants_a_depth_limit():
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=0)
+    with pytest.raises(ValueError):
+        serve.solve_depth_limited(spec, None, None, 10)
