@@ -253,23 +253,45 @@ def algorithmic_bytes(shape, stage: str, value_bytes: int) -> float:
     raise ValueError(stage)
 
 
-def kernels_digest() -> str:
+def without_sections(text: str, names) -> str:
+    """kernels.cu without the named sections: a section runs from its header line
+    ('// ----- name') to the next header."""
+    out, skip = [], False
+    for line in text.splitlines(keepends=True):
+        m = re.match(r"// -{10,} (.+)$", line.rstrip("\n"))
+        if m:
+            skip = m.group(1).strip() in names
+        if not skip:
+            out.append(line)
+    return "".join(out)
+
+
+def kernels_digest(exclude=()) -> str:
+    """First 16 hex digits of the sha256 of the kernel sources (kernels.cu, then
+    pcfr_internal.h), leaving out the sections of kernels.cu named in `exclude`: the digest
+    of a profiled kernel that uses none of them stays the same when only they change."""
     h = hashlib.sha256()
     for name in ("kernels.cu", "pcfr_internal.h"):
         with open(os.path.join(ROOT, "paper_2605_19928_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+            data = f.read()
+        if name == "kernels.cu" and exclude:
+            data = without_sections(data.decode(), set(exclude)).encode()
+        h.update(data)
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(stage: str, workload: str = "river1081"):
-    """DRAM bytes per launch from the committed ncu summary, if it matches these kernels."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches these kernels
+    (its digest, over the sources without the sections it names as unused by its kernel)."""
     path = os.path.join(ROOT, "profiles", f"{stage}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"kernels_digest:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernels_digest():
+    x = re.search(r"kernels_digest_excludes:\s*(.+)", text)
+    exclude = tuple(n.strip() for n in x.group(1).split(",")) if x else ()
+    if not m or not t or m.group(1) != kernels_digest(exclude):
         return None
     return float(t.group(1))
 

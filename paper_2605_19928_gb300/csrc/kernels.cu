@@ -961,6 +961,33 @@ __device__ __forceinline__ void regret_match(const double (&Rv)[kStreamMaxAction
   }
 }
 
+// regret_match with a compile-time action count (same arithmetic, no per-action guards).
+template <typename P, int NA>
+__device__ __forceinline__ void regret_match_n(const double (&Rv)[NA], typename P::V (&sg)[NA]) {
+  using V = typename P::V;
+  V tot = P::zero();
+  int npos = 0, last = 0;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const V x = __double_as_longlong(Rv[a]) > 0 ? P::of_double(Rv[a]) : P::zero();
+    sg[a] = x;
+    if (P::positive(x)) ++npos, last = a;
+    tot = P::add(tot, x);
+  }
+  if (npos == 1) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) sg[a] = a == last ? P::one() : P::zero();
+  } else if (npos > 1) {
+    const V inv = P::recip(tot);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) sg[a] = P::mul(sg[a], inv);
+  } else {
+    const V uni = P::uniform(NA);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) sg[a] = uni;
+  }
+}
+
 __device__ __forceinline__ void load_rows(const double* __restrict__ base, size_t stride, int A,
                                           double (&out)[kStreamMaxActions]) {
 #pragma unroll
@@ -1054,6 +1081,63 @@ __device__ __forceinline__ typename P::V ring_value(const uint64_t* slot) {
   }
 }
 
+// Bottom-up work at one of the player's decision nodes with NA actions (Stages 6-7): the
+// children's values (ring or stack), regret matching of R (R + M for Predictive CFR+), the
+// node value, and the new R, S (and M) rows.  NA is a compile-time constant so that the
+// actions' FP64 update chains are straight-line code the compiler can interleave.
+template <typename P, int NA>
+__device__ __forceinline__ typename P::V decision_back(const StreamLane<P>& L, const Op& nd, const uint64_t* ring,
+                                                       int& u, int& sp, const Discount& d, int variant) {
+  using V = typename P::V;
+  V* st = L.st;
+  V c[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    if ((nd.tmask >> a) & 1)
+      c[a] = ring_value<P>(ring + (size_t)(u++) * 32);
+    else
+      c[a] = st[(--sp) * 32];
+  }
+  const bool pred = L.M != nullptr;  // Predictive CFR+: R, M, S, reach
+  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
+  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * 32);
+  const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + (pred ? 2 : 1) * NA) * 32);
+  const V pi = ring_value<P>(ring + (size_t)(u + (pred ? 3 : 2) * NA) * 32);
+  u += (pred ? 3 : 2) * NA + 1;
+  double Rv[NA];
+  V sg[NA];
+  {
+    double Rm[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) Rv[a] = Rm[a] = Rr[(size_t)a * 32];
+    if (pred) {  // Predictive CFR+ matches R + M (no FP64 add for the other variants)
+#pragma unroll
+      for (int a = 0; a < NA; ++a) Rm[a] = Rv[a] + Mr[(size_t)a * 32];
+    }
+    regret_match_n<P, NA>(Rm, sg);
+  }
+  typename P::Acc acc = P::acc0();
+#pragma unroll
+  for (int a = 0; a < NA; ++a) P::acc_mul(acc, sg[a], c[a]);
+  const V val = P::value(acc);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const V rr = P::sub(c[a], val);                          // instantaneous regret
+    const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
+    const double rd = P::to_double(rr);
+    double x = Rv[a] + rd;
+    if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+    if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;
+    const double sn = fma(Sr[(size_t)a * 32], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
+    if (L.valid) {
+      L.R[(size_t)nd.row_off + (size_t)a * L.stride] = x;
+      L.S[(size_t)nd.row_off + (size_t)a * L.stride] = sn;
+      if (pred) L.M[(size_t)nd.row_off + (size_t)a * L.stride] = rd;
+    }
+  }
+  return val;
+}
+
 // Bottom-up pass over chunk [k0, k1) (program positions counted from its end).  A node's
 // children values come from the ring (terminal children, in child order) or from the stack
 // (inner children, child 0 on top).
@@ -1088,57 +1172,16 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
         P::acc(acc, x);
       }
       val = P::value(acc);
-    } else {
-      V c[kStreamMaxActions];
-#pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a) {
-        if (a < A) {
-          if ((nd.tmask >> a) & 1)
-            c[a] = ring_value<P>(ring + (size_t)(u++) * 32);
-          else
-            c[a] = st[(--sp) * 32];
-        }
-      }
-      const bool pred = L.M != nullptr;  // Predictive CFR+: R, M, S, reach
-      const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-      const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
-      const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + (pred ? 2 : 1) * A) * 32);
-      const V pi = ring_value<P>(ring + (size_t)(u + (pred ? 3 : 2) * A) * 32);
-      u += (pred ? 3 : 2) * A + 1;
-      double Rv[kStreamMaxActions];
-      V sg[kStreamMaxActions];
-      {
-        double Rm[kStreamMaxActions];
-#pragma unroll
-        for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = Rm[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
-        if (pred) {  // Predictive CFR+ matches R + M (no FP64 add for the other variants)
-#pragma unroll
-          for (int a = 0; a < kStreamMaxActions; ++a)
-            if (a < A) Rm[a] = Rv[a] + Mr[(size_t)a * 32];
-        }
-        regret_match<P>(Rm, A, sg);
-      }
-      typename P::Acc acc = P::acc0();
-#pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a)
-        if (a < A) P::acc_mul(acc, sg[a], c[a]);
-      val = P::value(acc);
-#pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a) {
-        if (a < A) {
-          const V rr = P::sub(c[a], val);                          // instantaneous regret
-          const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
-          const double rd = P::to_double(rr);
-          double x = Rv[a] + rd;
-          if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
-          if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;
-          const double sn = fma(Sr[(size_t)a * 32], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
-          if (L.valid) {
-            L.R[(size_t)nd.row_off + (size_t)a * L.stride] = x;
-            L.S[(size_t)nd.row_off + (size_t)a * L.stride] = sn;
-            if (pred) L.M[(size_t)nd.row_off + (size_t)a * L.stride] = rd;
-          }
-        }
+    } else {  // the player's decision node: its action count as a compile-time constant
+      switch (A) {
+        case 1: val = decision_back<P, 1>(L, nd, ring, u, sp, d, variant); break;
+        case 2: val = decision_back<P, 2>(L, nd, ring, u, sp, d, variant); break;
+        case 3: val = decision_back<P, 3>(L, nd, ring, u, sp, d, variant); break;
+        case 4: val = decision_back<P, 4>(L, nd, ring, u, sp, d, variant); break;
+        case 5: val = decision_back<P, 5>(L, nd, ring, u, sp, d, variant); break;
+        case 6: val = decision_back<P, 6>(L, nd, ring, u, sp, d, variant); break;
+        case 7: val = decision_back<P, 7>(L, nd, ring, u, sp, d, variant); break;
+        default: val = decision_back<P, kStreamMaxActions>(L, nd, ring, u, sp, d, variant); break;
       }
     }
     st[(sp++) * 32] = val;
