@@ -1,0 +1,61 @@
+"""The benchmark's link to the committed ncu summaries: a summary's DRAM counters are used
+only while the kernel sources it was taken on are unchanged (per-section digests)."""
+from __future__ import annotations
+
+import os
+import re
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+SRC = """// ------------------------------------------------------------------ first
+int a;
+// ------------------------------------------------------------------ stream schedule
+int b;
+int c;
+// ------------------------------------------------------------------ wide schedule
+int d;
+"""
+
+
+def test_without_sections_drops_a_section_up_to_the_next_header():
+    out = bench.without_sections(SRC, {"stream schedule"})
+    assert "int b;" not in out and "int c;" not in out
+    assert "int a;" in out and "int d;" in out and "wide schedule" in out
+    assert bench.without_sections(SRC, set()) == SRC
+    both = bench.without_sections(SRC, {"stream schedule", "wide schedule"})
+    assert both.splitlines() == SRC.splitlines()[:2]
+
+
+def test_kernel_sources_have_the_sections_the_summaries_name():
+    text = open(os.path.join(ROOT, "paper_2605_19928_gb300", "csrc", "kernels.cu")).read()
+    headers = set(re.findall(r"^// -{10,} (.+)$", text, flags=re.M))
+    for name in os.listdir(os.path.join(ROOT, "profiles")):
+        summary = open(os.path.join(ROOT, "profiles", name)).read()
+        x = re.search(r"kernels_digest_excludes:\s*(.+)", summary)
+        if x:
+            for section in x.group(1).split(","):
+                assert section.strip() in headers, (name, section)
+    # leaving a section out changes the digest, and only then
+    assert bench.kernels_digest(("stream schedule",)) != bench.kernels_digest()
+    assert bench.kernels_digest(("no such section",)) == bench.kernels_digest()
+
+
+def test_profiled_traffic_needs_a_matching_digest(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    good = bench.kernels_digest(("stream schedule",))
+    (prof / "update_toy.md").write_text(f"kernels_digest: {good}\nkernels_digest_excludes: stream schedule\n"
+                                        "dram_bytes_per_launch: 1234\n")
+    (prof / "update_stale.md").write_text("kernels_digest: 0000000000000000\ndram_bytes_per_launch: 99\n")
+    (prof / "update_full.md").write_text(f"kernels_digest: {good}\ndram_bytes_per_launch: 5\n")
+    real_root = bench.ROOT
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "paper_2605_19928_gb300").symlink_to(os.path.join(real_root, "paper_2605_19928_gb300"))
+    assert bench.profiled_traffic("update", "toy") == 1234.0
+    assert bench.profiled_traffic("update", "stale") is None
+    assert bench.profiled_traffic("update", "full") is None  # a full-source digest would differ
+    assert bench.profiled_traffic("update", "missing") is None
