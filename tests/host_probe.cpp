@@ -1,0 +1,93 @@
+// A C shim over the library's host-side tree construction (paper_2605_19928_gb300/csrc/tree.cpp)
+// for CPU tests: the tests compile it with g++ next to tree.cpp and read the public tree,
+// the stream schedule's program and load tables, and the run-out reach sources that the
+// kernels are given.  Nothing here computes; it copies HostGame fields out.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tree.h"
+
+using pcfr::HostGame;
+
+namespace {
+struct Probe {
+  HostGame g;
+  std::vector<int32_t> prog;
+  int depth = 0, max_actions = 0;
+  bool ok = false;
+};
+thread_local std::string last_error;
+}  // namespace
+
+extern "C" {
+
+// Builds one subgame; NULL on a rejected spec (probe_error() says why).
+void* probe_create(const cfr_game_spec* spec) {
+  Probe* p = new Probe();
+  if (pcfr::build_game(*spec, p->g, last_error) != 0) {
+    delete p;
+    return nullptr;
+  }
+  p->prog = pcfr::dfs_program(p->g, &p->depth, &p->max_actions, &p->ok);
+  return p;
+}
+
+void probe_destroy(void* h) { delete static_cast<Probe*>(h); }
+
+const char* probe_error(void) { return last_error.c_str(); }
+
+// sizes: n_nodes, n_hands, hstride, n_rows, program length, stack depth, max actions, ok
+void probe_sizes(void* h, int32_t out[8]) {
+  const Probe& p = *static_cast<Probe*>(h);
+  out[0] = (int32_t)p.g.nodes.size();
+  out[1] = p.g.n_hands;
+  out[2] = p.g.hstride;
+  out[3] = p.g.n_rows;
+  out[4] = (int32_t)p.prog.size();
+  out[5] = p.depth;
+  out[6] = p.max_actions;
+  out[7] = p.ok ? 1 : 0;
+}
+
+// per node (level order): parent, first_kid, n_kids, type, player, deal, row, reach_src;
+// contrib [n][2]
+void probe_nodes(void* h, int32_t* out8, double* contrib) {
+  const Probe& p = *static_cast<Probe*>(h);
+  for (size_t n = 0; n < p.g.nodes.size(); ++n) {
+    const pcfr::NodeDev& nd = p.g.nodes[n];
+    int32_t* o = out8 + 8 * n;
+    o[0] = nd.parent;
+    o[1] = nd.first_kid;
+    o[2] = nd.n_kids;
+    o[3] = nd.type;
+    o[4] = nd.player;
+    o[5] = nd.deal;
+    o[6] = nd.row;
+    o[7] = p.g.reach_src[n];
+    contrib[2 * n] = p.g.contrib[2 * n];
+    contrib[2 * n + 1] = p.g.contrib[2 * n + 1];
+  }
+}
+
+void probe_program(void* h, int32_t* out) {
+  const Probe& p = *static_cast<Probe*>(h);
+  std::memcpy(out, p.prog.data(), p.prog.size() * sizeof(int32_t));
+}
+
+// The load tables for ring halves of `half` units: returns the unit count (units copied if
+// cap allows) and fills unit_off/unit_count/chunk_off/chunk_count [4]; chunks (pairs,
+// n_chunk_ints entries) copied if chunk_cap allows.
+int probe_tables(void* h, int half, int pred, uint32_t* units, int cap, int32_t meta[16], int32_t* chunks,
+                 int chunk_cap, int32_t* n_chunk_ints) {
+  const Probe& p = *static_cast<Probe*>(h);
+  std::vector<uint32_t> u;
+  const std::vector<int32_t> ch =
+      pcfr::stream_tables(p.g, p.prog, half, pred != 0, u, &meta[0], &meta[4], &meta[8], &meta[12]);
+  if ((int)u.size() <= cap) std::memcpy(units, u.data(), u.size() * sizeof(uint32_t));
+  if ((int)ch.size() <= chunk_cap) std::memcpy(chunks, ch.data(), ch.size() * sizeof(int32_t));
+  *n_chunk_ints = (int32_t)ch.size();
+  return (int)u.size();
+}
+
+}  // extern "C"

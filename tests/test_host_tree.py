@@ -1,0 +1,269 @@
+"""The CUDA path's host-side construction (csrc/tree.cpp), on the CPU.
+
+tree.cpp builds what the kernels are given: the public tree in level order, the depth-first
+program and load tables of the stream schedule, and the run-out reach sources.  Here it is
+compiled with g++ beside a copying shim (tests/host_probe.cpp) and checked against the
+oracle's independently built trees (node by node, by action path) and against the
+definitions of the program, the loads and the chunking, re-derived in Python."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2605_19928_gb300 import capi, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2605_19928_gb300", "csrc")
+DECISION, FOLD, SHOWDOWN, CHANCE, LEAF = 0, 1, 2, 3, 4
+NO_CARD = 255
+# load descriptors: array << 29 | element offset (R, S, reach, values, prediction M)
+SHIFT, ARR_R, ARR_S, ARR_REACH, ARR_CFV, ARR_M = 29, 0, 1, 2, 3, 4
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    out = str(tmp_path_factory.mktemp("host_probe") / "libhostprobe.so")
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                    os.path.join(ROOT, "tests", "host_probe.cpp"), os.path.join(CSRC, "tree.cpp"), "-o", out],
+                   check=True, capture_output=True)
+    lib = C.CDLL(out)
+    lib.probe_create.restype = C.c_void_p
+    lib.probe_create.argtypes = [C.c_void_p]
+    lib.probe_destroy.argtypes = [C.c_void_p]
+    lib.probe_error.restype = C.c_char_p
+    for f in ("probe_sizes", "probe_nodes", "probe_program", "probe_tables"):
+        getattr(lib, f).argtypes = None
+    return lib
+
+
+class Built:
+    def __init__(self, lib, spec):
+        self.lib = lib
+        s, self._keep = capi.make_spec(spec)
+        self.h = lib.probe_create(C.byref(s))
+        assert self.h, lib.probe_error()
+        sz = np.zeros(8, np.int32)
+        lib.probe_sizes(C.c_void_p(self.h), sz.ctypes.data_as(C.c_void_p))
+        (self.n_nodes, self.n_hands, self.hstride, self.n_rows, n_prog, self.depth, self.max_actions,
+         self.ok) = (int(x) for x in sz)
+        self.nodes = np.zeros((self.n_nodes, 8), np.int32)
+        self.contrib = np.zeros((self.n_nodes, 2), np.float64)
+        lib.probe_nodes(C.c_void_p(self.h), self.nodes.ctypes.data_as(C.c_void_p),
+                        self.contrib.ctypes.data_as(C.c_void_p))
+        self.prog = np.zeros(n_prog, np.int32)
+        lib.probe_program(C.c_void_p(self.h), self.prog.ctypes.data_as(C.c_void_p))
+        (self.parent, self.first, self.n_kids, self.type, self.player, self.deal, self.row,
+         self.reach_src) = (self.nodes[:, k] for k in range(8))
+
+    def kids(self, n):
+        return list(range(self.first[n], self.first[n] + self.n_kids[n]))
+
+    def tables(self, half, pred):
+        cap = 1 << 20
+        units = np.zeros(cap, np.uint32)
+        meta = np.zeros(16, np.int32)
+        chunks = np.zeros(cap, np.int32)
+        n_ch = C.c_int32()
+        n = self.lib.probe_tables(C.c_void_p(self.h), C.c_int(half), C.c_int(int(pred)),
+                                  units.ctypes.data_as(C.c_void_p), C.c_int(cap), meta.ctypes.data_as(C.c_void_p),
+                                  chunks.ctypes.data_as(C.c_void_p), C.c_int(cap), C.byref(n_ch))
+        assert n <= cap and n_ch.value <= cap
+        return units[:n], meta, chunks[:n_ch.value]
+
+    def close(self):
+        self.lib.probe_destroy(C.c_void_p(self.h))
+
+
+def is_end(t):
+    return t in (FOLD, SHOWDOWN, LEAF)
+
+
+SPECS = {
+    "kuhn": synth.kuhn,
+    "leduc": synth.leduc,
+    "river": lambda: synth.river_subgame(n_hands=12, seed=3, range_seed=4, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN),
+                                         max_raises=4),
+    "turn": lambda: synth.turn_subgame(n_hands=10, seed=5, range_seed=6, bet_sizes=(1.0, synth.ALL_IN),
+                                       max_raises=2),
+    "turn_limited": lambda: _limited(synth.turn_subgame(n_hands=10, seed=5, range_seed=6,
+                                                        bet_sizes=(0.5, synth.ALL_IN), max_raises=2)),
+    "flop": lambda: synth.flop_subgame(n_hands=4, seed=3, range_seed=4, bet_sizes=(synth.ALL_IN,), max_raises=1),
+    "flop_limited": lambda: _limited(synth.flop_subgame(n_hands=6, seed=7, range_seed=8, bet_sizes=(1.0, synth.ALL_IN),
+                                                        max_raises=1)),
+}
+
+
+def _limited(spec):
+    spec.depth_limit = 1
+    return spec
+
+
+@pytest.mark.parametrize("case", list(SPECS))
+def test_public_tree_matches_the_oracle(probe, oracle_mod, case):
+    spec = SPECS[case]()
+    t = Built(probe, spec)
+    o = oracle_mod.Oracle(spec, variant="dcfr", threads=1)
+    try:
+        assert t.n_nodes == o.n_nodes
+        info = o.nodes()
+        # walk both trees by action path
+        todo = [(0, 0)]
+        seen = 0
+        while todo:
+            g, n = todo.pop()
+            seen += 1
+            oi = info[n]
+            assert t.type[g] == oi["type"], (case, g)
+            assert t.n_kids[g] == oi["n_actions"], (case, g)
+            if t.type[g] in (DECISION, FOLD):
+                assert t.player[g] == oi["player"], (case, g)
+            assert tuple(t.contrib[g]) == pytest.approx(oi["contrib"], abs=1e-9), (case, g)
+            deal = -1 if t.deal[g] == NO_CARD else int(t.deal[g])
+            assert deal == oi["deal"], (case, g)
+            kids = t.kids(g)
+            assert all(t.parent[k] == g for k in kids)
+            todo.extend(zip(kids, oi["kids"]))
+        assert seen == t.n_nodes
+        # level order: parents come before children, children consecutive
+        assert t.parent[0] == -1 and np.all(t.parent[1:] < np.arange(1, t.n_nodes))
+        # regret rows: each decision node's actions, player 0's rows first
+        dec = np.flatnonzero(t.type == DECISION)
+        rows = sorted((int(t.row[n]), int(t.n_kids[n]), int(t.player[n])) for n in dec)
+        assert sum(r[1] for r in rows) == t.n_rows
+        start = 0
+        for r, a, _ in rows:
+            assert r == start
+            start += a
+        players = [p for _, _, p in rows]
+        assert players == sorted(players)
+        if case.endswith("limited"):
+            assert (t.type == LEAF).any()
+    finally:
+        t.close()
+
+
+@pytest.mark.parametrize("case", ["leduc", "river", "turn", "flop", "flop_limited"])
+def test_program_is_the_inner_nodes_in_preorder(probe, case):
+    t = Built(probe, SPECS[case]())
+    try:
+        pre, todo = [], [0]
+        while todo:
+            n = todo.pop()
+            if is_end(t.type[n]):
+                continue
+            pre.append(n)
+            todo.extend(reversed(t.kids(n)))
+        assert t.prog.tolist() == pre
+        # the stacks the kernel keeps: top-down pops a node's reach and pushes its inner
+        # children's; bottom-up pushes a node's value and pops its inner children's
+        inner = [sum(not is_end(t.type[k]) for k in t.kids(n)) for n in pre]
+        sp, most = 1, 1
+        for c in inner:
+            sp += c - 1
+            most = max(most, sp)
+        assert sp == 0
+        sp = 0
+        for c in reversed(inner):
+            sp += 1 - c
+            most = max(most, sp)
+        assert sp == 1
+        assert t.depth == most
+        assert t.max_actions == max(int(t.n_kids[n]) for n in pre if t.type[n] == DECISION)
+        # a chance node's children are all inner or all terminal
+        for n in pre:
+            if t.type[n] == CHANCE:
+                assert len({is_end(t.type[k]) for k in t.kids(n)}) == 1
+        assert t.ok == 1
+    finally:
+        t.close()
+
+
+def expected_loads(t, n, p, backward, pred):
+    """The loads of node n in one pass: bottom-up, the values of its terminal children in
+    child order, then at p's decision nodes R (and M) and S of each action and p's reach;
+    top-down, R (and M) of each action at p's decision nodes."""
+    S = t.hstride
+    out = []
+    if backward:
+        out += [ARR_CFV << SHIFT | k * S for k in t.kids(n) if is_end(t.type[k])]
+    if t.type[n] == DECISION and t.player[n] == p:
+        rows = range(t.row[n], t.row[n] + t.n_kids[n])
+        out += [ARR_R << SHIFT | r * S for r in rows]
+        if pred:
+            out += [ARR_M << SHIFT | r * S for r in rows]
+        if backward:
+            out += [ARR_S << SHIFT | r * S for r in rows]
+            out.append(ARR_REACH << SHIFT | n * S)
+    return out
+
+
+@pytest.mark.parametrize("case,pred", [("river", False), ("river", True), ("turn", False), ("flop", False),
+                                       ("turn_limited", True)])
+def test_load_tables_and_chunks_follow_the_definitions(probe, case, pred):
+    t = Built(probe, SPECS[case]())
+    try:
+        N = len(t.prog)
+        most = max(len(expected_loads(t, n, p, True, pred)) for n in t.prog for p in (0, 1))
+        for half in (most, most + 5):
+            units, meta, chunks = t.tables(half, pred)
+            unit_off, unit_count, chunk_off, chunk_count = meta[0:4], meta[4:8], meta[8:12], meta[12:16]
+            for q in range(4):
+                p, backward = q & 1, q < 2
+                order = list(reversed(t.prog)) if backward else list(t.prog)
+                per_node = [expected_loads(t, n, p, backward, pred) for n in order]
+                want = [u for loads in per_node for u in loads]
+                got = units[unit_off[q]:unit_off[q] + unit_count[q]].tolist()
+                assert got == want, (case, q)
+                # chunks: (first node position, first unit) pairs, then (N, unit count)
+                pairs = chunks[2 * chunk_off[q]:2 * (chunk_off[q] + chunk_count[q] + 1)].reshape(-1, 2)
+                assert pairs[0].tolist() == [0, 0] and pairs[-1].tolist() == [N, unit_count[q]]
+                starts = np.concatenate([[0], np.cumsum([len(x) for x in per_node])])
+                for c in range(len(pairs) - 1):
+                    k0, k1 = pairs[c, 0], pairs[c + 1, 0]
+                    assert k0 < k1 and pairs[c, 1] == starts[k0]
+                    assert starts[k1] - starts[k0] <= half  # one ring half holds the chunk
+                    if c + 1 < len(pairs) - 1:  # greedy: the next node did not fit
+                        assert starts[k1] - starts[k0] + len(per_node[k1]) > half
+    finally:
+        t.close()
+
+
+@pytest.mark.parametrize("case", ["turn", "flop", "flop_limited"])
+def test_run_out_reach_sources(probe, case):
+    """A node's reach source is the top chance node of the all-in run-out it lies in (its
+    reach up to zeroing the hands that hold a dealt card), the node itself elsewhere."""
+    t = Built(probe, SPECS[case]())
+    try:
+        sub_has_action = np.zeros(t.n_nodes, bool)
+        for n in range(t.n_nodes - 1, -1, -1):  # children come after their parent
+            sub_has_action[n] = t.type[n] in (DECISION, LEAF) or any(sub_has_action[k] for k in t.kids(n))
+        redirected = 0
+        for n in range(t.n_nodes):
+            s = t.reach_src[n]
+            if s == n:
+                continue
+            redirected += 1
+            assert t.type[n] in (CHANCE, SHOWDOWN, FOLD)
+            assert t.type[s] == CHANCE and t.reach_src[s] == s
+            assert not sub_has_action[s]  # nobody acts below the run-out's top
+            assert t.parent[s] < 0 or t.type[t.parent[s]] != CHANCE
+            a = t.parent[n]
+            while a != s:  # only chance nodes between them
+                assert t.type[a] == CHANCE
+                a = t.parent[a]
+        # every chance or showdown node below a chance node is redirected
+        for n in range(1, t.n_nodes):
+            if t.type[t.parent[n]] == CHANCE and t.type[n] in (CHANCE, SHOWDOWN):
+                assert t.reach_src[n] != n
+        if case != "turn":
+            assert redirected > 0
+    finally:
+        t.close()
