@@ -90,4 +90,32 @@ int probe_tables(void* h, int half, int pred, uint32_t* units, int cap, int32_t 
   return (int)u.size();
 }
 
+// game, deck, hand_size, n_boards
+void probe_game(void* h, int32_t out[4]) {
+  const Probe& p = *static_cast<Probe*>(h);
+  out[0] = p.g.game;
+  out[1] = p.g.deck;
+  out[2] = p.g.hand_size;
+  out[3] = p.g.n_boards;
+}
+
+// public cards at every node (bit c = card c)
+void probe_boards(void* h, uint64_t* out) {
+  const Probe& p = *static_cast<Probe*>(h);
+  for (size_t n = 0; n < p.g.nodes.size(); ++n) out[n] = p.g.nodes[n].board;
+}
+
+// The terminal kernel's packed tables (one block per showdown board): offsets of the
+// sections (clh, cards, cloff, fold_len, perm, gs, ge, lo, hi, len) and the blocks, copied
+// if cap allows; returns the number of uint16 entries.
+int probe_term_tables(void* h, int32_t tt_out[10], uint16_t* out, int cap) {
+  const Probe& p = *static_cast<Probe*>(h);
+  const pcfr::TermTab tt(p.g.n_hands, p.g.hand_size, p.g.deck);
+  const int32_t v[10] = {tt.clh, tt.cards, tt.cloff, tt.fold_len, tt.perm, tt.gs, tt.ge, tt.lo, tt.hi, tt.len};
+  std::memcpy(tt_out, v, sizeof(v));
+  const std::vector<uint16_t> t = pcfr::pack_term_tables(p.g);
+  if ((int)t.size() <= cap) std::memcpy(out, t.data(), t.size() * sizeof(uint16_t));
+  return (int)t.size();
+}
+
 }  // extern "C"

@@ -1,10 +1,12 @@
 """The CUDA path's host-side construction (csrc/tree.cpp), on the CPU.
 
 tree.cpp builds what the kernels are given: the public tree in level order, the depth-first
-program and load tables of the stream schedule, and the run-out reach sources.  Here it is
-compiled with g++ beside a copying shim (tests/host_probe.cpp) and checked against the
-oracle's independently built trees (node by node, by action path) and against the
-definitions of the program, the loads and the chunking, re-derived in Python."""
+program and load tables of the stream schedule, the run-out reach sources, and the
+showdown tables of the O(n) terminal evaluation (Section 4.3: strength-sorted order, tie
+groups, per-card hand lists).  Here it is compiled with g++ beside a copying shim
+(tests/host_probe.cpp) and checked against the oracle's independently built trees (node
+by node, by action path) and against the definitions of the program, the loads, the
+chunking and the tables, re-derived in Python."""
 from __future__ import annotations
 
 import ctypes as C
@@ -265,5 +267,87 @@ def test_run_out_reach_sources(probe, case):
                 assert t.reach_src[n] != n
         if case != "turn":
             assert redirected > 0
+    finally:
+        t.close()
+
+
+TABLE_SPECS = {
+    "river": SPECS["river"],
+    "river_ranked": lambda: _ranked_river(),
+    "turn": SPECS["turn"],
+    "turn_ranked": lambda: synth.ranked_turn_subgame(n_hands=40, seed=2, range_seed=3, bet_sizes=(1.0, synth.ALL_IN),
+                                                     max_raises=1),
+    "flop": SPECS["flop"],
+}
+
+
+def _ranked_river():
+    g = synth.river_subgame(n_hands=60, seed=9, range_seed=10, bet_sizes=(synth.ALL_IN,), max_raises=1)
+    g.strength = synth.rank_strength(g.board, g.hands)[None, :].astype(np.int32)  # many ties
+    return g
+
+
+@pytest.mark.parametrize("case", list(TABLE_SPECS))
+def test_showdown_tables_follow_their_definitions(probe, case):
+    """Per showdown board: perm sorts the hands by strength, [gs, ge) is each hand's tie
+    group, clh / cloff list the hands holding each card in sorted order, and lo / hi give,
+    per (hand, card), the first list entry at or after the tie group's start / end."""
+    spec = TABLE_SPECS[case]()
+    t = Built(probe, spec)
+    try:
+        meta = np.zeros(4, np.int32)
+        probe.probe_game(C.c_void_p(t.h), meta.ctypes.data_as(C.c_void_p))
+        _, deck, k, n_boards = (int(x) for x in meta)
+        tt = np.zeros(10, np.int32)
+        n = probe.probe_term_tables(C.c_void_p(t.h), tt.ctypes.data_as(C.c_void_p), None, C.c_int(0))
+        tab = np.zeros(n, np.uint16)
+        probe.probe_term_tables(C.c_void_p(t.h), tt.ctypes.data_as(C.c_void_p), tab.ctypes.data_as(C.c_void_p),
+                                C.c_int(n))
+        clh, cards, cloff, _, perm, gs, ge, lo, hi, L = (int(x) for x in tt)
+        assert n == n_boards * L and L % 8 == 0
+        boards = np.zeros(t.n_nodes, np.uint64)
+        probe.probe_boards(C.c_void_p(t.h), boards.ctypes.data_as(C.c_void_p))
+        H = spec.n_hands
+        hands = spec.hands.astype(np.int64)
+        base = set(int(c) for c in spec.board)
+        checked = set()
+        for nd in np.flatnonzero(t.type == SHOWDOWN):
+            b = int(t.row[nd])
+            if b in checked:
+                continue
+            checked.add(b)
+            dealt = sorted(c for c in range(52) if (int(boards[nd]) >> c) & 1 and c not in base)
+            if len(base) == 5:
+                srow = spec.strength[0]
+            elif len(base) == 4:
+                srow = spec.strength[dealt[0]]
+            else:
+                srow = spec.strength[dealt[0] * 52 + dealt[1]]
+            blk = tab[b * L:(b + 1) * L].astype(np.int64)
+            P = blk[perm:perm + H]
+            assert sorted(P.tolist()) == list(range(H))
+            s_sorted = srow[P]
+            assert np.all(np.diff(s_sorted) >= 0) or np.all(np.diff(s_sorted) <= 0)
+            pos = np.empty(H, np.int64)
+            pos[P] = np.arange(H)
+            for h in range(H):
+                group = np.flatnonzero(s_sorted == srow[h])
+                assert (blk[gs + h], blk[ge + h]) == (group[0], group[-1] + 1), (case, b, h)
+            for c in range(deck):
+                lst = blk[clh + blk[cloff + c]:clh + blk[cloff + c + 1]]
+                holders = [h for h in range(H) if c in hands[h]]
+                assert sorted(lst.tolist()) == sorted(holders)
+                assert np.all(np.diff(pos[lst]) > 0)  # rank-sorted order
+            for h in range(H):
+                for s in range(k):
+                    c = int(hands[h, s])
+                    lst_pos = pos[blk[clh + blk[cloff + c]:clh + blk[cloff + c + 1]]]
+                    first_lo = blk[cloff + c] + int(np.searchsorted(lst_pos, blk[gs + h], side="left"))
+                    first_hi = blk[cloff + c] + int(np.searchsorted(lst_pos, blk[ge + h], side="left"))
+                    assert blk[lo + 2 * h + s] == first_lo and blk[hi + 2 * h + s] == first_hi, (case, b, h, s)
+                c1 = int(blk[cards + h]) & 0xFF
+                c2 = int(blk[cards + h]) >> 8
+                assert (c1, c2) == (int(hands[h, 0]), int(hands[h, 1]))
+        assert len(checked) == n_boards or case.startswith("river")
     finally:
         t.close()
