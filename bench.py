@@ -335,7 +335,10 @@ def run_reference(args):
     value = total_iters / total_s
     unit = "subgame iter/s" if batch else "iter/s"
     what = f"subgames {picks} of the {len(specs)}-subgame batch in turn" if batch else "the 1081-hand river subgame"
-    config = batch_config(args, specs, [{"nodes": 0}]) if batch else workload_config(args, specs[0], None)
+    from oracle.oracle import Oracle
+    nodes = [Oracle(s, variant="dcfr", threads=1).n_nodes for s in specs]  # the oracle's own trees
+    config = (batch_config(args, specs, [{"nodes": n} for n in nodes]) if batch
+              else workload_config(args, specs[0], nodes[0]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
