@@ -186,7 +186,8 @@ def solve_depth_limited(spec, weights, biases, iters: int, opts=None, tol: float
                         judge_rows: int = 64, judge_iters: int = 300, seed: int = 0, stream=None) -> Served:
     """Solve `spec` (depth_limit 1) with network leaves for `iters` iterations, judge the
     network on its own leaf rows, and keep the result if the reach-weighted error is at most
-    `tol` (pot units); otherwise solve the full-depth subgame for `iters` iterations."""
+    `tol` (pot units); otherwise -- or if no leaf row could be judged -- solve the full-depth
+    subgame for `iters` iterations."""
     if spec.depth_limit != 1:
         raise ValueError("solve_depth_limited takes a depth-limited subgame (depth_limit 1)")
     opts = opts if opts is not None else capi.make_opts("dcfr")

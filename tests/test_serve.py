@@ -1,6 +1,7 @@
 """Host logic of the served depth-limited solve (learned leaves judged against exact
-continuation solves, Section 3): continuation specs, leaf boards, row order and the error
-statistic.  No GPU: the tree walk runs on a fake public tree."""
+continuation solves, Section 3): continuation specs, leaf boards, row order, the error
+statistic, and the keep-or-fall-back decision with its handle bookkeeping.  No GPU: the
+tree walk runs on a fake public tree and the decision on a fake C ABI."""
 from __future__ import annotations
 
 import numpy as np
@@ -100,3 +101,71 @@ def test_solve_depth_limited_wants_a_depth_limit():
     spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=0)
     with pytest.raises(ValueError):
         serve.solve_depth_limited(spec, None, None, 10)
+
+
+class FakeABI:
+    """Records the handles the served solve creates and destroys (no GPU)."""
+
+    def __init__(self, fail_iterate=False):
+        self.live, self.created, self.fail_iterate = set(), [], fail_iterate
+
+    def cfr_tree_create(self, spec, opts, stream=None):
+        h = ("exact" if spec.depth_limit == 0 else "learned", len(self.created))
+        self.created.append(h)
+        self.live.add(h)
+        return h
+
+    def cfr_tree_destroy(self, h):
+        self.live.discard(h)
+
+    def cfr_iterate(self, h, n):
+        if self.fail_iterate:
+            raise RuntimeError("iterate failed")
+
+    def noop(self, *a, **k):
+        return None
+
+
+def _fake(monkeypatch, error, rows=8, fail_iterate=False):
+    abi = FakeABI(fail_iterate)
+    for name in ("cfr_tree_create", "cfr_tree_destroy", "cfr_iterate"):
+        monkeypatch.setattr(serve.capi, name, getattr(abi, name))
+    for name in ("cfr_set_leaf_net", "cfr_exploitability", "cfr_sync"):
+        monkeypatch.setattr(serve.capi, name, abi.noop)
+    monkeypatch.setattr(serve.capi, "make_opts", lambda *a, **k: None)
+    j = serve.Judgement(rows, 100, error, error, error, 0.1, 1.0)
+    monkeypatch.setattr(serve, "judge_leaves", lambda *a, **k: j)
+    return abi
+
+
+def test_served_solve_keeps_the_learned_form_within_tolerance(monkeypatch):
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
+    abi = _fake(monkeypatch, error=5e-4)
+    s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3)
+    assert s.form == "learned" and s.tree[0] == "learned" and abi.live == {s.tree}
+    assert s.ms["exact"] == 0.0
+
+
+def test_served_solve_falls_back_above_tolerance_or_without_rows(monkeypatch):
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
+    for error, rows in ((2e-3, 8), (0.0, 0)):  # too large; nothing could be judged
+        abi = _fake(monkeypatch, error=error, rows=rows)
+        s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3)
+        assert s.form == "exact" and s.tree[0] == "exact"
+        assert abi.live == {s.tree}  # the learned handle was released
+        assert spec.depth_limit == 1  # the caller's spec is left as it was
+
+
+def test_served_solve_releases_its_handle_on_errors(monkeypatch):
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
+    abi = _fake(monkeypatch, error=0.0, fail_iterate=True)
+    with pytest.raises(RuntimeError):
+        serve.solve_depth_limited(spec, None, None, 10)
+    assert abi.created and not abi.live
+
+
+def test_judge_without_leaves_judges_nothing(monkeypatch):
+    monkeypatch.setattr(serve.capi, "cfr_leaf_info", lambda tree: [])
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
+    j = serve.judge_leaves(None, spec)
+    assert (j.rows, j.candidates) == (0, 0)
