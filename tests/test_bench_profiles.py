@@ -1,5 +1,7 @@
 """The benchmark's link to the committed ncu summaries: a summary's DRAM counters are used
-only while the kernel sources it was taken on are unchanged (per-section digests)."""
+only while the kernel sources it was taken on are unchanged (per-section digests), and the
+algorithmic bytes the summaries and the roofline divide by follow the per-unit model on the
+workloads' trees."""
 from __future__ import annotations
 
 import os
@@ -59,3 +61,36 @@ def test_profiled_traffic_needs_a_matching_digest(tmp_path, monkeypatch):
     assert bench.profiled_traffic("update", "stale") is None
     assert bench.profiled_traffic("update", "full") is None  # a full-source digest would differ
     assert bench.profiled_traffic("update", "missing") is None
+
+
+def _oracle_shape(om, spec):
+    """The bench's tree shape (nodes, hands, regret rows per player, terminals), taken from
+    the oracle's own tree."""
+    o = om.Oracle(spec, variant="dcfr", threads=1)
+    rows, ends = [0, 0], 0
+    for nd in o.nodes():
+        if nd["type"] == 0:
+            rows[nd["player"]] += nd["n_actions"]
+        elif nd["type"] in (1, 2, 4):
+            ends += 1
+    return {"nodes": o.n_nodes, "hands": o.n_hands, "rows": rows, "terminals": ends}
+
+
+def _profile_figure(name, pattern):
+    text = open(os.path.join(ROOT, "profiles", name)).read()
+    return int(re.search(pattern, text).group(1).replace(",", ""))
+
+
+def test_roofline_numerators_of_the_summaries(oracle_mod):
+    """The algorithmic bytes the committed summaries divide by: the benchmark's per-unit
+    model applied to the workloads' trees, built here by the oracle."""
+    from paper_2605_19928_gb300 import synth
+    river = _oracle_shape(oracle_mod, bench.workload_spec(0))
+    assert river["hands"] == 1081
+    want = _profile_figure("update_river1081.md", r"algorithmic bytes per launch \| ([\d,]+) B")
+    assert bench.algorithmic_bytes(river, "update", 8) == want
+    batch = [_oracle_shape(oracle_mod, s) for s in synth.batch_rivers(256)]
+    total = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch)
+    half = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch[:128])
+    text = open(os.path.join(ROOT, "profiles", "update_batch256.md")).read()
+    assert f"{int(half):,}" in text and f"{int(total):,}" in text
