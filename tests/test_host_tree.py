@@ -348,6 +348,34 @@ def test_showdown_tables_follow_their_definitions(probe, case):
                 c1 = int(blk[cards + h]) & 0xFF
                 c2 = int(blk[cards + h]) >> 8
                 assert (c1, c2) == (int(hands[h, 0]), int(hands[h, 1]))
+            _check_sorted_prefix_sums(blk, clh, cloff, perm, gs, ge, lo, hi, H, hands, srow,
+                                      np.sign(s_sorted[-1] - s_sorted[0]))
         assert len(checked) == n_boards or case.startswith("river")
     finally:
         t.close()
+
+
+def _check_sorted_prefix_sums(blk, clh, cloff, perm, gs, ge, lo, hi, H, hands, srow, order):
+    """Section 4.3, Stage 4 on these tables: with q the opponent reach, W(h) (mass of the
+    opponent hands weaker than h sharing no card with it) is the prefix of q before h's tie
+    group minus, for each of h's cards, the prefix of that card's list up to lo; L(h)
+    (stronger) is the suffix after the group minus the card lists' suffixes from hi.
+    Compared with a direct sum over the opponent hands."""
+    rng = np.random.default_rng(H)
+    q = rng.random(H) * (rng.random(H) < 0.8)
+    P = np.concatenate([[0.0], np.cumsum(q[blk[perm:perm + H]])])
+    T = P[-1]
+    weaker_first = order >= 0  # sorted by increasing strength
+    for h in range(H):
+        pre, post = P[blk[gs + h]], T - P[blk[ge + h]]
+        for s_ in range(2):
+            c = int(hands[h, s_])
+            lst = blk[clh + blk[cloff + c]:clh + blk[cloff + c + 1]]
+            cp = np.concatenate([[0.0], np.cumsum(q[lst])])
+            pre -= cp[blk[lo + 2 * h + s_] - blk[cloff + c]]
+            post -= cp[-1] - cp[blk[hi + 2 * h + s_] - blk[cloff + c]]
+        W, L = (pre, post) if weaker_first else (post, pre)
+        disjoint = ~np.isin(hands, hands[h]).any(axis=1)
+        W_ref = q[disjoint & (srow < srow[h])].sum()
+        L_ref = q[disjoint & (srow > srow[h])].sum()
+        assert W == pytest.approx(W_ref, abs=1e-12) and L == pytest.approx(L_ref, abs=1e-12), h
