@@ -350,6 +350,8 @@ def test_showdown_tables_follow_their_definitions(probe, case):
                 assert (c1, c2) == (int(hands[h, 0]), int(hands[h, 1]))
             _check_sorted_prefix_sums(blk, clh, cloff, perm, gs, ge, lo, hi, H, hands, srow,
                                       np.sign(s_sorted[-1] - s_sorted[0]))
+            if b == 0:
+                _check_fold_inclusion_exclusion(blk, clh, cloff, H, hands, deck)
         assert len(checked) == n_boards or case.startswith("river")
     finally:
         t.close()
@@ -379,3 +381,15 @@ def _check_sorted_prefix_sums(blk, clh, cloff, perm, gs, ge, lo, hi, H, hands, s
         W_ref = q[disjoint & (srow < srow[h])].sum()
         L_ref = q[disjoint & (srow > srow[h])].sum()
         assert W == pytest.approx(W_ref, abs=1e-12) and L == pytest.approx(L_ref, abs=1e-12), h
+
+
+def _check_fold_inclusion_exclusion(blk, clh, cloff, H, hands, deck):
+    """Section 4.3, Stages 2-3 on the card lists the fold nodes read: the opponent mass
+    sharing no card with h is T - C(c1) - C(c2) + q(h), C(c) the mass of card c's list."""
+    rng = np.random.default_rng(H + 1)
+    q = rng.random(H)
+    C_ = np.array([q[blk[clh + blk[cloff + c]:clh + blk[cloff + c + 1]]].sum() for c in range(deck)])
+    for h in range(H):
+        M = q.sum() - C_[hands[h, 0]] - C_[hands[h, 1]] + q[h]
+        disjoint = ~np.isin(hands, hands[h]).any(axis=1)
+        assert M == pytest.approx(q[disjoint].sum(), abs=1e-12), h
