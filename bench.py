@@ -685,7 +685,8 @@ def run_leaf(args):
     e_leaf_own, _ = capi.cfr_exploitability_result(L)
     # the served form: the network judged on 64 of its own leaf rows against exact river
     # solves of their continuations, falling back to the exact subgame above the tolerance
-    judge = serve.judge_leaves(L, spec_leaf, n_rows=64, iters=300, seed=rank, stream=stream.cuda_stream)
+    judge = serve.judge_leaves(L, spec_leaf, n_rows=64, iters=300, seed=rank, stream=stream.cuda_stream,
+                               evaluated=True)
     exact_steps = 1 if flop else max(1, args.steps // 4)
     t_exact = timed(E, exact_steps, 1)
     e_exact, _ = capi.cfr_exploitability_result(E)

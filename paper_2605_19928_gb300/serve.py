@@ -123,12 +123,16 @@ def row_errors(y_net, y_exact, mask, ranges, hands) -> tuple[float, float, int]:
     return tot, weighted, cnt
 
 
-def judge_leaves(tree, spec, n_rows: int = 64, iters: int = 300, seed: int = 0, stream=None) -> Judgement:
-    """Judge the network of a depth-limited handle whose average strategy has just been
-    evaluated (cfr_exploitability was the last pass): sample up to n_rows leaf rows reached
-    by both players, solve their continuations exactly in one batched handle (`iters` DCFR
-    iterations, FP32 values) and compare the network's values on the same rows."""
+def judge_leaves(tree, spec, n_rows: int = 64, iters: int = 300, seed: int = 0, stream=None,
+                 evaluated: bool = False) -> Judgement:
+    """Judge the network of a depth-limited handle at its average strategy: sample up to
+    n_rows leaf rows reached by both players, solve their continuations exactly in one
+    batched handle (`iters` DCFR iterations, FP32 values) and compare the network's values
+    on the same rows.  The leaf reach comes from an exploitability pass, run here unless
+    `evaluated` says that cfr_exploitability was the handle's last pass."""
     t0 = time.perf_counter()
+    if not evaluated:
+        capi.cfr_exploitability(tree)
     cap = spec.pot / 2.0 + spec.stack
     hands = np.asarray(spec.hands, np.int64)
     leaves, pool = [], []
@@ -199,7 +203,7 @@ def solve_depth_limited(spec, weights, biases, iters: int, opts=None, tol: float
         capi.cfr_iterate(tree, iters)
         capi.cfr_exploitability(tree)
         ms["learned"] = 1000.0 * (time.perf_counter() - t0)
-        j = judge_leaves(tree, spec, judge_rows, judge_iters, seed, stream)
+        j = judge_leaves(tree, spec, judge_rows, judge_iters, seed, stream, evaluated=True)
     except BaseException:
         capi.cfr_tree_destroy(tree)
         raise

@@ -165,7 +165,12 @@ def test_served_solve_releases_its_handle_on_errors(monkeypatch):
 
 
 def test_judge_without_leaves_judges_nothing(monkeypatch):
+    passes = []
     monkeypatch.setattr(serve.capi, "cfr_leaf_info", lambda tree: [])
+    monkeypatch.setattr(serve.capi, "cfr_exploitability", lambda tree: passes.append(tree))
     spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
-    j = serve.judge_leaves(None, spec)
+    j = serve.judge_leaves("handle", spec)
     assert (j.rows, j.candidates) == (0, 0)
+    assert passes == ["handle"]  # the leaf reach comes from a fresh exploitability pass
+    serve.judge_leaves("handle", spec, evaluated=True)
+    assert passes == ["handle"]
