@@ -174,3 +174,30 @@ def test_judge_without_leaves_judges_nothing(monkeypatch):
     assert passes == ["handle"]  # the leaf reach comes from a fresh exploitability pass
     serve.judge_leaves("handle", spec, evaluated=True)
     assert passes == ["handle"]
+
+
+def test_exact_targets_of_a_check_down_river(oracle_mod):
+    """The judge's exact values per unit pot (leafnet_train.example, also the training
+    target) on a river with no betting: hand h of player i is worth pot/2 x (W - L) / Z,
+    W / L the opponent reach weaker / stronger than h sharing no card with it, so the
+    target is (W - L) / (2 M) with M the opponent reach sharing no card with h."""
+    from paper_2605_19928_gb300 import leafnet_train
+    spec = synth.river_subgame(n_hands=40, seed=6, range_seed=7, max_raises=0)
+    spec.strength = synth.rank_strength(spec.board, spec.hands)[None, :].astype(np.int32)  # ties
+    o = oracle_mod.Oracle(spec, variant="dcfr", threads=1)
+    v = []
+    for i in (0, 1):
+        o.values_current(i)
+        v.append(o.cfv(i, 0))
+    _, y, m = leafnet_train.example(spec, v)
+    r = spec.ranges.astype(np.float64)
+    r = r / r.sum(axis=1, keepdims=True)
+    s = spec.strength[0]
+    sl = leafnet_train.slot_of(spec.hands)
+    for i in (0, 1):
+        for h in range(spec.n_hands):
+            dis = ~np.isin(spec.hands, spec.hands[h]).any(axis=1)
+            q = r[1 - i] * dis
+            W, L, M = q[s < s[h]].sum(), q[s > s[h]].sum(), q.sum()
+            assert m[i * serve.SLOTS + sl[h]] == 1.0
+            assert y[i * serve.SLOTS + sl[h]] == pytest.approx((W - L) / (2 * M), rel=1e-5, abs=1e-7)
