@@ -274,10 +274,22 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
       for (int h = 0; h < H; ++h) g.range[p][h] = spec.range[p][h] / s;
     }
   }
+  // Z = sum of r0(a) r1(b) over the pairs of hands sharing no card, in O(H): for each a,
+  // player 1's mass minus the mass of the hands holding one of a's cards (inclusion-
+  // exclusion; a two-card hand holding both of a's cards is a itself, hands are distinct)
+  std::vector<double> card_mass((size_t)g.deck, 0.0);
+  double total1 = 0.0;
+  for (int b = 0; b < H; ++b) {
+    total1 += g.range[1][b];
+    for (int t = 0; t < g.hand_size; ++t) card_mass[g.hand_cards[2 * (size_t)b + t]] += g.range[1][b];
+  }
   double Z = 0.0;
-  for (int a = 0; a < H; ++a)
-    for (int b = 0; b < H; ++b)
-      if (!(g.hand_mask[a] & g.hand_mask[b])) Z += g.range[0][a] * g.range[1][b];
+  for (int a = 0; a < H; ++a) {
+    double m = total1;
+    for (int t = 0; t < g.hand_size; ++t) m -= card_mass[g.hand_cards[2 * (size_t)a + t]];
+    if (g.hand_size == 2) m += g.range[1][a];
+    Z += g.range[0][a] * std::max(m, 0.0);
+  }
   if (!(Z > 0.0)) {
     err = "no pair of hands can be dealt with positive probability";
     return CFR_EINVAL;
@@ -460,18 +472,22 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     }
     int32_t* lo = &g.cl_lo[(size_t)b * H * 2];
     int32_t* hi = &g.cl_hi[(size_t)b * H * 2];
-    for (int h = 0; h < H; ++h)
-      for (int t = 0; t < k; ++t) {
-        const int c = g.hand_cards[2 * h + t];
-        int a = off[c], z = off[c + 1];
-        // entries of card c's list are in increasing sorted position
-        int x = a;
+    // for the hands holding card c (its list, in increasing sorted position, so their tie
+    // groups' bounds never decrease): the first entry at or after gs and at or after ge,
+    // found by two pointers walking the list once
+    for (int c = 0; c < g.deck; ++c) {
+      const int a = off[c], z = off[c + 1];
+      int x = a, y = a;
+      for (int j = a; j < z; ++j) {
+        const int h = lst[j];
         while (x < z && pos[lst[x]] < gs[h]) ++x;
-        lo[2 * h + t] = x;
-        int y = x;
+        if (y < x) y = x;
         while (y < z && pos[lst[y]] < ge[h]) ++y;
+        const int t = g.hand_cards[2 * (size_t)h] == c ? 0 : 1;
+        lo[2 * h + t] = x;
         hi[2 * h + t] = y;
       }
+    }
   }
   return CFR_OK;
 }

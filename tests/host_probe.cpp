@@ -90,6 +90,9 @@ int probe_tables(void* h, int half, int pred, uint32_t* units, int cap, int32_t 
   return (int)u.size();
 }
 
+// the deal normaliser Z (sum of r0 r1 over the pairs of hands sharing no card)
+double probe_Z(void* h) { return static_cast<Probe*>(h)->g.Z; }
+
 // game, deck, hand_size, n_boards
 void probe_game(void* h, int32_t out[4]) {
   const Probe& p = *static_cast<Probe*>(h);

@@ -393,3 +393,25 @@ def _check_fold_inclusion_exclusion(blk, clh, cloff, H, hands, deck):
         M = q.sum() - C_[hands[h, 0]] - C_[hands[h, 1]] + q[h]
         disjoint = ~np.isin(hands, hands[h]).any(axis=1)
         assert M == pytest.approx(q[disjoint].sum(), abs=1e-12), h
+
+
+@pytest.mark.parametrize("case", list(SPECS) + ["river_full"])
+def test_deal_normaliser_matches_the_oracle(probe, oracle_mod, case):
+    """Z, the probability mass of the private deals (pairs of hands sharing no card), which
+    scales every terminal value: the library's O(H) inclusion-exclusion against the
+    oracle's sum over every pair."""
+    spec = synth.river_subgame() if case == "river_full" else SPECS[case]()
+    t = Built(probe, spec)
+    try:
+        probe.probe_Z.restype = C.c_double
+        z = probe.probe_Z(C.c_void_p(t.h))
+        o = oracle_mod.Oracle(spec, variant="dcfr", threads=1)
+        assert z == pytest.approx(o.Z, rel=1e-13)
+        if spec.game == synth.GAME_HOLDEM:  # and against a direct sum here
+            r = spec.ranges.astype(np.float64)
+            r = r / r.sum(axis=1, keepdims=True)
+            h = spec.hands.astype(np.int64)
+            clash = (h[:, None, :, None] == h[None, :, None, :]).any(axis=(2, 3))
+            assert z == pytest.approx(float(r[0] @ (~clash * 1.0) @ r[1]), rel=1e-13)
+    finally:
+        t.close()
