@@ -90,6 +90,19 @@ int probe_tables(void* h, int half, int pred, uint32_t* units, int cap, int32_t 
   return (int)u.size();
 }
 
+// the stream program as the kernel reads it: per node (pre-order) node_off, row_off,
+// code, first_kid
+void probe_program_ops(void* h, int32_t* out4) {
+  const Probe& p = *static_cast<Probe*>(h);
+  const std::vector<pcfr::ProgOp> ops = pcfr::program_ops(p.g, p.prog);
+  for (size_t k = 0; k < ops.size(); ++k) {
+    out4[4 * k] = ops[k].node_off;
+    out4[4 * k + 1] = ops[k].row_off;
+    out4[4 * k + 2] = (int32_t)ops[k].code;
+    out4[4 * k + 3] = ops[k].first_kid;
+  }
+}
+
 // the deal normaliser Z (sum of r0 r1 over the pairs of hands sharing no card)
 double probe_Z(void* h) { return static_cast<Probe*>(h)->g.Z; }
 

@@ -415,3 +415,29 @@ def test_deal_normaliser_matches_the_oracle(probe, oracle_mod, case):
             assert z == pytest.approx(float(r[0] @ (~clash * 1.0) @ r[1]), rel=1e-13)
     finally:
         t.close()
+
+
+@pytest.mark.parametrize("case", ["leduc", "river", "turn", "flop", "flop_limited"])
+def test_program_ops_encode_the_tree(probe, case):
+    """The 16-byte program entries the stream kernel decodes: node and row offsets in
+    elements (x hstride), and a code of type (2 bits), player (1), child count (6), dealt
+    card (8) and the terminal-children mask (bit a: child a is a fold, showdown or leaf;
+    chance nodes: bit 0 when all children are)."""
+    t = Built(probe, SPECS[case]())
+    try:
+        ops = np.zeros((len(t.prog), 4), np.int32)
+        probe.probe_program_ops(C.c_void_p(t.h), ops.ctypes.data_as(C.c_void_p))
+        for (node_off, row_off, code, first_kid), n in zip(ops.tolist(), t.prog.tolist()):
+            code &= 0xFFFFFFFF
+            assert node_off == n * t.hstride and first_kid == t.first[n]
+            assert code & 3 == t.type[n]
+            assert (code >> 3) & 63 == t.n_kids[n]
+            assert (code >> 9) & 0xFF == t.deal[n]
+            ends = [is_end(t.type[k]) for k in t.kids(n)]
+            if t.type[n] == DECISION:
+                assert row_off == t.row[n] * t.hstride and (code >> 2) & 1 == t.player[n]
+                assert code >> 17 == sum(1 << a for a, e in enumerate(ends) if e)
+            else:
+                assert row_off == 0 and code >> 17 == (1 if all(ends) else 0)
+    finally:
+        t.close()
