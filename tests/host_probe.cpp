@@ -103,6 +103,12 @@ void probe_program_ops(void* h, int32_t* out4) {
   }
 }
 
+// per node: the terminal payoff times the chance probability the kernels multiply by
+void probe_payoff(void* h, double* out) {
+  const Probe& p = *static_cast<Probe*>(h);
+  for (size_t n = 0; n < p.g.payoff.size(); ++n) out[n] = p.g.payoff[n];
+}
+
 // the deal normaliser Z (sum of r0 r1 over the pairs of hands sharing no card)
 double probe_Z(void* h) { return static_cast<Probe*>(h)->g.Z; }
 

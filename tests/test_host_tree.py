@@ -441,3 +441,50 @@ def test_program_ops_encode_the_tree(probe, case):
                 assert row_off == 0 and code >> 17 == (1 if all(ends) else 0)
     finally:
         t.close()
+
+
+@pytest.mark.parametrize("case", list(SPECS))
+def test_terminal_payoffs_and_chance_weights(probe, case):
+    """The per-node factor of the terminal values: a fold costs the folder its whole
+    contribution, a showdown moves the loser's contribution (both equal there), a
+    depth-limit leaf carries the pot times the chance of each river card; each is times
+    the chance of the cards dealt on the way, 1 / (cards left given the board and both
+    private hands) per chance node: 1/44 per river card below a turn, 1/45 per turn card
+    below a flop, 1/4 per public card in Leduc."""
+    spec = SPECS[case]()
+    t = Built(probe, spec)
+    try:
+        pay = np.zeros(t.n_nodes)
+        probe.probe_payoff(C.c_void_p(t.h), pay.ctypes.data_as(C.c_void_p))
+        boards = np.zeros(t.n_nodes, np.uint64)
+        probe.probe_boards(C.c_void_p(t.h), boards.ctypes.data_as(C.c_void_p))
+        meta = np.zeros(4, np.int32)
+        probe.probe_game(C.c_void_p(t.h), meta.ctypes.data_as(C.c_void_p))
+        deck, k = int(meta[1]), int(meta[2])
+
+        def left(n):  # cards chance can deal at node n, given its board and both hands
+            return deck - bin(int(boards[n])).count("1") - 2 * k
+
+        chance = np.ones(t.n_nodes)
+        for n in range(1, t.n_nodes):
+            par = t.parent[n]
+            chance[n] = chance[par] / left(par) if t.type[par] == CHANCE else chance[par]
+        for n in range(t.n_nodes):
+            c0, c1 = t.contrib[n]
+            if t.type[n] == FOLD:
+                want = (c0, c1)[t.player[n]] * chance[n]
+            elif t.type[n] == SHOWDOWN:
+                assert c0 == c1
+                want = c0 * chance[n]
+            elif t.type[n] == LEAF:
+                assert left(n) == 44
+                want = (c0 + c1) * chance[n] / 44.0
+            else:
+                continue
+            assert pay[n] == pytest.approx(want, rel=1e-15), (case, n)
+        if case == "leduc":
+            assert {left(n) for n in range(t.n_nodes) if t.type[n] == CHANCE} == {4}
+        if case.startswith("flop"):
+            assert {left(n) for n in range(t.n_nodes) if t.type[n] == CHANCE} >= {45}
+    finally:
+        t.close()
