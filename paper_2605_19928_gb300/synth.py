@@ -160,7 +160,7 @@ def batch_rivers(n: int = 256, seed: int = 0, n_hands: int | None = None) -> lis
     """Uneven river subgames for batched serving: seeded boards, strengths and ranges (seeds
     1000 + k and 5000 + k), 1-4 pot-fraction bet sizes (at least one below 1 pot) plus
     all-in, stacks 100-1000 behind a pot of 100, and 2-3 bets/raises (2 when four sizes meet
-    a stack above 400), which gives 27 to 357 public nodes per tree."""
+    a stack above 400); the 256 subgames of seed 0 have 21 to 315 public nodes (median 84)."""
     rng = np.random.default_rng(10_000 + seed)
     menu = np.array([0.33, 0.5, 0.75, 1.0, 1.5, 2.0])
     out = []

@@ -71,3 +71,18 @@ def test_training_turns_are_seeded_and_valid():
         assert np.allclose(x.ranges.sum(axis=1), 1.0, atol=1e-5)
         assert 100.0 <= x.pot <= 400.0 and 100.0 <= x.stack <= 600.0
         assert x.bet_sizes[-1] == synth.ALL_IN and 2 <= x.max_raises <= 3
+
+
+def test_batch_shape(oracle_mod):
+    """The batched-serving workload: 1-4 pot-fraction sizes (one below 1 pot) plus all-in,
+    stacks 100-1000 behind a pot of 100, 2-3 bets/raises, and trees of 21 to 315 public
+    nodes (median 84), counted on the oracle's own trees."""
+    specs = synth.batch_rivers(256)
+    nodes = []
+    for g in specs:
+        assert g.pot == 100.0 and 100 <= g.stack <= 1000 and g.max_raises in (2, 3)
+        sizes = [x for x in g.bet_sizes if x > 0]
+        assert 1 <= len(sizes) <= 4 and min(sizes) < 1.0 and g.bet_sizes[-1] == synth.ALL_IN
+        assert g.n_hands == 1081
+        nodes.append(oracle_mod.Oracle(g, variant="dcfr", threads=1).n_nodes)
+    assert (min(nodes), float(np.median(nodes)), max(nodes)) == (21, 84.0, 315)
