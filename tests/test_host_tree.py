@@ -488,3 +488,53 @@ def test_terminal_payoffs_and_chance_weights(probe, case):
             assert {left(n) for n in range(t.n_nodes) if t.type[n] == CHANCE} >= {45}
     finally:
         t.close()
+
+
+def _rejected(lib, spec):
+    s, keep = capi.make_spec(spec)
+    h = lib.probe_create(C.byref(s))
+    if h:
+        lib.probe_destroy(C.c_void_p(h))
+        return None
+    return lib.probe_error().decode()
+
+
+def test_invalid_subgames_are_rejected(probe):
+    """build_game's checks (what cfr_tree_create reports as CFR_EINVAL), on the CPU."""
+    import copy
+
+    def river(**kw):
+        return synth.river_subgame(n_hands=12, seed=3, range_seed=4, **kw)
+
+    assert _rejected(probe, river()) is None
+    bad = river()
+    bad.hands = bad.hands.copy()
+    bad.hands[1] = bad.hands[0]
+    assert "duplicate" in _rejected(probe, bad)
+    bad = river()
+    bad.hands = bad.hands.copy()
+    bad.hands[0, 0] = bad.board[0]
+    assert "board" in _rejected(probe, bad)
+    bad = river()
+    bad.ranges = bad.ranges.copy()
+    bad.ranges[0, 3] = -1.0
+    assert "non-negative" in _rejected(probe, bad)
+    bad = river()
+    bad.ranges = np.zeros_like(bad.ranges)
+    assert "sums to zero" in _rejected(probe, bad)
+    bad = river()
+    bad.depth_limit = 1  # a river has no card to come
+    assert "depth_limit" in _rejected(probe, bad)
+    bad = synth.turn_subgame(n_hands=10, seed=5, range_seed=6)
+    bad.strength = bad.strength[:1].copy()  # a turn needs one row per river card
+    assert "strength" in _rejected(probe, bad)
+    bad = copy.deepcopy(river())
+    bad.pot = 0.0
+    assert "pot" in _rejected(probe, bad)
+    # every hand of player 0 blocks every hand of player 1: no deal is possible
+    bad = river()
+    keep = np.flatnonzero((bad.hands == bad.hands[0, 0]).any(axis=1))
+    bad.hands = bad.hands[keep].copy()
+    bad.strength = bad.strength[:, keep].copy()
+    bad.ranges = np.ones((2, len(keep)), np.float32)
+    assert "no pair of hands" in _rejected(probe, bad)
