@@ -36,12 +36,14 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
-def _load():
+def _load(path: str | None = None):
+    """The oracle library, bound once per process; `path` binds another build of the same
+    source instead (the tests compile copies with planted mistakes to check the pins)."""
     global _lib
     with _lock:
-        if _lib is not None:
+        if path is None and _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(path or build())
         P, I, D = C.c_void_p, C.c_int, C.c_double
         pi = C.POINTER(C.c_int)
         pd = C.POINTER(C.c_double)
@@ -81,7 +83,8 @@ def _load():
         lib.ocfr_node_reach.restype = I
         lib.ocfr_set_leaf_values.argtypes = [P, I, pd]
         lib.ocfr_set_leaf_values.restype = I
-        _lib = lib
+        if path is None:
+            _lib = lib
         return lib
 
 
@@ -93,8 +96,8 @@ class Oracle:
     """FP64 CFR over one subgame (a ``synth.GameSpec``)."""
 
     def __init__(self, spec, variant: str = "dcfr", alpha: float = 1.5, beta: float = 0.0, gamma: float = 2.0,
-                 alternating: bool = True, threads: int | None = None):
-        lib = _load()
+                 alternating: bool = True, threads: int | None = None, lib_path: str | None = None):
+        lib = _load(lib_path)
         self._lib = lib
         self.spec = spec
         nh = spec.n_hands

@@ -311,3 +311,108 @@ def kuhn_best_response_bruteforce(opp_profile, i):
         merged.update(table)
         best = max(best, profile_value(g, Profile(merged), i))
     return best
+
+
+# ------------------------------------------------------------ hold'em best response and reach
+
+def pure_best_response(g, prof, i):
+    """Best-response value of player i by definition: the largest expected utility of player
+    i over every pure strategy (one action at each of its infosets), the opponent playing
+    `prof`.  Only for games with a handful of infosets."""
+    keys = sorted({infoset_key(i, hands[i], hist) for hands, hist, *_ in decision_histories(g, prof)
+                   if g.state(hist)["to_act"] == i}, key=repr)
+    n_acts = [len(g.legal(k[2])) for k in keys]
+    best = -1e300
+    for choice in itertools.product(*[range(a) for a in n_acts]):
+        table = dict(prof.table)
+        table.update({k: [float(j == c) for j in range(a)] for k, a, c in zip(keys, n_acts, choice)})
+        best = max(best, profile_value(g, Profile(table), i))
+    return best
+
+
+def best_response(g, prof, i):
+    """Best response of player i against the opponent's behaviour in `prof`, as a maximum at
+    each of player i's infosets (own hand h, public history).  The value of an infoset is the
+    sum, over the opponent's hands o that share no card with h and over the public cards to
+    come, of u_i weighted by r_{-i}(o) / Z, the opponent's action probabilities and the
+    chance probability of each card -- 1 / (live cards of the pair (h, o)), a card held by o
+    not being dealt to that pair at all.  Returns (BR_i, {(h, hist): v*_i(h, hist)}) with
+    BR_i = sum_h r_i(h) v*_i(h, ()); histories below a card that h holds get no entry."""
+    n = len(g.hands)
+    vals = {}
+
+    def pair(h, o):
+        return (h, o) if i == 0 else (o, h)
+
+    def rec(h, hist, w):
+        if not w:
+            vals[(h, hist)] = 0.0
+            return 0.0
+        o0 = next(iter(w))
+        u = g.utility(pair(h, o0), hist, i)
+        if u is not None:
+            v = sum(wo * g.utility(pair(h, o), hist, i) for o, wo in w.items())
+        elif g.chance_cards(pair(h, o0), hist) is not None:
+            s = g.state(hist)
+            v = 0.0
+            for x in range(g.deck):
+                if x in s["board"] or x in g.hands[h]:
+                    continue
+                w2 = {}
+                for o, wo in w.items():
+                    live = g.chance_cards(pair(h, o), hist)
+                    if x in live:
+                        w2[o] = wo / len(live)
+                v += rec(h, hist + (("d", x),), w2)
+        else:
+            s = g.state(hist)
+            acts = g.legal(hist)
+            if s["to_act"] == i:
+                v = max(rec(h, hist + (a,), w) for a in acts)
+            else:
+                v = 0.0
+                for k, a in enumerate(acts):
+                    w2 = {o: wo * prof.probs(infoset_key(1 - i, o, hist), len(acts))[k] for o, wo in w.items()}
+                    v += rec(h, hist + (a,), w2)
+        vals[(h, hist)] = v
+        return v
+
+    br = 0.0
+    for h in range(n):
+        w = {o: g.r[1 - i][o] / g.Z for o in range(n) if g.compatible(h, o)}
+        br += g.r[i][h] * rec(h, (), w)
+    return br, vals
+
+
+def reach_at_histories(g, prof, p):
+    """pi_p at every history (decision, chance and terminal), including player p's range
+    weight r_p(h): {(h, hist): r_p(h) times p's action probabilities on the path}, from the
+    enumeration of every deal and every history of it (a card dealt on the path is live for
+    the deal, so a hand holding it never gets an entry)."""
+    out = {}
+
+    def rec(hands, hist, pi):
+        key = (hands[p], hist)
+        if key in out:
+            assert out[key] == pi, (key, out[key], pi)
+        out[key] = pi
+        if g.utility(hands, hist, 0) is not None:
+            return
+        live = g.chance_cards(hands, hist)
+        if live is not None:
+            for x in live:
+                rec(hands, hist + (("d", x),), pi)
+            return
+        s = g.state(hist)
+        acts = g.legal(hist)
+        if s["to_act"] == p:
+            pr = prof.probs(infoset_key(p, hands[p], hist), len(acts))
+            for k, a in enumerate(acts):
+                rec(hands, hist + (a,), pi * pr[k])
+        else:
+            for a in acts:
+                rec(hands, hist + (a,), pi)
+
+    for h0, h1 in g.deals():
+        rec((h0, h1), (), g.r[p][(h0, h1)[p]])
+    return out
