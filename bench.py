@@ -1,23 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark: Parallel CFR iterations per second on GB300.
 
-Workload (one "step"): one complete solve of the river subgame -- 5 seeded board cards,
-1081 two-card hands per player with seeded integer showdown strengths in [0, 2000),
-Dirichlet(1) ranges, pot 100, stacks 400, bet sizes {0.5, 1.0 pot, all-in}, at most 3 bets
-or raises -- by DCFR (alpha 1.5, beta 0, gamma 2) from scratch: reset, 1000 alternating
-iterations (every stage of the paper's pipeline, Section 4.1), then the best-response
-exploitability pass.  `value` is CFR iterations per second of device time over the K
-timed steps (L2 flushed between steps with a 256 MB write, outside the timed events).
+Default workload (one "step"): batched serving of 256 independent river subgames of uneven
+size in one handle -- seeded 5-card boards, 1081 two-card hands per player with seeded
+integer showdown strengths in [0, 2000), Dirichlet(1) ranges, 1-4 pot-fraction bet sizes
+plus all-in, stacks 100-1000, 21-315 public nodes each -- solved together by DCFR (alpha
+1.5, beta 0, gamma 2) from scratch: reset, 500 alternating iterations of every subgame
+(every stage of the paper's pipeline, Section 4.1), then the best-response exploitability
+pass of every subgame.  `value` is subgame-iterations per second of device time over the K
+timed steps (the state of all subgames, about 2.5 GB, is larger than L2, and L2 is also
+flushed between steps with a 256 MB write outside the timed events).  The launch tiling is
+autotuned before the timed region.
 
-Under torchrun each rank solves its own subgame (seeds offset by rank) with no
-collective: weak scaling, value = all ranks' iterations / the slowest rank's time.
+Under torchrun each rank solves its own batch (seeds offset by rank) with no collective:
+weak scaling, value = all ranks' subgame-iterations / the slowest rank's time.
 
 `--impl reference` times the FP64 CPU oracle (the paper publishes no code, so the oracle is
-the reference implementation) on the same workload instead, on the host cores.
+the reference implementation) on a bounded sample of the same workload instead, on the
+host cores.
 
-Other workloads (`--workload`): `batch` (256 uneven river subgames in one handle, the
-launch tiling autotuned first), `leaf` and `flop` (depth-limited turn and flop subgames
-with the BF16 leaf network, against the exact subgames), `gemm` (the network's layers).
+Other workloads (`--workload`): `river` (one 1081-hand river subgame, pot 100, stacks 400,
+bet sizes {0.5, 1.0 pot, all-in}, at most 3 bets or raises, 1000 iterations per step),
+`leaf` and `flop` (depth-limited turn and flop subgames with the BF16 leaf network, against
+the exact subgames), `gemm` (the network's layers).
 """
 from __future__ import annotations
 
@@ -46,8 +51,9 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["river", "batch", "leaf", "flop", "gemm"], default="river",
-                    help="river: one 1081-hand river subgame; batch: 256 uneven river subgames in one handle; "
+    ap.add_argument("--workload", choices=["river", "batch", "leaf", "flop", "gemm"], default="batch",
+                    help="batch (default): 256 uneven river subgames in one handle; river: one 1081-hand river "
+                         "subgame; "
                          "leaf: depth-limited turn subgame with the BF16 leaf network, against the exact turn; "
                          "flop: depth-limited flop subgame (leaves at the river card), against the exact flop; "
                          "gemm: the leaf network's dense layers alone")
@@ -235,7 +241,7 @@ def tree_shape(capi, tree, game: int = 0):
     return {"nodes": n_nodes, "hands": n_hands, "rows": rows, "terminals": ends}
 
 
-def algorithmic_bytes(shape, stage: str, value_bytes: int) -> float:
+def algorithmic_bytes(shape, stage: str, value_bytes: int = 4) -> float:
     """Algorithmic bytes of one launch, from the per-unit figures of the traversal:
     per (decision row, hand) and iteration R and S read + written (32 B) and the strategy
     written once and read by the two traversals (3 V); per (node, hand) and traversal the
@@ -453,10 +459,11 @@ def run_ours(args):
     shapes = [tree_shape(capi, tree, g) for g in range(G)]
     capi.cfr_reset(tree)
     stages = capi.cfr_stage_times(tree, min(ips, 200 if not batch else 20))
-    vbytes = 8 if args.precision == "pairs" else 4
+    vbytes = 8 if args.precision == "pairs" else 4  # bytes of one stored value
     per_step = {k: stages[k][0] * (2 * ips if k in ("terminal", "update") else 1) for k in stages}
     dom = max(("update", "terminal"), key=lambda k: per_step[k])
-    alg = sum(algorithmic_bytes(sh, dom, vbytes) for sh in shapes)
+    # the roofline model counts 4-byte values whatever the storage precision
+    alg = sum(algorithmic_bytes(sh, dom, 4) for sh in shapes)
     achieved = alg / (stages[dom][0] * 1e-3) / 1e9
     peak, peak_kind = peaks()
     schedule = "stream" if capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_STREAM else "level"
@@ -465,8 +472,11 @@ def run_ours(args):
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": profiled_traffic(dom, "batch256" if batch else "river1081"),
-                "algorithmic_bytes_per_launch": alg, "launch_ms": stages[dom][0],
+                "algorithmic_bytes_per_launch": alg, "value_bytes_in_model": 4, "launch_ms": stages[dom][0],
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
+    if vbytes != 4:  # the same model with the stored pair values, for comparison only
+        roofline["algorithmic_bytes_per_launch_pair_storage"] = sum(algorithmic_bytes(sh, dom, vbytes)
+                                                                    for sh in shapes)
 
     target = None
     if not batch:  # the single subgame: iterations (and device time) to 1 mbb/hand
