@@ -268,14 +268,13 @@ def cfr_gemm_bf16(A, B, bias, C, act: bool, err, stream=None):
 
 
 def cfr_set_leaf_net(tree, weights, biases):
-    """weights: 4 arrays (bfloat16 bit patterns as uint16, or float32 rounded to BF16 here)
-    of shapes LEAF_SHAPES; biases: 4 float32 arrays."""
+    """weights: 4 uint16 arrays of BF16 bit patterns (as leafnet_train writes them) of shapes
+    LEAF_SHAPES; biases: 4 float32 arrays."""
     Ws, bs = [], []
     for k, (w, b) in enumerate(zip(weights, biases)):
         w = np.asarray(w)
         if w.dtype != np.uint16:
-            f = np.ascontiguousarray(w, dtype=np.float32).reshape(-1).view(np.uint32).astype(np.uint64)
-            w = (((f + 0x7FFF + ((f >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16).reshape(w.shape)
+            raise TypeError(f"layer {k}: weights must be BF16 bit patterns (uint16), not {w.dtype}")
         assert w.shape == LEAF_SHAPES[k], (k, w.shape)
         Ws.append(np.ascontiguousarray(w))
         bs.append(np.ascontiguousarray(b, dtype=np.float32).reshape(LEAF_SHAPES[k][0]))

@@ -91,3 +91,13 @@ def test_bad_options_are_rejected_before_any_device_call(lib):
     good = capi.make_opts()
     assert lib.cfr_autotune(C.byref(s), 1, C.byref(good), None, 0, C.byref(best), C.byref(ms)) == capi.CFR_EINVAL
     assert lib.cfr_autotune(None, 1, C.byref(good), None, 5, C.byref(best), C.byref(ms)) == capi.CFR_EINVAL
+
+
+def test_leaf_net_setter_only_marshals_bf16_bit_patterns():
+    """The binding does no arithmetic on the network: FP32 weights are refused, not rounded
+    in Python (the training script writes BF16 bit patterns)."""
+    import numpy as np
+    W = [np.zeros(s, np.float32) for s in capi.LEAF_SHAPES]
+    b = [np.zeros(s[0], np.float32) for s in capi.LEAF_SHAPES]
+    with pytest.raises(TypeError):
+        capi.cfr_set_leaf_net(None, W, b)

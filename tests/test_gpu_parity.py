@@ -137,7 +137,12 @@ def test_uniform_kuhn_and_leduc_converge_like_the_oracle(game, variant, iters, b
         orc.iterate(iters)
         expl, br = capi.cfr_exploitability(tree)
         e_o, b0, b1 = orc.exploitability()
+        print(game, variant, "exploitability gpu", expl[0], "oracle", e_o)
         assert 0.0 <= expl[0] < bound and e_o < bound
+        # not within 1 % of each other: with uniform deals exact ties between action values
+        # recur every iteration, FP64 and double-float break them differently, and the two
+        # (equally correct) trajectories end at different points of the same small
+        # exploitability; the 1 % bar is met on inputs without such ties (above)
         assert expl[0] < 3.0 * e_o + 1e-4
         if game == "kuhn":
             # BR_0 >= game value >= -BR_1, both within the exploitability of -1/18
@@ -150,8 +155,48 @@ def test_uniform_kuhn_and_leduc_converge_like_the_oracle(game, variant, iters, b
 def test_full_size_river_ten_iterations():
     """The benchmarked workload itself: 1081 hands, pot 100, stacks 400, {0.5, 1, all-in},
     3 raises, DCFR(1.5, 0, 2), in the benchmark's launch configuration."""
-    worst = run_pair(synth.river_subgame(), "dcfr", iters=10, forced=False, check_every=5)
+    worst = run_pair(synth.river_subgame(), "dcfr", iters=10, forced=False, check_every=1)
     print("full river", worst)
+
+
+def free_running_exploitability(spec, variant, iters, precision="pairs", schedule="auto"):
+    """Both solvers run `iters` iterations independently from scratch; their final
+    exploitabilities (average strategy, in chips)."""
+    from oracle.oracle import Oracle
+    tree = capi.cfr_tree_create(spec, capi.make_opts(variant, precision=precision, schedule=schedule))
+    try:
+        orc = Oracle(spec, variant=variant)
+        capi.cfr_iterate(tree, iters)
+        orc.iterate(iters)
+        e_g, _ = capi.cfr_exploitability(tree)
+        return float(e_g[0]), orc.exploitability()[0]
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("case,iters", [("river_203", 1000), ("river_1081", 300)])
+def test_converged_exploitability_within_one_percent(case, iters):
+    """Spec bar for the final result: after a long free-running solve (DCFR 1.5/0/2,
+    default pair values) the GPU's exploitability is within 1 % of the oracle's.  The
+    1081-hand river is the single-subgame benchmark workload."""
+    spec = river(203) if case == "river_203" else synth.river_subgame()
+    e_g, e_o = free_running_exploitability(spec, "dcfr", iters)
+    print(case, iters, "exploitability gpu", e_g, "oracle", e_o, "relative", abs(e_g - e_o) / e_o)
+    assert e_g == pytest.approx(e_o, rel=1e-2)
+
+
+def test_batch_subgame_converged_exploitability_within_one_percent():
+    """A subgame of the benchmarked batch (its smallest tree) solved for the batch's 500
+    iterations in its precision (FP32 values) on the stream schedule, free-running, against
+    the oracle: final exploitability within 1 %."""
+    specs = synth.batch_rivers(256)
+    from oracle.oracle import Oracle
+    sizes = [Oracle(s, variant="dcfr", threads=1).n_nodes for s in specs[:32]]
+    spec = specs[int(np.argmin(sizes))]
+    e_g, e_o = free_running_exploitability(spec, "dcfr", 500, precision="single", schedule="stream")
+    print("batch subgame", min(sizes), "nodes: exploitability gpu", e_g, "oracle", e_o, "relative",
+          abs(e_g - e_o) / e_o)
+    assert e_g == pytest.approx(e_o, rel=1e-2)
 
 
 def test_simultaneous_updates_match_oracle():

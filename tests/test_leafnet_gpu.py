@@ -141,7 +141,7 @@ def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
     W, b = _random_net(1)
     tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", schedule=schedule))
     try:
-        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_set_leaf_net(tree, [ln.bf16_bits(w) for w in W], b)
         capi.cfr_iterate(tree, 3)
         capi.cfr_eval_leaves(tree)
         orc = Oracle(spec, variant="dcfr")
@@ -166,9 +166,10 @@ def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, varia
     from oracle.oracle import Oracle
     spec = _leaf_spec(n_hands=32, seed=9, street=street)
     W, b = _random_net(2)
+    Wbits = [ln.bf16_bits(w) for w in W]
     tree = capi.cfr_tree_create(spec, capi.make_opts(variant, schedule=schedule))
     try:
-        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_set_leaf_net(tree, Wbits, b)
         capi.cfr_iterate(tree, 2)
         orc = Oracle(spec, variant=variant)
         mapping = node_map(tree, orc)
