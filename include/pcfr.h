@@ -195,7 +195,10 @@ int cfr_exploitability_result(cfr_tree* tree, double* expl, double* br);
  * does a one-time setup (resolves the array's address, loads the reduction kernel): make
  * it before any stream capture begins.  All calls on one device share the array, so calls
  * must not overlap: two calls in flight at once (other threads or other streams) race.
- * Synchronises. */
+ * The device the handle was created on must be the current device (CFR_EINVAL otherwise).
+ * The handle's own best-response pass still reduces its root values into the handle's
+ * buffers; this call adds one more reduction of the same values into the static array and
+ * reads the result from there.  Synchronises. */
 int cfr_exploitability_noalloc(cfr_tree* tree, double* expl, double* br);
 
 /* Start the solve again: R = S = 0, iteration count 0, uniform strategy, initial reach
@@ -251,8 +254,21 @@ int cfr_read_values(cfr_tree* tree, int game, int what, int player, int node, do
  * average strategy follows S at the next exploitability or cfr_strategy call. */
 int cfr_write_values(cfr_tree* tree, int game, int what, int node, const double* in, size_t in_len);
 
-/* Block until all work queued on the handle's stream has finished. */
+/* Block until all work queued on the handle's stream has finished.  Reports CFR_ETIMEOUT if
+ * a bounded device-side wait of the handle's kernels gave up (the flag stays set: release
+ * the handle). */
 int cfr_sync(cfr_tree* tree);
+
+/* Testing aid for the device-side timeout path (the paper has no counterpart; the bounded
+ * waits are this library's safety net, not part of the method).  Sets how many times the
+ * terminal kernel's first bulk-copy wait of each block polls its barrier before giving up
+ * on the current device: polls < 0 restores the default (2^20); 0 gives up before the copy
+ * can land.  A block that gives up still waits, with the default limit, for its own copies
+ * to land, then sets the handle's device flag and returns without computing its values,
+ * so the next synchronising call on the handle reports CFR_ETIMEOUT and the CUDA context
+ * stays usable.  Call it while none of the library's kernels are in flight (e.g. after
+ * cfr_sync); it applies to every handle on the device until it is called again. */
+int cfr_debug_first_wait_polls(long polls);
 
 /* Per-stage device time, after the paper's per-stage breakdown (Section 5, Table 3).
  * Runs n_iters iterations (advancing the solve exactly like cfr_iterate) launch by launch

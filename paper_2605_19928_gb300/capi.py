@@ -37,7 +37,7 @@ EXPORTS = ("cfr_set_allocator", "cfr_tree_create", "cfr_batch_create", "cfr_iter
            "cfr_stage_times", "cfr_counters", "cfr_exploitability_async", "cfr_exploitability_result",
            "cfr_reset", "cfr_tree_destroy", "cfr_last_error", "cfr_exploitability_noalloc", "cfr_schedule",
            "cfr_gemm_bf16", "cfr_set_leaf_net", "cfr_leaf_info", "cfr_read_leaf_rows",
-           "cfr_eval_leaves", "cfr_write_values", "cfr_autotune")
+           "cfr_eval_leaves", "cfr_write_values", "cfr_autotune", "cfr_debug_first_wait_polls")
 
 
 class CfrError(RuntimeError):
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         lib.cfr_exploitability_noalloc.argtypes = [P, pd, pd]
         lib.cfr_schedule.argtypes = [P]
         lib.cfr_gemm_bf16.argtypes = [P, P, P, P, I, I, I, I, I, P, P]
+        lib.cfr_debug_first_wait_polls.argtypes = [C.c_long]
         lib.cfr_set_leaf_net.argtypes = [P, C.POINTER(P), C.POINTER(P)]
         lib.cfr_leaf_info.argtypes = [P, I, pi, pi, pi, pi]
         lib.cfr_read_leaf_rows.argtypes = [P, I, I, I, P]
@@ -281,6 +282,11 @@ def cfr_set_leaf_net(tree, weights, biases):
     Wp = (C.c_void_p * 4)(*[w.ctypes.data for w in Ws])
     bp = (C.c_void_p * 4)(*[b.ctypes.data for b in bs])
     _check(load().cfr_set_leaf_net(tree, Wp, bp))
+
+
+def cfr_debug_first_wait_polls(polls: int):
+    """Testing aid: polls of the terminal kernel's first bulk-copy wait (< 0: the default)."""
+    _check(load().cfr_debug_first_wait_polls(int(polls)))
 
 
 def cfr_eval_leaves(tree, average: bool = False):

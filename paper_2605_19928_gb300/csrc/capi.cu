@@ -75,6 +75,7 @@ struct cfr_tree {
   int64_t device_bytes = 0;
   int64_t h2d_bytes = 0;
   int launches_per_iteration = 0;
+  int device = -1;              // the device current when the handle was created
   std::vector<std::pair<void*, bool>> blocks;  // (pointer, from hook)
   void* stream_arg = nullptr;
 
@@ -301,6 +302,10 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
 
   cfr_tree* t = new cfr_tree();
   t->opts = o;
+  if (cudaGetDevice(&t->device) != cudaSuccess) {
+    delete t;
+    return fail(CFR_ECUDA, "cudaGetDevice failed");
+  }
   t->stream = (cudaStream_t)stream;
   t->stream_arg = stream;
   t->host.resize(n_games);
@@ -724,6 +729,11 @@ int cfr_sync(cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   CK(cudaStreamSynchronize(t->stream));
   return check_device_flag(t);
+}
+
+int cfr_debug_first_wait_polls(long polls) {
+  if (set_first_wait_polls(polls) != 0) return fail(CFR_ECUDA, "could not set the wait limit");
+  return CFR_OK;
 }
 
 int cfr_strategy(cfr_tree* t, int game, int node, int average, float* out, size_t out_len) {
@@ -1301,6 +1311,12 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
   if (c.n_games > kStaticMaxGames)
     return fail(CFR_EINVAL, "cfr_exploitability_noalloc: the handle has " + std::to_string(c.n_games) +
                                 " games; its static scratch holds at most " + std::to_string(kStaticMaxGames));
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != t->device)
+    return fail(CFR_EINVAL, "cfr_exploitability_noalloc: the handle was created on device " +
+                                std::to_string(t->device) + "; make it the current device (current: " +
+                                std::to_string(dev) + ")");
   if (c.n_chunk_work > kStaticMaxChunks)
     return fail(CFR_EINVAL, "cfr_exploitability_noalloc: the handle has " + std::to_string(c.n_chunk_work) +
                                 " hand chunks per player; its static scratch holds at most " +
@@ -1315,7 +1331,8 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
     return fail(CFR_ECUDA, "exploitability launch failed");
   k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);
   CK(cudaGetLastError());
-  t->launches += (c.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) + 1;
+  t->launches += (c.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) +
+                 leaf_launches(t, 3) + 1;
   CK(cudaMemcpyAsync(br, scratch + kStaticPartialBytes, (size_t)c.n_games * 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

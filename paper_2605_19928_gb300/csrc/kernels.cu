@@ -340,13 +340,20 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Bounded wait for phase `parity` of the barrier: false if it did not complete in time.
+// Bounded wait for phase `parity` of the barrier: false if it did not complete within
+// `limit` polls.
 constexpr long kWaitLimit = 1l << 20;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (long k = 0; k < kWaitLimit; ++k)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long limit = kWaitLimit) {
+  for (long k = 0; k < limit; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+
+// Polls the terminal kernel's first bulk-copy wait of each block makes before it gives up:
+// kWaitLimit, unless a test lowers it to exercise the timeout path (with 0 the block gives
+// up before its copies can land, drains them with the full limit, sets the error flag and
+// returns).  Every other wait keeps kWaitLimit.
+__device__ long g_first_wait_polls = kWaitLimit;
 
 // ------------------------------------------------------------------ terminal values (Stages 2-4)
 
@@ -583,7 +590,8 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
     // payoff for player i per unit of (opponent reach) x kappa, in FP64
     const double pay = G.payoff[n];
     const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
-    const bool ok = threadIdx.x >= 32 || mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1);  // one warp polls
+    const bool ok = threadIdx.x >= 32 ||  // one warp polls
+                    mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, j == 0 ? g_first_wait_polls : kWaitLimit);
     if (__syncthreads_or(!ok)) {  // a copy did not land: report, let the copies drain, leave
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
@@ -1641,6 +1649,11 @@ static cudaError_t configure_precision() {
   if (e == cudaSuccess) e = configure_one(k_stream_update<P>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_current_rows<P>, 0);
   return e;
+}
+
+int set_first_wait_polls(long polls) {
+  const long v = polls < 0 ? kWaitLimit : polls;
+  return cudaMemcpyToSymbol(g_first_wait_polls, &v, sizeof(v)) == cudaSuccess ? 0 : -1;
 }
 
 int configure_kernels() {

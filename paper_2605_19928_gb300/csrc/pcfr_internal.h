@@ -218,6 +218,9 @@ int hand_kernel_smem_limit();
 // Shared memory the per-hand kernel needs to stage one game (es = bytes per value).
 size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
 int configure_kernels();  // once per process, before the first launch
+// Polls of the terminal kernel's first bulk-copy wait on the current device (< 0: the
+// default limit); for tests of the timeout path.  Returns 0 or -1.
+int set_first_wait_polls(long polls);
 // Dense layer of the leaf network (leafnet.cu): C[M][N] = act(A[M][K] B[N][K]^T + bias), BF16
 // A and B, FP32 accumulation, C in BF16 (out_f32 = 0) or FP32; N a multiple of 128, K of 64.
 // Returns 0, -1 (launch failed), -2 (bad shape or alignment), -3 (no tensor-map encoder).

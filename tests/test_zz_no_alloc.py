@@ -40,10 +40,13 @@ def _check(tree, n_games, pot):
     return expl
 
 
-@pytest.mark.parametrize("precision", ["pairs", "single"])
-def test_noalloc_matches_on_river_two_calls(precision):
+@pytest.mark.parametrize("precision,schedule", [("pairs", "level"), ("single", "level"), ("pairs", "stream"),
+                                                ("single", "stream"), ("pairs", "wide"), ("single", "wide")])
+def test_noalloc_matches_on_river_two_calls(precision, schedule):
+    """Every launch layout leaves the best-response values where the static reduction reads
+    them: the per-hand, stream and wide schedules."""
     spec = synth.river_subgame(n_hands=1081, seed=0, range_seed=1)
-    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision=precision))
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision=precision, schedule=schedule))
     try:
         capi.cfr_iterate(tree, 30)
         e1 = _check(tree, 1, spec.pot)
@@ -85,5 +88,41 @@ def test_noalloc_rejects_handles_beyond_its_scratch():
         # the handle still works through the allocating entry point
         e, _ = capi.cfr_exploitability(tree, 8)
         assert np.all(np.isfinite(e))
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def _random_net(seed):
+    """A random leaf network as BF16 bit patterns (weights) and FP32 biases."""
+    from oracle.leafnet import bf16_bits
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for k, shape in enumerate(capi.LEAF_SHAPES):
+        w = rng.standard_normal(shape).astype(np.float32) * np.float32(2.0 / np.sqrt(shape[1]))
+        W.append(bf16_bits(w * (0.2 if k == 3 else 1.0)))
+        b.append(rng.standard_normal(shape[0]).astype(np.float32) * 0.05)
+    return W, b
+
+
+@pytest.mark.parametrize("schedule", ["level", "stream", "wide"])
+def test_noalloc_matches_with_depth_limit_leaves(schedule):
+    """A depth-limited turn (network leaves at the river card): the call also runs the leaf
+    network under the average strategy, and counts its launches as the allocating pass
+    does (plus its one reduction kernel)."""
+    spec = synth.turn_subgame(n_hands=40, seed=5, range_seed=6, bet_sizes=(1.0, synth.ALL_IN), max_raises=2)
+    spec.depth_limit = 1
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", schedule=schedule))
+    try:
+        W, b = _random_net(3)
+        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_iterate(tree, 6)
+        for _ in range(2):
+            l0 = capi.cfr_counters(tree)["kernel_launches"]
+            e_ref, br_ref = capi.cfr_exploitability(tree, 1)
+            l1 = capi.cfr_counters(tree)["kernel_launches"]
+            _check(tree, 1, spec.pot)
+            l2 = capi.cfr_counters(tree)["kernel_launches"]
+            # _check runs cfr_exploitability once more, then the call itself
+            assert (l2 - l1) - (l1 - l0) == (l1 - l0) + 1
     finally:
         capi.cfr_tree_destroy(tree)
