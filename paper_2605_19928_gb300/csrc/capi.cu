@@ -453,6 +453,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     const std::vector<uint16_t> tab = pack_term_tables(h);
     const std::vector<int32_t> rown = row_nodes(h);
     const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
+    std::vector<float> pay32(h.payoff.size());
+    for (size_t n = 0; n < pay32.size(); ++n) pay32[n] = (float)(h.payoff[n] * d.kappa64);
     NodeDev* nodes;
     int32_t *ls, *rn, *dn, *chk;
     uint32_t* un;
@@ -466,18 +468,19 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     }
     uint16_t* tb;
     uint64_t* hm;
-    float* rrv;
+    float *rrv, *pay32d;
     double *rr64, *pay;
     if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
         (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
-        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, tab, &tb)) || (rc = upload(t, decn, &dn)) ||
+        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, pay32, &pay32d)) || (rc = upload(t, tab, &tb)) ||
+        (rc = upload(t, decn, &dn)) ||
         (rc = upload(t, ops, &prog)) || (rc = upload(t, chunk_lists[g], &chk)) ||
         (rc = upload(t, unit_lists[g], &un))) {
       delete t;
       return rc;
     }
     d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
+    d.payoff = pay; d.payoff32 = pay32d; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
     d.prog_len = (int)programs[g].size();
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value

@@ -370,7 +370,7 @@ __device__ long g_first_wait_polls = kWaitLimit;
 // Sums and differences are double-float with FP32-pair values, plain FP32 with FP32
 // values.  Every thread of the block calls it (it holds block barriers).
 template <typename P>
-__device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev& nd, int i, double u64,
+__device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev& nd, int i, double u64, float uf,
                                                 const TermTab& tt, const uint16_t* tab,
                                                 const typename P::V* __restrict__ qs, ff* CP, ff* Psc,
                                                 typename P::V* __restrict__ out) {
@@ -379,7 +379,6 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
   const int H = G.n_hands, k = G.hand_size;
   const bool show = nd.type == kShowdown;
   const uint64_t board = nd.board;
-  const ff u = d2ff(u64);
   const uint16_t* clh = tab + tt.clh;
   const uint16_t* cards = tab + tt.cards;
   const uint16_t* cloff = tab + tt.cloff;
@@ -405,7 +404,6 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
       __syncthreads();
       float T = 0.f;
       for (int w = 0; w < kTermThreads / 32; ++w) T = __fadd_rn(T, redt[w]);
-      const float uf = __double2float_rn(u64);
       for (int h = threadIdx.x; h < H; h += kTermThreads) {
         const unsigned cw = cards[h];
         const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
@@ -433,7 +431,6 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
     else
       group_exclusive_scan_f32<half>(k * H, [&](int j) { return qs[clh[j]]; }, CPf, redf[1], gtid);
     const float T = Pf[H];
-    const float uf = __double2float_rn(u64);
     if (!show) {
       for (int h = threadIdx.x; h < H; h += kTermThreads) {
         const unsigned cw = cards[h];
@@ -468,6 +465,7 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
     }
     return;
   }
+  const ff u = d2ff(u64);
   // Two scans at once, one per half of the block: the first half takes the reach in
   // rank-sorted order (showdown) or in hand order (fold, for the total T), the second half
   // the reach along the per-card hand lists.
@@ -587,9 +585,17 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
   for (int j = 0; j < count; ++j) {
     const int n = work[first + j].unit;
     const NodeDev nd = G.nodes[n];
-    // payoff for player i per unit of (opponent reach) x kappa, in FP64
-    const double pay = G.payoff[n];
-    const double u64 = (nd.type == kFold ? (nd.player == i ? -pay : pay) : pay) * G.kappa64;
+    // payoff for player i per unit of (opponent reach) x kappa: in FP64 for pair values; for
+    // FP32 values the host's FP32 rounding of the same product (no FP64 work per thread)
+    const bool neg = nd.type == kFold && nd.player == i;
+    double u64 = 0.0;
+    float uf = 0.f;
+    if constexpr (std::is_same<P, Single>::value) {
+      uf = neg ? -G.payoff32[n] : G.payoff32[n];
+    } else {
+      const double pay = G.payoff[n];
+      u64 = (neg ? -pay : pay) * G.kappa64;
+    }
     const bool ok = threadIdx.x >= 32 ||  // one warp polls
                     mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, j == 0 ? g_first_wait_polls : kWaitLimit);
     if (__syncthreads_or(!ok)) {  // a copy did not land: report, let the copies drain, leave
@@ -607,7 +613,8 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
         if (G.hand_mask[h] & nd.board) qb[h] = P::zero();
       __syncthreads();
     }
-    terminal_values<P>(G, nd, i, u64, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc, dst + (size_t)n * stride);
+    terminal_values<P>(G, nd, i, u64, uf, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc,
+                       dst + (size_t)n * stride);
     if (!RUNS) break;
     __syncthreads();  // buffer j & 1 and the scan arrays are free again
     if (threadIdx.x == 0 && j + 2 < count) {
@@ -1196,6 +1203,40 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
   }
 }
 
+// Top-down work at one of the player's decision nodes with NA actions: the reach x there is
+// recorded, sigma = RM(R) (of R + M for Predictive CFR+) is formed from the ring, and each
+// child's reach x sigma(a) goes to the terminal's row or onto the stack (child 0 on top).  NA
+// is a compile-time constant, as in decision_back.
+template <typename P, int NA>
+__device__ __forceinline__ void decision_fwd(const StreamLane<P>& L, const Op& nd, const uint64_t* ring, int& u,
+                                             int& sp, typename P::V x) {
+  using V = typename P::V;
+  V* st = L.st;
+  if (L.valid) L.reach[nd.node_off] = x;
+  const bool pred = L.M != nullptr;  // Predictive CFR+: R then M
+  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
+  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * 32);
+  u += (pred ? 2 : 1) * NA;
+  double Rv[NA];
+  V sg[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) Rv[a] = Rr[(size_t)a * 32];
+  if (pred) {  // Predictive CFR+ matches R + M
+#pragma unroll
+    for (int a = 0; a < NA; ++a) Rv[a] += Mr[(size_t)a * 32];
+  }
+  regret_match_n<P, NA>(Rv, sg);
+#pragma unroll
+  for (int a = NA - 1; a >= 0; --a) {
+    const V y = P::mul(x, sg[a]);
+    if ((nd.tmask >> a) & 1) {
+      if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
+    } else {
+      st[(sp++) * 32] = y;
+    }
+  }
+}
+
 // Top-down pass over chunk [k0, k1) with sigma = RM(R): records the reach at the player's
 // decision nodes, at chance nodes and, for the terminal children, at the terminals; pushes
 // the reach of the inner children (child 0 on top).
@@ -1210,32 +1251,16 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
     V x = st[(--sp) * 32];
     if (nd.deal != kNoCard && ((L.hmask >> nd.deal) & 1ull)) x = P::zero();
     const int A = nd.A;
-    if (nd.type == kDecision && nd.player == L.p) {
-      if (L.valid) L.reach[nd.node_off] = x;
-      const bool pred = L.M != nullptr;  // Predictive CFR+: R then M
-      const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-      const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + A) * 32);
-      u += (pred ? 2 : 1) * A;
-      double Rv[kStreamMaxActions];
-      V sg[kStreamMaxActions];
-#pragma unroll
-      for (int a = 0; a < kStreamMaxActions; ++a) Rv[a] = a < A ? Rr[(size_t)a * 32] : 0.0;
-      if (pred) {  // Predictive CFR+ matches R + M
-#pragma unroll
-        for (int a = 0; a < kStreamMaxActions; ++a)
-          if (a < A) Rv[a] += Mr[(size_t)a * 32];
-      }
-      regret_match<P>(Rv, A, sg);
-#pragma unroll
-      for (int a = kStreamMaxActions - 1; a >= 0; --a) {
-        if (a < A) {
-          const V y = P::mul(x, sg[a]);
-          if ((nd.tmask >> a) & 1) {
-            if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
-          } else {
-            st[(sp++) * 32] = y;
-          }
-        }
+    if (nd.type == kDecision && nd.player == L.p) {  // its action count as a compile-time constant
+      switch (A) {
+        case 1: decision_fwd<P, 1>(L, nd, ring, u, sp, x); break;
+        case 2: decision_fwd<P, 2>(L, nd, ring, u, sp, x); break;
+        case 3: decision_fwd<P, 3>(L, nd, ring, u, sp, x); break;
+        case 4: decision_fwd<P, 4>(L, nd, ring, u, sp, x); break;
+        case 5: decision_fwd<P, 5>(L, nd, ring, u, sp, x); break;
+        case 6: decision_fwd<P, 6>(L, nd, ring, u, sp, x); break;
+        case 7: decision_fwd<P, 7>(L, nd, ring, u, sp, x); break;
+        default: decision_fwd<P, kStreamMaxActions>(L, nd, ring, u, sp, x); break;
       }
     } else if (nd.type == kChance) {  // the player's reach passes through to each card
       if (L.valid) L.reach[nd.node_off] = x;  // read by the showdowns of an all-in run-out
