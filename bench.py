@@ -64,6 +64,8 @@ def parse_args(argv=None):
                          "the single river, FP32 for the batch and the depth-limited workloads")
     ap.add_argument("--chunk-hands", type=int, default=0)
     ap.add_argument("--schedule", choices=["auto", "level", "stream"], default="auto")
+    ap.add_argument("--warp-hands", type=int, choices=[0, 32, 64], default=0,
+                    help="stream schedule: hands per warp (0 = automatic)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -405,13 +407,14 @@ def run_ours(args):
     specs = workload_specs(args, rank)
     G = len(specs)
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
-                          precision=args.precision, schedule=args.schedule)
+                          precision=args.precision, schedule=args.schedule, warp_hands=args.warp_hands)
     tuned = None
-    if batch and not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0:
+    if batch and not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0:
         # launch tiling (schedule, hands per block, terminal nodes per block), outside the timed region
         opts, ms_tuned = capi.cfr_autotune(specs, opts, iters=20, stream=stream.cuda_stream)
         names = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream", capi.CFR_SCHEDULE_WIDE: "wide"}
         tuned = {"schedule": names[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
+                 "warp_hands": opts.warp_hands,
                  "ms_per_iter_while_tuning": ms_tuned}
 
     def create(sp):

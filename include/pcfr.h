@@ -122,7 +122,7 @@ typedef struct cfr_game_spec {
  * walks the tree level by level (lowest latency for one subgame).  CFR_SCHEDULE_STREAM: one
  * warp per 32 hands walks a depth-first program of its tree with no block barriers and no
  * inner-node state in DRAM (highest throughput for batches; needs at most 8 actions per
- * decision node).  CFR_SCHEDULE_WIDE: every pass (update, initial strategy, average, best
+ * decision node; warp_hands sets 32 or 64 hands per warp).  CFR_SCHEDULE_WIDE: every pass (update, initial strategy, average, best
  * response) is one launch per tree level over all of that level's (node, hand) pairs, one
  * thread each (for one tree too large for a block to stage in shared memory: exact turns
  * and flops; one subgame per handle, at most 8 actions per decision node).
@@ -131,6 +131,11 @@ typedef struct cfr_game_spec {
  * term_nodes: fold and showdown nodes per CUDA block of the terminal launch (nodes of one
  * board; 0 = automatic: one while the nodes do not fill the GPU eight times over, up to
  * eight when they do; otherwise 1 to 8).  Results are the same bits for every value.
+ * warp_hands: hands per warp of the stream schedule's update launch: 32 (one per lane), 64
+ * (two per lane: the walk's control work is shared by two hands; needs every subgame's
+ * hand rows padded to a multiple of 64, i.e. the hand count rounded up to 32 is a multiple
+ * of 64, CFR_EINVAL otherwise), or 0 = automatic (32; cfr_autotune tries both).  Other
+ * schedules ignore it.  Results are the same bits either way.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
 enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2, CFR_SCHEDULE_WIDE = 3 };
@@ -144,6 +149,7 @@ typedef struct cfr_solver_opts {
   int precision;
   int schedule;
   int term_nodes;
+  int warp_hands;
 } cfr_solver_opts;
 
 typedef struct cfr_tree cfr_tree;

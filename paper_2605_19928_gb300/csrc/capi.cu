@@ -294,6 +294,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if (o.chunk_hands < 0 || o.chunk_hands > 32 || (o.chunk_hands & (o.chunk_hands - 1)))
     return fail(CFR_EINVAL, "chunk_hands must be 0 or a power of two up to 32");
   if (o.term_nodes < 0 || o.term_nodes > 8) return fail(CFR_EINVAL, "term_nodes must be 0 to 8");
+  if (o.warp_hands != 0 && o.warp_hands != 32 && o.warp_hands != 64)
+    return fail(CFR_EINVAL, "warp_hands must be 0, 32 or 64");
   if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_WIDE) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
@@ -380,7 +382,21 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   }
   stream_units_max = (stream_units_max + 3) / 4 * 4;  // keeps the ring 16-byte aligned
   const int stream_units = stream_prog ? stream_units_max : 0;
-  stream_ok = stream_ok && stream_smem_size(stream_prog, stream_units, stream_half, stream_depth, es) <= 200 * 1024;
+  // hands per lane: one (32 per warp) unless the options ask for 64 per warp.  Two per lane
+  // share the walk's control work but double the ring and stack, which halves the warps an
+  // SM holds; on the 256-subgame batch that made the update slower (0.41 vs 0.27 ms), so
+  // only the autotuner tries it.
+  bool rows64 = true;
+  for (int g = 0; g < n_games; ++g) rows64 = rows64 && t->host[g].hstride % 64 == 0;
+  auto smem_fits = [&](int hp) {
+    return stream_smem_size(stream_prog, stream_units, stream_half, stream_depth, es, hp) <= 200 * 1024;
+  };
+  const int stream_hp = o.warp_hands == 64 ? 2 : 1;
+  if (stream_hp == 2 && !rows64) {
+    delete t;
+    return fail(CFR_EINVAL, "warp_hands = 64 needs every subgame's hand rows padded to a multiple of 64");
+  }
+  stream_ok = stream_ok && smem_fits(stream_hp);
   int schedule = kScheduleLevel;
   if (o.schedule == CFR_SCHEDULE_STREAM) {
     if (!stream_ok) {
@@ -533,8 +549,9 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   for (int g = 0; g < n_games; ++g) by_size[g] = g;
   std::stable_sort(by_size.begin(), by_size.end(),
                    [&](int a, int b) { return t->host[a].nodes.size() > t->host[b].nodes.size(); });
+  const int warp_span = 32 * stream_hp;
   for (int g : by_size)
-    for (int u = 0; u < (t->host[g].n_hands + 31) / 32; u += kStreamWarps) warp_work.push_back({g, u});
+    for (int u = 0; u < (t->host[g].n_hands + warp_span - 1) / warp_span; u += kStreamWarps) warp_work.push_back({g, u});
   if ((rc = upload(t, t->dev, &t->d_games)) || (rc = upload(t, chunk_work, &t->d_chunk_work)) ||
       (rc = upload(t, term_work, &t->d_term_work)) || (rc = upload(t, warp_work, &t->d_warp_work)) ||
       (rc = upload(t, term_src, &t->d_term_src)) ||
@@ -572,6 +589,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_prog = stream_prog;
   c.stream_half = stream_half;
   c.stream_units = stream_units;
+  c.stream_hp = stream_hp;
   if (schedule == kScheduleWide) {
     const HostGame& h = t->host[0];
     c.wide_levels = (int)t->wide_inner_off.size() - 1;
@@ -1179,8 +1197,13 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
     if (rc || (sch == CFR_SCHEDULE_WIDE && n_games != 1)) continue;
     cand.schedule = sch;
     cand.chunk_hands = 0;
-    rc = trial(cand, &ms);
-    if (!rc && ms < top_ms) top_ms = ms, top = cand;
+    for (int wh : {32, 64}) {  // stream schedule: hands per warp
+      if (rc || (sch == CFR_SCHEDULE_WIDE && wh == 64)) continue;
+      cand.warp_hands = sch == CFR_SCHEDULE_STREAM ? wh : 0;
+      rc = trial(cand, &ms);
+      if (!rc && ms < top_ms) top_ms = ms, top = cand;
+    }
+    cand.warp_hands = 0;
   }
   cand = top;
   for (int tn : {1, 2, 4, 8}) {  // terminal nodes per block, for the fastest layout

@@ -186,9 +186,10 @@ struct Single {  // plain FP32 values
   static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ V vmax(V a, V b) { return fmaxf(a, b); }
   static __device__ __forceinline__ bool positive(V a) { return a > 0.f; }
-  static __device__ __forceinline__ V recip(V a) { return __fdiv_rn(1.f, a); }
+  // correctly rounded reciprocal: the same bits as 1 / a in IEEE division
+  static __device__ __forceinline__ V recip(V a) { return __frcp_rn(a); }
   static __device__ __forceinline__ V one() { return 1.f; }
-  static __device__ __forceinline__ V uniform(int A) { return __fdiv_rn(1.f, (float)A); }
+  static __device__ __forceinline__ V uniform(int A) { return __frcp_rn((float)A); }
   static __device__ __forceinline__ V of_double(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ double to_double(V a) { return f2d(a); }
   static __device__ __forceinline__ ff to_ff(V a) { return ff_of(a); }
@@ -976,7 +977,9 @@ __device__ __forceinline__ void regret_match(const double (&Rv)[kStreamMaxAction
   }
 }
 
-// regret_match with a compile-time action count (same arithmetic, no per-action guards).
+// regret_match with a compile-time action count (same arithmetic, no per-action guards), with
+// the three cases selected per lane instead of branched on: the hands of a warp often fall
+// in different cases, and a branch would run all three paths for them.
 template <typename P, int NA>
 __device__ __forceinline__ void regret_match_n(const double (&Rv)[NA], typename P::V (&sg)[NA]) {
   using V = typename P::V;
@@ -989,17 +992,12 @@ __device__ __forceinline__ void regret_match_n(const double (&Rv)[NA], typename 
     if (P::positive(x)) ++npos, last = a;
     tot = P::add(tot, x);
   }
-  if (npos == 1) {
+  const V inv = P::recip(tot);  // unused (and possibly not finite) unless npos > 1
+  const V uni = P::uniform(NA);
 #pragma unroll
-    for (int a = 0; a < NA; ++a) sg[a] = a == last ? P::one() : P::zero();
-  } else if (npos > 1) {
-    const V inv = P::recip(tot);
-#pragma unroll
-    for (int a = 0; a < NA; ++a) sg[a] = P::mul(sg[a], inv);
-  } else {
-    const V uni = P::uniform(NA);
-#pragma unroll
-    for (int a = 0; a < NA; ++a) sg[a] = uni;
+  for (int a = 0; a < NA; ++a) {
+    const V many = P::mul(sg[a], inv);
+    sg[a] = npos > 1 ? many : npos == 1 ? (a == last ? P::one() : P::zero()) : uni;
   }
 }
 
@@ -1024,41 +1022,46 @@ __device__ __forceinline__ Op decode(const ProgOp& o) {
           o.first_kid};
 }
 
-// One lane's view of its subgame for the stream passes.
-template <typename P>
+// One lane's view of its subgame for the stream passes.  A warp owns 32 * HP consecutive
+// hands; lane l holds hands l, l + 32, ..., l + 32 (HP - 1) of them (HP = 1 or 2), so the
+// walk's control work (program decode, branches, stack and ring bookkeeping, load issue)
+// is shared by HP hands per lane and each lane has HP independent arithmetic chains.
+template <typename P, int HP>
 struct StreamLane {
   using V = typename P::V;
   const GameDev& G;
   const ProgOp* prog;     // the program (shared memory when staged)
   const uint32_t* units;  // this player's loads, bottom-up pass then top-down pass
   int p;
-  bool valid;
-  uint64_t hmask;
+  bool valid[HP];         // hand l + 32 k exists
+  uint64_t hmask[HP];
   size_t stride;
-  double* R;        // column h of R
+  double* R;        // column of the lane's first hand of R (hand k: + 32 k)
   double* S;
-  double* M;        // column h of the Predictive CFR+ prediction (null otherwise)
-  V* reach;         // column h of player p's reach plane
-  V* cfv;           // column h of player p's value plane
-  uint64_t* ring;   // this lane's prefetch ring: unit u of half k at ring[(k * half + u) * 32]
-  int half;         // 8-byte units per lane in each half of the ring
-  V* st;            // this lane's stack: slot s at st[s * 32]
+  double* M;        // the same of the Predictive CFR+ prediction (null otherwise)
+  V* reach;         // column of the lane's first hand in player p's reach plane
+  V* cfv;           // the same in player p's value plane
+  uint64_t* ring;   // this lane's entry of the prefetch ring: unit u of half k at
+                    // ring[(k * half + u) * 32 * HP], its hand k at + 32 k
+  int half;         // units in each half of the ring
+  V* st;            // this lane's stack: slot s, hand k at st[(s * HP + k) * 32]
 };
 
 // Issue loads [u0, u1) of a pass into ring half `half` (one commit group).  A unit is the
-// warp's 32-hand segment of one row: 256 bytes of FP64 (or pair) values, 128 of FP32 ones,
-// landing at 256-byte slot u - u0 of the ring half.  The warp's lanes split the units into
-// 16-byte pieces (16 per 256-byte unit, 8 per 128-byte one), so one copy instruction moves
-// pieces of two units.
-template <typename P>
-__device__ __forceinline__ void stream_issue(const StreamLane<P>& L, const uint32_t* units, int u0, int u1,
+// warp's segment of 32 * HP consecutive elements of one row (256 * HP bytes of FP64 or pair
+// values, 128 * HP of FP32 ones), landing at slot u - u0 of the ring half.  The warp's lanes
+// split the units into 16-byte pieces (16 * HP per FP64 unit), so that one copy instruction
+// moves pieces of several units.
+template <typename P, int HP>
+__device__ __forceinline__ void stream_issue(const StreamLane<P, HP>& L, const uint32_t* units, int u0, int u1,
                                              int half) {
   using V = typename P::V;
+  constexpr int kPieces = 16 * HP;  // 16-byte pieces of one unit
   const int lane = threadIdx.x & 31;
-  unsigned char* ring = reinterpret_cast<unsigned char*>(L.ring - lane + (size_t)half * L.half * 32);
-  const int pieces = (u1 - u0) * 16;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(L.ring - lane + (size_t)half * L.half * 32 * HP);
+  const int pieces = (u1 - u0) * kPieces;
   for (int k = lane; k < pieces; k += 32) {
-    const int u = u0 + (k >> 4), part = k & 15;
+    const int u = u0 + k / kPieces, part = k % kPieces;
     const uint32_t d = units[u];
     const uint32_t arr = d >> kArrShift, off = d & kArrOffMask;
     // the row's segment starts at the warp's first hand: the lane's column pointer minus its lane
@@ -1069,11 +1072,11 @@ __device__ __forceinline__ void stream_issue(const StreamLane<P>& L, const uint3
       src = L.S - lane + off + 2 * part;
     else if (arr == kArrM)
       src = L.M - lane + off + 2 * part;
-    else if (part * 16 >= 32 * (int)sizeof(V))  // FP32 rows fill half a slot
+    else if (part * 16 >= 32 * HP * (int)sizeof(V))  // FP32 rows fill half a slot
       continue;
     else
       src = reinterpret_cast<const unsigned char*>((arr == kArrReach ? L.reach : L.cfv) - lane + off) + part * 16;
-    cp_async<16>(ring + (size_t)(u - u0) * 256 + (size_t)part * 16, src);
+    cp_async<16>(ring + (size_t)(u - u0) * 256 * HP + (size_t)part * 16, src);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -1083,123 +1086,85 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// This lane's value in a ring unit (slot: the lane's 8-byte entry of the unit): 8-byte
-// values sit at entry `lane`, FP32 values packed at float `lane` of the unit.
-template <typename P>
-__device__ __forceinline__ typename P::V ring_value(const uint64_t* slot) {
+// This lane's value of its hand k in a ring unit (slot: the lane's entry of the unit):
+// 8-byte values sit at entry lane + 32 k, FP32 values packed at float lane + 32 k.
+template <typename P, int HP>
+__device__ __forceinline__ typename P::V ring_value(const uint64_t* slot, int k) {
   using V = typename P::V;
   if constexpr (sizeof(V) == 4) {
     const int lane = threadIdx.x & 31;
-    return reinterpret_cast<const V*>(slot - lane)[lane];
+    return reinterpret_cast<const V*>(slot - lane)[lane + 32 * k];
   } else {
-    return *reinterpret_cast<const V*>(slot);
+    return *reinterpret_cast<const V*>(slot + 32 * k);
   }
 }
 
-// Bottom-up work at one of the player's decision nodes with NA actions (Stages 6-7): the
-// children's values (ring or stack), regret matching of R (R + M for Predictive CFR+), the
-// node value, and the new R, S (and M) rows.  NA is a compile-time constant so that the
-// actions' FP64 update chains are straight-line code the compiler can interleave.
-template <typename P, int NA>
-__device__ __forceinline__ typename P::V decision_back(const StreamLane<P>& L, const Op& nd, const uint64_t* ring,
-                                                       int& u, int& sp, const Discount& d, int variant) {
+// Bottom-up work at one of the player's decision nodes with NA actions (Stages 6-7), for
+// each of the lane's HP hands: the children's values (ring or stack), regret matching of R
+// (R + M for Predictive CFR+), the node value, and the new R, S (and M) rows.  NA is a
+// compile-time constant so that the actions' FP64 update chains are straight-line code the
+// compiler can interleave.
+template <typename P, int NA, int HP>
+__device__ __forceinline__ void decision_back(const StreamLane<P, HP>& L, const Op& nd, const uint64_t* ring, int& u,
+                                              int& sp, const Discount& d, int variant, typename P::V (&val)[HP]) {
   using V = typename P::V;
+  constexpr int U = 32 * HP;  // ring entries per unit
   V* st = L.st;
-  V c[NA];
+  V c[NA][HP];
 #pragma unroll
   for (int a = 0; a < NA; ++a) {
-    if ((nd.tmask >> a) & 1)
-      c[a] = ring_value<P>(ring + (size_t)(u++) * 32);
-    else
-      c[a] = st[(--sp) * 32];
+    if ((nd.tmask >> a) & 1) {
+#pragma unroll
+      for (int k = 0; k < HP; ++k) c[a][k] = ring_value<P, HP>(ring + (size_t)u * U, k);
+      ++u;
+    } else {
+      --sp;
+#pragma unroll
+      for (int k = 0; k < HP; ++k) c[a][k] = st[(sp * HP + k) * 32];
+    }
   }
   const bool pred = L.M != nullptr;  // Predictive CFR+: R, M, S, reach
-  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * 32);
-  const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + (pred ? 2 : 1) * NA) * 32);
-  const V pi = ring_value<P>(ring + (size_t)(u + (pred ? 3 : 2) * NA) * 32);
+  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * U);
+  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * U);
+  const double* Sr = reinterpret_cast<const double*>(ring + (size_t)(u + (pred ? 2 : 1) * NA) * U);
+  const uint64_t* pislot = ring + (size_t)(u + (pred ? 3 : 2) * NA) * U;
   u += (pred ? 3 : 2) * NA + 1;
-  double Rv[NA];
-  V sg[NA];
-  {
-    double Rm[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) Rv[a] = Rm[a] = Rr[(size_t)a * 32];
-    if (pred) {  // Predictive CFR+ matches R + M (no FP64 add for the other variants)
+  for (int k = 0; k < HP; ++k) {
+    const V pi = ring_value<P, HP>(pislot, k);
+    double Rv[NA];
+    V sg[NA];
+    {
+      double Rm[NA];
 #pragma unroll
-      for (int a = 0; a < NA; ++a) Rm[a] = Rv[a] + Mr[(size_t)a * 32];
-    }
-    regret_match_n<P, NA>(Rm, sg);
-  }
-  typename P::Acc acc = P::acc0();
+      for (int a = 0; a < NA; ++a) Rv[a] = Rm[a] = Rr[(size_t)a * U + 32 * k];
+      if (pred) {  // Predictive CFR+ matches R + M (no FP64 add for the other variants)
 #pragma unroll
-  for (int a = 0; a < NA; ++a) P::acc_mul(acc, sg[a], c[a]);
-  const V val = P::value(acc);
-#pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    const V rr = P::sub(c[a], val);                          // instantaneous regret
-    const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
-    const double rd = P::to_double(rr);
-    double x = Rv[a] + rd;
-    if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
-    if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;
-    const double sn = fma(Sr[(size_t)a * 32], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
-    if (L.valid) {
-      L.R[(size_t)nd.row_off + (size_t)a * L.stride] = x;
-      L.S[(size_t)nd.row_off + (size_t)a * L.stride] = sn;
-      if (pred) L.M[(size_t)nd.row_off + (size_t)a * L.stride] = rd;
-    }
-  }
-  return val;
-}
-
-// Bottom-up pass over chunk [k0, k1) (program positions counted from its end).  A node's
-// children values come from the ring (terminal children, in child order) or from the stack
-// (inner children, child 0 on top).
-template <typename P>
-__device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp,
-                                                      const Discount& d, int variant) {
-  using V = typename P::V;
-  const int N = L.G.prog_len;
-  const uint64_t* ring = L.ring + (size_t)half * L.half * 32;
-  V* st = L.st;
-  int u = 0;
-  for (int k = k0; k < k1; ++k) {
-    const Op nd = decode(L.prog[N - 1 - k]);
-    const int A = nd.A;
-    V val;
-    if (nd.type == kChance) {  // children values carry the card probabilities
-      typename P::Acc acc = P::acc0();
-      const bool term = nd.tmask & 1;  // all children terminal (after an all-in) or all inner
-      for (int a = 0; a < A; ++a) {
-        const V x = term ? ring_value<P>(ring + (size_t)(u++) * 32) : st[(--sp) * 32];
-        if (!((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull)) P::acc(acc, x);
+        for (int a = 0; a < NA; ++a) Rm[a] = Rv[a] + Mr[(size_t)a * U + 32 * k];
       }
-      val = P::value(acc);
-    } else if (nd.player != L.p) {
-      typename P::Acc acc = P::acc0();
-      for (int a = 0; a < A; ++a) {
-        V x;
-        if ((nd.tmask >> a) & 1)
-          x = ring_value<P>(ring + (size_t)(u++) * 32);
-        else
-          x = st[(--sp) * 32];
-        P::acc(acc, x);
-      }
-      val = P::value(acc);
-    } else {  // the player's decision node: its action count as a compile-time constant
-      switch (A) {
-        case 1: val = decision_back<P, 1>(L, nd, ring, u, sp, d, variant); break;
-        case 2: val = decision_back<P, 2>(L, nd, ring, u, sp, d, variant); break;
-        case 3: val = decision_back<P, 3>(L, nd, ring, u, sp, d, variant); break;
-        case 4: val = decision_back<P, 4>(L, nd, ring, u, sp, d, variant); break;
-        case 5: val = decision_back<P, 5>(L, nd, ring, u, sp, d, variant); break;
-        case 6: val = decision_back<P, 6>(L, nd, ring, u, sp, d, variant); break;
-        case 7: val = decision_back<P, 7>(L, nd, ring, u, sp, d, variant); break;
-        default: val = decision_back<P, kStreamMaxActions>(L, nd, ring, u, sp, d, variant); break;
+      regret_match_n<P, NA>(Rm, sg);
+    }
+    typename P::Acc acc = P::acc0();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) P::acc_mul(acc, sg[a], c[a][k]);
+    val[k] = P::value(acc);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const V rr = P::sub(c[a][k], val[k]);                    // instantaneous regret
+      const double contrib = P::to_double(P::mul(pi, sg[a]));  // pi_i(I) sigma(I, a)
+      const double rd = P::to_double(rr);
+      double x = Rv[a] + rd;
+      if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+      if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;
+      const double sn =
+          fma(Sr[(size_t)a * U + 32 * k], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
+      if (L.valid[k]) {
+        const size_t at = (size_t)nd.row_off + (size_t)a * L.stride + 32 * k;
+        L.R[at] = x;
+        L.S[at] = sn;
+        if (pred) L.M[at] = rd;
       }
     }
-    st[(sp++) * 32] = val;
   }
 }
 
@@ -1207,77 +1172,161 @@ __device__ __forceinline__ void stream_backward_chunk(const StreamLane<P>& L, in
 // recorded, sigma = RM(R) (of R + M for Predictive CFR+) is formed from the ring, and each
 // child's reach x sigma(a) goes to the terminal's row or onto the stack (child 0 on top).  NA
 // is a compile-time constant, as in decision_back.
-template <typename P, int NA>
-__device__ __forceinline__ void decision_fwd(const StreamLane<P>& L, const Op& nd, const uint64_t* ring, int& u,
-                                             int& sp, typename P::V x) {
+template <typename P, int NA, int HP>
+__device__ __forceinline__ void decision_fwd(const StreamLane<P, HP>& L, const Op& nd, const uint64_t* ring, int& u,
+                                             int& sp, const typename P::V (&x)[HP]) {
   using V = typename P::V;
+  constexpr int U = 32 * HP;
   V* st = L.st;
-  if (L.valid) L.reach[nd.node_off] = x;
   const bool pred = L.M != nullptr;  // Predictive CFR+: R then M
-  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * 32);
-  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * 32);
+  const double* Rr = reinterpret_cast<const double*>(ring + (size_t)u * U);
+  const double* Mr = reinterpret_cast<const double*>(ring + (size_t)(u + NA) * U);
   u += (pred ? 2 : 1) * NA;
-  double Rv[NA];
-  V sg[NA];
+  V sg[NA][HP];
 #pragma unroll
-  for (int a = 0; a < NA; ++a) Rv[a] = Rr[(size_t)a * 32];
-  if (pred) {  // Predictive CFR+ matches R + M
+  for (int k = 0; k < HP; ++k) {
+    if (L.valid[k]) L.reach[(size_t)nd.node_off + 32 * k] = x[k];
+    double Rv[NA];
+    V s1[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) Rv[a] += Mr[(size_t)a * 32];
+    for (int a = 0; a < NA; ++a) Rv[a] = Rr[(size_t)a * U + 32 * k];
+    if (pred) {  // Predictive CFR+ matches R + M
+#pragma unroll
+      for (int a = 0; a < NA; ++a) Rv[a] += Mr[(size_t)a * U + 32 * k];
+    }
+    regret_match_n<P, NA>(Rv, s1);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) sg[a][k] = s1[a];
   }
-  regret_match_n<P, NA>(Rv, sg);
 #pragma unroll
   for (int a = NA - 1; a >= 0; --a) {
-    const V y = P::mul(x, sg[a]);
     if ((nd.tmask >> a) & 1) {
-      if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
+#pragma unroll
+      for (int k = 0; k < HP; ++k)
+        if (L.valid[k]) L.reach[(size_t)(nd.first_kid + a) * L.stride + 32 * k] = P::mul(x[k], sg[a][k]);
     } else {
-      st[(sp++) * 32] = y;
+#pragma unroll
+      for (int k = 0; k < HP; ++k) st[(sp * HP + k) * 32] = P::mul(x[k], sg[a][k]);
+      ++sp;
     }
+  }
+}
+
+// Bottom-up pass over chunk [k0, k1) (program positions counted from its end).  A node's
+// children values come from the ring (terminal children, in child order) or from the stack
+// (inner children, child 0 on top).
+template <typename P, int HP>
+__device__ __forceinline__ void stream_backward_chunk(const StreamLane<P, HP>& L, int k0, int k1, int half, int& sp,
+                                                      const Discount& d, int variant) {
+  using V = typename P::V;
+  constexpr int U = 32 * HP;
+  const int N = L.G.prog_len;
+  const uint64_t* ring = L.ring + (size_t)half * L.half * U;
+  V* st = L.st;
+  int u = 0;
+  for (int k = k0; k < k1; ++k) {
+    const Op nd = decode(L.prog[N - 1 - k]);
+    const int A = nd.A;
+    V val[HP];
+    if (nd.type == kChance || nd.player != L.p) {
+      // chance: children values carry the card probabilities (a hand holding the card gets
+      // nothing from that child); opponent: the plain sum
+      const bool chance = nd.type == kChance;
+      const bool term_all = nd.tmask & 1;  // chance: all children terminal (after an all-in) or all inner
+      typename P::Acc acc[HP];
+#pragma unroll
+      for (int j = 0; j < HP; ++j) acc[j] = P::acc0();
+      for (int a = 0; a < A; ++a) {
+        const bool term = chance ? term_all : ((nd.tmask >> a) & 1);
+        const int deal = chance ? L.G.nodes[nd.first_kid + a].deal : 0;
+        if (!term) --sp;
+#pragma unroll
+        for (int j = 0; j < HP; ++j) {
+          const V x = term ? ring_value<P, HP>(ring + (size_t)u * U, j) : st[(sp * HP + j) * 32];
+          if (!chance || !((L.hmask[j] >> deal) & 1ull)) P::acc(acc[j], x);
+        }
+        if (term) ++u;
+      }
+#pragma unroll
+      for (int j = 0; j < HP; ++j) val[j] = P::value(acc[j]);
+    } else {  // the player's decision node: its action count as a compile-time constant
+      switch (A) {
+        case 1: decision_back<P, 1, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 2: decision_back<P, 2, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 3: decision_back<P, 3, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 4: decision_back<P, 4, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 5: decision_back<P, 5, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 6: decision_back<P, 6, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        case 7: decision_back<P, 7, HP>(L, nd, ring, u, sp, d, variant, val); break;
+        default: decision_back<P, kStreamMaxActions, HP>(L, nd, ring, u, sp, d, variant, val); break;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < HP; ++j) st[(sp * HP + j) * 32] = val[j];
+    ++sp;
   }
 }
 
 // Top-down pass over chunk [k0, k1) with sigma = RM(R): records the reach at the player's
 // decision nodes, at chance nodes and, for the terminal children, at the terminals; pushes
 // the reach of the inner children (child 0 on top).
-template <typename P>
-__device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int k0, int k1, int half, int& sp) {
+template <typename P, int HP>
+__device__ __forceinline__ void stream_forward_chunk(const StreamLane<P, HP>& L, int k0, int k1, int half, int& sp) {
   using V = typename P::V;
-  const uint64_t* ring = L.ring + (size_t)half * L.half * 32;
+  constexpr int U = 32 * HP;
+  const uint64_t* ring = L.ring + (size_t)half * L.half * U;
   V* st = L.st;
   int u = 0;
   for (int k = k0; k < k1; ++k) {
     const Op nd = decode(L.prog[k]);
-    V x = st[(--sp) * 32];
-    if (nd.deal != kNoCard && ((L.hmask >> nd.deal) & 1ull)) x = P::zero();
+    --sp;
+    V x[HP];
+#pragma unroll
+    for (int j = 0; j < HP; ++j) {
+      x[j] = st[(sp * HP + j) * 32];
+      if (nd.deal != kNoCard && ((L.hmask[j] >> nd.deal) & 1ull)) x[j] = P::zero();
+    }
     const int A = nd.A;
     if (nd.type == kDecision && nd.player == L.p) {  // its action count as a compile-time constant
       switch (A) {
-        case 1: decision_fwd<P, 1>(L, nd, ring, u, sp, x); break;
-        case 2: decision_fwd<P, 2>(L, nd, ring, u, sp, x); break;
-        case 3: decision_fwd<P, 3>(L, nd, ring, u, sp, x); break;
-        case 4: decision_fwd<P, 4>(L, nd, ring, u, sp, x); break;
-        case 5: decision_fwd<P, 5>(L, nd, ring, u, sp, x); break;
-        case 6: decision_fwd<P, 6>(L, nd, ring, u, sp, x); break;
-        case 7: decision_fwd<P, 7>(L, nd, ring, u, sp, x); break;
-        default: decision_fwd<P, kStreamMaxActions>(L, nd, ring, u, sp, x); break;
+        case 1: decision_fwd<P, 1, HP>(L, nd, ring, u, sp, x); break;
+        case 2: decision_fwd<P, 2, HP>(L, nd, ring, u, sp, x); break;
+        case 3: decision_fwd<P, 3, HP>(L, nd, ring, u, sp, x); break;
+        case 4: decision_fwd<P, 4, HP>(L, nd, ring, u, sp, x); break;
+        case 5: decision_fwd<P, 5, HP>(L, nd, ring, u, sp, x); break;
+        case 6: decision_fwd<P, 6, HP>(L, nd, ring, u, sp, x); break;
+        case 7: decision_fwd<P, 7, HP>(L, nd, ring, u, sp, x); break;
+        default: decision_fwd<P, kStreamMaxActions, HP>(L, nd, ring, u, sp, x); break;
       }
     } else if (nd.type == kChance) {  // the player's reach passes through to each card
-      if (L.valid) L.reach[nd.node_off] = x;  // read by the showdowns of an all-in run-out
+#pragma unroll
+      for (int j = 0; j < HP; ++j)
+        if (L.valid[j]) L.reach[(size_t)nd.node_off + 32 * j] = x[j];  // read by an all-in run-out's showdowns
       if (nd.tmask & 1) {  // terminal children: their reach, zero where the hand holds the card
         for (int a = 0; a < A; ++a) {
-          const V y = ((L.hmask >> L.G.nodes[nd.first_kid + a].deal) & 1ull) ? P::zero() : x;
-          if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = y;
+          const int deal = L.G.nodes[nd.first_kid + a].deal;
+#pragma unroll
+          for (int j = 0; j < HP; ++j)
+            if (L.valid[j])
+              L.reach[(size_t)(nd.first_kid + a) * L.stride + 32 * j] = ((L.hmask[j] >> deal) & 1ull) ? P::zero() : x[j];
         }
       } else {  // inner children apply their own card when they pop it
-        for (int a = 0; a < A; ++a) st[(sp++) * 32] = x;
+        for (int a = 0; a < A; ++a) {
+#pragma unroll
+          for (int j = 0; j < HP; ++j) st[(sp * HP + j) * 32] = x[j];
+          ++sp;
+        }
       }
     } else {  // opponent decision: the player's reach passes through
       for (int a = A - 1; a >= 0; --a) {
         if ((nd.tmask >> a) & 1) {
-          if (L.valid) L.reach[(size_t)(nd.first_kid + a) * L.stride] = x;
+#pragma unroll
+          for (int j = 0; j < HP; ++j)
+            if (L.valid[j]) L.reach[(size_t)(nd.first_kid + a) * L.stride + 32 * j] = x[j];
         } else {
-          st[(sp++) * 32] = x;
+#pragma unroll
+          for (int j = 0; j < HP; ++j) st[(sp * HP + j) * 32] = x[j];
+          ++sp;
         }
       }
     }
@@ -1285,14 +1334,14 @@ __device__ __forceinline__ void stream_forward_chunk(const StreamLane<P>& L, int
 }
 
 // One pass (list q of the load tables): chunk c + 1 loads while chunk c computes.
-template <typename P, typename F>
-__device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int q, const uint32_t* units, F compute) {
+template <typename P, int HP, typename F>
+__device__ __forceinline__ void stream_pass(const StreamLane<P, HP>& L, int q, const uint32_t* units, F compute) {
   const int32_t* ch = L.G.chunks + 2 * (size_t)L.G.chunk_off[q];  // (node, unit) pairs
   const int nch = L.G.chunk_count[q];
-  stream_issue<P>(L, units, ch[1], ch[3], 0);
+  stream_issue<P, HP>(L, units, ch[1], ch[3], 0);
   for (int c = 0; c < nch; ++c) {
     if (c + 1 < nch)
-      stream_issue<P>(L, units, ch[2 * c + 3], ch[2 * c + 5], (c + 1) & 1);
+      stream_issue<P, HP>(L, units, ch[2 * c + 3], ch[2 * c + 5], (c + 1) & 1);
     else
       asm volatile("cp.async.commit_group;" ::: "memory");
     cp_async_wait_group<1>();  // chunk c has landed: this lane's pieces
@@ -1303,8 +1352,8 @@ __device__ __forceinline__ void stream_pass(const StreamLane<P>& L, int q, const
 }
 
 // Grid: one block per (player, work item); a work item is a game and the first of the
-// kStreamWarps consecutive groups of 32 hands its warps own.
-template <typename P>
+// kStreamWarps consecutive groups of 32 * HP hands its warps own.
+template <typename P, int HP>
 __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
     const GameDev* __restrict__ games, const Work* __restrict__ work, int n_work, int player_mask, int advance,
     int* iter, unsigned* done, const Discount* __restrict__ disc_tab, int variant, int depth, int prog_nodes,
@@ -1319,16 +1368,16 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
   const Work wk = work[item];
   const GameDev& G = games[wk.game];
   const int unit = wk.unit + warp;
-  const bool active = unit * 32 < G.n_hands;
+  const bool active = unit * 32 * HP < G.n_hands;
   if (threadIdx.x == 0) disc = disc_tab[*iter];
   // shared memory: the program, then per warp a prefetch ring (2 halves of half_units
-  // 8-byte units per lane) and a stack
+  // units of 32 * HP 8-byte entries) and a stack (depth slots of HP values per lane)
   const size_t tables = (size_t)prog_nodes * sizeof(ProgOp) + (size_t)prog_units * 4;  // multiple of 16
   ProgOp* sprog = reinterpret_cast<ProgOp*>(sms);
   uint32_t* sunits = reinterpret_cast<uint32_t*>(sms + (size_t)prog_nodes * sizeof(ProgOp));
-  uint64_t* ring = reinterpret_cast<uint64_t*>(sms + tables) + (size_t)warp * 2 * half_units * 32 + lane;
-  V* st = reinterpret_cast<V*>(sms + tables + (size_t)kStreamWarps * 2 * half_units * 32 * 8) +
-          (size_t)warp * depth * 32 + lane;
+  uint64_t* ring = reinterpret_cast<uint64_t*>(sms + tables) + (size_t)warp * 2 * half_units * 32 * HP + lane;
+  V* st = reinterpret_cast<V*>(sms + tables + (size_t)kStreamWarps * 2 * half_units * 32 * HP * 8) +
+          (size_t)warp * depth * 32 * HP + lane;
   // this player's loads: the bottom-up pass's, then the top-down pass's
   const uint32_t* gunits_b = G.units + G.unit_off[p];
   const uint32_t* gunits_f = G.units + G.unit_off[2 + p];
@@ -1344,27 +1393,34 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_stream_update(
   pdl_trigger();
   __syncthreads();  // disc, program
   if (active) {
-    const int h = unit * 32 + lane;  // < hstride (a multiple of 32)
-    const bool valid = h < G.n_hands;
+    const int h = unit * 32 * HP + lane;  // hand k is h + 32 k < hstride (a multiple of 32 * HP)
     const size_t stride = (size_t)G.hstride;
     const size_t plane = (size_t)p * G.n_nodes * stride + h;
     const bool staged = prog_nodes > 0;
-    const StreamLane<P> L{G, staged ? sprog : G.prog, staged ? sunits : gunits_b, p, valid,
-                          valid ? G.hand_mask[h] : 0ull, stride,
-                          G.R + h, G.S + h, G.M ? G.M + h : nullptr, static_cast<V*>(G.reach) + plane,
-                          static_cast<V*>(G.cfv) + plane, ring, half_units, st};
+    StreamLane<P, HP> L{G, staged ? sprog : G.prog, staged ? sunits : gunits_b, p, {}, {}, stride,
+                        G.R + h, G.S + h, G.M ? G.M + h : nullptr, static_cast<V*>(G.reach) + plane,
+                        static_cast<V*>(G.cfv) + plane, ring, half_units, st};
+#pragma unroll
+    for (int k = 0; k < HP; ++k) {
+      L.valid[k] = h + 32 * k < G.n_hands;
+      L.hmask[k] = L.valid[k] ? G.hand_mask[h + 32 * k] : 0ull;
+    }
     const Discount d = disc;
     int sp = 0;
-    stream_pass<P>(L, p, L.units, [&](int k0, int k1, int half) {
-      stream_backward_chunk<P>(L, k0, k1, half, sp, d, variant);
+    stream_pass<P, HP>(L, p, L.units, [&](int k0, int k1, int half) {
+      stream_backward_chunk<P, HP>(L, k0, k1, half, sp, d, variant);
     });
-    if (valid) L.cfv[0] = st[0];  // root value (read-back)
-    __threadfence_block();       // the new R rows are read back by the warp's copies below
+#pragma unroll
+    for (int k = 0; k < HP; ++k)
+      if (L.valid[k]) L.cfv[32 * k] = st[k * 32];  // root value (read-back)
+    __threadfence_block();  // the new R rows are read back by the warp's copies below
     __syncwarp();
-    st[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
+#pragma unroll
+    for (int k = 0; k < HP; ++k)
+      st[k * 32] = L.valid[k] ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h + 32 * k] : P::zero();
     sp = 1;
-    stream_pass<P>(L, 2 + p, staged ? sunits + nb : gunits_f,
-                   [&](int k0, int k1, int half) { stream_forward_chunk<P>(L, k0, k1, half, sp); });
+    stream_pass<P, HP>(L, 2 + p, staged ? sunits + nb : gunits_f,
+                       [&](int k0, int k1, int half) { stream_forward_chunk<P, HP>(L, k0, k1, half, sp); });
   }
 
   if (advance) {
@@ -1671,7 +1727,8 @@ static cudaError_t configure_precision() {
   if (e == cudaSuccess) e = configure_one(k_terminal<P, false>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_terminal<P, true>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_average_rows<P>, 0);
-  if (e == cudaSuccess) e = configure_one(k_stream_update<P>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_stream_update<P, 1>, 200 * 1024);
+  if (e == cudaSuccess) e = configure_one(k_stream_update<P, 2>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_current_rows<P>, 0);
   return e;
 }
@@ -1831,13 +1888,13 @@ int launch_init(const LaunchCtx& c, void* stream) {
   if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeInit, 3, 0, stream);
   return launch_hand<kModeInit>(c, 3, 0, stream, false);
 }
-template <typename P>
+template <typename P, int HP>
 static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   const int players = player_mask == 3 ? 2 : 1;
   const int grid = c.n_warp_work * players;
   const size_t smem =
-      stream_smem_size(c.stream_prog, c.stream_units, c.stream_half, c.stream_depth, sizeof(typename P::V));
-  const cudaError_t e = launch_kernel(k_stream_update<P>, grid, kStreamWarps * 32, smem, stream, c.pdl != 0,
+      stream_smem_size(c.stream_prog, c.stream_units, c.stream_half, c.stream_depth, sizeof(typename P::V), HP);
+  const cudaError_t e = launch_kernel(k_stream_update<P, HP>, grid, kStreamWarps * 32, smem, stream, c.pdl != 0,
                                       c.games, c.warp_work, c.n_warp_work, player_mask, advance, c.iter, c.done,
                                       c.disc, c.variant, c.stream_depth, c.stream_prog, c.stream_units,
                                       c.stream_half);
@@ -1851,8 +1908,11 @@ static int launch_stream_p(const LaunchCtx& c, int player_mask, int advance, voi
 int launch_update(const LaunchCtx& c, int player_mask, int advance, void* stream) {
   if (c.schedule == kScheduleWide) return launch_wide_pass(c, kModeUpdate, player_mask, advance, stream);
   if (c.schedule == kScheduleStream)
-    return c.precision == kPrecisionSingle ? launch_stream_p<Single>(c, player_mask, advance, stream)
-                                           : launch_stream_p<Pairs>(c, player_mask, advance, stream);
+    return c.precision == kPrecisionSingle
+               ? (c.stream_hp == 2 ? launch_stream_p<Single, 2>(c, player_mask, advance, stream)
+                                   : launch_stream_p<Single, 1>(c, player_mask, advance, stream))
+               : (c.stream_hp == 2 ? launch_stream_p<Pairs, 2>(c, player_mask, advance, stream)
+                                   : launch_stream_p<Pairs, 1>(c, player_mask, advance, stream));
   return launch_hand<kModeUpdate>(c, player_mask, advance, stream, c.pdl != 0);
 }
 

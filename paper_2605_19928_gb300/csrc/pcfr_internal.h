@@ -194,6 +194,7 @@ struct LaunchCtx {
                                // memory; 0 = read from global memory
   int stream_half;             // units per lane in each half of the stream prefetch ring
   int stream_units;            // load descriptors staged per block (0 when the program is not)
+  int stream_hp;               // hands per lane of the stream schedule (1 or 2): a warp owns 32 * stream_hp
   // wide schedule (one game): level l's inner nodes are wide_inner[wide_inner_off[l] ..
   // wide_inner_off[l + 1]), the nodes whose reach is stored wide_fwd[wide_fwd_off[l] ..
   // wide_fwd_off[l + 1]) (all but the run-out nodes that read their source's reach)
@@ -274,11 +275,11 @@ int launch_leaf_inputs(const LaunchCtx& c, const LeafCtx& L, int use_bar, void* 
 int launch_leaf_net(const LaunchCtx& c, const LeafCtx& L, void* stream);
 int launch_leaf_values(const LaunchCtx& c, const LeafCtx& L, int player, int use_bar, void* stream);
 // Dynamic shared memory of one stream-schedule block: the staged program (prog_nodes nodes)
-// and one player's load descriptors (prog_units), a prefetch ring of 2 x half 8-byte units
-// and a stack of `depth` slots (es bytes) per lane.
-inline size_t stream_smem_size(int prog_nodes, int prog_units, int half, int depth, size_t es) {
+// and one player's load descriptors (prog_units), and per lane a prefetch ring of 2 x half
+// units of hp 8-byte entries and a stack of `depth` slots of hp values (es bytes each).
+inline size_t stream_smem_size(int prog_nodes, int prog_units, int half, int depth, size_t es, int hp) {
   return (size_t)prog_nodes * sizeof(ProgOp) + (size_t)prog_units * 4 +
-         (size_t)kStreamWarps * 32 * (2 * (size_t)half * 8 + (size_t)depth * es);
+         (size_t)kStreamWarps * 32 * hp * (2 * (size_t)half * 8 + (size_t)depth * es);
 }
 
 }  // namespace pcfr

@@ -390,15 +390,25 @@ def _state(tree, n_games, with_pred=False):
     return out
 
 
+@pytest.mark.parametrize("warp_hands", [32, 64])
 @pytest.mark.parametrize("precision", ["pairs", "single"])
 @pytest.mark.parametrize("variant,alternating", [("dcfr", True), ("cfr+", True), ("cfr", False), ("pcfr+", True)])
-def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alternating):
-    specs = [river(203, seed=51), river(64, seed=52, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
-             leduc_random(seed=53), turn(40, seed=54), kuhn_random(seed=55)]
+def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alternating, warp_hands):
+    """Both hands-per-warp forms of the stream update.  64 hands per warp (two per lane) needs
+    rows padded to 64, so that batch has no one-card games, and rivers only (a turn's chance
+    node stacks 48 subtrees per hand, which two hands per lane do not fit); 100 hands leave
+    the last warp's second hand of each lane partly beyond the hand list."""
+    if warp_hands == 32:
+        specs = [river(203, seed=51), river(64, seed=52, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
+                 leduc_random(seed=53), turn(40, seed=54), kuhn_random(seed=55)]
+    else:
+        specs = [river(120, seed=51), river(64, seed=52, bet_sizes=(0.33, 0.75, 1.25, synth.ALL_IN), max_raises=4),
+                 river(100, seed=56)]
     states, expl = [], []
     for schedule in ("level", "stream"):
         tree = capi.cfr_batch_create(specs, capi.make_opts(variant, alternating=alternating, precision=precision,
-                                                           schedule=schedule))
+                                                           schedule=schedule,
+                                                           warp_hands=warp_hands if schedule == "stream" else 0))
         try:
             assert capi.cfr_schedule(tree) == capi.SCHEDULES[schedule]
             capi.cfr_iterate(tree, 7)
@@ -410,6 +420,12 @@ def test_stream_and_level_schedules_give_the_same_bits(precision, variant, alter
     for a, b in zip(*states):
         assert np.array_equal(a, b)
     assert np.array_equal(expl[0][0], expl[1][0]) and np.array_equal(expl[0][1], expl[1][1])
+
+
+def test_64_hands_per_warp_needs_rows_padded_to_64():
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_batch_create([river(203)], capi.make_opts("dcfr", schedule="stream", warp_hands=64))
+    assert e.value.code == capi.CFR_EINVAL
 
 
 @pytest.mark.parametrize("precision", ["pairs", "single"])
@@ -571,6 +587,7 @@ def test_autotune_picks_a_layout_with_the_same_results():
     assert ms > 0
     assert best.schedule in (capi.CFR_SCHEDULE_LEVEL, capi.CFR_SCHEDULE_STREAM)
     assert best.term_nodes in (0, 1, 2, 4, 8) and best.variant == base.variant and best.precision == base.precision
+    assert best.warp_hands in (0, 32, 64)
     states = []
     for o in (base, best):
         tree = capi.cfr_batch_create(specs, o)
