@@ -421,16 +421,24 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
     }
     // FP32 values: the same scans and differences in plain FP32 (a value's error stays
     // within about 1e-6 of the largest value at the node)
-    __shared__ float redf[2][kTermThreads / 64];
+    __shared__ float redf[2][kTermThreads / 32];
+    __shared__ float cps[kMaxDeck], cpe[kMaxDeck];  // prefix at the start / end of each card's list
     float* CPf = reinterpret_cast<float*>(CP);  // [k H + 1]
     float* Pf = CPf + (k * H + 1);             // [H + 1]
-    constexpr int half = kTermThreads / 2;
-    const bool first = threadIdx.x < half;
-    const int gtid = first ? threadIdx.x : threadIdx.x - half;
-    if (first)
-      group_exclusive_scan_f32<half>(H, [&](int j) { return qs[show ? perm[j] : j]; }, Pf, redf[0], gtid);
-    else
-      group_exclusive_scan_f32<half>(k * H, [&](int j) { return qs[clh[j]]; }, CPf, redf[1], gtid);
+    {  // two-card hands' card lists hold 2 H entries, so 11 warps scan them and 5 the H
+       // rank-ordered entries (about 7 entries per thread on both sides)
+      constexpr int gp = 5 * 32;
+      if (threadIdx.x < gp)
+        group_exclusive_scan_f32<gp>(H, [&](int j) { return qs[show ? perm[j] : j]; }, Pf, redf[0], threadIdx.x);
+      else
+        group_exclusive_scan_f32<kTermThreads - gp>(k * H, [&](int j) { return qs[clh[j]]; }, CPf, redf[1],
+                                                     threadIdx.x - gp);
+    }
+    for (int c = threadIdx.x; c < G.deck; c += kTermThreads) {
+      cps[c] = CPf[cloff[c]];
+      cpe[c] = CPf[cloff[c + 1]];
+    }
+    __syncthreads();
     const float T = Pf[H];
     if (!show) {
       for (int h = threadIdx.x; h < H; h += kTermThreads) {
@@ -450,18 +458,26 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
       const uint16_t* ge = tab + tt.ge;
       const uint16_t* lo = tab + tt.lo;
       const uint16_t* hi = tab + tt.hi;
-      for (int h = threadIdx.x; h < H; h += kTermThreads) {
-        const unsigned cw = cards[h];
-        float Wn = Pf[gs[h]];
-        float Ln = __fsub_rn(T, Pf[ge[h]]);
-        bool blocked = false;
-        for (int s = 0; s < k; ++s) {
-          const unsigned c = s == 0 ? (cw & 0xffu) : (cw >> 8);
-          Wn = __fsub_rn(Wn, __fsub_rn(CPf[lo[2 * h + s]], CPf[cloff[c]]));
-          Ln = __fsub_rn(Ln, __fsub_rn(CPf[cloff[c + 1]], CPf[hi[2 * h + s]]));
-          blocked = blocked || ((board >> c) & 1ull);
+      if (k == 2) {  // the same differences, card 1 then card 2, in straight-line code
+        for (int h = threadIdx.x; h < H; h += kTermThreads) {
+          const unsigned cw = cards[h];
+          const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
+          float Wn = Pf[gs[h]];
+          float Ln = __fsub_rn(T, Pf[ge[h]]);
+          Wn = __fsub_rn(Wn, __fsub_rn(CPf[lo[2 * h]], cps[c1]));
+          Ln = __fsub_rn(Ln, __fsub_rn(cpe[c1], CPf[hi[2 * h]]));
+          Wn = __fsub_rn(Wn, __fsub_rn(CPf[lo[2 * h + 1]], cps[c2]));
+          Ln = __fsub_rn(Ln, __fsub_rn(cpe[c2], CPf[hi[2 * h + 1]]));
+          const bool blocked = ((board >> c1) | (board >> c2)) & 1ull;
+          out[h] = blocked ? 0.f : __fmul_rn(uf, __fsub_rn(Wn, Ln));
         }
-        out[h] = blocked ? 0.f : __fmul_rn(uf, __fsub_rn(Wn, Ln));
+      } else {  // one-card hands (Kuhn, Leduc)
+        for (int h = threadIdx.x; h < H; h += kTermThreads) {
+          const unsigned c = cards[h] & 0xffu;
+          const float Wn = __fsub_rn(Pf[gs[h]], __fsub_rn(CPf[lo[2 * h]], cps[c]));
+          const float Ln = __fsub_rn(__fsub_rn(T, Pf[ge[h]]), __fsub_rn(cpe[c], CPf[hi[2 * h]]));
+          out[h] = ((board >> c) & 1ull) ? 0.f : __fmul_rn(uf, __fsub_rn(Wn, Ln));
+        }
       }
     }
     return;
