@@ -88,7 +88,7 @@ def test_roofline_numerators_of_the_summaries(oracle_mod):
     river = _oracle_shape(oracle_mod, bench.workload_spec(0))
     assert river["hands"] == 1081
     want = _profile_figure("update_river1081.md", r"algorithmic bytes per launch \| ([\d,]+) B")
-    assert bench.algorithmic_bytes(river, "update", 8) == want
+    assert bench.algorithmic_bytes(river, "update", 4) == want
     batch = [_oracle_shape(oracle_mod, s) for s in synth.batch_rivers(256)]
     total = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch)
     half = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch[:128])
