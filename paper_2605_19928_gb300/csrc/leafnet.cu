@@ -2,16 +2,20 @@
 // Section 4.3): C = act(A B^T + bias) with A the [M][K] BF16 activations, B the [N][K] BF16
 // weights (both K-major), FP32 accumulation on the 5th-generation tensor cores.
 //
-// One CTA computes a 128 x 128 tile of C, two CTAs per SM (one's epilogue overlaps the
-// other's main loop):
-//   * warp 0 allocates 128 TMEM columns (the FP32 accumulator: lane = row, column = col)
-//     and, from one lane, streams 128 x 64 tiles of A and B into a 3-stage ring of shared
-//     memory with TMA (128-byte swizzle, the layout the MMA descriptors below describe);
-//   * one lane of warp 1 issues tcgen05.mma (M 128, N 128, K 16 per instruction, four per
-//     64-wide stage) and commits each stage back to its "empty" barrier;
-//   * after the last commit, all four warps read their 32-lane quarter of the accumulator
-//     with tcgen05.ld, add the bias, apply GELU (hidden layers) and store BF16 or FP32.
-// Every mbarrier wait is bounded; a wait that gives up sets *err and the CTA stops issuing.
+// A persistent kernel, one CTA per SM, walks 128 x BN tiles of C (BN = 256, 192 or 128,
+// the largest that divides N; the N tiles of one block of rows are consecutive so that the
+// CTAs reading that block of A run together and share it through L2):
+//   * one lane of warp 0 streams 128 x 64 tiles of A and BN x 64 tiles of B into a 4-stage
+//     ring of shared memory with TMA (128-byte swizzle, the layout the MMA descriptors below
+//     describe);
+//   * one lane of warp 1 issues tcgen05.mma (M 128, N BN, K 16 per instruction, four per
+//     64-wide stage) into one of two TMEM accumulators, commits each stage back to its
+//     "empty" barrier and each finished tile to its accumulator's "full" barrier;
+//   * warps 2-5 each read one 32-lane quarter of the finished accumulator with tcgen05.ld,
+//     add the bias, apply GELU (hidden layers), store BF16 or FP32 and hand the accumulator
+//     back, so a tile's epilogue runs while the next tile's MMAs fill the other one.
+// Every mbarrier wait is bounded; a wait that gives up sets *err, the CTA stops issuing,
+// waits for the copies and MMAs it has in flight and frees its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -24,9 +28,11 @@ namespace pcfr {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;  // 97 KB: two CTAs per SM
-constexpr int kTileBytes = kBM * kBK * 2;  // 16 KB, one A or one B stage
-constexpr int kGemmThreads = 128;
+constexpr int kBM = 128, kBK = 64, kStages = 4, kBNMax = 256;
+constexpr int kATile = kBM * kBK * 2;        // 16 KB: one A stage
+constexpr int kBTileMax = kBNMax * kBK * 2;  // 32 KB: one B stage of the widest tile
+constexpr int kGemmThreads = 192;            // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTmemCols = 512;               // two accumulators of up to 256 columns
 constexpr long kGemmWaitLimit = 1l << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -75,16 +81,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major,
-// N = kBN, M = kBM.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, N = bn,
+// M = kBM.
+__host__ __device__ constexpr uint32_t instr_desc(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -100,34 +108,42 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {  // round to nearest even
   return (uint16_t)(u >> 16);
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 2)
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                const float* __restrict__ bias, void* __restrict__ out, int M, int N, int K, int act, int out_f32,
-                int* err) {
+                const float* __restrict__ bias, void* __restrict__ out, int M, int N, int K, int bn, int act,
+                int out_f32, int* err) {
   extern __shared__ __align__(1024) unsigned char smg[];
   // 1024-byte aligned stage buffers: A stages, then B stages
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smg) + 1023) & ~(uintptr_t)1023);
   unsigned char* sa = base;
-  unsigned char* sb = base + kStages * kTileBytes;
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  unsigned char* sb = base + kStages * kATile;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_base;
-  __shared__ int failed;
+  __shared__ volatile int failed;  // set by any role whose bounded wait gave up; the others poll it
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int kb_count = K / kBK;
+  const int n_nt = N / bn, n_tiles = n_nt * ((M + kBM - 1) / kBM), kb_count = K / kBK;
+  const uint32_t b_bytes = (uint32_t)bn * kBK * 2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       bar_init(&full[s], 1);
       bar_init(&empty[s], 1);
     }
-    bar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&acc_full[b], 1);   // one tcgen05.commit per finished tile
+      bar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
+    bar_init(&mma_done, 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                 "r"(kBN)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -136,85 +152,124 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0 && lane == 0) {  // TMA producer
-    for (int kb = 0; kb < kb_count; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t round = (uint32_t)(kb / kStages);
-      if (!bar_wait(&empty[s], (round & 1u) ^ 1u)) {
-        failed = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int it = 0;
+      for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const int m0 = (tile / n_nt) * kBM, n0 = (tile % n_nt) * bn;
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % kStages;
+          if (!bar_wait(&empty[s], ((uint32_t)(it / kStages) & 1u) ^ 1u)) {
+            failed = 1;
+            break;
+          }
+          bar_expect_tx(&full[s], kATile + b_bytes);
+          tma_load_2d(sa + s * kATile, &map_a, kb * kBK, m0, &full[s]);
+          tma_load_2d(sb + s * kBTileMax, &map_b, kb * kBK, n0, &full[s]);
+        }
       }
-      bar_expect_tx(&full[s], 2 * kTileBytes);
-      tma_load_2d(sa + s * kTileBytes, &map_a, kb * kBK, m0, &full[s]);
-      tma_load_2d(sb + s * kTileBytes, &map_b, kb * kBK, n0, &full[s]);
+      // the copies of the last round of each stage have landed before the CTA can leave
+      for (int j = it - 1; j >= 0 && j >= it - kStages; --j) bar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
     }
-  } else if (warp == 1 && lane == 0) {  // MMA issuer
-    for (int kb = 0; kb < kb_count; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t round = (uint32_t)(kb / kStages);
-      if (!bar_wait(&full[s], round & 1u)) {
-        failed = 1;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = instr_desc(bn);
+      int it = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, ++lt) {
+        const int acc = lt & 1;
+        if (!bar_wait(&acc_empty[acc], ((uint32_t)(lt >> 1) & 1u) ^ 1u)) {  // the epilogue has drained it
+          failed = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * kBNMax);
+        bool ok = true;
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % kStages;
+          if (!bar_wait(&full[s], (uint32_t)(it / kStages) & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_addr(sa + s * kATile), b0 = smem_addr(sb + s * kBTileMax);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        }
+        if (!ok) {
+          failed = 1;
+          break;
+        }
+        mma_commit(&acc_full[acc]);  // the tile's accumulator is complete
+      }
+      mma_commit(&mma_done);  // every MMA issued above has completed
+      bar_wait(&mma_done, 0);
+    }
+    __syncwarp();
+  } else {  // epilogue: warp w reads accumulator lanes (rows) 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
+      const int acc = lt & 1;
+      const bool ok = bar_wait(&acc_full[acc], (uint32_t)(lt >> 1) & 1u);
+      if (!__all_sync(0xffffffffu, ok) || failed) {
+        if (lane == 0) failed = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_addr(sa + s * kTileBytes), b0 = smem_addr(sb + s * kTileBytes);
+      const int m0 = (tile / n_nt) * kBM, n0 = (tile % n_nt) * bn;
+      const int row = m0 + q * 32 + lane;
+      for (int c0 = 0; c0 < bn; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBNMax + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M) {
+          const int col = n0 + c0;
+          float y[32];
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)
-        mma_bf16(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
-    }
-    mma_commit(&done);  // every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
-  const bool ok = bar_wait(&done, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok || failed) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-  } else {
-    const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        const int col = n0 + c0;
-        float y[32];
+          for (int j = 0; j < 32; ++j) {
+            y[j] = __uint_as_float(v[j]) + (bias ? bias[col + j] : 0.f);
+            if (act) y[j] = gelu(y[j]);
+          }
+          if (out_f32) {
+            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)row * N + col);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          y[j] = __uint_as_float(v[j]) + (bias ? bias[col + j] : 0.f);
-          if (act) y[j] = gelu(y[j]);
-        }
-        if (out_f32) {
-          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)row * N + col);
+            for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+          } else {
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + (size_t)row * N + col);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-        } else {
-          uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + (size_t)row * N + col);
+            for (int j = 0; j < 4; ++j) {
+              uint32_t w[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              w[e] = (uint32_t)to_bf16(y[8 * j + 2 * e]) | ((uint32_t)to_bf16(y[8 * j + 2 * e + 1]) << 16);
-            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+              for (int e = 0; e < 4; ++e)
+                w[e] = (uint32_t)to_bf16(y[8 * j + 2 * e]) | ((uint32_t)to_bf16(y[8 * j + 2 * e + 1]) << 16);
+              dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(&acc_empty[acc]);  // this quarter of the accumulator is free
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+  if (failed && threadIdx.x == 0) atomicExch(err, 1);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
 }
 
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -235,13 +290,13 @@ EncodeTiled encoder() {
   return fn;
 }
 
-// Row-major [rows][cols] BF16 matrix, 128 x 64 boxes with 128-byte swizzle.
-bool encode(CUtensorMap* map, const void* ptr, int rows, int cols) {
+// Row-major [rows][cols] BF16 matrix, box_rows x 64 boxes with 128-byte swizzle.
+bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows) {
   EncodeTiled fn = encoder();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -250,7 +305,7 @@ bool encode(CUtensorMap* map, const void* ptr, int rows, int cols) {
 
 }  // namespace
 
-size_t gemm_smem_bytes() { return (size_t)2 * kStages * kTileBytes + 1024; }
+size_t gemm_smem_bytes() { return (size_t)kStages * (kATile + kBTileMax) + 1024; }
 
 int configure_gemm() {
   return cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes()) ==
@@ -261,13 +316,20 @@ int configure_gemm() {
 
 int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, int M, int N, int K, int act,
                      int out_f32, int* err, void* stream) {
-  if (M <= 0 || N <= 0 || K <= 0 || N % kBN || K % kBK) return -2;
+  if (M <= 0 || N <= 0 || K <= 0 || N % 128 || K % kBK) return -2;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) return -2;
+  const int bn = N % 256 == 0 ? 256 : N % 192 == 0 ? 192 : 128;  // the widest tile that divides N
+  const long tiles = (long)(N / bn) * ((M + kBM - 1) / kBM);
+  if (tiles > (1l << 30)) return -2;
   CUtensorMap ma, mb;
-  if (!encode(&ma, A, M, K) || !encode(&mb, B, N, K)) return -3;
-  const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / kBN));
-  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(), (cudaStream_t)stream>>>(ma, mb, bias, C, M, N, K, act, out_f32,
-                                                                               err);
+  if (!encode(&ma, A, M, K, kBM) || !encode(&mb, B, N, K, bn)) return -3;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return -1;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
+  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(), (cudaStream_t)stream>>>(ma, mb, bias, C, M, N, K, bn, act,
+                                                                               out_f32, err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_gemm_bf16 failed: %s\n", cudaGetErrorString(e));
