@@ -11,9 +11,10 @@
 //   * one lane of warp 1 issues tcgen05.mma (M 128, N BN, K 16 per instruction, four per
 //     64-wide stage) into one of two TMEM accumulators, commits each stage back to its
 //     "empty" barrier and each finished tile to its accumulator's "full" barrier;
-//   * warps 2-5 each read one 32-lane quarter of the finished accumulator with tcgen05.ld,
-//     add the bias, apply GELU (hidden layers), store BF16 or FP32 and hand the accumulator
-//     back, so a tile's epilogue runs while the next tile's MMAs fill the other one.
+//   * eight warps each read half the columns of one 32-lane quarter of the finished
+//     accumulator with tcgen05.ld, add the bias, apply GELU (hidden layers), store BF16 (or
+//     FP32, staged in shared memory and written by bulk tensor stores) and hand the
+//     accumulator back, so a tile's epilogue runs while the next tile's MMAs fill the other.
 // Every mbarrier wait is bounded; a wait that gives up sets *err, the CTA stops issuing,
 // waits for the copies and MMAs it has in flight and frees its TMEM.
 #include <cuda.h>
@@ -31,7 +32,9 @@ namespace {
 constexpr int kBM = 128, kBK = 64, kStages = 4, kBNMax = 256;
 constexpr int kATile = kBM * kBK * 2;        // 16 KB: one A stage
 constexpr int kBTileMax = kBNMax * kBK * 2;  // 32 KB: one B stage of the widest tile
-constexpr int kGemmThreads = 192;            // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, each half the columns
+constexpr int kStageBufs = 8 / kEpiWarps;    // 4 KB output staging blocks per epilogue warp (32 KB in all)
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, then the epilogue warps
 constexpr int kTmemCols = 512;               // two accumulators of up to 256 columns
 constexpr long kGemmWaitLimit = 1l << 22;
 
@@ -108,14 +111,23 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {  // round to nearest even
   return (uint16_t)(u >> 16);
 }
 
+// Bulk tensor store shared -> global of one box (the issuing thread's bulk async-group).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_addr(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                const float* __restrict__ bias, void* __restrict__ out, int M, int N, int K, int bn, int act,
-                int out_f32, int* err) {
+                const __grid_constant__ CUtensorMap map_c, const float* __restrict__ bias, void* __restrict__ out,
+                int M, int N, int K, int bn, int act, int out_f32, int* err) {
   extern __shared__ __align__(1024) unsigned char smg[];
   // 1024-byte aligned stage buffers: A stages, then B stages
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smg) + 1023) & ~(uintptr_t)1023);
@@ -135,7 +147,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       bar_init(&acc_full[b], 1);   // one tcgen05.commit per finished tile
-      bar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+      bar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
     }
     bar_init(&mma_done, 1);
     failed = 0;
@@ -208,8 +220,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       bar_wait(&mma_done, 0);
     }
     __syncwarp();
-  } else {  // epilogue: warp w reads accumulator lanes (rows) 32 (w % 4) .. + 31
-    const int q = warp & 3;
+  } else {  // epilogue: warp w reads accumulator lanes (rows) 32 (w % 4) .. + 31, columns of part
+            // (w - 2) / 4 of the tile
+    constexpr int parts = kEpiWarps / 4;  // warps per lane quarter, each a share of the columns
+    const int q = warp & 3, part = (warp - 2) >> 2;
+    const int c_begin = part * (bn / parts), c_end = c_begin + bn / parts;
+    // FP32 output: 32 x 32 staging blocks in the TMA store's 128-byte-swizzled layout
+    // (16-byte chunk j of row r at chunk j ^ (r % 8)), each written by the warp and stored by
+    // one bulk tensor copy
+    unsigned char* stage = sb + kStages * kBTileMax + (size_t)(warp - 2) * kStageBufs * 4096;
+    int cc = 0;  // 32-column blocks this warp has staged
     int lt = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
       const int acc = lt & 1;
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int m0 = (tile / n_nt) * kBM, n0 = (tile % n_nt) * bn;
       const int row = m0 + q * 32 + lane;
-      for (int c0 = 0; c0 < bn; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBNMax + c0);
         asm volatile(
@@ -233,19 +253,40 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < M) {
-          const int col = n0 + c0;
+        const int col = n0 + c0;
+        if (out_f32) {
+          unsigned char* buf = stage + (cc % kStageBufs) * 4096;
+          if (cc >= kStageBufs) {  // the store that last read this block has finished reading it
+            if (lane == 0) {
+              if (kStageBufs == 2)
+                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+              else
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+            __syncwarp();
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              y[e] = __uint_as_float(v[4 * j + e]) + (bias ? bias[col + 4 * j + e] : 0.f);
+              if (act) y[e] = gelu(y[e]);
+            }
+            *reinterpret_cast<float4*>(buf + lane * 128 + ((j ^ (lane & 7)) << 4)) = make_float4(y[0], y[1], y[2], y[3]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
+          __syncwarp();
+          if (lane == 0) tma_store_2d(&map_c, col, m0 + q * 32, buf);  // rows past M are clipped
+          ++cc;
+        } else if (row < M) {
           float y[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             y[j] = __uint_as_float(v[j]) + (bias ? bias[col + j] : 0.f);
             if (act) y[j] = gelu(y[j]);
           }
-          if (out_f32) {
-            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(out) + (size_t)row * N + col);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-          } else {
+          {
             uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + (size_t)row * N + col);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -262,6 +303,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       __syncwarp();
       if (lane == 0) bar_arrive(&acc_empty[acc]);  // this quarter of the accumulator is free
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // every store has completed
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -290,6 +333,20 @@ EncodeTiled encoder() {
   return fn;
 }
 
+// Row-major [rows][cols] FP32 matrix, 32 x 32 boxes with 128-byte swizzle (the epilogue's
+// bulk stores).
+bool encode_out_f32(CUtensorMap* map, void* ptr, int rows, int cols) {
+  EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // Row-major [rows][cols] BF16 matrix, box_rows x 64 boxes with 128-byte swizzle.
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows) {
   EncodeTiled fn = encoder();
@@ -305,7 +362,8 @@ bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows)
 
 }  // namespace
 
-size_t gemm_smem_bytes() { return (size_t)kStages * (kATile + kBTileMax) + 1024; }
+// stages of A and B, the epilogue warps' 4 KB output staging blocks, alignment slack
+size_t gemm_smem_bytes() { return (size_t)kStages * (kATile + kBTileMax) + kEpiWarps * kStageBufs * 4096 + 1024; }
 
 int configure_gemm() {
   return cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes()) ==
@@ -321,15 +379,16 @@ int launch_gemm_bf16(const void* A, const void* B, const float* bias, void* C, i
   const int bn = N % 256 == 0 ? 256 : N % 192 == 0 ? 192 : 128;  // the widest tile that divides N
   const long tiles = (long)(N / bn) * ((M + kBM - 1) / kBM);
   if (tiles > (1l << 30)) return -2;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mc = {};
   if (!encode(&ma, A, M, K, kBM) || !encode(&mb, B, N, K, bn)) return -3;
+  if (out_f32 && !encode_out_f32(&mc, C, M, N)) return -3;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
     return -1;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
-  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(), (cudaStream_t)stream>>>(ma, mb, bias, C, M, N, K, bn, act,
-                                                                               out_f32, err);
+  k_gemm_bf16<<<grid, kGemmThreads, gemm_smem_bytes(), (cudaStream_t)stream>>>(ma, mb, mc, bias, C, M, N, K, bn,
+                                                                               act, out_f32, err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     fprintf(stderr, "pcfr: launch of k_gemm_bf16 failed: %s\n", cudaGetErrorString(e));
