@@ -469,8 +469,12 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     const std::vector<uint16_t> tab = pack_term_tables(h);
     const std::vector<int32_t> rown = row_nodes(h);
     const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
-    std::vector<float> pay32(h.payoff.size());
-    for (size_t n = 0; n < pay32.size(); ++n) pay32[n] = (float)(h.payoff[n] * d.kappa64);
+    std::vector<float> pay32(2 * h.payoff.size());  // (hi, lo) of payoff * kappa per node
+    for (size_t n = 0; n < h.payoff.size(); ++n) {
+      const double x = h.payoff[n] * d.kappa64;
+      pay32[2 * n] = (float)x;
+      pay32[2 * n + 1] = (float)(x - (double)pay32[2 * n]);
+    }
     NodeDev* nodes;
     int32_t *ls, *rn, *dn, *chk;
     uint32_t* un;
@@ -496,7 +500,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       return rc;
     }
     d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.payoff32 = pay32d; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
+    d.payoff = pay; d.payoff_ff = pay32d; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
     d.prog_len = (int)programs[g].size();
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
     const size_t vf = es / 4;  // floats per value

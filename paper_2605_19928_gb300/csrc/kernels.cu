@@ -371,12 +371,13 @@ __device__ long g_first_wait_polls = kWaitLimit;
 // Sums and differences are double-float with FP32-pair values, plain FP32 with FP32
 // values.  Every thread of the block calls it (it holds block barriers).
 template <typename P>
-__device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev& nd, int i, double u64, float uf,
+__device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev& nd, int i, ff u,
                                                 const TermTab& tt, const uint16_t* tab,
                                                 const typename P::V* __restrict__ qs, ff* CP, ff* Psc,
                                                 typename P::V* __restrict__ out) {
   using V = typename P::V;
   __shared__ acc2 red[2][kTermThreads / 64];
+  const float uf = u.hi;  // FP32 values: the scale rounded once to FP32
   const int H = G.n_hands, k = G.hand_size;
   const bool show = nd.type == kShowdown;
   const uint64_t board = nd.board;
@@ -482,7 +483,6 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
     }
     return;
   }
-  const ff u = d2ff(u64);
   // Two scans at once, one per half of the block: the first half takes the reach in
   // rank-sorted order (showdown) or in hand order (fold, for the total T), the second half
   // the reach along the per-card hand lists.
@@ -602,17 +602,10 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
   for (int j = 0; j < count; ++j) {
     const int n = work[first + j].unit;
     const NodeDev nd = G.nodes[n];
-    // payoff for player i per unit of (opponent reach) x kappa: in FP64 for pair values; for
-    // FP32 values the host's FP32 rounding of the same product (no FP64 work per thread)
+    // payoff for player i per unit of (opponent reach) x kappa: the FP64 product as a pair of
+    // FP32 rounded once on the host (FP32 values use its high part): no FP64 work per thread
     const bool neg = nd.type == kFold && nd.player == i;
-    double u64 = 0.0;
-    float uf = 0.f;
-    if constexpr (std::is_same<P, Single>::value) {
-      uf = neg ? -G.payoff32[n] : G.payoff32[n];
-    } else {
-      const double pay = G.payoff[n];
-      u64 = (neg ? -pay : pay) * G.kappa64;
-    }
+    const ff u = {neg ? -G.payoff_ff[2 * n] : G.payoff_ff[2 * n], neg ? -G.payoff_ff[2 * n + 1] : G.payoff_ff[2 * n + 1]};
     const bool ok = threadIdx.x >= 32 ||  // one warp polls
                     mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, j == 0 ? g_first_wait_polls : kWaitLimit);
     if (__syncthreads_or(!ok)) {  // a copy did not land: report, let the copies drain, leave
@@ -630,8 +623,7 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
         if (G.hand_mask[h] & nd.board) qb[h] = P::zero();
       __syncthreads();
     }
-    terminal_values<P>(G, nd, i, u64, uf, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc,
-                       dst + (size_t)n * stride);
+    terminal_values<P>(G, nd, i, u, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc, dst + (size_t)n * stride);
     if (!RUNS) break;
     __syncthreads();  // buffer j & 1 and the scan arrays are free again
     if (threadIdx.x == 0 && j + 2 < count) {

@@ -119,8 +119,8 @@ struct GameDev {
   const double* payoff;        // [n_nodes] terminal payoff magnitude times the probability of
                                // the public cards dealt on the path (fold: folder's chips in,
                                // showdown: each player's chips in); 0 elsewhere
-  const float* payoff32;       // [n_nodes] (float)(payoff * kappa64): the FP32-value path's
-                               // terminal scale, rounded once on the host
+  const float* payoff_ff;      // [n_nodes][2] payoff * kappa64 as an FP32 pair (hi, lo), rounded
+                               // once on the host: the terminal scale (FP32 values use hi)
   const int32_t* level_start;  // [n_levels + 1]
   const int32_t* row_node;     // [n_rows] decision node owning each row
   const int32_t* dec_nodes;    // decision nodes of player 0, then of player 1
