@@ -27,6 +27,7 @@ the exact subgames), `gemm` (the network's layers).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -696,10 +697,14 @@ def run_leaf(args):
     gpu_launches = capi.cfr_counters(L)["kernel_launches"] - launches0
     value, t_max = aggregate(args.steps * ips, t_leaf, world, dist, device)
     e_leaf_own, _ = capi.cfr_exploitability_result(L)
-    # the served form: the network judged on 64 of its own leaf rows against exact river
-    # solves of their continuations, falling back to the exact subgame above the tolerance
+    # the served form: the network judged on its own leaf rows (per leaf: 4 rows of each turn
+    # leaf, 1 of each flop leaf) against exact river solves of their continuations; the
+    # leaves above the tolerance are solved exactly beside the network leaves of the rest
+    per_leaf = 1 if flop else 4
     judge = serve.judge_leaves(L, spec_leaf, n_rows=64, iters=300, seed=rank, stream=stream.cuda_stream,
-                               evaluated=True)
+                               evaluated=True, per_leaf=per_leaf)
+    n_leaves_total = len(capi.cfr_leaf_info(L))
+    exact_leaves = serve.fallback_leaves(judge.leaf_errors, serve.DEFAULT_TOL)
     exact_steps = 1 if flop else max(1, args.steps // 4)
     t_exact = timed(E, exact_steps, 1)
     e_exact, _ = capi.cfr_exploitability_result(E)
@@ -751,19 +756,39 @@ def run_leaf(args):
                                "tflops_incl_input_and_value_kernels": flops / (stages["leaf"][0] * 1e-3) / 1e12},
                 "stage_ms": {k: v[0] for k, v in stages.items()}}
     mbb = lambda e: 1000.0 * float(e) / BB_CHIPS
-    learned_ok = judge.rows > 0 and judge.reach_weighted_error <= serve.DEFAULT_TOL
     ms_leaf_step, ms_exact_step = 1000.0 * t_leaf / args.steps, 1000.0 * t_exact / exact_steps
-    served = {"form": "learned" if learned_ok else "exact (fallback)", "tol_pot": serve.DEFAULT_TOL,
+    if not exact_leaves:
+        form, e_served, ms_fallback = "learned", e_hybrid[0], 0.0
+    elif len(exact_leaves) == n_leaves_total:
+        form, e_served, ms_fallback = "exact (every leaf failed)", e_exact[0], ms_exact_step
+    else:  # one handle: exact river subtrees at the failed leaves, the network at the rest
+        Mx = capi.cfr_tree_create(dataclasses.replace(spec_leaf, exact_leaves=tuple(exact_leaves)), opts,
+                                  stream=stream.cuda_stream)
+        try:
+            capi.cfr_set_leaf_net(Mx, W, b)
+            ms_fallback = 1000.0 * timed(Mx, 1, 1)
+            pm = node_paths(capi, Mx)
+            for path, nm in pm.items():  # its strategy in the exact game, E's river play elsewhere
+                if capi.cfr_node_info(Mx, nm)["type"] == capi.CFR_NODE_DECISION:
+                    capi.cfr_write_values(E, capi.CFR_READ_AVG_SUM, pe[path],
+                                          capi.cfr_read_values(Mx, capi.CFR_READ_AVG_SUM, nm))
+            e_served = capi.cfr_exploitability(E)[0][0]
+        finally:
+            capi.cfr_tree_destroy(Mx)
+        form = "mixed"
+    served = {"form": form, "tol_pot": serve.DEFAULT_TOL,
+              "leaves": n_leaves_total, "exact_leaves": len(exact_leaves), "judged_rows_per_leaf": per_leaf,
               "judge": {"rows": judge.rows, "candidates": judge.candidates,
                         "mean_abs_error_pot": judge.mean_abs_error,
                         "reach_weighted_error_pot": judge.reach_weighted_error,
                         "max_row_error_pot": judge.max_row_error,
                         "continuation_exploitability_mbb": judge.continuation_exploitability_mbb,
                         "ms": judge.ms, "continuation_iters": 300},
-              "exploitability_in_exact_game_mbb": mbb(e_hybrid[0]) if learned_ok else mbb(e_exact[0]),
-              "ms_per_solve": ms_leaf_step + judge.ms + (0.0 if learned_ok else ms_exact_step),
+              "exploitability_in_exact_game_mbb": mbb(e_served),
+              "ms_per_solve": ms_leaf_step + judge.ms + ms_fallback,
               "note": "one solve = the depth-limited solve (one step), the judge (host wall time, "
-                      "continuation solves included) and, after a fallback, the exact solve (one step)"}
+                      "continuation solves included) and, where leaves failed, the solve with those "
+                      "leaves exact (one step; the whole exact subgame when all failed)"}
     n_exact = capi.cfr_tree_info(E)[0]
     n_leaf_nodes = capi.cfr_tree_info(L)[0]
     sched = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream",

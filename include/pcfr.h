@@ -83,6 +83,15 @@ enum {
  *               chance node that deals the river card with chips behind becomes a
  *               CFR_NODE_LEAF whose values the leaf network gives (cfr_set_leaf_net); the
  *               flop's turn card stays a chance node and all-in run-outs stay exact.
+ *   exact_leaves [n_exact_leaves] (depth_limit 1 only; may be NULL with 0): leaves to solve
+ *               exactly instead, so that one handle mixes network leaves and exact river
+ *               subtrees (the fallback of a leaf whose network values were judged wrong).
+ *               A leaf is named by its index in the order cfr_leaf_info lists the leaves
+ *               of the same subgame built with no exact leaves (the tree's breadth-first
+ *               order: by the length of the action path from the root, then by the path in
+ *               lexicographic order); each named position becomes the river-card chance
+ *               node with its exact river subtrees.  Indices must be distinct and name
+ *               leaves (CFR_EINVAL otherwise).
  */
 typedef struct cfr_game_spec {
   int game;
@@ -99,6 +108,8 @@ typedef struct cfr_game_spec {
   const double* bet_sizes;
   int max_raises;
   int depth_limit;
+  const int32_t* exact_leaves;
+  int n_exact_leaves;
 } cfr_game_spec;
 
 /*

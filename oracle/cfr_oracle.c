@@ -85,6 +85,10 @@ typedef struct Oracle {
   int alternating;
   int nthreads;
   int depth_limit;       /* 1: a river chance node with chips behind is a leaf */
+  int* exact_flags;      /* [n_exact_flags]: leaf position k (in the order the builder meets
+                            them, depth first) is solved exactly instead (depth_limit 1) */
+  int n_exact_flags;
+  int leaf_seq;          /* leaf positions met so far while building */
 
   Node* nodes;
   int nn, ncap;
@@ -139,8 +143,11 @@ static int build_street_end(Oracle* o, int parent, int paction, int street, cons
   if (street + 1 >= o->nstreets)
     return new_node(o, T_SHOW, -1, parent, paction, street, c, nboard, board, deal);
   /* the depth limit ends the tree where the river card is to come, unless nobody can bet */
-  if (o->depth_limit && o->game == G_HOLDEM && street + 2 == o->nstreets && !(c[0] >= o->cap || c[1] >= o->cap))
-    return new_node(o, T_LEAF, -1, parent, paction, street, c, nboard, board, deal);
+  if (o->depth_limit && o->game == G_HOLDEM && street + 2 == o->nstreets && !(c[0] >= o->cap || c[1] >= o->cap)) {
+    int seq = o->leaf_seq++;
+    if (!(seq < o->n_exact_flags && o->exact_flags[seq]))  /* else: the exact river card chance node */
+      return new_node(o, T_LEAF, -1, parent, paction, street, c, nboard, board, deal);
+  }
   int id = new_node(o, T_CHANCE, -1, parent, paction, street, c, nboard, board, deal);
   int live[64], nlive = 0;
   for (int card = 0; card < o->deck; ++card) {
@@ -279,7 +286,7 @@ static double leaf_utility(const Oracle* o, const Node* n, int i, int hi, int ho
 Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* cards, const double* r0,
                     const double* r1, const int* strength, int nstr, double pot, double stack, int nsizes,
                     const double* sizes, int max_raises, int variant, double alpha, double beta, double gamma,
-                    int alternating, int nthreads, int depth_limit) {
+                    int alternating, int nthreads, int depth_limit, const int* exact_flags, int n_exact_flags) {
   g_err[0] = 0;
   if (nh <= 0 || !cards || !r0 || !r1) {
     snprintf(g_err, sizeof g_err, "empty hand list or range");
@@ -296,6 +303,11 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
   o->nthreads = nthreads < 1 ? 1 : nthreads;
   o->max_raises = max_raises;
   o->depth_limit = depth_limit;
+  if (n_exact_flags > 0 && exact_flags) {
+    o->exact_flags = (int*)malloc(sizeof(int) * (size_t)n_exact_flags);
+    memcpy(o->exact_flags, exact_flags, sizeof(int) * (size_t)n_exact_flags);
+    o->n_exact_flags = n_exact_flags;
+  }
   int start_board[5] = {0};
   int nb0 = 0;
   if (game == G_KUHN) {
@@ -307,7 +319,7 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
     if (nboard == 5) o->nstreets = 1;
     else if (nboard == 4) o->nstreets = 2;
     else if (nboard == 3) o->nstreets = 3;
-    else { snprintf(g_err, sizeof g_err, "hold'em subgames start on the flop, turn or river"); free(o); return NULL; }
+    else { snprintf(g_err, sizeof g_err, "hold'em subgames start on the flop, turn or river"); free(o->exact_flags); free(o); return NULL; }
     nb0 = nboard;
     for (int k = 0; k < nboard; ++k) start_board[k] = board[k];
     o->pot = pot;
@@ -320,6 +332,8 @@ Oracle* ocfr_create(int game, int nboard, const int* board, int nh, const int* c
     o->nstr = nstr;
     if (!((nboard == 5 && nstr == 1) || (nboard == 4 && nstr == 52) || (nboard == 3 && nstr == 52 * 52))) {
       snprintf(g_err, sizeof g_err, "strength rows do not match the board");
+      free(o->strength);
+      free(o->exact_flags);
       free(o);
       return NULL;
     }
@@ -390,7 +404,7 @@ void ocfr_destroy(Oracle* o) {
   free(o->nodes);
   free(o->cards); free(o->hmask); free(o->r[0]); free(o->r[1]); free(o->strength);
   free(o->R); free(o->S); free(o->sig); free(o->prof); free(o->rinst); free(o->M);
-  free(o->cfv[0]); free(o->cfv[1]); free(o->compat);
+  free(o->cfv[0]); free(o->cfv[1]); free(o->compat); free(o->exact_flags);
   free(o);
 }
 

@@ -48,7 +48,7 @@ def _load(path: str | None = None):
         pi = C.POINTER(C.c_int)
         pd = C.POINTER(C.c_double)
         lib.ocfr_create.restype = P
-        lib.ocfr_create.argtypes = [I, I, pi, I, pi, pd, pd, pi, I, D, D, I, pd, I, I, D, D, D, I, I, I]
+        lib.ocfr_create.argtypes = [I, I, pi, I, pi, pd, pd, pi, I, D, D, I, pd, I, I, D, D, D, I, I, I, pi, I]
         lib.ocfr_destroy.argtypes = [P]
         lib.ocfr_error.restype = C.c_char_p
         lib.ocfr_iterate.argtypes = [P, I]
@@ -117,18 +117,38 @@ class Oracle:
         if threads is None:
             threads = os.cpu_count() or 1
         self.threads = int(threads)
-        self._keep = (cards, r0, r1, board, strength, sizes)
+        flags = self._exact_flags(spec, lib_path)
+        self._keep = (cards, r0, r1, board, strength, sizes, flags)
         self.variant = variant
         self._h = lib.ocfr_create(spec.game, int(board.size), _ptr(board, C.c_int), nh, _ptr(cards, C.c_int),
                                   _ptr(r0, C.c_double), _ptr(r1, C.c_double), _ptr(strength, C.c_int), nstr,
                                   float(spec.pot), float(spec.stack), len(spec.bet_sizes), _ptr(sizes, C.c_double),
                                   int(spec.max_raises), VARIANTS[variant], alpha, beta, gamma, int(alternating),
-                                  self.threads, int(getattr(spec, "depth_limit", 0)))
+                                  self.threads, int(getattr(spec, "depth_limit", 0)),
+                                  _ptr(flags, C.c_int) if flags.size else None, int(flags.size))
         if not self._h:
             raise ValueError("oracle: " + lib.ocfr_error().decode())
         self.n_nodes = lib.ocfr_n_nodes(self._h)
         self.n_hands = nh
         self._info = None
+
+    @staticmethod
+    def _exact_flags(spec, lib_path=None) -> np.ndarray:
+        """Leaves the spec asks to solve exactly (`exact_leaves`: indices in the breadth-first
+        order of the depth-limited tree -- by action-path length, then lexicographically) as
+        flags in the order this oracle's depth-first builder meets leaf positions."""
+        exact = sorted(int(k) for k in getattr(spec, "exact_leaves", ()) or ())
+        if not exact:
+            return np.zeros(0, np.int32)
+        import dataclasses
+        pure = Oracle(dataclasses.replace(spec, exact_leaves=()), variant="cfr", threads=1, lib_path=lib_path)
+        paths = {n: p for p, n in pure.paths().items()}
+        leaves = [n for n in range(pure.n_nodes) if pure.node(n)["type"] == T_LEAF]  # depth first: by id
+        rank = {n: k for k, n in enumerate(sorted(leaves, key=lambda n: (len(paths[n]), paths[n])))}
+        if exact[-1] >= len(leaves) or exact[0] < 0 or len(set(exact)) != len(exact):
+            raise ValueError("exact_leaves must be distinct leaf indices")
+        want = set(exact)
+        return np.array([1 if rank[n] in want else 0 for n in leaves], np.int32)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -51,7 +51,8 @@ class cfr_game_spec(C.Structure):
                 ("hands", C.POINTER(C.c_uint8)), ("range", C.POINTER(C.c_float) * 2),
                 ("strength", C.POINTER(C.c_int32)), ("n_strength_rows", C.c_int), ("pot", C.c_double),
                 ("stack", C.c_double), ("n_bet_sizes", C.c_int), ("bet_sizes", C.POINTER(C.c_double)),
-                ("max_raises", C.c_int), ("depth_limit", C.c_int)]
+                ("max_raises", C.c_int), ("depth_limit", C.c_int), ("exact_leaves", C.POINTER(C.c_int32)),
+                ("n_exact_leaves", C.c_int)]
 
 
 class cfr_solver_opts(C.Structure):
@@ -185,7 +186,10 @@ def make_spec(g) -> tuple[cfr_game_spec, tuple]:
     s.bet_sizes = sizes.ctypes.data_as(C.POINTER(C.c_double))
     s.max_raises = int(g.max_raises)
     s.depth_limit = int(getattr(g, "depth_limit", 0))
-    return s, (board, hands, r0, r1, strength, sizes)
+    exact = np.ascontiguousarray(np.array(getattr(g, "exact_leaves", ()), dtype=np.int32).reshape(-1))
+    s.n_exact_leaves = int(exact.size)
+    s.exact_leaves = exact.ctypes.data_as(C.POINTER(C.c_int32)) if exact.size else None
+    return s, (board, hands, r0, r1, strength, sizes, exact)
 
 
 def make_opts(variant="dcfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True, chunk_hands=0,

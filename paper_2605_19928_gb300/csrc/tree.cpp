@@ -241,6 +241,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
       err = "depth_limit 1 applies to flop and turn subgames only";
       return CFR_EINVAL;
     }
+    if (spec.n_exact_leaves < 0 || (spec.n_exact_leaves > 0 && (spec.depth_limit != 1 || !spec.exact_leaves))) {
+      err = "exact_leaves applies to depth-limited subgames (depth_limit 1) and needs its list";
+      return CFR_EINVAL;
+    }
     if (!spec.strength || spec.n_strength_rows != want_rows) {
       err = "strength must have 1 row (river), 52 rows (turn) or 52 x 52 rows (flop)";
       return CFR_EINVAL;
@@ -296,6 +300,20 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
   }
   g.Z = Z;
 
+  // leaves the caller wants solved exactly, by their index among the leaf positions in the
+  // order they are met below (breadth first, as cfr_leaf_info lists a tree with no exact
+  // leaves: expanding a leaf adds only river subtrees, which hold no leaf positions)
+  std::vector<int32_t> exact;
+  if (spec.game == CFR_GAME_HOLDEM && spec.n_exact_leaves > 0) {
+    exact.assign(spec.exact_leaves, spec.exact_leaves + spec.n_exact_leaves);
+    std::sort(exact.begin(), exact.end());
+    if (exact.front() < 0 || std::adjacent_find(exact.begin(), exact.end()) != exact.end()) {
+      err = "exact_leaves must be distinct leaf indices";
+      return CFR_EINVAL;
+    }
+  }
+  int leaf_seq = 0;
+
   // ---- public tree, breadth first: ids are level order, children consecutive
   std::deque<Pending> queue;
   queue.push_back(root);
@@ -323,8 +341,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
     // chips behind; the leaf network values it
     const bool all_in = std::max(s.c[0], s.c[1]) >= R.cap;
     if (s.type == kChance && spec.depth_limit && spec.game == CFR_GAME_HOLDEM && s.nboard == 4 && !all_in) {
-      s.type = kLeaf;
-      nd.type = kLeaf;
+      if (!std::binary_search(exact.begin(), exact.end(), leaf_seq++)) {  // else: exact river subtrees
+        s.type = kLeaf;
+        nd.type = kLeaf;
+      }
     }
     if (s.type == kDecision) decision_children(R, s, kids);
     else if (s.type == kChance) chance_children(R, s, kids);
@@ -394,6 +414,10 @@ int build_game(const cfr_game_spec& spec, HostGame& g, std::string& err) {
       g.nodes[n].arow = par.row + g.nodes[n].paction;
       g.nodes[n].aplayer = par.player;
     }
+  }
+  if (!exact.empty() && exact.back() >= leaf_seq) {
+    err = "exact_leaves names leaf " + std::to_string(exact.back()) + " of " + std::to_string(leaf_seq);
+    return CFR_EINVAL;
   }
   for (int n = 0; n < N; ++n) {
     if (g.nodes[n].type == kFold || g.nodes[n].type == kShowdown) g.terminals.push_back(n);

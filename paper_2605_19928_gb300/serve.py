@@ -1,5 +1,5 @@
 """Depth-limited solving with the learned leaf network, judged against exact solving of the
-continuation, with a fallback to the exact (full-depth) subgame.
+continuation, with a per-leaf fallback to exact solving.
 
 Section 3 (depth-limited solving): at a depth limit the tree stops and a network supplies
 the counterfactual values of the rest of the game from both players' ranges and the public
@@ -9,8 +9,10 @@ at the average strategy's reach, each row's continuation -- the river subgame be
 card, with the leaf's pot, chips behind, bet tree and the two players' reach as ranges --
 is solved exactly (DCFR, all sampled rows in one batched handle), and the network's values
 on the same rows are compared with the exact best-response values, per unit pot as the
-network is trained.  If the reach-weighted error is above the tolerance, the depth-limited
-result is dropped and the subgame is solved to full depth instead.
+network is trained.  Rows are sampled per leaf, and every leaf whose reach-weighted error is
+above the tolerance is solved exactly in a new handle -- its position becomes the river-card
+chance node with the exact river subtrees -- while the other leaves keep the network: the
+fallback is per leaf, in one handle (the whole subgame to full depth when every leaf fails).
 
 Host orchestration only: every solve, network evaluation and exploitability pass runs in
 the library's kernels through the C ABI (capi); this module builds continuation specs from
@@ -46,14 +48,18 @@ class Judgement:
     continuation_exploitability_mbb: float  # median over the exact continuation solves
     ms: float                      # wall time of the judge (continuation solves included)
     samples: list = field(default_factory=list, repr=False)  # (network row, continuation spec)
+    leaf_errors: list = field(default_factory=list)  # per leaf (cfr_leaf_info order): mean
+                                                     # reach-weighted error of its judged rows,
+                                                     # None where none was judged
 
 
 @dataclass
 class Served:
     tree: object                   # the handle of the chosen form (the caller destroys it)
-    form: str                      # "learned" or "exact"
+    form: str                      # "learned", "mixed" (some leaves exact) or "exact"
     judgement: Judgement
     ms: dict                       # wall time per phase: learned, judge, exact
+    exact_leaves: tuple = ()       # leaves solved exactly (cfr_leaf_info order of the learned form)
 
 
 def leaf_board(tree, node: int, spec) -> list[int]:
@@ -123,13 +129,20 @@ def row_errors(y_net, y_exact, mask, ranges, hands) -> tuple[float, float, int]:
     return tot, weighted, cnt
 
 
+def fallback_leaves(leaf_errors, tol: float) -> list[int]:
+    """The leaves to solve exactly: those whose judged error is above `tol` (a leaf none of
+    whose rows was reached by both players keeps the network)."""
+    return [k for k, e in enumerate(leaf_errors) if e is not None and e > tol]
+
+
 def judge_leaves(tree, spec, n_rows: int = 64, iters: int = 300, seed: int = 0, stream=None,
-                 evaluated: bool = False) -> Judgement:
+                 evaluated: bool = False, per_leaf: int = 0) -> Judgement:
     """Judge the network of a depth-limited handle at its average strategy: sample up to
-    n_rows leaf rows reached by both players, solve their continuations exactly in one
-    batched handle (`iters` DCFR iterations, FP32 values) and compare the network's values
-    on the same rows.  The leaf reach comes from an exploitability pass, run here unless
-    `evaluated` says that cfr_exploitability was the handle's last pass."""
+    n_rows leaf rows reached by both players (per_leaf > 0: up to per_leaf rows of every
+    leaf instead), solve their continuations exactly in one batched handle (`iters` DCFR
+    iterations, FP32 values) and compare the network's values on the same rows.  The leaf
+    reach comes from an exploitability pass, run here unless `evaluated` says that
+    cfr_exploitability was the handle's last pass."""
     t0 = time.perf_counter()
     if not evaluated:
         capi.cfr_exploitability(tree)
@@ -153,16 +166,25 @@ def judge_leaves(tree, spec, n_rows: int = 64, iters: int = 300, seed: int = 0, 
             if live[0][r] > 0.0 and live[1][r] > 0.0:
                 pool.append((row0 + j, len(leaves) - 1, r))
     rng = np.random.default_rng(seed)
-    pick = sorted(rng.choice(len(pool), size=min(n_rows, len(pool)), replace=False).tolist()) if pool else []
-    chosen = []
+    if per_leaf > 0:  # up to per_leaf rows of each leaf
+        pick = []
+        for leaf in range(len(leaves)):
+            mine = [k for k, e in enumerate(pool) if e[1] == leaf]
+            pick += rng.choice(mine, size=min(per_leaf, len(mine)), replace=False).tolist() if mine else []
+        pick.sort()
+    else:
+        pick = sorted(rng.choice(len(pool), size=min(n_rows, len(pool)), replace=False).tolist()) if pool else []
+    chosen, leaf_of = [], []
     for k in pick:
         row, leaf, r = pool[k]
         board, reach, pot, behind = leaves[leaf]
         cont = continuation_spec(spec, board, r, reach, pot, behind, name=f"leaf_row{row}")
         if cont is not None:
             chosen.append((row, cont))
+            leaf_of.append(leaf)
     if not chosen:
-        return Judgement(0, len(pool), 0.0, 0.0, 0.0, 0.0, 1000.0 * (time.perf_counter() - t0))
+        return Judgement(0, len(pool), 0.0, 0.0, 0.0, 0.0, 1000.0 * (time.perf_counter() - t0),
+                         leaf_errors=[None] * len(leaves))
     capi.cfr_eval_leaves(tree, average=True)
     y_net = [capi.cfr_read_leaf_rows(tree, 1, row, 1)[0] for row, _ in chosen]
     specs = [c for _, c in chosen]
@@ -182,16 +204,26 @@ def judge_leaves(tree, spec, n_rows: int = 64, iters: int = 300, seed: int = 0, 
         tot += t
         cnt += c
         per_row.append(w)
+    leaf_errors = [None] * len(leaves)
+    for leaf in range(len(leaves)):
+        mine = [w for w, l in zip(per_row, leaf_of) if l == leaf]
+        if mine:
+            leaf_errors[leaf] = float(np.mean(mine))
     return Judgement(len(specs), len(pool), tot / max(cnt, 1), float(np.mean(per_row)), float(np.max(per_row)),
-                     float(np.median(1000.0 * expl / 100.0)), 1000.0 * (time.perf_counter() - t0), chosen)
+                     float(np.median(1000.0 * expl / 100.0)), 1000.0 * (time.perf_counter() - t0), chosen,
+                     leaf_errors)
 
 
 def solve_depth_limited(spec, weights, biases, iters: int, opts=None, tol: float = DEFAULT_TOL,
-                        judge_rows: int = 64, judge_iters: int = 300, seed: int = 0, stream=None) -> Served:
-    """Solve `spec` (depth_limit 1) with network leaves for `iters` iterations, judge the
-    network on its own leaf rows, and keep the result if the reach-weighted error is at most
-    `tol` (pot units); otherwise -- or if no leaf row could be judged -- solve the full-depth
-    subgame for `iters` iterations."""
+                        judge_rows: int = 64, judge_iters: int = 300, seed: int = 0, stream=None,
+                        per_leaf: int = 4) -> Served:
+    """Solve `spec` (depth_limit 1) with network leaves for `iters` iterations and judge the
+    network on its own leaf rows.  per_leaf > 0: up to per_leaf rows of every leaf are
+    judged, the leaves whose error is above `tol` (pot units) are solved exactly in a new
+    handle beside the network leaves of the rest ("mixed"; the full-depth subgame when every
+    leaf fails, "exact"), and the learned result is kept when none fails.  per_leaf = 0:
+    judge_rows rows of all leaves together, and the full-depth subgame when their mean error
+    is above `tol` or no row could be judged."""
     if spec.depth_limit != 1:
         raise ValueError("solve_depth_limited takes a depth-limited subgame (depth_limit 1)")
     opts = opts if opts is not None else capi.make_opts("dcfr")
@@ -203,21 +235,32 @@ def solve_depth_limited(spec, weights, biases, iters: int, opts=None, tol: float
         capi.cfr_iterate(tree, iters)
         capi.cfr_exploitability(tree)
         ms["learned"] = 1000.0 * (time.perf_counter() - t0)
-        j = judge_leaves(tree, spec, judge_rows, judge_iters, seed, stream, evaluated=True)
+        j = judge_leaves(tree, spec, judge_rows, judge_iters, seed, stream, evaluated=True, per_leaf=per_leaf)
+        n_leaves = len(capi.cfr_leaf_info(tree))
     except BaseException:
         capi.cfr_tree_destroy(tree)
         raise
     ms["judge"] = j.ms
-    if j.rows > 0 and j.reach_weighted_error <= tol:
+    if per_leaf > 0:
+        exact = fallback_leaves(j.leaf_errors, tol)
+        if not exact:
+            return Served(tree, "learned", j, ms)
+    elif j.rows > 0 and j.reach_weighted_error <= tol:
         return Served(tree, "learned", j, ms)
+    else:
+        exact = list(range(n_leaves))
     capi.cfr_tree_destroy(tree)
     t1 = time.perf_counter()
-    exact = capi.cfr_tree_create(dataclasses.replace(spec, depth_limit=0), opts, stream=stream)
+    whole = len(exact) == n_leaves
+    sub = dataclasses.replace(spec, depth_limit=0) if whole else dataclasses.replace(spec, exact_leaves=tuple(exact))
+    fallback = capi.cfr_tree_create(sub, opts, stream=stream)
     try:
-        capi.cfr_iterate(exact, iters)
-        capi.cfr_sync(exact)
+        if not whole:
+            capi.cfr_set_leaf_net(fallback, weights, biases)
+        capi.cfr_iterate(fallback, iters)
+        capi.cfr_sync(fallback)
     except BaseException:
-        capi.cfr_tree_destroy(exact)
+        capi.cfr_tree_destroy(fallback)
         raise
     ms["exact"] = 1000.0 * (time.perf_counter() - t1)
-    return Served(exact, "exact", j, ms)
+    return Served(fallback, "exact" if whole else "mixed", j, ms, tuple(exact))

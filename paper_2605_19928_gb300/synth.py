@@ -47,6 +47,8 @@ class GameSpec:
     max_raises: int = 0                   # bets + raises allowed per street
     seeds: dict = field(default_factory=dict)
     depth_limit: int = 0                  # 1: the tree stops where the river card is to come (leaf network)
+    exact_leaves: tuple = ()              # depth_limit 1: leaves (by index in the depth-limited tree's
+                                          # breadth-first order) solved exactly instead
 
     @property
     def n_hands(self) -> int:

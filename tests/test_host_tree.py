@@ -100,11 +100,17 @@ SPECS = {
     "flop": lambda: synth.flop_subgame(n_hands=4, seed=3, range_seed=4, bet_sizes=(synth.ALL_IN,), max_raises=1),
     "flop_limited": lambda: _limited(synth.flop_subgame(n_hands=6, seed=7, range_seed=8, bet_sizes=(1.0, synth.ALL_IN),
                                                         max_raises=1)),
+    # depth-limited with some leaves solved exactly (mixed network leaves and river subtrees)
+    "turn_mixed": lambda: _limited(synth.turn_subgame(n_hands=10, seed=5, range_seed=6,
+                                                      bet_sizes=(0.5, synth.ALL_IN), max_raises=2), exact=(1, 3)),
+    "flop_mixed": lambda: _limited(synth.flop_subgame(n_hands=6, seed=7, range_seed=8, bet_sizes=(1.0, synth.ALL_IN),
+                                                      max_raises=1), exact=(0, 17, 60)),
 }
 
 
-def _limited(spec):
+def _limited(spec, exact=()):
     spec.depth_limit = 1
+    spec.exact_leaves = tuple(exact)
     return spec
 
 
@@ -538,3 +544,18 @@ def test_invalid_subgames_are_rejected(probe):
     bad.strength = bad.strength[:, keep].copy()
     bad.ranges = np.ones((2, len(keep)), np.float32)
     assert "no pair of hands" in _rejected(probe, bad)
+
+
+def test_exact_leaves_are_checked(probe):
+    """exact_leaves: depth-limited subgames only, distinct indices naming leaves."""
+    def turn(**kw):
+        spec = synth.turn_subgame(n_hands=10, seed=5, range_seed=6, bet_sizes=(0.5, synth.ALL_IN), max_raises=2)
+        for k, v in kw.items():
+            setattr(spec, k, v)
+        return spec
+
+    assert _rejected(probe, turn(depth_limit=1, exact_leaves=(0, 4))) is None  # five leaf positions
+    assert "exact_leaves" in _rejected(probe, turn(depth_limit=1, exact_leaves=(5,)))
+    assert "exact_leaves" in _rejected(probe, turn(depth_limit=1, exact_leaves=(2, 2)))
+    assert "exact_leaves" in _rejected(probe, turn(depth_limit=1, exact_leaves=(-1,)))
+    assert "exact_leaves" in _rejected(probe, turn(depth_limit=0, exact_leaves=(0,)))

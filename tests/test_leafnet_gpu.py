@@ -1,5 +1,7 @@
 """The leaf network's dense layers on the tensor cores (cfr_gemm_bf16) against the FP64
 reference on the same BF16 operands."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -159,12 +161,15 @@ def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
         capi.cfr_tree_destroy(tree)
 
 
-@pytest.mark.parametrize("schedule,variant,street", [("level", "dcfr", "turn"), ("stream", "dcfr", "turn"),
-                                                     ("level", "cfr+", "turn"), ("level", "dcfr", "flop"),
-                                                     ("wide", "dcfr", "flop"), ("wide", "pcfr+", "turn")])
-def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant, street):
+@pytest.mark.parametrize("schedule,variant,street,exact", [
+    ("level", "dcfr", "turn", ()), ("stream", "dcfr", "turn", ()), ("level", "cfr+", "turn", ()),
+    ("level", "dcfr", "flop", ()), ("wide", "dcfr", "flop", ()), ("wide", "pcfr+", "turn", ()),
+    # the per-leaf fallback's trees: network leaves beside exact river subtrees
+    ("level", "dcfr", "turn", (1,)), ("stream", "dcfr", "turn", (0, 2)), ("wide", "dcfr", "flop", (0, 20))])
+def test_iterations_with_leaves_match_oracle_from_the_same_state(schedule, variant, street, exact):
     from oracle.oracle import Oracle
     spec = _leaf_spec(n_hands=32, seed=9, street=street)
+    spec.exact_leaves = exact
     W, b = _random_net(2)
     Wbits = [ln.bf16_bits(w) for w in W]
     tree = capi.cfr_tree_create(spec, capi.make_opts(variant, schedule=schedule))
@@ -234,3 +239,33 @@ def test_full_size_flop_with_network_leaves():
             assert np.max(np.abs(Y[:, :2 * ln.SLOTS] - Yr[:, :2 * ln.SLOTS]) / scale) <= 3e-2
     finally:
         capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("schedule", ["level", "wide"])
+def test_every_leaf_exact_gives_the_full_depth_bits(schedule):
+    """A depth-limited subgame with all its leaves solved exactly is the full-depth subgame:
+    the same tree, so the same bits after the same iterations."""
+    spec = _leaf_spec(n_hands=24, seed=4)
+    probe = capi.cfr_tree_create(spec)
+    try:
+        n_leaves = len(capi.cfr_leaf_info(probe))
+    finally:
+        capi.cfr_tree_destroy(probe)
+    states = []
+    for sp in (dataclasses.replace(spec, exact_leaves=tuple(range(n_leaves))), dataclasses.replace(spec, depth_limit=0)):
+        tree = capi.cfr_tree_create(sp, capi.make_opts("dcfr", schedule=schedule))
+        try:
+            assert capi.cfr_leaf_info(tree) == []
+            capi.cfr_iterate(tree, 5)
+            n_nodes = capi.cfr_tree_info(tree)[0]
+            st = []
+            for n in range(n_nodes):
+                if capi.cfr_node_info(tree, n)["type"] == capi.CFR_NODE_DECISION:
+                    st.append(capi.cfr_read_values(tree, capi.CFR_READ_REGRET, n))
+                    st.append(capi.cfr_read_values(tree, capi.CFR_READ_AVG_SUM, n))
+            states.append((n_nodes, st, capi.cfr_exploitability(tree)[0][0]))
+        finally:
+            capi.cfr_tree_destroy(tree)
+    assert states[0][0] == states[1][0]
+    assert all(np.array_equal(a, b) for a, b in zip(states[0][1], states[1][1]))
+    assert states[0][2] == states[1][2]

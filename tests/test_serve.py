@@ -110,10 +110,14 @@ class FakeABI:
         self.live, self.created, self.fail_iterate = set(), [], fail_iterate
 
     def cfr_tree_create(self, spec, opts, stream=None):
-        h = ("exact" if spec.depth_limit == 0 else "learned", len(self.created))
+        kind = "exact" if spec.depth_limit == 0 else ("mixed" if getattr(spec, "exact_leaves", ()) else "learned")
+        h = (kind, len(self.created), tuple(getattr(spec, "exact_leaves", ())))
         self.created.append(h)
         self.live.add(h)
         return h
+
+    def cfr_leaf_info(self, h):
+        return [(0, 10 + k, 48 * k) for k in range(4)]  # four leaves
 
     def cfr_tree_destroy(self, h):
         self.live.discard(h)
@@ -126,31 +130,53 @@ class FakeABI:
         return None
 
 
-def _fake(monkeypatch, error, rows=8, fail_iterate=False):
+def _fake(monkeypatch, error, rows=8, fail_iterate=False, leaf_errors=None):
     abi = FakeABI(fail_iterate)
-    for name in ("cfr_tree_create", "cfr_tree_destroy", "cfr_iterate"):
+    for name in ("cfr_tree_create", "cfr_tree_destroy", "cfr_iterate", "cfr_leaf_info"):
         monkeypatch.setattr(serve.capi, name, getattr(abi, name))
     for name in ("cfr_set_leaf_net", "cfr_exploitability", "cfr_sync"):
         monkeypatch.setattr(serve.capi, name, abi.noop)
     monkeypatch.setattr(serve.capi, "make_opts", lambda *a, **k: None)
-    j = serve.Judgement(rows, 100, error, error, error, 0.1, 1.0)
+    j = serve.Judgement(rows, 100, error, error, error, 0.1, 1.0,
+                        leaf_errors=[error] * 4 if leaf_errors is None else list(leaf_errors))
     monkeypatch.setattr(serve, "judge_leaves", lambda *a, **k: j)
     return abi
 
 
+def test_fallback_leaves_are_those_above_tolerance():
+    assert serve.fallback_leaves([5e-4, 2e-3, None, 3e-3, 1e-3], 1e-3) == [1, 3]
+    assert serve.fallback_leaves([None, None], 1e-3) == []
+
+
 def test_served_solve_keeps_the_learned_form_within_tolerance(monkeypatch):
     spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
-    abi = _fake(monkeypatch, error=5e-4)
+    for per_leaf in (4, 0):
+        abi = _fake(monkeypatch, error=5e-4)
+        s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3, per_leaf=per_leaf)
+        assert s.form == "learned" and s.tree[0] == "learned" and abi.live == {s.tree}
+        assert s.ms["exact"] == 0.0 and s.exact_leaves == ()
+
+
+def test_served_solve_falls_back_per_leaf(monkeypatch):
+    """Leaves above the tolerance become exact river subtrees in one handle beside the
+    network leaves of the rest; every leaf failing means the full-depth subgame."""
+    spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
+    abi = _fake(monkeypatch, error=0.0, leaf_errors=[5e-4, 2e-3, None, 3e-3])
     s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3)
-    assert s.form == "learned" and s.tree[0] == "learned" and abi.live == {s.tree}
-    assert s.ms["exact"] == 0.0
+    assert s.form == "mixed" and s.tree == ("mixed", 1, (1, 3)) and s.exact_leaves == (1, 3)
+    assert abi.live == {s.tree}
+    abi = _fake(monkeypatch, error=0.0, leaf_errors=[2e-3] * 4)
+    s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3)
+    assert s.form == "exact" and s.tree[0] == "exact" and abi.live == {s.tree}
+    assert spec.depth_limit == 1 and spec.exact_leaves == ()  # the caller's spec is left as it was
 
 
 def test_served_solve_falls_back_above_tolerance_or_without_rows(monkeypatch):
+    """Judged over all leaves together (per_leaf = 0): the whole subgame to full depth."""
     spec = synth.ranked_turn_subgame(n_hands=20, seed=1, range_seed=2, depth_limit=1)
     for error, rows in ((2e-3, 8), (0.0, 0)):  # too large; nothing could be judged
         abi = _fake(monkeypatch, error=error, rows=rows)
-        s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3)
+        s = serve.solve_depth_limited(spec, None, None, 10, tol=1e-3, per_leaf=0)
         assert s.form == "exact" and s.tree[0] == "exact"
         assert abi.live == {s.tree}  # the learned handle was released
         assert spec.depth_limit == 1  # the caller's spec is left as it was

@@ -1,6 +1,7 @@
 """The served depth-limited solve on the GPU (Section 3): the continuation subgames the
 judge solves exactly are the states the network was given, and the fallback returns the
-full-depth subgame."""
+full-depth subgame, or, leaf by leaf, one handle with exact river subtrees where the
+network failed and network leaves elsewhere."""
 import numpy as np
 import pytest
 
@@ -74,13 +75,13 @@ def test_fallback_returns_the_full_depth_subgame():
     spec = synth.ranked_turn_subgame(depth_limit=1)
     W, b = leafnet_train.load_weights()
     opts = capi.make_opts("dcfr", precision="single")
-    kept = serve.solve_depth_limited(spec, W, b, 50, opts, tol=np.inf, judge_rows=4, judge_iters=50)
+    kept = serve.solve_depth_limited(spec, W, b, 50, opts, tol=np.inf, judge_rows=4, judge_iters=50, per_leaf=0)
     try:
         assert kept.form == "learned" and len(capi.cfr_leaf_info(kept.tree)) > 0
         n_learned = capi.cfr_tree_info(kept.tree)[0]
     finally:
         capi.cfr_tree_destroy(kept.tree)
-    dropped = serve.solve_depth_limited(spec, W, b, 50, opts, tol=0.0, judge_rows=4, judge_iters=50)
+    dropped = serve.solve_depth_limited(spec, W, b, 50, opts, tol=0.0, judge_rows=4, judge_iters=50, per_leaf=0)
     try:
         assert dropped.form == "exact" and dropped.judgement.rows == 4
         assert capi.cfr_leaf_info(dropped.tree) == []
@@ -90,3 +91,48 @@ def test_fallback_returns_the_full_depth_subgame():
         assert np.isfinite(e[0]) and e[0] >= 0.0
     finally:
         capi.cfr_tree_destroy(dropped.tree)
+
+
+def _paths(tree):
+    n_nodes = capi.cfr_tree_info(tree)[0]
+    paths = {0: ()}
+    for n in range(1, n_nodes):
+        info = capi.cfr_node_info(tree, n)
+        paths[n] = paths[info["parent"]] + (info["action"],)
+    return paths
+
+
+def test_per_leaf_fallback_mixes_exact_subtrees_and_network_leaves():
+    """With the tolerance at the median judged leaf error, the leaves above it come back as
+    exact river-card chance nodes and the rest stay network leaves, in one handle."""
+    spec = synth.ranked_turn_subgame(depth_limit=1)
+    W, b = leafnet_train.load_weights()
+    opts = capi.make_opts("dcfr", precision="single")
+    tree = capi.cfr_tree_create(spec, opts)
+    try:
+        capi.cfr_set_leaf_net(tree, W, b)
+        capi.cfr_iterate(tree, 50)
+        capi.cfr_exploitability(tree)
+        j = serve.judge_leaves(tree, spec, iters=50, per_leaf=2)
+        leaf_paths = [_paths(tree)[node] for _, node, _ in capi.cfr_leaf_info(tree)]
+    finally:
+        capi.cfr_tree_destroy(tree)
+    judged = [e for e in j.leaf_errors if e is not None]
+    assert len(judged) >= 2 and j.rows <= 2 * len(leaf_paths)
+    tol = float(np.median(judged))
+    want = serve.fallback_leaves(j.leaf_errors, tol)
+    assert 0 < len(want) < len(leaf_paths)
+    s = serve.solve_depth_limited(spec, W, b, 50, opts, tol=tol, judge_iters=50, per_leaf=2)
+    try:
+        assert s.form == "mixed" and list(s.exact_leaves) == want
+        paths = _paths(s.tree)
+        by_path = {p: n for n, p in paths.items()}
+        left = [_paths(s.tree)[node] for _, node, _ in capi.cfr_leaf_info(s.tree)]
+        assert left == [p for k, p in enumerate(leaf_paths) if k not in want]
+        for k in want:  # the river card is dealt by chance there now
+            assert capi.cfr_node_info(s.tree, by_path[leaf_paths[k]])["type"] == capi.CFR_NODE_CHANCE
+        assert capi.cfr_tree_info(s.tree)[2] == 50
+        e, _ = capi.cfr_exploitability(s.tree)
+        assert np.isfinite(e[0])
+    finally:
+        capi.cfr_tree_destroy(s.tree)
