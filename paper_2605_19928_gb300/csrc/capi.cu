@@ -8,6 +8,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "pcfr.h"
@@ -54,6 +56,7 @@ struct cfr_tree {
   std::vector<int> wide_inner_off, wide_fwd_off;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
+  unsigned* d_res_sync = nullptr;   // resident schedule: barrier and exit counters
   int* d_err = nullptr;
   Discount* d_disc = nullptr;
   int disc_capacity = 0;
@@ -122,6 +125,47 @@ int upload(cfr_tree* t, const std::vector<T>& v, T** out) {
   *out = (T*)p;
   return CFR_OK;
 }
+
+// One device block for every subgame's tables and state: the tables are staged on the host
+// and sent with one copy, the state after them zeroed with one memset, and each buffer's
+// pointer field is set once the block exists (a handle of many subgames makes a handful of
+// allocations instead of a couple of dozen per subgame).  Buffers start 256-byte aligned.
+struct Packer {
+  std::vector<unsigned char> stage;              // host bytes of the tables
+  size_t zero_bytes = 0;                         // bytes of zeroed state after the tables
+  std::vector<std::pair<size_t, void**>> tabs;   // (offset in the tables, field to set)
+  std::vector<std::pair<size_t, void**>> state;  // (offset in the state, field to set)
+  static size_t round(size_t b) { return (b + 255) / 256 * 256; }
+  template <typename T, typename F>
+  void table(const std::vector<T>& v, F** where) {
+    *where = nullptr;
+    if (v.empty()) return;
+    const size_t off = stage.size(), bytes = v.size() * sizeof(T);
+    stage.resize(off + round(bytes), 0);
+    memcpy(stage.data() + off, v.data(), bytes);
+    tabs.push_back({off, reinterpret_cast<void**>(const_cast<typename std::remove_const<F>::type**>(where))});
+  }
+  template <typename F>
+  void zeroed(size_t bytes, F** where) {
+    state.push_back({zero_bytes, reinterpret_cast<void**>(where)});
+    zero_bytes += round(std::max<size_t>(bytes, 1));
+  }
+  // allocate, copy, zero and set the fields
+  int commit(cfr_tree* t) {
+    const size_t total = stage.size() + zero_bytes;
+    if (total == 0) return CFR_OK;
+    unsigned char* block = static_cast<unsigned char*>(t->alloc(total));
+    if (!block) return fail(CFR_ENOMEM, "device allocation failed");
+    if (!stage.empty()) {
+      CK(cudaMemcpyAsync(block, stage.data(), stage.size(), cudaMemcpyHostToDevice, t->stream));
+      t->h2d_bytes += (int64_t)stage.size();
+    }
+    if (zero_bytes) CK(cudaMemsetAsync(block + stage.size(), 0, zero_bytes, t->stream));
+    for (auto& f : tabs) *f.second = block + f.first;
+    for (auto& f : state) *f.second = block + stage.size() + f.first;
+    return CFR_OK;
+  }
+};
 
 template <typename T>
 int zeros(cfr_tree* t, size_t n, T** out) {
@@ -296,7 +340,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if (o.term_nodes < 0 || o.term_nodes > 8) return fail(CFR_EINVAL, "term_nodes must be 0 to 8");
   if (o.warp_hands != 0 && o.warp_hands != 32 && o.warp_hands != 64)
     return fail(CFR_EINVAL, "warp_hands must be 0, 32 or 64");
-  if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_WIDE) return fail(CFR_EINVAL, "unknown schedule");
+  if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_RESIDENT) return fail(CFR_EINVAL, "unknown schedule");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
   static int configured = configure_kernels();
@@ -323,12 +367,27 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   // tree and state in shared memory when every game of the handle fits in 96 KB (two blocks
   // per SM); otherwise all games work on the global arrays, which stay in L2 for trees of
   // this size.
+  // The resident schedule gives every chunk a block of its own, one block per SM: its default
+  // chunk is the smallest of 8, 16 and 32 hands with which the handle's chunks fit the SMs.
+  const bool resident = o.schedule == CFR_SCHEDULE_RESIDENT;
+  int n_sms = 0;
+  if (cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess || n_sms < 1) {
+    delete t;
+    return fail(CFR_ECUDA, "cudaDeviceGetAttribute failed");
+  }
+  auto chunks_of = [&](int W) {
+    long n = 0;
+    for (int g = 0; g < n_games; ++g) n += (t->host[g].n_hands + W - 1) / W;
+    return n;
+  };
+  int res_W = 8;
+  while (resident && !o.chunk_hands && res_W < 32 && chunks_of(res_W) > n_sms) res_W *= 2;
   size_t smem_hand = 0, smem_term = 0;
   std::vector<int> chunk(n_games);
   std::vector<int> use_smem(n_games);
   bool all_fit = true;
   for (int g = 0; g < n_games; ++g) {
-    const int W = o.chunk_hands ? o.chunk_hands : 8;
+    const int W = o.chunk_hands ? o.chunk_hands : res_W;
     chunk[g] = W;
     all_fit = all_fit && hand_smem(t->host[g], W, es) <= 96 * 1024;
   }
@@ -421,6 +480,25 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   } else if (o.schedule == CFR_SCHEDULE_AUTO && schedule == kScheduleLevel && wide_ok && !all_fit) {
     schedule = kScheduleWide;
   }
+  // Resident schedule: one block per SM holds a chunk's state of both players beside a terminal
+  // node's board table, and every chunk has a block.
+  size_t res_term = 0, res_hand = 0;
+  if (resident) {
+    for (int g = 0; g < n_games; ++g) {
+      const HostGame& h = t->host[g];
+      const int rows_max = std::max(h.row_begin[1] - h.row_begin[0], h.row_begin[2] - h.row_begin[1]);
+      res_term = std::max(res_term, resident_term_size(h.n_hands, h.hand_size, h.deck, h.hstride, es));
+      res_hand = std::max(res_hand, resident_hand_size((int)h.nodes.size(), (int)h.level_start.size() - 1, rows_max,
+                                                       chunk[g], es));
+    }
+    const int per_sm = res_term + res_hand <= 200 * 1024 ? resident_blocks_per_sm(o.precision, res_term + res_hand) : 0;
+    if (per_sm < 1 || chunks_of(chunk[0]) > (long)per_sm * n_sms) {
+      delete t;
+      return fail(CFR_EINVAL, "the resident schedule needs every chunk of hands resident at once (" +
+                                  std::to_string(chunks_of(chunk[0])) + " chunks, " + std::to_string(per_sm * n_sms) +
+                                  " blocks fit)");
+    }
+  }
   if (schedule == kScheduleWide) {  // per level: the inner nodes, and the nodes whose reach is stored
     const HostGame& h = t->host[0];
     const int L = (int)h.level_start.size() - 1;
@@ -442,7 +520,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   }
 
   std::vector<Work> chunk_work, term_work, warp_work;
-  t->dev.resize(n_games);
+  Packer packer;
+  t->dev.resize(n_games);  // not resized again: the packer holds the addresses of its fields
   for (int g = 0; g < n_games; ++g) {
     const HostGame& h = t->host[g];
     GameDev& d = t->dev[g];
@@ -475,10 +554,6 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       pay32[2 * n] = (float)x;
       pay32[2 * n + 1] = (float)(x - (double)pay32[2 * n]);
     }
-    NodeDev* nodes;
-    int32_t *ls, *rn, *dn, *chk;
-    uint32_t* un;
-    ProgOp* prog;
     const std::vector<ProgOp> ops = program_ops(h, programs[g]);
     for (int q = 0; q < 4; ++q) {
       d.unit_off[q] = table_meta[g][q];
@@ -486,35 +561,33 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       d.chunk_off[q] = table_meta[g][8 + q];
       d.chunk_count[q] = table_meta[g][12 + q];
     }
-    uint16_t* tb;
-    uint64_t* hm;
-    float *rrv, *pay32d;
-    double *rr64, *pay;
-    if ((rc = upload(t, h.nodes, &nodes)) || (rc = upload(t, h.level_start, &ls)) || (rc = upload(t, rown, &rn)) ||
-        (rc = upload(t, h.hand_mask, &hm)) || (rc = upload(t, rv, &rrv)) || (rc = upload(t, r64, &rr64)) ||
-        (rc = upload(t, h.payoff, &pay)) || (rc = upload(t, pay32, &pay32d)) || (rc = upload(t, tab, &tb)) ||
-        (rc = upload(t, decn, &dn)) ||
-        (rc = upload(t, ops, &prog)) || (rc = upload(t, chunk_lists[g], &chk)) ||
-        (rc = upload(t, unit_lists[g], &un))) {
-      delete t;
-      return rc;
-    }
-    d.nodes = nodes; d.level_start = ls; d.row_node = rn; d.hand_mask = hm; d.range_v = rrv; d.range64 = rr64;
-    d.payoff = pay; d.payoff_ff = pay32d; d.term_tab = tb; d.dec_nodes = dn; d.prog = prog; d.chunks = chk; d.units = un;
+    packer.table(h.nodes, &d.nodes);
+    packer.table(h.level_start, &d.level_start);
+    packer.table(rown, &d.row_node);
+    packer.table(h.hand_mask, &d.hand_mask);
+    packer.table(rv, &d.range_v);
+    packer.table(r64, &d.range64);
+    packer.table(h.payoff, &d.payoff);
+    packer.table(pay32, &d.payoff_ff);
+    packer.table(tab, &d.term_tab);
+    packer.table(decn, &d.dec_nodes);
+    packer.table(ops, &d.prog);
+    packer.table(chunk_lists[g], &d.chunks);
+    packer.table(unit_lists[g], &d.units);
     d.prog_len = (int)programs[g].size();
     const size_t rows = (size_t)h.n_rows * S, cells = 2 * N * S;
-    const size_t vf = es / 4;  // floats per value
-    float *sig, *sigb, *rch, *rchb, *cf, *cfb;
-    if ((rc = zeros(t, rows, &d.R)) || (rc = zeros(t, rows, &d.S)) || (rc = zeros(t, rows * vf, &sig)) ||
-        (rc = zeros(t, rows * vf, &sigb)) || (rc = zeros(t, cells * vf, &rch)) || (rc = zeros(t, cells * vf, &rchb)) ||
-        (rc = zeros(t, cells * vf, &cf)) || (rc = zeros(t, cells * vf, &cfb)) ||
-        (o.variant == CFR_VARIANT_PCFRPLUS && (rc = zeros(t, rows, &d.M))) ||
-        (rc = zeros(t, (size_t)2 * d.n_chunks, &d.br_partial)) || (rc = zeros(t, 2, &d.br_out)) ||
-        (rc = zeros(t, 1, &d.br_done))) {
-      delete t;
-      return rc;
-    }
-    d.sigma = sig; d.sigbar = sigb; d.reach = rch; d.reach_bar = rchb; d.cfv = cf; d.cfv_br = cfb;
+    packer.zeroed(rows * 8, &d.R);
+    packer.zeroed(rows * 8, &d.S);
+    packer.zeroed(rows * es, &d.sigma);
+    packer.zeroed(rows * es, &d.sigbar);
+    packer.zeroed(cells * es, &d.reach);
+    packer.zeroed(cells * es, &d.reach_bar);
+    packer.zeroed(cells * es, &d.cfv);
+    packer.zeroed(cells * es, &d.cfv_br);
+    if (o.variant == CFR_VARIANT_PCFRPLUS) packer.zeroed(rows * 8, &d.M);
+    packer.zeroed((size_t)2 * d.n_chunks * 8, &d.br_partial);
+    packer.zeroed(2 * 8, &d.br_out);
+    packer.zeroed(4, &d.br_done);
     for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
 
     // terminals grouped by board table (fold nodes read only the board-free part of table 0)
@@ -522,6 +595,10 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     auto table = [&](int n) { return h.nodes[(size_t)n].type == kShowdown ? h.nodes[(size_t)n].row : 0; };
     std::stable_sort(term.begin(), term.end(), [&](int a, int b2) { return table(a) < table(b2); });
     for (int n : term) term_work.push_back({g, n});
+  }
+  if ((rc = packer.commit(t))) {
+    delete t;
+    return rc;
   }
   std::vector<int32_t> term_src(term_work.size());
   for (size_t k = 0; k < term_work.size(); ++k)
@@ -561,7 +638,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       (rc = upload(t, term_src, &t->d_term_src)) ||
       (rc = upload(t, term_runs, &t->d_term_runs)) ||
       (rc = zeros(t, 1, &t->d_iter)) ||
-      (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) ||
+      (rc = zeros(t, 1, &t->d_done)) || (rc = zeros(t, 1, &t->d_err)) || (rc = zeros(t, 2, &t->d_res_sync)) ||
       (rc = upload(t, discount_table(o, kDiscountCapacity), &t->d_disc))) {
     delete t;
     return rc;
@@ -594,6 +671,15 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   c.stream_half = stream_half;
   c.stream_units = stream_units;
   c.stream_hp = stream_hp;
+  c.alternating = o.alternating ? 1 : 0;
+  c.resident = resident ? 1 : 0;
+  c.resident_sync = t->d_res_sync;
+  if (resident) {
+    c.resident_term = (unsigned)res_term;
+    c.smem_resident = res_term + res_hand;
+    const long items = (long)term_work.size() * (o.alternating ? 1 : 2);
+    c.resident_grid = (int)std::max<long>(chunk_work.size(), std::min<long>(items, n_sms));
+  }
   if (schedule == kScheduleWide) {
     const HostGame& h = t->host[0];
     c.wide_levels = (int)t->wide_inner_off.size() - 1;
@@ -613,6 +699,10 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if ((rc = setup_leaves(t, specs, n_games))) {
     delete t;
     return rc;
+  }
+  if (resident && t->leaf.n_leaves > 0) {
+    delete t;
+    return fail(CFR_EINVAL, "the resident schedule has no leaf-network stage: depth-limited trees take another");
   }
   t->launches_per_iteration =
       (o.alternating ? pass_launches(t, kModeUpdate, 1, 0) + pass_launches(t, kModeUpdate, 2, 1)
@@ -731,7 +821,7 @@ int cfr_iterate(cfr_tree* t, int n_iters) {
   if (n_iters == 0) return CFR_OK;
   int rc0 = ensure_discounts(t, (int64_t)t->iters_done + n_iters);
   if (rc0) return rc0;
-  if (!t->iter_graph) {
+  if (!t->iter_graph && !t->ctx.resident) {
     if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
@@ -744,6 +834,15 @@ int cfr_iterate(cfr_tree* t, int n_iters) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
   t->state_gen += 1;
+  if (t->ctx.resident) {  // one cooperative launch per 2^20 iterations (its barrier count stays in 32 bits)
+    for (int done = 0; done < n_iters; done += 1 << 20) {
+      if (launch_resident(t->ctx, std::min(n_iters - done, 1 << 20), t->stream) != 0)
+        return fail(CFR_ECUDA, "resident launch failed");
+      t->launches += 1;
+    }
+    t->iters_done += n_iters;
+    return CFR_OK;
+  }
   for (int k = 0; k < n_iters; ++k) CK(cudaGraphLaunch(t->iter_graph, t->stream));
   t->iters_done += n_iters;
   t->launches += (int64_t)n_iters * t->launches_per_iteration;
@@ -860,7 +959,8 @@ int cfr_reset(cfr_tree* t) {
 
 int cfr_schedule(const cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
-  return t->ctx.schedule == kScheduleStream ? CFR_SCHEDULE_STREAM
+  return t->ctx.resident ? CFR_SCHEDULE_RESIDENT
+         : t->ctx.schedule == kScheduleStream ? CFR_SCHEDULE_STREAM
          : t->ctx.schedule == kScheduleWide ? CFR_SCHEDULE_WIDE
                                             : CFR_SCHEDULE_LEVEL;
 }
