@@ -44,6 +44,7 @@ if ROOT not in sys.path:
 METRIC = "CFR iters/sec (ms/iter) per GB300 at fixed exploitability vs plain exact form; HBM GB/s"
 BB_CHIPS = 100.0  # big blind used for mbb/hand (the pot is 100 chips)
 L2_FLUSH_BYTES = 256 << 20
+SCHEDULE_NAMES = {1: "level", 2: "stream", 3: "wide", 4: "resident"}  # cfr_schedule's values (include/pcfr.h)
 
 
 def parse_args(argv=None):
@@ -64,7 +65,7 @@ def parse_args(argv=None):
                     help="values as FP32 pairs or plain FP32 (R and S are FP64 either way); default pairs for "
                          "the single river, FP32 for the batch and the depth-limited workloads")
     ap.add_argument("--chunk-hands", type=int, default=0)
-    ap.add_argument("--schedule", choices=["auto", "level", "stream"], default="auto")
+    ap.add_argument("--schedule", choices=["auto", "level", "stream", "wide", "resident"], default="auto")
     ap.add_argument("--warp-hands", type=int, choices=[0, 32, 64], default=0,
                     help="stream schedule: hands per warp (0 = automatic)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
@@ -413,8 +414,7 @@ def run_ours(args):
     if batch and not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0:
         # launch tiling (schedule, hands per block, terminal nodes per block), outside the timed region
         opts, ms_tuned = capi.cfr_autotune(specs, opts, iters=20, stream=stream.cuda_stream)
-        names = {capi.CFR_SCHEDULE_LEVEL: "level", capi.CFR_SCHEDULE_STREAM: "stream", capi.CFR_SCHEDULE_WIDE: "wide"}
-        tuned = {"schedule": names[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
+        tuned = {"schedule": SCHEDULE_NAMES[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
                  "warp_hands": opts.warp_hands,
                  "ms_per_iter_while_tuning": ms_tuned}
 
@@ -466,21 +466,45 @@ def run_ours(args):
     vbytes = 8 if args.precision == "pairs" else 4  # bytes of one stored value
     per_step = {k: stages[k][0] * (2 * ips if k in ("terminal", "update") else 1) for k in stages}
     dom = max(("update", "terminal"), key=lambda k: per_step[k])
-    # the roofline model counts 4-byte values whatever the storage precision
-    alg = sum(algorithmic_bytes(sh, dom, 4) for sh in shapes)
-    achieved = alg / (stages[dom][0] * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    schedule = "stream" if capi.cfr_schedule(tree) == capi.CFR_SCHEDULE_STREAM else "level"
-    upd_kernel = "k_stream_update" if schedule == "stream" else "k_hand<update>"
-    roofline = {"bound": "hbm", "kernel": upd_kernel if dom == "update" else "k_terminal",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": profiled_traffic(dom, "batch256" if batch else "river1081"),
-                "algorithmic_bytes_per_launch": alg, "value_bytes_in_model": 4, "launch_ms": stages[dom][0],
-                "stage_ms": {k: v[0] for k, v in stages.items()}}
-    if vbytes != 4:  # the same model with the stored pair values, for comparison only
-        roofline["algorithmic_bytes_per_launch_pair_storage"] = sum(algorithmic_bytes(sh, dom, vbytes)
-                                                                    for sh in shapes)
+    schedule = SCHEDULE_NAMES[capi.cfr_schedule(tree)]
+    if schedule == "resident":
+        # one launch runs whole iterations: per iteration both players' terminal and update
+        # launches' algorithmic bytes, over the launch's own device time
+        n_res = min(ips, 200)
+        capi.cfr_reset(tree)
+        torch.cuda.synchronize(device)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        capi.cfr_iterate(tree, n_res)
+        r1.record(stream)
+        torch.cuda.synchronize(device)
+        launch_ms = r0.elapsed_time(r1)
+        per_iter = lambda v: sum(2 * (algorithmic_bytes(sh, "update", v) + algorithmic_bytes(sh, "terminal", v))
+                                 for sh in shapes)
+        alg = n_res * per_iter(4)
+        roofline = {"bound": "hbm", "kernel": "k_resident", "achieved": alg / (launch_ms * 1e-3) / 1e9,
+                    "peak": peak, "unit": "GB/s", "frac": alg / (launch_ms * 1e-3) / 1e9 / peak,
+                    "peak_source": f"{peak_kind} hbm_gbs", "traffic": profiled_traffic("resident", "river1081"),
+                    "algorithmic_bytes_per_launch": alg, "value_bytes_in_model": 4, "launch_ms": launch_ms,
+                    "iterations_per_launch": n_res,
+                    "stage_ms_level_kernels": {k: v[0] for k, v in stages.items()}}
+        if vbytes != 4:
+            roofline["algorithmic_bytes_per_launch_pair_storage"] = n_res * per_iter(vbytes)
+    else:
+        # the roofline model counts 4-byte values whatever the storage precision
+        alg = sum(algorithmic_bytes(sh, dom, 4) for sh in shapes)
+        achieved = alg / (stages[dom][0] * 1e-3) / 1e9
+        upd_kernel = "k_stream_update" if schedule == "stream" else "k_hand<update>"
+        roofline = {"bound": "hbm", "kernel": upd_kernel if dom == "update" else "k_terminal",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_kind} hbm_gbs",
+                    "traffic": profiled_traffic(dom, "batch256" if batch else "river1081"),
+                    "algorithmic_bytes_per_launch": alg, "value_bytes_in_model": 4, "launch_ms": stages[dom][0],
+                    "stage_ms": {k: v[0] for k, v in stages.items()}}
+        if vbytes != 4:  # the same model with the stored pair values, for comparison only
+            roofline["algorithmic_bytes_per_launch_pair_storage"] = sum(algorithmic_bytes(sh, dom, vbytes)
+                                                                        for sh in shapes)
 
     target = None
     if not batch:  # the single subgame: iterations (and device time) to 1 mbb/hand

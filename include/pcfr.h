@@ -137,6 +137,16 @@ typedef struct cfr_game_spec {
  * response) is one launch per tree level over all of that level's (node, hand) pairs, one
  * thread each (for one tree too large for a block to stage in shared memory: exact turns
  * and flops; one subgame per handle, at most 8 actions per decision node).
+ * CFR_SCHEDULE_RESIDENT: cfr_iterate runs all its iterations in one cooperative launch;
+ * each block keeps one chunk of hands of both players (regrets, strategy sums, strategy,
+ * reach) in shared memory for the whole launch, and a grid barrier separates an iteration's
+ * phases (the terminal values of a player, then its update), so no phase is a launch of its
+ * own (lowest latency for one small subgame).  Every chunk must have a block of its own at
+ * one block per SM (chunk_hands = 0 takes the smallest of 8, 16 and 32 hands that allows
+ * it) and the tree must have no depth-limit leaves: CFR_EINVAL otherwise.  The other passes
+ * (initial strategy, average, best response) use the level schedule's kernels.  A grid
+ * barrier that waits too long gives up (about a second): cfr_sync then returns
+ * CFR_ETIMEOUT and the handle's state is undefined.
  * CFR_SCHEDULE_AUTO (0) picks STREAM when the handle has at least 1216 such warps (8 per
  * SM) and every tree allows it, WIDE for one subgame too large to stage, else LEVEL.
  * term_nodes: fold and showdown nodes per CUDA block of the terminal launch (nodes of one
@@ -149,7 +159,13 @@ typedef struct cfr_game_spec {
  * schedules ignore it.  Results are the same bits either way.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
-enum { CFR_SCHEDULE_AUTO = 0, CFR_SCHEDULE_LEVEL = 1, CFR_SCHEDULE_STREAM = 2, CFR_SCHEDULE_WIDE = 3 };
+enum {
+  CFR_SCHEDULE_AUTO = 0,
+  CFR_SCHEDULE_LEVEL = 1,
+  CFR_SCHEDULE_STREAM = 2,
+  CFR_SCHEDULE_WIDE = 3,
+  CFR_SCHEDULE_RESIDENT = 4
+};
 typedef struct cfr_solver_opts {
   int variant;
   double alpha;
@@ -236,8 +252,8 @@ int cfr_reset(cfr_tree* tree);
 int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream, int iters,
                  cfr_solver_opts* best, double* ms_per_iter);
 
-/* The schedule the handle uses (CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM or
- * CFR_SCHEDULE_WIDE), or a negative status. */
+/* The schedule the handle uses (CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM,
+ * CFR_SCHEDULE_WIDE or CFR_SCHEDULE_RESIDENT), or a negative status. */
 int cfr_schedule(const cfr_tree* tree);
 
 /* Sizes of one subgame and the number of iterations done.  Any out pointer may be NULL. */
@@ -283,8 +299,11 @@ int cfr_sync(cfr_tree* tree);
  * can land.  A block that gives up still waits, with the default limit, for its own copies
  * to land, then sets the handle's device flag and returns without computing its values,
  * so the next synchronising call on the handle reports CFR_ETIMEOUT and the CUDA context
- * stays usable.  Call it while none of the library's kernels are in flight (e.g. after
- * cfr_sync); it applies to every handle on the device until it is called again. */
+ * stays usable.  The same limit applies to the first grid barrier of each resident-schedule
+ * launch (CFR_SCHEDULE_RESIDENT): with 0 every block but the last to arrive gives up, sets
+ * the flag, and the others see it at their next barrier and leave.  Call it while none of
+ * the library's kernels are in flight (e.g. after cfr_sync); it applies to every handle on
+ * the device until it is called again. */
 int cfr_debug_first_wait_polls(long polls);
 
 /* Per-stage device time, after the paper's per-stage breakdown (Section 5, Table 3).

@@ -26,9 +26,9 @@ CFR_READ_REGRET, CFR_READ_AVG_SUM, CFR_READ_CFV, CFR_READ_BR_CFV, CFR_READ_PREDI
 CFR_READ_AVG_REACH = 5
 CFR_PRECISION_PAIRS, CFR_PRECISION_SINGLE = 0, 1
 PRECISIONS = {"pairs": CFR_PRECISION_PAIRS, "single": CFR_PRECISION_SINGLE}
-CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM, CFR_SCHEDULE_WIDE = 0, 1, 2, 3
+CFR_SCHEDULE_AUTO, CFR_SCHEDULE_LEVEL, CFR_SCHEDULE_STREAM, CFR_SCHEDULE_WIDE, CFR_SCHEDULE_RESIDENT = 0, 1, 2, 3, 4
 SCHEDULES = {"auto": CFR_SCHEDULE_AUTO, "level": CFR_SCHEDULE_LEVEL, "stream": CFR_SCHEDULE_STREAM,
-             "wide": CFR_SCHEDULE_WIDE}
+             "wide": CFR_SCHEDULE_WIDE, "resident": CFR_SCHEDULE_RESIDENT}
 VARIANTS = {"cfr": CFR_VARIANT_CFR, "cfr+": CFR_VARIANT_CFRPLUS, "dcfr": CFR_VARIANT_DCFR,
             "pcfr+": CFR_VARIANT_PCFRPLUS}
 CFR_STAGES = ("terminal", "update", "avg_reach", "br_terminal", "br", "leaf")

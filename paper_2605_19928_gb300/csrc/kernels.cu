@@ -656,6 +656,146 @@ __host__ __device__ inline size_t hand_smem_bytes(int n_nodes, int n_levels, int
          (size_t)(2 * n_nodes + rows_max) * W * es;
 }
 
+// The per-hand passes of one chunk of W hands of player p, on whichever arrays hold the
+// chunk's columns (shared memory, or the global arrays at column h).  Each node and each row
+// is computed by one thread in a fixed order, so the result does not depend on how many
+// threads share the work (slot / nslots): the level and resident schedules give the same bits.
+template <typename P>
+struct HandView {
+  const NodeDev* nodes;
+  const int* ls;      // level offsets [L + 1]
+  const int* rown;    // node of each row of p
+  const int* decs;    // decision nodes of p
+  int L, ndec, nrows, rb, p;
+  int slot, nslots;   // this thread's slot and the block's slot count
+  bool valid;         // a real hand (h < n_hands)
+  bool wr;            // this lane may write its column of the working arrays
+  uint64_t hmask;     // cards of the hand
+  Col<typename P::V> v, rch, sg;
+  Col<double> Rc, Sc;
+};
+
+// Backward values (Stage 6, Eq. backward), level by level from the leaves; MODE = kModeBR
+// takes the max over p's actions (best response).
+template <int MODE, typename P>
+__device__ __forceinline__ void hand_backward(const HandView<P>& hv) {
+  using V = typename P::V;
+  for (int l = hv.L - 1; l >= 0; --l) {
+    const int a0 = hv.ls[l], cnt = hv.ls[l + 1] - a0;
+    for (int idx = hv.slot; idx < cnt; idx += hv.nslots) {
+      const int n = a0 + idx;
+      const NodeDev nd = hv.nodes[n];
+      if (is_end(nd.type)) continue;
+      const int A = nd.n_kids, k0 = nd.first_kid;
+      V val;
+      if (MODE == kModeBR && nd.type == kDecision && nd.player == hv.p) {
+        val = hv.v[k0];
+        for (int a = 1; a < A; ++a) val = P::vmax(val, hv.v[k0 + a]);
+      } else {
+        typename P::Acc acc = P::acc0();
+        if (nd.type == kChance) {
+          // children values already carry the card probabilities; cards in the hand are out
+          for (int a = 0; a < A; ++a)
+            if (!((hv.hmask >> hv.nodes[k0 + a].deal) & 1ull)) P::acc(acc, hv.v[k0 + a]);
+        } else if (nd.player != hv.p) {
+          for (int a = 0; a < A; ++a) P::acc(acc, hv.v[k0 + a]);
+        } else {
+          const int r0 = nd.row - hv.rb;
+          for (int a = 0; a < A; ++a) P::acc_mul(acc, hv.sg[r0 + a], hv.v[k0 + a]);
+        }
+        val = P::value(acc);
+      }
+      if (hv.wr) hv.v[n] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Positive parts of the strategy source into sg, one (row, hand) item per thread:
+//   update: the Stage 7 update of R and S (new rows to Rout / Sout where out_ok, the
+//           prediction to M where the hand is real), then the positive part of the new R;
+//   init: the positive part of R (+ M);  average: S.
+// (sign tests of FP64 values read the sign bit on the integer pipe: x > 0 exactly when the
+// bits, as a signed integer, are positive)
+template <int MODE, typename P>
+__device__ __forceinline__ void hand_rows(const HandView<P>& hv, const Discount& d, int variant, Col<double> Rout,
+                                          Col<double> Sout, bool out_ok, Col<double> M) {
+  using V = typename P::V;
+  for (int r = hv.slot; r < hv.nrows; r += hv.nslots) {
+    double x;
+    if (MODE == kModeUpdate) {
+      const int n = hv.rown[r];
+      const NodeDev nd = hv.nodes[n];
+      const V rr = P::sub(hv.v[nd.first_kid + (hv.rb + r - nd.row)], hv.v[n]);  // instantaneous regret
+      const double contrib = P::to_double(P::mul(hv.rch[n], hv.sg[r]));      // pi_i(I) sigma(I, a)
+      const double rd = P::to_double(rr);
+      x = hv.Rc[r] + rd;
+      if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
+      if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;  // CFR+, Predictive CFR+
+      const double sn = fma(hv.Sc[r], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
+      if (out_ok) {
+        Rout[r] = x;
+        Sout[r] = sn;
+      }
+      if (variant == 3 && hv.valid) M[r] = rd;  // the prediction of the next regret
+      if (variant == 3) x += rd;                // Predictive CFR+ matches R + M
+    } else {
+      x = MODE == kModeInit ? hv.Rc[r] : hv.Sc[r];
+      if (MODE == kModeInit && M.base) x += hv.valid ? M[r] : 0.0;
+    }
+    if (hv.wr) hv.sg[r] = __double_as_longlong(x) > 0 ? P::of_double(x) : P::zero();
+  }
+  __syncthreads();
+}
+
+// Regret matching (Eq. rm) / normalisation of the average, per decision node of p.
+template <typename P>
+__device__ __forceinline__ void hand_rm(const HandView<P>& hv) {
+  using V = typename P::V;
+  for (int k = hv.slot; k < hv.ndec; k += hv.nslots) {
+    const NodeDev nd = hv.nodes[hv.decs[k]];
+    const int A = nd.n_kids, r0 = nd.row - hv.rb;
+    V tot = P::zero();
+    int npos = 0, last = 0;
+    for (int a = 0; a < A; ++a) {
+      const V x = hv.sg[r0 + a];
+      if (P::positive(x)) ++npos, last = a;
+      tot = P::add(tot, x);
+    }
+    if (!hv.wr) continue;
+    if (npos == 1) {  // x / x = 1 exactly, as the definition gives
+      for (int a = 0; a < A; ++a) hv.sg[r0 + a] = a == last ? P::one() : P::zero();
+    } else if (npos > 1) {
+      const V inv = P::recip(tot);
+      for (int a = 0; a < A; ++a) hv.sg[r0 + a] = P::mul(hv.sg[r0 + a], inv);
+    } else {
+      const V uni = P::uniform(A);
+      for (int a = 0; a < A; ++a) hv.sg[r0 + a] = uni;
+    }
+  }
+  __syncthreads();
+}
+
+// Forward reach of player p (Stages 1-2) under the strategy in sg, from the root reach `root`.
+template <typename P>
+__device__ __forceinline__ void hand_forward(const HandView<P>& hv, typename P::V root) {
+  using V = typename P::V;
+  if (hv.slot == 0 && hv.wr) hv.rch[0] = root;
+  __syncthreads();
+  for (int l = 1; l < hv.L; ++l) {
+    const int a0 = hv.ls[l], cnt = hv.ls[l + 1] - a0;
+    for (int idx = hv.slot; idx < cnt; idx += hv.nslots) {
+      const int n = a0 + idx;
+      const NodeDev nd = hv.nodes[n];
+      V x = hv.wr ? hv.rch[nd.parent] : P::zero();
+      if (nd.aplayer == hv.p) x = P::mul(x, hv.sg[nd.arow - hv.rb]);
+      if (nd.deal != kNoCard && ((hv.hmask >> nd.deal) & 1ull)) x = P::zero();
+      if (hv.wr) hv.rch[n] = x;
+    }
+    __syncthreads();
+  }
+}
+
 // Per-hand tree passes for one chunk of W hands of player p (grid: (player, chunk)).
 //   kModeInit:   sigma_p = RM(R_p) (Eq. rm), forward reach of p (Stage 1).
 //   kModeUpdate: backward values of p (Stage 6, Eq. backward) from the terminal values,
@@ -770,37 +910,11 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
   }
   __syncthreads();
 
-  // ---- backward pass (Stage 6), double-float only, level by level from the leaves
+  const HandView<P> hv{nodes, ls, rown, decs, L, ndec, nrows, rb, p, slot, nslots, valid, wr, hmask, v, rch, sg, Rc, Sc};
+
+  // ---- backward pass (Stage 6), level by level from the leaves
   if (MODE == kModeUpdate || MODE == kModeBR) {
-    for (int l = L - 1; l >= 0; --l) {
-      const int a0 = ls[l], cnt = ls[l + 1] - a0;
-      for (int idx = slot; idx < cnt; idx += nslots) {
-        const int n = a0 + idx;
-        const NodeDev nd = nodes[n];
-        if (is_end(nd.type)) continue;
-        const int A = nd.n_kids, k0 = nd.first_kid;
-        V val;
-        if (MODE == kModeBR && nd.type == kDecision && nd.player == p) {
-          val = v[k0];
-          for (int a = 1; a < A; ++a) val = P::vmax(val, v[k0 + a]);
-        } else {
-          typename P::Acc acc = P::acc0();
-          if (nd.type == kChance) {
-            // children values already carry the card probabilities; cards in the hand are out
-            for (int a = 0; a < A; ++a)
-              if (!((hmask >> nodes[k0 + a].deal) & 1ull)) P::acc(acc, v[k0 + a]);
-          } else if (nd.player != p) {
-            for (int a = 0; a < A; ++a) P::acc(acc, v[k0 + a]);
-          } else {
-            const int r0 = nd.row - rb;
-            for (int a = 0; a < A; ++a) P::acc_mul(acc, sg[r0 + a], v[k0 + a]);
-          }
-          val = P::value(acc);
-        }
-        if (wr) v[n] = val;
-      }
-      __syncthreads();
-    }
+    hand_backward<MODE, P>(hv);
     if (sm && valid)
       for (int n = slot; n < N; n += nslots) gv[(size_t)n * stride] = v[n];
   }
@@ -839,79 +953,13 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
     return;
   }
 
-  // ---- positive parts of the strategy source, one (row, hand) item per thread:
-  //      (sign tests of FP64 values read the sign bit on the integer pipe: x > 0 exactly
-  //      when the bits, as a signed integer, are positive)
-  //      update: the Stage 7 update of R and S, then the positive part of the new R;
-  //      init: the positive part of R;  average: S
-  {
-    const Discount d = disc;
-    for (int r = slot; r < nrows; r += nslots) {
-      double x;
-      if (MODE == kModeUpdate) {
-        const int n = rown[r];
-        const NodeDev nd = nodes[n];
-        const V rr = P::sub(v[nd.first_kid + (rb + r - nd.row)], v[n]);  // instantaneous regret
-        const double contrib = P::to_double(P::mul(rch[n], sg[r]));     // pi_i(I) sigma(I, a)
-        const double rd = P::to_double(rr);
-        x = Rc[r] + rd;
-        if (variant == 2) x *= __double_as_longlong(x) > 0 ? d.dpos : d.dneg;
-        if ((variant == 1 || variant == 3) && __double_as_longlong(x) < 0) x = 0.0;  // CFR+, Predictive CFR+
-        const double sn = fma(Sc[r], d.dS, (variant == 1 || variant == 3) ? d.wS * contrib : contrib);
-        if (valid) {
-          gR[(size_t)r * stride] = x;
-          gS[(size_t)r * stride] = sn;
-          if (variant == 3) G.M[(size_t)(rb + r) * stride + h] = rd;  // the prediction of the next regret
-        }
-        if (variant == 3) x += rd;  // Predictive CFR+ matches R + M
-      } else {
-        x = MODE == kModeInit ? Rc[r] : Sc[r];
-        if (MODE == kModeInit && G.M) x += valid ? G.M[(size_t)(rb + r) * stride + h] : 0.0;
-      }
-      if (wr) sg[r] = __double_as_longlong(x) > 0 ? P::of_double(x) : P::zero();
-    }
-  }
-  __syncthreads();
-
+  // ---- positive parts of the strategy source (the update writes R and S to the global rows)
+  hand_rows<MODE, P>(hv, disc, variant, Col<double>{gR, stride}, Col<double>{gS, stride}, valid,
+                     Col<double>{G.M ? G.M + (size_t)rb * stride + h : nullptr, stride});
   // ---- regret matching (Eq. rm) / normalisation of the average, per decision node of p
-  for (int k = slot; k < ndec; k += nslots) {
-    const NodeDev nd = nodes[decs[k]];
-    const int A = nd.n_kids, r0 = nd.row - rb;
-    V tot = P::zero();
-    int npos = 0, last = 0;
-    for (int a = 0; a < A; ++a) {
-      const V x = sg[r0 + a];
-      if (P::positive(x)) ++npos, last = a;
-      tot = P::add(tot, x);
-    }
-    if (!wr) continue;
-    if (npos == 1) {  // x / x = 1 exactly, as the definition gives
-      for (int a = 0; a < A; ++a) sg[r0 + a] = a == last ? P::one() : P::zero();
-    } else if (npos > 1) {
-      const V inv = P::recip(tot);
-      for (int a = 0; a < A; ++a) sg[r0 + a] = P::mul(sg[r0 + a], inv);
-    } else {
-      const V uni = P::uniform(A);
-      for (int a = 0; a < A; ++a) sg[r0 + a] = uni;
-    }
-  }
-  __syncthreads();
-
+  hand_rm<P>(hv);
   // ---- forward reach of player p (Stages 1-2) under the strategy in sg
-  if (slot == 0 && wr) rch[0] = valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero();
-  __syncthreads();
-  for (int l = 1; l < L; ++l) {
-    const int a0 = ls[l], cnt = ls[l + 1] - a0;
-    for (int idx = slot; idx < cnt; idx += nslots) {
-      const int n = a0 + idx;
-      const NodeDev nd = nodes[n];
-      V x = wr ? rch[nd.parent] : P::zero();
-      if (nd.aplayer == p) x = P::mul(x, sg[nd.arow - rb]);
-      if (nd.deal != kNoCard && ((hmask >> nd.deal) & 1ull)) x = P::zero();
-      if (wr) rch[n] = x;
-    }
-    __syncthreads();
-  }
+  hand_forward<P>(hv, valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero());
   if (sm && valid) {
     for (int n = slot; n < N; n += nslots) grch[(size_t)n * stride] = rch[n];
     for (int r = slot; r < nrows; r += nslots) gsg[(size_t)r * stride] = sg[r];
@@ -931,6 +979,261 @@ __global__ void __launch_bounds__(kHandThreads, 1) k_hand(const GameDev* __restr
   }
 }
 
+
+// ------------------------------------------------------------------ resident schedule
+//
+// The latency form of whole iterations, for handles whose hand chunks all fit the GPU at
+// once (a single subgame): one cooperative launch runs n iterations.  Block b owns hand chunk
+// b of both players and keeps its R, S, strategy and reach rows in shared memory for the whole
+// launch, beside the board table of the terminal nodes it evaluates.  An iteration's phases --
+// the terminal values of player i (Stages 2-4), then i's update (Stages 6, 7 and 1) -- each
+// read what the whole grid wrote in the phase before, so a grid barrier separates them.  What
+// crosses blocks (terminal values, reach rows) goes through global memory and is read past L1
+// (ld.global.cg), since another block of the same launch wrote it.  The arithmetic is that of
+// k_terminal and k_hand, and the global state left at the end is theirs: the level and
+// resident schedules give the same bits.
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+template <typename V>
+__device__ __forceinline__ V ld_cg(const V* p);
+template <>
+__device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ ff ld_cg<ff>(const ff* p) {
+  const float2 x = __ldcg(reinterpret_cast<const float2*>(p));
+  return {x.x, x.y};
+}
+
+// Bounded grid barrier: the block's arrival is counted once its writes are visible, then one
+// thread polls until `target` arrivals (a multiple of the grid size) have been counted.  False
+// when the wait gave up, after `limit` polls or because another block gave up: the error flag
+// is then set and the caller leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err, long limit) {
+  __shared__ int s_ok;
+  __syncthreads();  // the block's writes of this phase are done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 1;
+    for (long k = 0; ld_acquire_u32(count) < target; ++k)
+      if (k >= limit || ld_relaxed_s32(err) != 0) {
+        ok = 0;
+        break;
+      }
+    if (!ok) atomicExch(err, 1);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__host__ __device__ inline size_t resident_term_bytes(int H, int k, int deck, int hstride, size_t es) {
+  return (size_t)TermTab(H, k, deck).len * 2 + (size_t)hstride * es + (size_t)(k * H + 1 + H + 1) * 8;
+}
+
+// Shared memory of the resident kernel's hand region for one game (must match k_resident):
+// nodes, level offsets, per player the row -> node map and decision-node list, R, S, then the
+// values (one player at a time), and per player the reach and strategy.
+__host__ __device__ inline size_t resident_hand_bytes(int n_nodes, int n_levels, int rows_max, int W, size_t es) {
+  return round16((size_t)n_nodes * sizeof(NodeDev)) + round16((size_t)(n_levels + 1) * 4) +
+         4 * round16((size_t)rows_max * 4) + 4 * round16((size_t)rows_max * W * 8) +
+         round16((size_t)n_nodes * W * es) + 2 * round16((size_t)n_nodes * W * es) +
+         2 * round16((size_t)rows_max * W * es);
+}
+
+// One terminal node of player i (Stages 2-4) in the resident kernel: the board table stays in
+// shared memory while the nodes the block evaluates read the same one (tab_game / tab_b name
+// it); the opponent's reach row is read past L1.  Ends with a block barrier.
+template <typename P>
+__device__ __forceinline__ void resident_terminal(const GameDev* __restrict__ games, Work e, int src, int i,
+                                                  unsigned char* smr, int& tab_game, int& tab_b) {
+  using V = typename P::V;
+  const GameDev& G = games[e.game];
+  const int n = e.unit;
+  const NodeDev nd = G.nodes[n];
+  const TermTab tt(G.n_hands, G.hand_size, G.deck);
+  const size_t stride = (size_t)G.hstride;
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smr);
+  V* qs = reinterpret_cast<V*>(smr + (size_t)tt.len * 2);
+  ff* CP = reinterpret_cast<ff*>(smr + (size_t)tt.len * 2 + stride * sizeof(V));
+  ff* Psc = CP + (G.hand_size * G.n_hands + 1);
+  // a fold reads table 0, as in k_terminal (each table orders its per-card hand lists by its
+  // own board's ranks, so another table's lists would sum the same reach in another order)
+  const int b = nd.type == kShowdown ? nd.row : 0;
+  if (tab_game != e.game || tab_b != b) {  // len is a multiple of 8 entries: 16-byte pieces
+    const uint4* src4 = reinterpret_cast<const uint4*>(G.term_tab + (size_t)b * tt.len);
+    for (int k = threadIdx.x; k < tt.len / 8; k += blockDim.x) reinterpret_cast<uint4*>(tab)[k] = __ldg(src4 + k);
+    tab_game = e.game;
+    tab_b = b;
+  }
+  {  // the row is a multiple of 128 bytes (hstride is a multiple of 32)
+    const uint4* q4 = reinterpret_cast<const uint4*>(static_cast<const V*>(G.reach) +
+                                                     ((size_t)(1 - i) * G.n_nodes + src) * stride);
+    for (int k = threadIdx.x; k < (int)(stride * sizeof(V) / 16); k += blockDim.x)
+      reinterpret_cast<uint4*>(qs)[k] = __ldcg(q4 + k);
+  }
+  __syncthreads();
+  if (src != n) {  // below an all-in run-out: zero the hands holding a card dealt on the way
+    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
+      if (G.hand_mask[h] & nd.board) qs[h] = P::zero();
+    __syncthreads();
+  }
+  const bool neg = nd.type == kFold && nd.player == i;
+  const ff u = {neg ? -G.payoff_ff[2 * n] : G.payoff_ff[2 * n], neg ? -G.payoff_ff[2 * n + 1] : G.payoff_ff[2 * n + 1]};
+  terminal_values<P>(G, nd, i, u, tt, tab, qs, CP, Psc,
+                     static_cast<V*>(G.cfv) + ((size_t)i * G.n_nodes + n) * stride);
+  __syncthreads();  // the row buffer and the scan arrays are free again
+}
+
+// n_iters iterations (alternating: terminal and update of player 0, then of player 1;
+// otherwise both players' terminals, then both updates).  Launched cooperatively, every block
+// resident: grid >= n_chunk_work.  sync[0] counts barrier arrivals, sync[1] blocks that have
+// finished; the last block to finish resets both and advances *iter by n_iters.
+template <typename P>
+__global__ void __launch_bounds__(kTermThreads, 1) k_resident(
+    const GameDev* __restrict__ games, const Work* __restrict__ chunk_work, int n_chunk_work,
+    const Work* __restrict__ term_work, const int32_t* __restrict__ term_src, int n_term_work, int alternating,
+    int n_iters, int* iter, const Discount* __restrict__ disc_tab, int variant, unsigned* sync, int* err,
+    unsigned term_bytes) {
+  using V = typename P::V;
+  constexpr size_t es = sizeof(V);
+  extern __shared__ __align__(16) unsigned char smr[];
+  const int tid = threadIdx.x;
+  const bool owner = (int)blockIdx.x < n_chunk_work;
+  const Work wk = owner ? chunk_work[blockIdx.x] : Work{0, 0};
+  const GameDev& G = games[wk.game];
+  const int W = G.chunk, w = tid % W, slot = tid / W, nslots = kTermThreads / W;
+  const int h = wk.unit * W + w;  // < hstride
+  const bool valid = owner && h < G.n_hands;
+  const int N = G.n_nodes, L = G.n_levels;
+  const size_t stride = (size_t)G.hstride;
+  const int rows_max = max(G.row_begin[1] - G.row_begin[0], G.row_begin[2] - G.row_begin[1]);
+  const uint64_t hmask = valid ? G.hand_mask[h] : 0ull;
+
+  // hand region (see resident_hand_bytes), after the terminal region
+  unsigned char* cur = smr + term_bytes;
+  NodeDev* snodes = reinterpret_cast<NodeDev*>(cur);
+  cur += round16((size_t)N * sizeof(NodeDev));
+  int* sls = reinterpret_cast<int*>(cur);
+  cur += round16((size_t)(L + 1) * 4);
+  const size_t ri = round16((size_t)rows_max * 4), rd8 = round16((size_t)rows_max * W * 8);
+  int* srow[2] = {reinterpret_cast<int*>(cur), reinterpret_cast<int*>(cur + ri)};
+  cur += 2 * ri;
+  int* sdec[2] = {reinterpret_cast<int*>(cur), reinterpret_cast<int*>(cur + ri)};
+  cur += 2 * ri;
+  double* sR[2] = {reinterpret_cast<double*>(cur), reinterpret_cast<double*>(cur + rd8)};
+  cur += 2 * rd8;
+  double* sS[2] = {reinterpret_cast<double*>(cur), reinterpret_cast<double*>(cur + rd8)};
+  cur += 2 * rd8;
+  const size_t nv = round16((size_t)N * W * es), rv = round16((size_t)rows_max * W * es);
+  V* sv = reinterpret_cast<V*>(cur);
+  cur += nv;
+  V* srch[2] = {reinterpret_cast<V*>(cur), reinterpret_cast<V*>(cur + nv)};
+  cur += 2 * nv;
+  V* ssg[2] = {reinterpret_cast<V*>(cur), reinterpret_cast<V*>(cur + rv)};
+
+  // ---- stage the tree and the chunk's state of both players (written by earlier launches)
+  if (owner) {
+    const int4* gn = reinterpret_cast<const int4*>(G.nodes);
+    for (int k = tid; k < 2 * N; k += kTermThreads) reinterpret_cast<int4*>(snodes)[k] = __ldg(gn + k);
+    for (int k = tid; k <= L; k += kTermThreads) sls[k] = G.level_start[k];
+    for (int p = 0; p < 2; ++p) {
+      const int rb = G.row_begin[p], nrows = G.row_begin[p + 1] - rb;
+      const int db = G.dec_begin[p], ndec = G.dec_begin[p + 1] - db;
+      for (int k = tid; k < nrows; k += kTermThreads) srow[p][k] = G.row_node[rb + k];
+      for (int k = tid; k < ndec; k += kTermThreads) sdec[p][k] = G.dec_nodes[db + k];
+      for (int r = slot; r < nrows; r += nslots) {
+        const size_t g = (size_t)(rb + r) * stride + h;
+        sR[p][r * W + w] = G.R[g];
+        sS[p][r * W + w] = G.S[g];
+        ssg[p][r * W + w] = static_cast<const V*>(G.sigma)[g];
+      }
+      const V* grch = static_cast<const V*>(G.reach) + (size_t)p * N * stride + h;
+      for (int n = slot; n < N; n += nslots) srch[p][n * W + w] = grch[(size_t)n * stride];
+    }
+  }
+  __syncthreads();
+
+  const int it0 = *iter;  // written only by the last block to finish
+  const int steps = alternating ? 2 : 1;
+  unsigned nbar = 0;
+  bool ok = true;
+  int tab_game = -1, tab_b = -1;
+  for (int it = 0; it < n_iters && ok; ++it) {
+    const Discount d = disc_tab[it0 + it];
+    for (int step = 0; step < steps && ok; ++step) {
+      const int pm = alternating ? 1 << step : 3;
+      const int p0 = pm == 2 ? 1 : 0, np = pm == 3 ? 2 : 1;
+      // ---- terminal values of the player(s) of this step (Stages 2-4)
+      for (int item = blockIdx.x; item < np * n_term_work; item += gridDim.x) {
+        const int e = item % n_term_work;
+        resident_terminal<P>(games, term_work[e], term_src[e], p0 + item / n_term_work, smr, tab_game, tab_b);
+      }
+      ++nbar;
+      ok = grid_barrier(&sync[0], nbar * gridDim.x, err, nbar == 1 ? g_first_wait_polls : kWaitLimit);
+      if (!ok) break;
+      // ---- the update of the chunk's hands (Stages 6, 7, then 1 with the new strategy)
+      if (owner) {
+        for (int p = p0; p < p0 + np; ++p) {
+          const int rb = G.row_begin[p], nrows = G.row_begin[p + 1] - rb;
+          const int ndec = G.dec_begin[p + 1] - G.dec_begin[p];
+          V* gv = static_cast<V*>(G.cfv) + (size_t)p * N * stride + h;
+          V* grch = static_cast<V*>(G.reach) + (size_t)p * N * stride + h;
+          const Col<V> v{sv + w, (size_t)W};
+          for (int n = slot; n < N; n += nslots) v[n] = ld_cg(gv + (size_t)n * stride);
+          __syncthreads();
+          const HandView<P> hv{snodes, sls, srow[p], sdec[p], L, ndec, nrows, rb, p, slot, nslots, valid, true, hmask,
+                               v, Col<V>{srch[p] + w, (size_t)W}, Col<V>{ssg[p] + w, (size_t)W},
+                               Col<double>{sR[p] + w, (size_t)W}, Col<double>{sS[p] + w, (size_t)W}};
+          hand_backward<kModeUpdate, P>(hv);
+          if (valid)
+            for (int n = slot; n < N; n += nslots) gv[(size_t)n * stride] = v[n];
+          hand_rows<kModeUpdate, P>(hv, d, variant, hv.Rc, hv.Sc, true,
+                                    Col<double>{G.M ? G.M + (size_t)rb * stride + h : nullptr, stride});
+          hand_rm<P>(hv);
+          hand_forward<P>(hv, valid ? static_cast<const V*>(G.range_v)[(size_t)p * stride + h] : P::zero());
+          if (valid)  // the opponent's terminal values read these rows
+            for (int n = slot; n < N; n += nslots) grch[(size_t)n * stride] = hv.rch[n];
+        }
+      }
+      ++nbar;
+      ok = grid_barrier(&sync[0], nbar * gridDim.x, err, kWaitLimit);
+    }
+  }
+
+  // ---- the chunk's R, S and strategy rows back to global memory
+  if (ok && valid) {
+    for (int p = 0; p < 2; ++p) {
+      const int rb = G.row_begin[p], nrows = G.row_begin[p + 1] - rb;
+      for (int r = slot; r < nrows; r += nslots) {
+        const size_t g = (size_t)(rb + r) * stride + h;
+        G.R[g] = sR[p][r * W + w];
+        G.S[g] = sS[p][r * W + w];
+        static_cast<V*>(G.sigma)[g] = ssg[p][r * W + w];
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&sync[1], 1u) == gridDim.x - 1) {  // every other block has left its waits
+      sync[0] = 0u;
+      sync[1] = 0u;
+      *iter += n_iters;
+      __threadfence();
+    }
+  }
+}
 
 // ------------------------------------------------------------------ stream schedule
 //
@@ -1708,6 +2011,21 @@ size_t hand_smem_size(int n_nodes, int n_levels, int rows_max, int W, size_t es)
   return hand_smem_bytes(n_nodes, n_levels, rows_max, W, es);
 }
 
+size_t resident_term_size(int n_hands, int hand_size, int deck, int hstride, size_t es) {
+  return round16(resident_term_bytes(n_hands, hand_size, deck, hstride, es));
+}
+size_t resident_hand_size(int n_nodes, int n_levels, int rows_max, int W, size_t es) {
+  return resident_hand_bytes(n_nodes, n_levels, rows_max, W, es);
+}
+int resident_blocks_per_sm(int precision, size_t smem) {
+  int n = 0;
+  const cudaError_t e =
+      precision == kPrecisionSingle
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_resident<Single>, kTermThreads, smem)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_resident<Pairs>, kTermThreads, smem);
+  return e == cudaSuccess ? n : 0;
+}
+
 // Every kernel asks for the same shared-memory carveout (the maximum), so the SMs never
 // have to be reconfigured between the terminal and per-hand launches of an iteration.
 template <typename K>
@@ -1738,6 +2056,7 @@ static cudaError_t configure_precision() {
   if (e == cudaSuccess) e = configure_one(k_stream_update<P, 1>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_stream_update<P, 2>, 200 * 1024);
   if (e == cudaSuccess) e = configure_one(k_current_rows<P>, 0);
+  if (e == cudaSuccess) e = configure_one(k_resident<P>, 200 * 1024);
   return e;
 }
 
@@ -1962,6 +2281,35 @@ int launch_terminal(const LaunchCtx& c, int player_mask, int use_bar, void* stre
     return -1;
   }
   return check_launch("k_terminal");
+}
+
+// One cooperative launch: every block is resident at once, which the grid barriers need
+// (the launch fails rather than run a grid that does not fit).
+template <typename P>
+static cudaError_t launch_resident_p(const LaunchCtx& c, int n_iters, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c.resident_grid);
+  cfg.blockDim = dim3(kTermThreads);
+  cfg.dynamicSmemBytes = c.smem_resident;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_resident<P>, c.games, c.chunk_work, c.n_chunk_work, c.term_work,
+                            static_cast<const int32_t*>(c.term_src), c.n_term_work, c.alternating, n_iters, c.iter,
+                            c.disc, c.variant, c.resident_sync, c.err, c.resident_term);
+}
+
+int launch_resident(const LaunchCtx& c, int n_iters, void* stream) {
+  const cudaError_t e = c.precision == kPrecisionSingle ? launch_resident_p<Single>(c, n_iters, stream)
+                                                        : launch_resident_p<Pairs>(c, n_iters, stream);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pcfr: launch of k_resident failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
+  return check_launch("k_resident");
 }
 
 int launch_average_rows(const LaunchCtx& c, void* stream) {

@@ -205,6 +205,13 @@ struct LaunchCtx {
   const int32_t* wide_fwd;     // device: node ids, level by level
   int wide_stride;             // hstride of the game
   int wide_max_dec;            // decision nodes of the player who has more
+  // resident schedule (cfr_iterate only; the other passes use the level schedule's kernels)
+  int resident;                // cfr_iterate runs k_resident
+  int resident_grid;           // blocks of the cooperative launch (>= n_chunk_work)
+  size_t smem_resident;        // its dynamic shared memory: terminal region, then hand region
+  unsigned resident_term;      // bytes of the terminal region
+  unsigned* resident_sync;     // device [2]: barrier arrivals, blocks finished (zero between launches)
+  int alternating;
 };
 
 int launch_init(const LaunchCtx& c, void* stream);
@@ -224,6 +231,12 @@ int configure_kernels();  // once per process, before the first launch
 // Polls of the terminal kernel's first bulk-copy wait on the current device (< 0: the
 // default limit); for tests of the timeout path.  Returns 0 or -1.
 int set_first_wait_polls(long polls);
+// Resident schedule: shared memory of its two regions for one game, the blocks of k_resident
+// one SM holds with `smem` bytes (0 if none), and the cooperative launch of n_iters iterations.
+size_t resident_term_size(int n_hands, int hand_size, int deck, int hstride, size_t es);
+size_t resident_hand_size(int n_nodes, int n_levels, int rows_max, int W, size_t es);
+int resident_blocks_per_sm(int precision, size_t smem);
+int launch_resident(const LaunchCtx& c, int n_iters, void* stream);
 // Dense layer of the leaf network (leafnet.cu): C[M][N] = act(A[M][K] B[N][K]^T + bias), BF16
 // A and B, FP32 accumulation, C in BF16 (out_f32 = 0) or FP32; N a multiple of 128, K of 64.
 // Returns 0, -1 (launch failed), -2 (bad shape or alignment), -3 (no tensor-map encoder).
