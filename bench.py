@@ -62,8 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--iters-per-step", type=int, default=None, help="default 1000 (river) or 500 (batch)")
     ap.add_argument("--precision", choices=["pairs", "single"], default=None,
-                    help="values as FP32 pairs or plain FP32 (R and S are FP64 either way); default pairs for "
-                         "the single river, FP32 for the batch and the depth-limited workloads")
+                    help="values as FP32 pairs or plain FP32 (R and S are FP64 either way); default FP32, "
+                         "the precision the method's values are specified in")
     ap.add_argument("--chunk-hands", type=int, default=0)
     ap.add_argument("--schedule", choices=["auto", "level", "stream", "wide", "resident"], default="auto")
     ap.add_argument("--warp-hands", type=int, choices=[0, 32, 64], default=0,
@@ -411,7 +411,7 @@ def run_ours(args):
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
                           precision=args.precision, schedule=args.schedule, warp_hands=args.warp_hands)
     tuned = None
-    if batch and not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0:
+    if not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0:
         # launch tiling (schedule, hands per block, terminal nodes per block), outside the timed region
         opts, ms_tuned = capi.cfr_autotune(specs, opts, iters=20, stream=stream.cuda_stream)
         tuned = {"schedule": SCHEDULE_NAMES[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
@@ -570,6 +570,8 @@ def run_ours(args):
                        "time_to_1mbb": target}
         else:
             config = {**workload_config(args, specs[0], shapes[0]["nodes"]), "schedule": schedule}
+            if tuned is not None:
+                config["autotune"] = tuned
             quality = {"exploitability_mbb": 1000.0 * float(expl[0]) / BB_CHIPS, "time_to_1mbb": target,
                        "exploitability_pct_pot": 100.0 * float(expl[0]) / specs[0].pot}
         line = {"metric": METRIC, "value": value, "unit": "subgame iter/s" if batch else "iter/s",
@@ -874,7 +876,7 @@ def main(argv=None):
     if args.iters_per_step is None:
         args.iters_per_step = {"batch": 500, "leaf": 300, "flop": 300}.get(args.workload, 1000)
     if args.precision is None:
-        args.precision = "pairs" if args.workload == "river" else "single"
+        args.precision = "single"
     if args.workload in ("leaf", "flop") and args.impl == "ours":
         return run_leaf(args)
     if args.workload == "gemm" and args.impl == "ours":

@@ -240,8 +240,9 @@ int cfr_reset(cfr_tree* tree);
 
 /* Autotuner of the launch tiling (batched serving): builds the subgames under each
  * candidate layout -- the level schedule with 4, 8, 16 and 32 hands per block, the stream
- * schedule (32 hands per warp), the wide schedule (one subgame), then 1, 2, 4 or 8
- * terminal nodes per block for the fastest -- times `iters` iterations of each after two warm-up
+ * schedule (32 and 64 hands per warp), the wide schedule (one subgame), the resident
+ * schedule (where it applies), then 1, 2, 4 or 8 terminal nodes per block for the fastest
+ * unless that is the resident schedule -- times `iters` iterations of each after two warm-up
  * iterations (CUDA events on `stream`, depth-limit leaves evaluated with an all-zero
  * network), and writes the fastest options to *best (opts with schedule, chunk_hands and
  * term_nodes set; term_nodes stays 0 when the automatic count was fastest) and its mean

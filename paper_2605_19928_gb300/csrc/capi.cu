@@ -1309,8 +1309,16 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
     }
     cand.warp_hands = 0;
   }
+  if (!rc) {  // resident schedule: whole iterations in one cooperative launch
+    cand.schedule = CFR_SCHEDULE_RESIDENT;
+    cand.chunk_hands = 0;
+    cand.warp_hands = 0;
+    rc = trial(cand, &ms);
+    if (!rc && ms < top_ms) top_ms = ms, top = cand;
+  }
   cand = top;
   for (int tn : {1, 2, 4, 8}) {  // terminal nodes per block, for the fastest layout
+    if (cand.schedule == CFR_SCHEDULE_RESIDENT) break;  // one node per block item: no runs
     if (rc) break;
     cand.term_nodes = tn;
     rc = trial(cand, &ms);

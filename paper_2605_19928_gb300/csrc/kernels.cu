@@ -1013,16 +1013,18 @@ __device__ __forceinline__ ff ld_cg<ff>(const ff* p) {
   return {x.x, x.y};
 }
 
-// Bounded grid barrier: the block's arrival is counted once its writes are visible, then one
-// thread polls until `target` arrivals (a multiple of the grid size) have been counted.  False
-// when the wait gave up, after `limit` polls or because another block gave up: the error flag
-// is then set and the caller leaves.
+// Bounded grid barrier: after a block barrier, one thread counts the block's arrival with a
+// release reduction (the block's writes of the phase, ordered before it by the block barrier,
+// are visible to whoever acquires the count) and polls with acquire loads until `target`
+// arrivals (a multiple of the grid size) have been counted; the block barrier after it orders
+// the other threads' reads after that acquire.  Those reads of other blocks' data go past L1
+// (ld.global.cg), so no stale line is read.  False when the wait gave up, after `limit` polls
+// or because another block gave up: the error flag is then set and the caller leaves.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err, long limit) {
   __shared__ int s_ok;
   __syncthreads();  // the block's writes of this phase are done
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     int ok = 1;
     for (long k = 0; ld_acquire_u32(count) < target; ++k)
       if (k >= limit || ld_relaxed_s32(err) != 0) {
@@ -1030,7 +1032,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
         break;
       }
     if (!ok) atomicExch(err, 1);
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
