@@ -68,6 +68,8 @@ def parse_args(argv=None):
     ap.add_argument("--schedule", choices=["auto", "level", "stream", "wide", "resident"], default="auto")
     ap.add_argument("--warp-hands", type=int, choices=[0, 32, 64], default=0,
                     help="stream schedule: hands per warp (0 = automatic)")
+    ap.add_argument("--term-nodes", type=int, choices=range(0, 9), default=0,
+                    help="terminal nodes per block of the terminal launch (0 = automatic)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -409,9 +411,11 @@ def run_ours(args):
     specs = workload_specs(args, rank)
     G = len(specs)
     opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, chunk_hands=args.chunk_hands,
-                          precision=args.precision, schedule=args.schedule, warp_hands=args.warp_hands)
+                          precision=args.precision, schedule=args.schedule, warp_hands=args.warp_hands,
+                          term_nodes=args.term_nodes)
     tuned = None
-    if not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0:
+    if (not args.no_autotune and args.schedule == "auto" and args.chunk_hands == 0 and args.warp_hands == 0
+            and args.term_nodes == 0):
         # launch tiling (schedule, hands per block, terminal nodes per block), outside the timed region
         opts, ms_tuned = capi.cfr_autotune(specs, opts, iters=20, stream=stream.cuda_stream)
         tuned = {"schedule": SCHEDULE_NAMES[opts.schedule], "chunk_hands": opts.chunk_hands, "term_nodes": opts.term_nodes,
@@ -470,8 +474,9 @@ def run_ours(args):
     schedule = SCHEDULE_NAMES[capi.cfr_schedule(tree)]
     if schedule == "resident":
         # one launch runs whole iterations: per iteration both players' terminal and update
-        # launches' algorithmic bytes, over the launch's own device time
-        n_res = min(ips, 200)
+        # launches' algorithmic bytes, over the launch's own device time (20 iterations, the
+        # launch the committed ncu summary captures)
+        n_res = min(ips, 20)
         capi.cfr_reset(tree)
         torch.cuda.synchronize(device)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -625,26 +630,31 @@ def node_paths(capi, tree, game: int = 0) -> dict:
 
 
 def gemm_throughput(capi, torch, device, M=16384, reps=20):
-    """TFLOP/s of the leaf network's layer shapes on the tensor cores (inputs in HBM)."""
+    """TFLOP/s of the leaf network's layers on the tensor cores (inputs in HBM), each as the
+    network runs it: the hidden layers with GELU and BF16 output, the output layer linear
+    with FP32 output."""
     out = {}
-    for name, (N, K) in (("layer1", (512, 2752)), ("layer4", (2688, 512))):
+    for name, (N, K, act, dtype) in (("layer1", (512, 2752, True, torch.bfloat16)),
+                                     ("layer2", (512, 512, True, torch.bfloat16)),
+                                     ("layer4", (2688, 512, False, torch.float32))):
         A = torch.randn(M, K, device=device).to(torch.bfloat16)
         B = (torch.randn(N, K, device=device) / K ** 0.5).to(torch.bfloat16)
         bias = torch.zeros(N, device=device)
-        C = torch.empty(M, N, device=device, dtype=torch.bfloat16)
+        C = torch.empty(M, N, device=device, dtype=dtype)
         err = torch.zeros(1, dtype=torch.int32, device=device)
         for _ in range(3):
-            capi.cfr_gemm_bf16(A, B, bias, C, True, err)
+            capi.cfr_gemm_bf16(A, B, bias, C, act, err)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(device)
         s.record()
         for _ in range(reps):
-            capi.cfr_gemm_bf16(A, B, bias, C, True, err)
+            capi.cfr_gemm_bf16(A, B, bias, C, act, err)
         e.record()
         torch.cuda.synchronize(device)
         ms = s.elapsed_time(e) / reps
-        out[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
-                     "wait_errors": int(err.item())}
+        out[name] = {"M": M, "N": N, "K": K, "gelu": act, "out": str(dtype).replace("torch.", ""), "ms": ms,
+                     "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
+                     "out_gbs": M * N * C.element_size() / (ms * 1e-3) / 1e9, "wait_errors": int(err.item())}
     return out
 
 

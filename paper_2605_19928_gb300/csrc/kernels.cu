@@ -698,9 +698,11 @@ __device__ __forceinline__ void hand_backward(const HandView<P>& hv) {
           for (int a = 0; a < A; ++a)
             if (!((hv.hmask >> hv.nodes[k0 + a].deal) & 1ull)) P::acc(acc, hv.v[k0 + a]);
         } else if (nd.player != hv.p) {
+#pragma unroll 4
           for (int a = 0; a < A; ++a) P::acc(acc, hv.v[k0 + a]);
         } else {
           const int r0 = nd.row - hv.rb;
+#pragma unroll 4  // the children's loads go out together; the sum keeps its order
           for (int a = 0; a < A; ++a) P::acc_mul(acc, hv.sg[r0 + a], hv.v[k0 + a]);
         }
         val = P::value(acc);

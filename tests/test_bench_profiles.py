@@ -87,8 +87,10 @@ def test_roofline_numerators_of_the_summaries(oracle_mod):
     from paper_2605_19928_gb300 import synth
     river = _oracle_shape(oracle_mod, bench.workload_spec(0))
     assert river["hands"] == 1081
-    want = _profile_figure("update_river1081.md", r"algorithmic bytes per launch \| ([\d,]+) B")
-    assert bench.algorithmic_bytes(river, "update", 4) == want
+    # the resident launch: 20 iterations of both players' update and terminal launches
+    want = _profile_figure("resident_river1081.md", r"algorithmic bytes per launch \| .*= ([\d,]+) B")
+    per_iter = 2 * (bench.algorithmic_bytes(river, "update", 4) + bench.algorithmic_bytes(river, "terminal", 4))
+    assert 20 * per_iter == want
     batch = [_oracle_shape(oracle_mod, s) for s in synth.batch_rivers(256)]
     total = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch)
     half = sum(bench.algorithmic_bytes(sh, "update", 4) for sh in batch[:128])
