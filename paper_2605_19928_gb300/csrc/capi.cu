@@ -3,11 +3,13 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -166,6 +168,29 @@ struct Packer {
     return CFR_OK;
   }
 };
+
+// Runs f(g) for every game g of a handle on up to one thread per host core: the host-side
+// construction of one subgame (tree, tables, programs) reads only its own spec and writes
+// only its own slot, so the result does not depend on the thread count.  Handles of a few
+// games run on the calling thread.
+template <typename F>
+void parallel_games(int n_games, F f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = n_games < 8 ? 1 : std::min(std::min(n_games, hw), 64);
+  if (nt <= 1) {
+    for (int g = 0; g < n_games; ++g) f(g);
+    return;
+  }
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int g = next.fetch_add(1); g < n_games; g = next.fetch_add(1)) f(g);
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nt - 1);
+  for (int k = 1; k < nt; ++k) pool.emplace_back(work);
+  work();
+  for (std::thread& th : pool) th.join();
+}
 
 template <typename T>
 int zeros(cfr_tree* t, size_t n, T** out) {
@@ -355,13 +380,15 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   t->stream = (cudaStream_t)stream;
   t->stream_arg = stream;
   t->host.resize(n_games);
-  for (int g = 0; g < n_games; ++g) {
-    std::string err;
-    rc = build_game(specs[g], t->host[g], err);
-    if (rc != CFR_OK) {
-      delete t;
-      return fail(rc, "game " + std::to_string(g) + ": " + err);
-    }
+  {
+    std::vector<int> rcs(n_games, CFR_OK);
+    std::vector<std::string> errs(n_games);
+    parallel_games(n_games, [&](int g) { rcs[g] = build_game(specs[g], t->host[g], errs[g]); });
+    for (int g = 0; g < n_games; ++g)  // the first rejected game, as a serial build reports it
+      if (rcs[g] != CFR_OK) {
+        delete t;
+        return fail(rcs[g], "game " + std::to_string(g) + ": " + errs[g]);
+      }
   }
   // Block shape: W hands per block (8 by default).  The per-hand pass stages each chunk's
   // tree and state in shared memory when every game of the handle fits in 96 KB (two blocks
@@ -403,26 +430,31 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   // Update schedule: one warp per 32 hands when the handle has enough of them to fill the
   // GPU (8 warps per SM) and every tree fits the warp's registers and stack.
   std::vector<std::vector<int32_t>> programs(n_games);
+  std::vector<std::array<int, 4>> prog_meta(n_games);  // depth, max actions, fits, max loads of a node
+  parallel_games(n_games, [&](int g) {
+    int depth = 0, amax = 0, loads = 0;
+    bool fits = false;
+    programs[g] = dfs_program(t->host[g], &depth, &amax, &fits);
+    for (int n : programs[g])
+      for (int p = 0; p < 2; ++p)
+        loads = std::max(loads, (int)node_loads(t->host[g], n, p, true, (uint32_t)t->host[g].hstride,
+                                                o.variant == CFR_VARIANT_PCFRPLUS).size());
+    prog_meta[g] = {depth, amax, fits ? 1 : 0, loads};
+  });
   int stream_depth = 1, stream_warps = 0, actions_max = 0;
   bool stream_ok = true;
   for (int g = 0; g < n_games; ++g) {
-    int depth = 0, amax = 0;
-    bool fits = false;
-    programs[g] = dfs_program(t->host[g], &depth, &amax, &fits);
-    stream_ok = stream_ok && fits;
-    stream_depth = std::max(stream_depth, depth);
-    actions_max = std::max(actions_max, amax);
-    stream_ok = stream_ok && amax <= kStreamMaxActions;
+    stream_ok = stream_ok && prog_meta[g][2];
+    stream_depth = std::max(stream_depth, prog_meta[g][0]);
+    actions_max = std::max(actions_max, prog_meta[g][1]);
+    stream_ok = stream_ok && prog_meta[g][1] <= kStreamMaxActions;
     stream_warps += (t->host[g].n_hands + 31) / 32;
   }
   // the program of the largest tree is staged in shared memory when it takes at most 64 KB
   int max_prog = 0, max_loads = 0;
   for (int g = 0; g < n_games; ++g) {
     max_prog = std::max(max_prog, (int)programs[g].size());
-    for (int n : programs[g])
-      for (int p = 0; p < 2; ++p)
-        max_loads = std::max(max_loads, (int)node_loads(t->host[g], n, p, true, (uint32_t)t->host[g].hstride,
-                                                        o.variant == CFR_VARIANT_PCFRPLUS).size());
+    max_loads = std::max(max_loads, prog_meta[g][3]);
   }
   const int stream_prog = max_prog * (int)sizeof(ProgOp) <= 64 * 1024 ? max_prog : 0;
   const int stream_half = std::max(kStreamHalfMin, max_loads);
@@ -431,10 +463,13 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   std::vector<std::vector<int32_t>> chunk_lists(n_games);
   std::vector<std::array<int, 16>> table_meta(n_games);
   int stream_units_max = 0;
-  for (int g = 0; g < n_games; ++g) {
+  parallel_games(n_games, [&](int g) {
     std::array<int, 16>& m = table_meta[g];
     chunk_lists[g] = stream_tables(t->host[g], programs[g], stream_half, o.variant == CFR_VARIANT_PCFRPLUS,
                                    unit_lists[g], &m[0], &m[4], &m[8], &m[12]);
+  });
+  for (int g = 0; g < n_games; ++g) {
+    const std::array<int, 16>& m = table_meta[g];
     for (int p = 0; p < 2; ++p) stream_units_max = std::max(stream_units_max, m[4 + p] + m[4 + 2 + p]);
     const size_t span = std::max(t->host[g].nodes.size(), (size_t)t->host[g].n_rows) * (size_t)t->host[g].hstride;
     stream_ok = stream_ok && span < (1u << kArrShift);
@@ -520,6 +555,36 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   }
 
   std::vector<Work> chunk_work, term_work, warp_work;
+  // each game's device tables, prepared on the host in parallel, then packed in game order
+  struct Prepared {
+    std::vector<double> r64;
+    std::vector<float> rv, pay32;
+    std::vector<uint16_t> tab;
+    std::vector<int32_t> rown, decn;
+    std::vector<ProgOp> ops;
+    int dec_begin[3];
+  };
+  std::vector<Prepared> prep(n_games);
+  parallel_games(n_games, [&](int g) {
+    const HostGame& h = t->host[g];
+    Prepared& q = prep[g];
+    const size_t S = (size_t)h.hstride;
+    q.r64.assign(2 * S, 0.0);
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < h.n_hands; ++k) q.r64[p * S + k] = h.range[p][k];
+    q.rv = to_value_type(q.r64, o.precision);
+    q.tab = pack_term_tables(h);
+    q.rown = row_nodes(h);
+    q.decn = decision_nodes(h, q.dec_begin);
+    const double kappa = 1.0 / h.Z;
+    q.pay32.resize(2 * h.payoff.size());  // (hi, lo) of payoff * kappa per node
+    for (size_t n = 0; n < h.payoff.size(); ++n) {
+      const double x = h.payoff[n] * kappa;
+      q.pay32[2 * n] = (float)x;
+      q.pay32[2 * n + 1] = (float)(x - (double)q.pay32[2 * n]);
+    }
+    q.ops = program_ops(h, programs[g]);
+  });
   Packer packer;
   t->dev.resize(n_games);  // not resized again: the packer holds the addresses of its fields
   for (int g = 0; g < n_games; ++g) {
@@ -541,20 +606,15 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     for (int k = 0; k < 3; ++k) d.row_begin[k] = h.row_begin[k];
     d.n_boards = h.n_boards;
     d.kappa64 = 1.0 / h.Z;
-    std::vector<double> r64(2 * S, 0.0);
-    for (int p = 0; p < 2; ++p)
-      for (int k = 0; k < h.n_hands; ++k) r64[p * S + k] = h.range[p][k];
-    const std::vector<float> rv = to_value_type(r64, o.precision);
-    const std::vector<uint16_t> tab = pack_term_tables(h);
-    const std::vector<int32_t> rown = row_nodes(h);
-    const std::vector<int32_t> decn = decision_nodes(h, d.dec_begin);
-    std::vector<float> pay32(2 * h.payoff.size());  // (hi, lo) of payoff * kappa per node
-    for (size_t n = 0; n < h.payoff.size(); ++n) {
-      const double x = h.payoff[n] * d.kappa64;
-      pay32[2 * n] = (float)x;
-      pay32[2 * n + 1] = (float)(x - (double)pay32[2 * n]);
-    }
-    const std::vector<ProgOp> ops = program_ops(h, programs[g]);
+    const Prepared& q = prep[g];
+    for (int k = 0; k < 3; ++k) d.dec_begin[k] = q.dec_begin[k];
+    const std::vector<double>& r64 = q.r64;
+    const std::vector<float>& rv = q.rv;
+    const std::vector<uint16_t>& tab = q.tab;
+    const std::vector<int32_t>& rown = q.rown;
+    const std::vector<int32_t>& decn = q.decn;
+    const std::vector<float>& pay32 = q.pay32;
+    const std::vector<ProgOp>& ops = q.ops;
     for (int q = 0; q < 4; ++q) {
       d.unit_off[q] = table_meta[g][q];
       d.unit_count[q] = table_meta[g][4 + q];
