@@ -41,10 +41,12 @@ def _check(tree, n_games, pot):
 
 
 @pytest.mark.parametrize("precision,schedule", [("pairs", "level"), ("single", "level"), ("pairs", "stream"),
-                                                ("single", "stream"), ("pairs", "wide"), ("single", "wide")])
+                                                ("single", "stream"), ("pairs", "wide"), ("single", "wide"),
+                                                ("pairs", "resident"), ("single", "resident")])
 def test_noalloc_matches_on_river_two_calls(precision, schedule):
     """Every launch layout leaves the best-response values where the static reduction reads
-    them: the per-hand, stream and wide schedules."""
+    them: the per-hand, stream, wide and resident schedules (the last iterates in one
+    cooperative launch and runs its exploitability pass with the per-hand kernels)."""
     spec = synth.river_subgame(n_hands=1081, seed=0, range_seed=1)
     tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", precision=precision, schedule=schedule))
     try:
