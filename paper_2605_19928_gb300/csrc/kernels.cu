@@ -675,38 +675,43 @@ struct HandView {
   Col<double> Rc, Sc;
 };
 
-// Backward values (Stage 6, Eq. backward), level by level from the leaves; MODE = kModeBR
-// takes the max over p's actions (best response).
+// Value of one inner node from its children's stored values (Stage 6, Eq. backward);
+// MODE = kModeBR takes the max over p's actions (best response).
+template <int MODE, typename P>
+__device__ __forceinline__ typename P::V node_value(const HandView<P>& hv, const NodeDev& nd) {
+  using V = typename P::V;
+  const int A = nd.n_kids, k0 = nd.first_kid;
+  if (MODE == kModeBR && nd.type == kDecision && nd.player == hv.p) {
+    V val = hv.v[k0];
+    for (int a = 1; a < A; ++a) val = P::vmax(val, hv.v[k0 + a]);
+    return val;
+  }
+  typename P::Acc acc = P::acc0();
+  if (nd.type == kChance) {
+    // children values already carry the card probabilities; cards in the hand are out
+    for (int a = 0; a < A; ++a)
+      if (!((hv.hmask >> hv.nodes[k0 + a].deal) & 1ull)) P::acc(acc, hv.v[k0 + a]);
+  } else if (nd.player != hv.p) {
+#pragma unroll 4  // the children's loads go out together; the sum keeps its order
+    for (int a = 0; a < A; ++a) P::acc(acc, hv.v[k0 + a]);
+  } else {
+    const int r0 = nd.row - hv.rb;
+#pragma unroll 4
+    for (int a = 0; a < A; ++a) P::acc_mul(acc, hv.sg[r0 + a], hv.v[k0 + a]);
+  }
+  return P::value(acc);
+}
+
+// Backward values (Stage 6, Eq. backward), level by level from the leaves.
 template <int MODE, typename P>
 __device__ __forceinline__ void hand_backward(const HandView<P>& hv) {
-  using V = typename P::V;
   for (int l = hv.L - 1; l >= 0; --l) {
     const int a0 = hv.ls[l], cnt = hv.ls[l + 1] - a0;
     for (int idx = hv.slot; idx < cnt; idx += hv.nslots) {
       const int n = a0 + idx;
       const NodeDev nd = hv.nodes[n];
       if (is_end(nd.type)) continue;
-      const int A = nd.n_kids, k0 = nd.first_kid;
-      V val;
-      if (MODE == kModeBR && nd.type == kDecision && nd.player == hv.p) {
-        val = hv.v[k0];
-        for (int a = 1; a < A; ++a) val = P::vmax(val, hv.v[k0 + a]);
-      } else {
-        typename P::Acc acc = P::acc0();
-        if (nd.type == kChance) {
-          // children values already carry the card probabilities; cards in the hand are out
-          for (int a = 0; a < A; ++a)
-            if (!((hv.hmask >> hv.nodes[k0 + a].deal) & 1ull)) P::acc(acc, hv.v[k0 + a]);
-        } else if (nd.player != hv.p) {
-#pragma unroll 4
-          for (int a = 0; a < A; ++a) P::acc(acc, hv.v[k0 + a]);
-        } else {
-          const int r0 = nd.row - hv.rb;
-#pragma unroll 4  // the children's loads go out together; the sum keeps its order
-          for (int a = 0; a < A; ++a) P::acc_mul(acc, hv.sg[r0 + a], hv.v[k0 + a]);
-        }
-        val = P::value(acc);
-      }
+      const typename P::V val = node_value<MODE, P>(hv, nd);
       if (hv.wr) hv.v[n] = val;
     }
     __syncthreads();
