@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -133,11 +134,16 @@ int upload(cfr_tree* t, const std::vector<T>& v, T** out) {
 // pointer field is set once the block exists (a handle of many subgames makes a handful of
 // allocations instead of a couple of dozen per subgame).  Buffers start 256-byte aligned.
 struct Packer {
-  std::vector<unsigned char> stage;              // host bytes of the tables
-  size_t zero_bytes = 0;                         // bytes of zeroed state after the tables
-  std::vector<std::pair<size_t, void**>> tabs;   // (offset in the tables, field to set)
-  std::vector<std::pair<size_t, void**>> state;  // (offset in the state, field to set)
+  using Setter = std::function<void(unsigned char*)>;  // sets one typed pointer field
+  std::vector<unsigned char> stage;                    // host bytes of the tables
+  size_t zero_bytes = 0;                               // bytes of zeroed state after the tables
+  std::vector<std::pair<size_t, Setter>> tabs;         // (offset in the tables, field to set)
+  std::vector<std::pair<size_t, Setter>> state;        // (offset in the state, field to set)
   static size_t round(size_t b) { return (b + 255) / 256 * 256; }
+  template <typename F>
+  static Setter setter(F** where) {
+    return [where](unsigned char* p) { *where = reinterpret_cast<F*>(p); };
+  }
   template <typename T, typename F>
   void table(const std::vector<T>& v, F** where) {
     *where = nullptr;
@@ -145,11 +151,11 @@ struct Packer {
     const size_t off = stage.size(), bytes = v.size() * sizeof(T);
     stage.resize(off + round(bytes), 0);
     memcpy(stage.data() + off, v.data(), bytes);
-    tabs.push_back({off, reinterpret_cast<void**>(const_cast<typename std::remove_const<F>::type**>(where))});
+    tabs.push_back({off, setter(where)});
   }
   template <typename F>
   void zeroed(size_t bytes, F** where) {
-    state.push_back({zero_bytes, reinterpret_cast<void**>(where)});
+    state.push_back({zero_bytes, setter(where)});
     zero_bytes += round(std::max<size_t>(bytes, 1));
   }
   // allocate, copy, zero and set the fields
@@ -163,8 +169,8 @@ struct Packer {
       t->h2d_bytes += (int64_t)stage.size();
     }
     if (zero_bytes) CK(cudaMemsetAsync(block + stage.size(), 0, zero_bytes, t->stream));
-    for (auto& f : tabs) *f.second = block + f.first;
-    for (auto& f : state) *f.second = block + stage.size() + f.first;
+    for (auto& f : tabs) f.second(block + f.first);
+    for (auto& f : state) f.second(block + stage.size() + f.first);
     return CFR_OK;
   }
 };

@@ -111,6 +111,14 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {  // round to nearest even
   return (uint16_t)(u >> 16);
 }
 
+// Hint: bring one box of the tensor into L2 (no shared memory, no barrier; a box past the
+// tensor's end is not fetched).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
 // Bulk tensor store shared -> global of one box (the issuing thread's bulk async-group).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
@@ -169,8 +177,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int it = 0;
       for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const int m0 = (tile / n_nt) * kBM, n0 = (tile % n_nt) * bn;
+        const int next = tile + (int)gridDim.x, m0_next = (next / n_nt) * kBM;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % kStages;
+          // the A box a full ring ahead (into the CTA's next tile near the end) goes to L2
+          // now, so that its load, issued when a stage frees up, waits on L2 rather than DRAM
+          if (kb + kStages < kb_count)
+            tma_prefetch_2d(&map_a, (kb + kStages) * kBK, m0);
+          else if (next < n_tiles && kb + kStages - kb_count < kb_count)
+            tma_prefetch_2d(&map_a, (kb + kStages - kb_count) * kBK, m0_next);
           if (!bar_wait(&empty[s], ((uint32_t)(it / kStages) & 1u) ^ 1u)) {
             failed = 1;
             break;
