@@ -199,7 +199,8 @@ int cfr_batch_create(const cfr_game_spec* specs, int n_games, const cfr_solver_o
 
 /* Run n_iters CFR iterations (Section 4.1 pipeline, both players), asynchronously on the
  * handle's stream, in place.  The first call records a CUDA graph of one iteration and
- * later calls replay it. */
+ * later calls replay it (the resident schedule instead runs all n_iters iterations in one
+ * cooperative launch). */
 int cfr_iterate(cfr_tree* tree, int n_iters);
 
 /* Strategy at a decision node: the current one (regret matching of R, Eq. rm) or, with
@@ -209,8 +210,9 @@ int cfr_strategy(cfr_tree* tree, int game, int node, int average, float* out, si
 
 /* Exploitability of the average strategy of every subgame: expl[g] = (BR_0 + BR_1) / 2 in
  * chips, where BR_i is player i's best-response value against the other player's average
- * strategy (root reductions in FP64).  expl: [n_games]; br: [n_games][2] or NULL.
- * Synchronises. */
+ * strategy (root reductions in FP64).  expl: [n_games]; br: [n_games][2] or NULL.  The
+ * first pass on a handle launches its kernels directly; the second records them as a CUDA
+ * graph, which later passes replay (same kernels, same results).  Synchronises. */
 int cfr_exploitability(cfr_tree* tree, double* expl, double* br);
 
 /* The same pass, enqueued without waiting; cfr_exploitability_result() waits for the most

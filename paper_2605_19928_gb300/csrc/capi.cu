@@ -67,6 +67,8 @@ struct cfr_tree {
   cudaStream_t capture = nullptr;
   cudaGraphExec_t iter_graph = nullptr;
   cudaGraphExec_t expl_graph = nullptr;
+  bool expl_once = false;       // one exploitability pass has run without a graph
+  double* d_br_all = nullptr;   // [n_games][2] best-response values, contiguous (one read-back)
   cfr_solver_opts opts{};
   LaunchCtx ctx{};
   int iters_done = 0;
@@ -592,6 +594,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     q.ops = program_ops(h, programs[g]);
   });
   Packer packer;
+  packer.zeroed((size_t)2 * n_games * sizeof(double), &t->d_br_all);
   t->dev.resize(n_games);  // not resized again: the packer holds the addresses of its fields
   for (int g = 0; g < n_games; ++g) {
     const HostGame& h = t->host[g];
@@ -652,7 +655,6 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     packer.zeroed(cells * es, &d.cfv_br);
     if (o.variant == CFR_VARIANT_PCFRPLUS) packer.zeroed(rows * 8, &d.M);
     packer.zeroed((size_t)2 * d.n_chunks * 8, &d.br_partial);
-    packer.zeroed(2 * 8, &d.br_out);
     packer.zeroed(4, &d.br_done);
     for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
 
@@ -666,6 +668,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     delete t;
     return rc;
   }
+  for (int g = 0; g < n_games; ++g) t->dev[g].br_out = t->d_br_all + 2 * g;
   std::vector<int32_t> term_src(term_work.size());
   for (size_t k = 0; k < term_work.size(); ++k)
     term_src[k] = t->host[term_work[k].game].reach_src[(size_t)term_work[k].unit];
@@ -959,22 +962,29 @@ int cfr_strategy(cfr_tree* t, int game, int node, int average, float* out, size_
 
 int cfr_exploitability_async(cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
-  if (!t->expl_graph) {
-    if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
-    cudaGraph_t graph;
-    CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
-    const LaunchCtx& c = t->ctx;
-    const int rc = launch_avg_reach(c, t->capture) || enqueue_leaves(t, 3, 1, t->capture) ||
-                   launch_terminal(c, 3, 1, t->capture) || launch_br(c, t->capture);
-    cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
-    if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&t->expl_graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  const LaunchCtx& c = t->ctx;
+  if (!t->expl_graph && !t->expl_once) {  // a first pass runs without recording a graph
+    if (launch_avg_reach(c, t->stream) || enqueue_leaves(t, 3, 1, t->stream) || launch_terminal(c, 3, 1, t->stream) ||
+        launch_br(c, t->stream))
+      return fail(CFR_ECUDA, "exploitability launch failed");
+    t->expl_once = true;
+  } else {  // later passes replay a graph recorded on the second call
+    if (!t->expl_graph) {
+      if (!t->capture) CK(cudaStreamCreateWithFlags(&t->capture, cudaStreamNonBlocking));
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_avg_reach(c, t->capture) || enqueue_leaves(t, 3, 1, t->capture) ||
+                     launch_terminal(c, 3, 1, t->capture) || launch_br(c, t->capture);
+      cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
+      if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&t->expl_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    CK(cudaGraphLaunch(t->expl_graph, t->stream));
   }
   t->avg_gen = -1;  // the pass rewrites sigbar with its own normalisation
-  CK(cudaGraphLaunch(t->expl_graph, t->stream));
   t->launches += (t->ctx.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) +
                  pass_launches(t, kModeBR, 3, 0) + leaf_launches(t, 3);
   return CFR_OK;
@@ -985,8 +995,7 @@ int cfr_exploitability_result(cfr_tree* t, double* expl, double* br) {
   if (!expl) return fail(CFR_EINVAL, "expl is NULL");
   const int G = (int)t->host.size();
   std::vector<double> vals(2 * G);
-  for (int g = 0; g < G; ++g)
-    CK(cudaMemcpyAsync(&vals[2 * g], t->dev[g].br_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, t->stream));
+  CK(cudaMemcpyAsync(vals.data(), t->d_br_all, 2 * G * sizeof(double), cudaMemcpyDeviceToHost, t->stream));
   CK(cudaStreamSynchronize(t->stream));
   const int frc = check_device_flag(t);
   if (frc) return frc;
@@ -1406,7 +1415,7 @@ const char* cfr_last_error(void) { return g_last_error.c_str(); }
 // ---------------------------------------------------------------------------------------
 // Exploitability without allocation.
 //
-// cfr_exploitability records and instantiates a CUDA graph on its first call and keeps
+// cfr_exploitability records and instantiates a CUDA graph on its second call and keeps
 // its per-block best-response sums in buffers of the handle.  Some callers cannot let a
 // call allocate: a serving loop that runs under a fixed device-memory budget, or a
 // real-time thread that must not wait in an allocator between two decisions (freeing
