@@ -218,9 +218,22 @@ size_t hand_smem(const HostGame& g, int W, size_t es) {
 // Update weights of iterations 1 .. capacity (Stage 7; CFR+ and DCFR from Section 2):
 // DCFR multiplies positive regrets by t^a / (t^a + 1), the others by t^b / (t^b + 1) and
 // the average by (t / (t + 1))^g; CFR+ weighs the new average contribution by t.
+// The first `capacity` entries of a variant's discount table.  Entry k depends only on the
+// options and k, so the entries are computed once per process for each set of options (three
+// pow calls per DCFR entry) and cut to the length asked for.
 std::vector<Discount> discount_table(const cfr_solver_opts& o, int capacity) {
-  std::vector<Discount> d((size_t)capacity);
-  for (int k = 0; k < capacity; ++k) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::array<double, 4>, std::vector<Discount>>> cache;
+  const std::array<double, 4> key{(double)o.variant, o.alpha, o.beta, o.gamma};
+  std::lock_guard<std::mutex> lock(mu);
+  std::vector<Discount>* d = nullptr;
+  for (auto& e : cache)
+    if (e.first == key) d = &e.second;
+  if (!d) {
+    cache.push_back({key, {}});
+    d = &cache.back().second;
+  }
+  for (int k = (int)d->size(); k < capacity; ++k) {
     const double t = (double)(k + 1);
     Discount x{1.0, 1.0, 1.0, 1.0};
     if (o.variant == CFR_VARIANT_DCFR) {
@@ -233,9 +246,9 @@ std::vector<Discount> discount_table(const cfr_solver_opts& o, int capacity) {
     } else if (o.variant == CFR_VARIANT_PCFRPLUS) {
       x.wS = t * t;  // quadratic averaging
     }
-    d[(size_t)k] = x;
+    d->push_back(x);
   }
-  return d;
+  return std::vector<Discount>(d->begin(), d->begin() + capacity);
 }
 
 // Host copy of a per-hand vector in the value type: one float, or a (hi, lo) float pair.
@@ -253,16 +266,16 @@ std::vector<float> to_value_type(const std::vector<double>& x, int precision) {
   return out;
 }
 
-int check_device() {
-  int dev = 0;
+int check_device() {  // two attribute queries: cudaGetDeviceProperties takes milliseconds
+  int dev = 0, major = 0, minor = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
-  cudaDeviceProp prop;
-  e = cudaGetDeviceProperties(&prop, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
-  if (prop.major != 10 || prop.minor != 3)
+  e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (major != 10 || minor != 3)
     return fail(CFR_ECUDA, "libpcfr needs a compute capability 10.3 (GB300) device, found " +
-                               std::to_string(prop.major) + "." + std::to_string(prop.minor));
+                               std::to_string(major) + "." + std::to_string(minor));
   return CFR_OK;
 }
 

@@ -42,7 +42,8 @@ constexpr int kMaxDeck = 52;
 constexpr uint8_t kNoCard = 255;
 constexpr int kPrecisionPairs = 0;   // values as double-float FP32 pairs
 constexpr int kPrecisionSingle = 1;  // values as FP32
-constexpr int kDiscountCapacity = 1 << 16;  // iterations covered by one discount table
+constexpr int kDiscountCapacity = 1 << 11;  // iterations a new handle's discount table covers
+                                            // (doubled on demand)
 // Passes of the per-hand kernel (and of the wide schedule).
 enum HandMode { kModeInit = 0, kModeUpdate = 1, kModeAvg = 2, kModeBR = 3 };
 
@@ -178,7 +179,7 @@ struct LaunchCtx {
   int* iter;                   // device: iterations completed
   unsigned* done;              // device: block arrival counter
   int* err;                    // device: nonzero after a bounded wait gave up
-  const Discount* disc;        // device [kDiscountCapacity]
+  const Discount* disc;        // device [iterations covered], one entry per iteration
   size_t smem_hand;            // dynamic shared memory of the per-hand kernel; 0 = every game
                                // works on the global arrays (some tree is too large to stage)
   size_t smem_term;            // dynamic shared memory of the terminal kernel
