@@ -387,25 +387,28 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
   const uint16_t* perm = tab + tt.perm;
   if constexpr (std::is_same<P, Single>::value) {
     if (!show) {
-      // fold (FP32 values): no prefix sums needed -- T is the block's sum of q (each thread
-      // a strided run, then a fixed-order tree), C[c] the sum along card c's list (one warp
-      // per card, lane-strided, xor-shuffle tree)
-      __shared__ float Cs[52];
-      __shared__ float redt[kTermThreads / 32];
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      float t = 0.f;
-      for (int h = threadIdx.x; h < H; h += kTermThreads) t = __fadd_rn(t, qs[h]);
-      for (int o = 16; o > 0; o >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
-      if (lane == 0) redt[warp] = t;
-      for (int c = warp; c < G.deck; c += kTermThreads / 32) {
+      // fold (FP32 values): no prefix sums needed.  T: warp 0 keeps 32 lane-strided partial
+      // sums of q and combines them by a fixed xor tree (lane 0's result); C[c]: one thread
+      // per card sums card c's list in list order.  Few warps work and the others wait at
+      // one barrier, which the other blocks on the SM fill.
+      __shared__ float Cs[kMaxDeck];
+      __shared__ float Tsh;
+      const int lane = threadIdx.x & 31;
+      if (threadIdx.x < 32) {
+        float t = 0.f;
+#pragma unroll 8
+        for (int h = lane; h < H; h += 32) t = __fadd_rn(t, qs[h]);
+        for (int o = 16; o > 0; o >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0) Tsh = t;
+      } else if (threadIdx.x - 32 < G.deck) {
+        const int c = threadIdx.x - 32;
         float x = 0.f;
-        for (int j = cloff[c] + lane; j < cloff[c + 1]; j += 32) x = __fadd_rn(x, qs[clh[j]]);
-        for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if (lane == 0) Cs[c] = x;
+#pragma unroll 4
+        for (int j = cloff[c]; j < cloff[c + 1]; ++j) x = __fadd_rn(x, qs[clh[j]]);
+        Cs[c] = x;
       }
       __syncthreads();
-      float T = 0.f;
-      for (int w = 0; w < kTermThreads / 32; ++w) T = __fadd_rn(T, redt[w]);
+      const float T = Tsh;
       for (int h = threadIdx.x; h < H; h += kTermThreads) {
         const unsigned cw = cards[h];
         const unsigned c1 = cw & 0xffu, c2 = cw >> 8;
@@ -417,7 +420,7 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
         }
         out[h] = blocked ? 0.f : __fmul_rn(uf, m);
       }
-      __syncthreads();  // Cs and redt are reused by the next node
+      __syncthreads();  // Cs and Tsh are reused by the next node
       return;
     }
     // FP32 values: the same scans and differences in plain FP32 (a value's error stays
