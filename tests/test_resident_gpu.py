@@ -155,3 +155,46 @@ def test_resident_barrier_timeout_reports_etimeout_and_the_context_survives():
         assert np.all(np.isfinite(expl)) and np.all(expl > 0)
     finally:
         capi.cfr_tree_destroy(ok)
+
+
+def test_discount_table_grows_past_its_first_capacity():
+    """A handle's discount table covers 2048 iterations and doubles on demand (the iteration
+    graph is recorded again, the resident launch reads the new table): 2100 iterations, in
+    one call and in calls that cross the boundary, give the same bits on both schedules."""
+    spec = river(64, seed=71)
+    out = []
+    for schedule, splits in (("level", [2100]), ("level", [2000, 100]), ("resident", [1500, 600]),
+                             ("resident", [2100])):
+        tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr", schedule=schedule))
+        try:
+            for k in splits:
+                capi.cfr_iterate(tree, k)
+            out.append((_state(tree, 1), capi.cfr_exploitability(tree)))
+        finally:
+            capi.cfr_tree_destroy(tree)
+    for state, expl in out[1:]:
+        for a, b in zip(out[0][0], state):
+            assert np.array_equal(a, b)
+        assert np.array_equal(out[0][1][0], expl[0])
+
+
+def test_autotune_picks_the_resident_layout_for_one_river():
+    """The autotuner times every layout of the 1081-hand river; whichever wins, the tuned
+    handle's state equals the default one's (the bench's river runs the tuned layout)."""
+    spec = synth.river_subgame(seed=0, range_seed=1)
+    base = capi.make_opts("dcfr", precision="single")
+    best, ms = capi.cfr_autotune([spec], base, iters=20)
+    assert ms > 0
+    assert best.schedule in (capi.CFR_SCHEDULE_LEVEL, capi.CFR_SCHEDULE_STREAM, capi.CFR_SCHEDULE_WIDE,
+                             capi.CFR_SCHEDULE_RESIDENT)
+    print("autotuned river layout:", best.schedule, best.chunk_hands, best.term_nodes, ms)
+    states = []
+    for o in (base, best):
+        tree = capi.cfr_tree_create(spec, o)
+        try:
+            capi.cfr_iterate(tree, 5)
+            states.append(_state(tree, 1))
+        finally:
+            capi.cfr_tree_destroy(tree)
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
