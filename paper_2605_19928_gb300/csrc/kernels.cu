@@ -358,6 +358,12 @@ __device__ long g_first_wait_polls = kWaitLimit;
 
 // ------------------------------------------------------------------ terminal values (Stages 2-4)
 
+// Whether hand h (its cards from the staged table: c1 | c2 << 8) holds a card of `board`.
+__device__ __forceinline__ bool holds_board_card(const uint16_t* cards, int h, int k, uint64_t board) {
+  const unsigned cw = cards[h];
+  return (((board >> (cw & 0xffu)) | (k == 2 ? board >> (cw >> 8) : 0ull)) & 1ull) != 0;
+}
+
 // Values of player i at one fold or showdown node n (Stages 2-4), the opponent's reach q
 // at n already in shared memory.  kappa = 1/Z, and the node's payoff already carries the
 // probability of the public cards dealt on its path, so every value is a counterfactual
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kTermThreads, RUNS ? 4 : 1) k_terminal(const G
     if (src[first + j] != n) {  // below an all-in run-out: the run-out's reach, without the
       V* qb = qbuf + (size_t)(j & 1) * stride;  // hands holding a card dealt on the way
       for (int h = threadIdx.x; h < H; h += blockDim.x)
-        if (G.hand_mask[h] & nd.board) qb[h] = P::zero();
+        if (holds_board_card(tab + tt.cards, h, k, nd.board)) qb[h] = P::zero();
       __syncthreads();
     }
     terminal_values<P>(G, nd, i, u, tt, tab, qbuf + (size_t)(j & 1) * stride, CP, Psc, dst + (size_t)n * stride);
@@ -1096,7 +1102,7 @@ __device__ __forceinline__ void resident_terminal(const GameDev* __restrict__ ga
   __syncthreads();
   if (src != n) {  // below an all-in run-out: zero the hands holding a card dealt on the way
     for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
-      if (G.hand_mask[h] & nd.board) qs[h] = P::zero();
+      if (holds_board_card(tab + tt.cards, h, G.hand_size, nd.board)) qs[h] = P::zero();
     __syncthreads();
   }
   const bool neg = nd.type == kFold && nd.player == i;
