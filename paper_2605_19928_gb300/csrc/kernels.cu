@@ -280,9 +280,10 @@ __device__ __forceinline__ float group_exclusive_scan_f32(int n, F value_at, flo
   }
   __syncthreads();
   if (warp > 0) run = __fadd_rn(run, red[warp - 1]);
-  for (int j = begin; j < end; ++j) {
+  for (int j = begin; j < end; ++j) {  // value read before out[j] is written: out may be the input
+    const float v = value_at(j);
     out[j] = run;
-    run = __fadd_rn(run, value_at(j));
+    run = __fadd_rn(run, v);
   }
   const float total = red[GT / 32 - 1];
   if (gtid == 0) out[n] = total;
@@ -435,13 +436,19 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
     __shared__ float cps[kMaxDeck], cpe[kMaxDeck];  // prefix at the start / end of each card's list
     float* CPf = reinterpret_cast<float*>(CP);  // [k H + 1]
     float* Pf = CPf + (k * H + 1);             // [H + 1]
-    {  // two-card hands' card lists hold 2 H entries, so 11 warps scan them and 5 the H
-       // rank-ordered entries (about 7 entries per thread on both sides)
+    {  // the reach in rank order and along the card lists, gathered once into the scans'
+       // output arrays (lanes on consecutive entries), then scanned in place, each thread
+       // over a contiguous run: the same sums as scanning the gathers directly, with half
+       // the random shared-memory reads.  Two-card hands' card lists hold 2 H entries, so 11
+       // warps scan them and 5 the H rank-ordered entries (about 7 per thread on both sides).
+      for (int j = threadIdx.x; j < H; j += kTermThreads) Pf[j] = qs[show ? perm[j] : j];
+      for (int j = threadIdx.x; j < k * H; j += kTermThreads) CPf[j] = qs[clh[j]];
+      __syncthreads();
       constexpr int gp = 5 * 32;
       if (threadIdx.x < gp)
-        group_exclusive_scan_f32<gp>(H, [&](int j) { return qs[show ? perm[j] : j]; }, Pf, redf[0], threadIdx.x);
+        group_exclusive_scan_f32<gp>(H, [&](int j) { return Pf[j]; }, Pf, redf[0], threadIdx.x);
       else
-        group_exclusive_scan_f32<kTermThreads - gp>(k * H, [&](int j) { return qs[clh[j]]; }, CPf, redf[1],
+        group_exclusive_scan_f32<kTermThreads - gp>(k * H, [&](int j) { return CPf[j]; }, CPf, redf[1],
                                                      threadIdx.x - gp);
     }
     for (int c = threadIdx.x; c < G.deck; c += kTermThreads) {
