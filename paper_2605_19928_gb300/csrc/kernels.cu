@@ -240,9 +240,10 @@ __device__ __forceinline__ ff group_exclusive_scan(int n, F value_at, ff* out, a
   }
   __syncthreads();
   if (warp > 0) acc_merge(run, red[warp - 1]);
-  for (int j = begin; j < end; ++j) {
+  for (int j = begin; j < end; ++j) {  // value read before out[j] is written: out may be the input
+    const ff v = value_at(j);
     out[j] = acc_value(run);
-    acc_add(run, value_at(j));
+    acc_add(run, v);
   }
   const ff total = acc_value(red[GT / 32 - 1]);
   if (gtid == 0) out[n] = total;
@@ -502,15 +503,17 @@ __device__ __forceinline__ void terminal_values(const GameDev& G, const NodeDev&
   // Two scans at once, one per half of the block: the first half takes the reach in
   // rank-sorted order (showdown) or in hand order (fold, for the total T), the second half
   // the reach along the per-card hand lists.
-  {
+  {  // each scan's values gathered once into its output array, then scanned in place
+    for (int j = threadIdx.x; j < H; j += kTermThreads) Psc[j] = P::to_ff(qs[show ? perm[j] : j]);
+    for (int j = threadIdx.x; j < k * H; j += kTermThreads) CP[j] = P::to_ff(qs[clh[j]]);
+    __syncthreads();
     constexpr int half = kTermThreads / 2;
     const bool first = threadIdx.x < half;
     const int gtid = first ? threadIdx.x : threadIdx.x - half;
     if (first)
-      group_exclusive_scan<half>(
-          H, [&](int j) { return P::to_ff(qs[show ? perm[j] : j]); }, Psc, red[0], gtid);
+      group_exclusive_scan<half>(H, [&](int j) { return Psc[j]; }, Psc, red[0], gtid);
     else
-      group_exclusive_scan<half>(k * H, [&](int j) { return P::to_ff(qs[clh[j]]); }, CP, red[1], gtid);
+      group_exclusive_scan<half>(k * H, [&](int j) { return CP[j]; }, CP, red[1], gtid);
   }
   const ff T = Psc[H];
 
