@@ -327,6 +327,21 @@ def test_invalid_specs_are_rejected():
         capi.cfr_tree_create(spec)
 
 
+def test_batch_reports_the_first_rejected_subgame():
+    """Batches of eight or more subgames are built on several host threads; a rejected spec is
+    still reported by its index, and the lowest one when several are bad."""
+    specs = [river(30, seed=40 + k) for k in range(12)]
+    specs[9].ranges[1, :] = 0.0
+    specs[6].hands[0, 0] = specs[6].board[0]
+    with pytest.raises(capi.CfrError) as e:
+        capi.cfr_batch_create(specs)
+    assert e.value.code == capi.CFR_EINVAL
+    assert "game 6:" in str(e.value), str(e.value)
+    good = [river(30, seed=40 + k) for k in range(12)]
+    tree = capi.cfr_batch_create(good)
+    capi.cfr_tree_destroy(tree)
+
+
 # ---------------------------------------------------------------- stream schedule
 # The one-warp-per-32-hands update (chosen automatically for large batches) must agree with
 # the oracle exactly like the level schedule, and with the level schedule bit for bit.
