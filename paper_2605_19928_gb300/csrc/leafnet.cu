@@ -456,110 +456,289 @@ __device__ __forceinline__ int pair_slot(int a, int b) {
   return b * (b - 1) / 2 + a;
 }
 
-// One block per network row (leaf, river card): writes the row of X.
+// Per input column of a leaf's rows, what the column depends on: the reach of the hand it
+// holds (player p = column / kLeafSlots) and that hand's two cards.
+constexpr int kLeafChunks = kLeafIn / 8;                 // 16-byte chunks of a row of X (344)
+constexpr int kLeafHandChunks = 2 * kLeafSlots / 8;      // chunks of player columns only (331)
+constexpr int kLeafInThreads = 352;                      // one thread per chunk (11 warps)
+constexpr int kLeafInWarps = kLeafInThreads / 32;
+constexpr int kStageCols = (kLeafIn + kLeafInThreads - 1) / kLeafInThreads;  // columns per thread
+constexpr uint16_t kNoHand = 0xffffu;                    // no hand, or one holding a board card
+static_assert((2 * kLeafSlots + 52) % 8 == 0, "the two features open a 16-byte chunk");
+
+// The k-th card not on a leaf's board (its board holds 4 cards; c stays a card regardless).
+__device__ __forceinline__ int river_card(uint64_t board, int k) {
+  int c = 0;
+  for (int n = -1; c < 51; ++c)
+    if (!((board >> c) & 1ull) && ++n == k) break;
+  return c;
+}
+
+// Two floats to BF16 (round to nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+__device__ __forceinline__ float warp_sum_f32(float x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ int warp_sum_i32(int x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block (leaf, part): rows [part R, part R + R) of the leaf's kLeafCards rows of X, R =
+// kLeafCards / gridDim.y, one contiguous span written in 16-byte chunks (thread j writes chunk
+// j of every row).  For river card r the inputs of player p are p's reach over the hands
+// holding neither a board card nor r, divided by their sum; a player with no such hand of
+// positive reach gets the uniform range over them (its values are then unused).  The sum is
+// the total of p's reach over the hands live on the board less the sum over the (at most 51)
+// of them holding r, both in FP32 in a fixed order: the total is at most 24 roundings deep
+// (8 terms a thread, 5 tree levels, 11 warps) and the held sum 7, so the difference is within
+// 2e-6 of the total.  Where the difference is below 2e-3 of the total (more than 99.8 % of
+// the reach on hands holding r) that bound is no longer 1e-3 of the result, and the sum is
+// taken directly over the hands instead.  The rows are written without regard to r, then the columns of the
+// hands holding r are cleared in each row.
 template <typename V>
-__global__ void __launch_bounds__(kLeafThreads) k_leaf_inputs(const GameDev* __restrict__ games, LeafCtx L,
-                                                              int use_bar) {
-  __shared__ float red[kLeafThreads / 32];
-  const int row = blockIdx.x;
-  const int li = row / kLeafCards, ri = row - li * kLeafCards;
-  const LeafDev lf = L.leaves[li];
+__global__ void __launch_bounds__(kLeafInThreads) k_leaf_inputs(const GameDev* __restrict__ games, LeafCtx L,
+                                                                int use_bar) {
+  __shared__ __align__(16) float qc[kLeafIn];       // reach of each column's live hand (0: none)
+  __shared__ __align__(16) uint16_t cc[kLeafIn];    // its cards c1 | c2 << 8, or kNoHand
+  __shared__ int16_t col_of[kLeafSlots];            // column of the hand in each slot, or -1
+  __shared__ float mul[2][kLeafCards], add[2][kLeafCards];
+  __shared__ int rc[kLeafCards];                    // this block's river cards, ascending
+  __shared__ int slow_row[kLeafCards];              // a player of the row takes the uniform range
+  __shared__ float tot_w[2][kLeafInWarps];
+  __shared__ int cnt_w[3][kLeafInWarps];
+  const LeafDev lf = L.leaves[blockIdx.x];
   const GameDev& G = games[lf.game];
   const NodeDev nd = G.nodes[lf.node];
-  // the ri-th card not on the board
-  int r = -1;
-  for (int c = 0, k = 0; c < 52; ++c)
-    if (!((nd.board >> c) & 1ull)) {
-      if (k == ri) {
-        r = c;
-        break;
-      }
-      ++k;
-    }
+  const int R = kLeafCards / gridDim.y, k0 = blockIdx.y * R;
+  const int nh = G.n_hands < kLeafSlots ? G.n_hands : kLeafSlots;
   const size_t stride = (size_t)G.hstride;
   const V* reach = static_cast<const V*>(use_bar ? G.reach_bar : G.reach);
-  const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
-  uint16_t* x = static_cast<uint16_t*>(L.X) + (size_t)row * kLeafIn;
-  for (int k = threadIdx.x; k < kLeafIn; k += blockDim.x) x[k] = 0;
-  // live hands hold neither a card of the leaf's board (the flop's turn card) nor r
-  const uint64_t dead = nd.board | (1ull << r);
-  float sum[2], cnt = 0.f;
-  for (int p = 0; p < 2; ++p) {
-    const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
-    float s = 0.f, n = 0.f;
-    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
-      if (!(G.hand_mask[h] & dead)) s += vf(q[h]), n += 1.f;
-    sum[p] = block_sum(s, red);
-    if (p == 0) cnt = block_sum(n, red);
+  const int16_t* hand_at = L.hand_at + (size_t)lf.game * kLeafSlots;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // stage the columns: three rounds of independent loads (slot table, hand masks, reach)
+  {
+    int hs[kStageCols], h[kStageCols];
+    uint64_t m[kStageCols];
+#pragma unroll
+    for (int u = 0; u < kStageCols; ++u) {
+      const int col = threadIdx.x + u * kLeafInThreads;
+      const int p = col >= kLeafSlots, s = col - p * kLeafSlots;
+      hs[u] = col < 2 * kLeafSlots && (p == 0 || !L.hand_order) ? hand_at[s] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kStageCols; ++u) {
+      const int col = threadIdx.x + u * kLeafInThreads;
+      const int p = col >= kLeafSlots, s = col - p * kLeafSlots;
+      h[u] = col >= 2 * kLeafSlots ? -1 : L.hand_order ? (s < nh ? s : -1) : hs[u];
+      m[u] = h[u] >= 0 ? G.hand_mask[h[u]] : 0ull;
+      if (col < kLeafSlots) col_of[s] = (int16_t)(hs[u] < 0 ? -1 : (L.hand_order ? hs[u] : s));
+    }
+    float t0 = 0.f, t1 = 0.f;
+    int n = 0, pos0 = 0, pos1 = 0;
+#pragma unroll
+    for (int u = 0; u < kStageCols; ++u) {
+      const int col = threadIdx.x + u * kLeafInThreads;
+      if (col >= kLeafIn) break;
+      const int p = col >= kLeafSlots;
+      const bool live = h[u] >= 0 && !(m[u] & nd.board);
+      const float q = live ? vf(reach[((size_t)p * G.n_nodes + lf.node) * stride + h[u]]) : 0.f;
+      qc[col] = q;
+      cc[col] = live ? (uint16_t)((__ffsll((long long)m[u]) - 1) | ((63 - __clzll((long long)m[u])) << 8)) : kNoHand;
+      if (p == 0) t0 += q, n += live, pos0 += q > 0.f;
+      else t1 += q, pos1 += q > 0.f;
+    }
+    t0 = warp_sum_f32(t0);
+    t1 = warp_sum_f32(t1);
+    n = warp_sum_i32(n);
+    pos0 = warp_sum_i32(pos0);
+    pos1 = warp_sum_i32(pos1);
+    if (lane == 0) {
+      tot_w[0][warp] = t0;
+      tot_w[1][warp] = t1;
+      cnt_w[0][warp] = n;
+      cnt_w[1][warp] = pos0;
+      cnt_w[2][warp] = pos1;
+    }
   }
-  __syncthreads();  // the zero fill is complete
-  for (int p = 0; p < 2; ++p) {
-    const V* q = reach + ((size_t)p * G.n_nodes + lf.node) * stride;
-    // a player who never reaches the leaf: uniform over the hands (the values are then unused)
-    const float inv = sum[p] > 0.f ? 1.f / sum[p] : 0.f;
-    for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x)
-      if (!(G.hand_mask[h] & dead)) {
-        const float v = sum[p] > 0.f ? vf(q[h]) * inv : 1.f / cnt;
-        x[p * kLeafSlots + (L.hand_order ? h : slot[h])] = to_bf16(v);
+  if ((int)threadIdx.x < R) {
+    rc[threadIdx.x] = river_card(nd.board, k0 + threadIdx.x);
+    slow_row[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  // per (player, river card): the sum over the hands holding r, one warp each
+  for (int item = warp; item < 2 * R; item += kLeafInWarps) {
+    const int p = item / R, k = item - p * R, r = rc[k];
+    float c = 0.f;
+    int nr = 0, posr = 0;
+    for (int x = lane; x < 52; x += 32) {
+      const int col = x == r ? -1 : col_of[pair_slot(r, x)];
+      if (col >= 0) {
+        const float q = qc[p * kLeafSlots + col];
+        c += q;
+        nr += cc[p * kLeafSlots + col] != kNoHand;
+        posr += q > 0.f;
       }
+    }
+    c = warp_sum_f32(c);
+    nr = warp_sum_i32(nr);
+    posr = warp_sum_i32(posr);
+    float tot = 0.f;
+    int n = 0, pos = 0;
+    for (int w = 0; w < kLeafInWarps; ++w) tot += tot_w[p][w], n += cnt_w[0][w], pos += cnt_w[1 + p][w];
+    const int live = n - nr;  // hands holding neither a board card nor r
+    float s = 0.f;
+    if (pos - posr > 0) {
+      const float d = tot - c;
+      if (d > 2e-3f * tot) {
+        s = d;
+      } else {  // most of the reach on hands holding r: sum directly
+        float a = 0.f;
+        for (int j = lane; j < kLeafSlots; j += 32) {
+          const uint32_t cards = cc[p * kLeafSlots + j];
+          if (cards != kNoHand && (cards & 0xffu) != (uint32_t)r && (cards >> 8) != (uint32_t)r)
+            a += qc[p * kLeafSlots + j];
+        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        s = a;
+      }
+    }
+    if (lane == 0) {  // input = q mul + add
+      // (finite, so that a column with no hand, q = 0, stays 0 when the sum is subnormal)
+      mul[p][k] = s > 0.f ? fminf(1.f / s, 3.402823466e38f) : 0.f;
+      add[p][k] = s > 0.f || live == 0 ? 0.f : 1.f / (float)live;
+      if (!(s > 0.f)) slow_row[k] = 1;
+    }
   }
-  if (threadIdx.x < 52) {
-    const bool on = ((nd.board >> threadIdx.x) & 1ull) || (int)threadIdx.x == r;
-    if (on) x[2 * kLeafSlots + threadIdx.x] = 0x3f80;  // 1.0
+  __syncthreads();
+  uint16_t* Xb = static_cast<uint16_t*>(L.X) + (size_t)(lf.row0 + k0) * kLeafIn;
+  const int j = threadIdx.x;
+  if (j < kLeafChunks) {
+    float q[8];
+    uint32_t dead = 0, p1 = 0, board_on = 0;  // per column: no live hand; player 1; board card
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int col = 8 * j + e;
+      q[e] = qc[col];
+      dead |= (cc[col] == kNoHand ? 1u : 0u) << e;
+      p1 |= (col >= kLeafSlots ? 1u : 0u) << e;
+      const int c = col - 2 * kLeafSlots;
+      board_on |= (c >= 0 && c < 52 && ((nd.board >> c) & 1ull) ? 1u : 0u) << e;
+    }
+    const int p = 8 * j >= kLeafSlots;
+    const bool one_player = j < kLeafHandChunks && (8 * j + 7 < kLeafSlots || 8 * j >= kLeafSlots);
+    const bool features = 8 * j == 2 * kLeafSlots + 52;
+    uint4* X = reinterpret_cast<uint4*>(Xb) + j;
+    for (int k = 0; k < R; ++k) {
+      uint4 out;
+      if (one_player && !slow_row[k]) {  // a dead column has q = 0
+        const float mk = mul[p][k];
+        out = make_uint4(pack_bf16x2(q[0] * mk, q[1] * mk), pack_bf16x2(q[2] * mk, q[3] * mk),
+                         pack_bf16x2(q[4] * mk, q[5] * mk), pack_bf16x2(q[6] * mk, q[7] * mk));
+      } else {  // the chunk straddling the players, the tail, and rows with a uniform range
+        const float m0 = mul[0][k], m1 = mul[1][k], a0 = add[0][k], a1 = add[1][k];
+        const int rpos = 2 * kLeafSlots + rc[k] - 8 * j;  // the river card's one-hot column
+        const uint32_t ones = board_on | (rpos >= 0 && rpos < 8 ? 1u << rpos : 0u);
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const bool pe = (p1 >> e) & 1u;
+          v[e] = (dead >> e) & 1u ? 0.f : fmaf(q[e], pe ? m1 : m0, pe ? a1 : a0);
+          if ((ones >> e) & 1u) v[e] = 1.f;
+        }
+        if (features) {  // both features open this chunk
+          v[0] = lf.feat[0];
+          v[1] = lf.feat[1];
+        }
+        out = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                         pack_bf16x2(v[6], v[7]));
+      }
+      X[(size_t)k * kLeafChunks] = out;
+    }
   }
-  if (threadIdx.x == 0) {
-    x[2 * kLeafSlots + 52] = to_bf16(lf.feat[0]);
-    x[2 * kLeafSlots + 53] = to_bf16(lf.feat[1]);
+  __syncthreads();  // the rows are written; clear the columns of the hands holding each r
+  for (int t = threadIdx.x; t < R * 52; t += blockDim.x) {
+    const int k = t / 52, x = t - k * 52, r = rc[k];
+    if (x == r) continue;
+    const int col = col_of[pair_slot(r, x)];
+    if (col >= 0) {
+      uint16_t* row = Xb + (size_t)k * kLeafIn;
+      row[col] = 0;
+      row[kLeafSlots + col] = 0;
+    }
   }
 }
 
-// One block per leaf: the leaf values of player i.
+// Block (leaf, part): the leaf values of player i for part of the leaf's hands.  The
+// opponent's reach is staged as a 52 x 52 table over card pairs (0 where no hand); the totals
+// T and C[c] (reach of the hands holding card c: the row of c, one warp per card, fixed order)
+// and T - C[r] per river card r feed the inclusion-exclusion of each (hand, river card) term.
 template <typename V>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf_values(const GameDev* __restrict__ games, LeafCtx L,
                                                               int i, int use_bar) {
+  struct RiverCard {
+    int c;     // the card
+    float tc;  // T - C[c]
+  };
+  __shared__ float Q2[52 * 52];
   __shared__ float C[52];
+  __shared__ RiverCard rt[kLeafCards];
   __shared__ float red[kLeafThreads / 32];
   const LeafDev lf = L.leaves[blockIdx.x];
   const GameDev& G = games[lf.game];
   const NodeDev nd = G.nodes[lf.node];
+  const int nh = G.n_hands < kLeafSlots ? G.n_hands : kLeafSlots;
   const size_t stride = (size_t)G.hstride;
   const V* q = static_cast<const V*>(use_bar ? G.reach_bar : G.reach) + ((size_t)(1 - i) * G.n_nodes + lf.node) * stride;
   V* out = static_cast<V*>(use_bar ? G.cfv_br : G.cfv) + ((size_t)i * G.n_nodes + lf.node) * stride;
   const int16_t* slot = L.slot + (size_t)lf.game * L.hstride_max;
-  const int16_t* hand_at = L.hand_at + (size_t)lf.game * kLeafSlots;
-  // opponent totals: T and C[c] = sum over hands holding c (one warp per card, fixed order)
+  for (int x = threadIdx.x; x < 52 * 52; x += blockDim.x) Q2[x] = 0.f;
+  if (threadIdx.x < kLeafCards) rt[threadIdx.x].c = river_card(nd.board, threadIdx.x);
+  __syncthreads();
   float t = 0.f;
-  for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x) t += vf(q[h]);
-  const float T = block_sum(t, red);
+  for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+    const uint64_t m = G.hand_mask[h];
+    const int a = __ffsll((long long)m) - 1, b = 63 - __clzll((long long)m);
+    const float x = vf(q[h]);
+    Q2[a * 52 + b] = x;
+    Q2[b * 52 + a] = x;
+    t += x;
+  }
+  const float T = block_sum(t, red);  // its barriers also publish Q2
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = warp; c < 52; c += kLeafThreads / 32) {
-    float s = 0.f;
-    for (int h = lane; h < G.n_hands; h += 32)
-      if ((G.hand_mask[h] >> c) & 1ull) s += vf(q[h]);
+    float s = Q2[c * 52 + lane];
+    if (lane < 20) s += Q2[c * 52 + 32 + lane];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) C[c] = s;
   }
   __syncthreads();
+  if (threadIdx.x < kLeafCards) rt[threadIdx.x].tc = T - C[rt[threadIdx.x].c];
+  __syncthreads();
   const float scale = (float)(G.payoff[lf.node] * G.kappa64);
-  for (int h = threadIdx.x; h < G.n_hands; h += blockDim.x) {
+  const float* Y = L.Y + (size_t)lf.row0 * kLeafOut + i * kLeafSlots;
+  const int per = (nh + gridDim.y - 1) / gridDim.y, h1 = min(nh, ((int)blockIdx.y + 1) * per);
+  for (int h = blockIdx.y * per + threadIdx.x; h < h1; h += blockDim.x) {
     const uint64_t hm = G.hand_mask[h];
-    int c1 = -1, c2 = -1;
-    for (int c = 0; c < 52; ++c)
-      if ((hm >> c) & 1ull) {
-        if (c1 < 0) c1 = c;
-        else c2 = c;
-      }
-    const float qh = vf(q[h]);
-    const int s = slot[h];
+    const int c1 = __ffsll((long long)hm) - 1, c2 = 63 - __clzll((long long)hm);
+    const float* q1row = Q2 + c1 * 52;
+    const float* q2row = Q2 + c2 * 52;
+    const float qh = q1row[c2], C1 = C[c1], C2 = C[c2];
+    const float* y = Y + (L.hand_order ? h : slot[h]);
     float acc = 0.f;
-    for (int c = 0, ri = 0; c < 52; ++c) {
-      if ((nd.board >> c) & 1ull) continue;
-      const int row = lf.row0 + ri++;
-      if ((hm >> c) & 1ull) continue;  // the hand holds the river card
-      const int h1 = hand_at[pair_slot(c1, c)], h2 = hand_at[pair_slot(c2, c)];
-      const float q1 = h1 >= 0 ? vf(q[h1]) : 0.f, q2 = h2 >= 0 ? vf(q[h2]) : 0.f;
-      const float M = T - C[c] - (C[c1] - q1) - (C[c2] - q2) + qh;
-      acc = fmaf(L.Y[(size_t)row * kLeafOut + i * kLeafSlots + (L.hand_order ? h : s)], M, acc);
+#pragma unroll 16
+    for (int k = 0; k < kLeafCards; ++k) {
+      const RiverCard e = rt[k];
+      const float yk = __ldg(y + (size_t)k * kLeafOut);
+      if (e.c == c1 || e.c == c2) continue;  // the hand holds the river card
+      const float M = e.tc - (C1 - q1row[e.c]) - (C2 - q2row[e.c]) + qh;
+      acc = fmaf(yk, M, acc);
     }
     const float v = ((nd.board & hm) ? 0.f : scale * acc);
     if constexpr (sizeof(V) == 4)
@@ -571,13 +750,26 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_values(const GameDev* __r
 
 }  // namespace
 
+// Blocks per leaf (a divisor of n) so that n_leaves x parts fills the GPU about `waves` times.
+static int leaf_parts(int n_leaves, int n, int waves) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  int parts = 1;
+  while (parts < n && (long long)n_leaves * parts < (long long)waves * sms) {
+    ++parts;
+    while (n % parts) ++parts;
+  }
+  return parts;
+}
+
 int launch_leaf_inputs(const LaunchCtx& c, const LeafCtx& L, int use_bar, void* stream) {
   if (L.n_leaves == 0) return 0;
-  const int rows = L.n_leaves * kLeafCards;
+  const dim3 grid((unsigned)L.n_leaves, (unsigned)leaf_parts(L.n_leaves, kLeafCards, 8));
   if (c.precision == kPrecisionSingle)
-    k_leaf_inputs<float><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+    k_leaf_inputs<float><<<grid, kLeafInThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
   else
-    k_leaf_inputs<float2><<<rows, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
+    k_leaf_inputs<float2><<<grid, kLeafInThreads, 0, (cudaStream_t)stream>>>(c.games, L, use_bar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -594,10 +786,15 @@ int launch_leaf_net(const LaunchCtx& c, const LeafCtx& L, void* stream) {
 
 int launch_leaf_values(const LaunchCtx& c, const LeafCtx& L, int player, int use_bar, void* stream) {
   if (L.n_leaves == 0) return 0;
+  // at most kLeafThreads hands per block, and enough blocks to fill the GPU about 4 times
+  const int per_block = (L.hstride_max + kLeafThreads - 1) / kLeafThreads;
+  int parts = leaf_parts(L.n_leaves, 16, 4);
+  if (parts < per_block) parts = per_block;
+  const dim3 grid((unsigned)L.n_leaves, (unsigned)parts);
   if (c.precision == kPrecisionSingle)
-    k_leaf_values<float><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
+    k_leaf_values<float><<<grid, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
   else
-    k_leaf_values<float2><<<L.n_leaves, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
+    k_leaf_values<float2><<<grid, kLeafThreads, 0, (cudaStream_t)stream>>>(c.games, L, player, use_bar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -102,13 +102,16 @@ def _random_net(seed):
     return W, b
 
 
-def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
-    """Check one evaluation's inputs and outputs against the oracle; load the GPU's outputs
-    into the oracle's leaves.  Returns the worst output error relative to the row maximum."""
+def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True, game=0):
+    """Check one evaluation's inputs and outputs of one subgame's leaves against the oracle;
+    load the GPU's outputs into the oracle's leaves.  Returns the worst output error relative
+    to the row maximum."""
     g2o = {g: o for g, o, _ in mapping}
     slots = np.array([ln.pair_slot(int(a), int(c)) for a, c in spec.hands])
     worst = 0.0
-    for game, node, row0 in capi.cfr_leaf_info(tree):
+    for g_leaf, node, row0 in capi.cfr_leaf_info(tree):
+        if g_leaf != game:
+            continue
         o = g2o[node]
         board = _node_board(orc, spec, o)
         live = [c for c in range(52) if c not in board]
@@ -117,7 +120,7 @@ def _leaf_rows(tree, orc, spec, mapping, W, b, check_inputs=True):
         Y = capi.cfr_read_leaf_rows(tree, 1, row0, 48)
         if check_inputs:
             reach = [orc.node_reach("current", p, o) for p in (0, 1)]
-            c = capi.cfr_node_info(tree, node)["contrib"]
+            c = capi.cfr_node_info(tree, node, game)["contrib"]
             feat = ln.leaf_features(c[0] + c[1], spec.pot / 2 + spec.stack - c[0])
             for k, r in enumerate(live):
                 x = ln.leaf_input(reach, spec.hands, board, r, feat)
@@ -157,6 +160,100 @@ def test_leaf_inputs_outputs_and_values_match_oracle(schedule, street):
                     got = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=i)
                     want = orc.cfv(i, o)
                     assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)) + 1e-9 * spec.pot, (i, g)
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+def _check_leaf_values(tree, orc, spec, mapping, game=0):
+    for i in (0, 1):
+        orc.values_current(i)
+        for g, o, info in mapping:
+            if info["type"] == capi.CFR_NODE_LEAF:
+                got = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=i, game=game)
+                want = orc.cfv(i, o)
+                assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)) + 1e-9 * spec.pot, (game, i, g)
+
+
+def test_leaf_rows_in_slot_order_for_subgames_with_different_hands():
+    """Two turn subgames with different hand lists in one handle: no common hand order, so
+    the network's range columns and value rows stay in card-pair slot order.  Each subgame's
+    inputs, outputs and leaf values match the oracle."""
+    from oracle.oracle import Oracle
+    specs = [_leaf_spec(n_hands=40, seed=5), _leaf_spec(n_hands=28, seed=9)]
+    W, b = _random_net(2)
+    tree = capi.cfr_batch_create(specs, capi.make_opts("dcfr"))
+    try:
+        capi.cfr_set_leaf_net(tree, [ln.bf16_bits(w) for w in W], b)
+        capi.cfr_iterate(tree, 3)
+        capi.cfr_eval_leaves(tree)
+        assert {g for g, _, _ in capi.cfr_leaf_info(tree)} == {0, 1}
+        for game, spec in enumerate(specs):
+            orc = Oracle(spec, variant="dcfr")
+            mapping = node_map(tree, orc, game=game)
+            inject(tree, orc, mapping, game=game)
+            _leaf_rows(tree, orc, spec, mapping, W, b, game=game)
+            _check_leaf_values(tree, orc, spec, mapping, game=game)
+    finally:
+        capi.cfr_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("street", ["turn", "flop"])
+@pytest.mark.parametrize("reach", ["unreached", "concentrated"])
+def test_leaf_rows_with_degenerate_normalisers(street, reach):
+    """The root player's regrets set so that the player checks at every later node and, at the
+    root,
+    - unreached: never checks, so none of the player's hands reaches the leaves below the check
+      (every flop leaf), whose rows then hold the uniform range over the live hands (the
+      oracle's reading of a zero normaliser);
+    - concentrated: checks with the hands holding one card X and with the rest with
+      probability 1e-6, so for river card X more than 99.8 % of a leaf's reach sits on hands
+      holding X and the normaliser is the small remainder (summed directly, not as the
+      difference of two sums).
+    Inputs, outputs and leaf values match the oracle."""
+    from oracle.oracle import Oracle
+    spec = _leaf_spec(n_hands=24, street="flop") if street == "flop" else _leaf_spec()
+    W, b = _random_net(3)
+    tree = capi.cfr_tree_create(spec, capi.make_opts("dcfr"))
+    try:
+        capi.cfr_set_leaf_net(tree, [ln.bf16_bits(w) for w in W], b)
+        capi.cfr_iterate(tree, 2)
+        orc = Oracle(spec, variant="dcfr")
+        mapping = node_map(tree, orc)
+        assert capi.cfr_node_info(tree, 0)["type"] == capi.CFR_NODE_DECISION
+        p0 = capi.cfr_node_info(tree, 0)["player"]
+        cards = np.array(spec.hands)
+        X = int(np.bincount(cards.ravel(), minlength=52).argmax())
+        holds = (cards == X).any(axis=1)
+        for g, o, info in mapping:
+            if info["type"] != capi.CFR_NODE_DECISION or info["player"] != p0:
+                continue
+            R = capi.cfr_read_values(tree, capi.CFR_READ_REGRET, g)
+            R[:] = -1.0
+            if g != 0:
+                R[0] = 1.0
+            elif reach == "unreached":
+                R[1] = 1.0
+            else:
+                R[0] = np.where(holds, 1.0, 1e-6)
+                R[1] = np.where(holds, -1.0, 1.0)
+            capi.cfr_write_values(tree, capi.CFR_READ_REGRET, g, R)
+        capi.cfr_eval_leaves(tree)
+        inject(tree, orc, mapping)
+        leaves = [o for g, o, info in mapping if info["type"] == capi.CFR_NODE_LEAF]
+        if reach == "unreached":
+            assert any(not np.any(orc.node_reach("current", p0, o) > 0) for o in leaves), "no leaf without reach"
+        else:  # some row's normaliser is below 2e-3 of the player's total at the leaf
+            small = False
+            for o in leaves:
+                q = orc.node_reach("current", p0, o)
+                board = _node_board(orc, spec, o)
+                live = np.array([not ({int(a), int(c)} & set(board)) for a, c in spec.hands])
+                rest = ~holds
+                tot, s_x = q[live].sum(), q[live & rest].sum()
+                small |= X not in board and tot > 0 and 0 < s_x < 2e-3 * tot
+            assert small, "no row with a concentrated range"
+        _leaf_rows(tree, orc, spec, mapping, W, b)
+        _check_leaf_values(tree, orc, spec, mapping)
     finally:
         capi.cfr_tree_destroy(tree)
 
