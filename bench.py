@@ -70,6 +70,9 @@ def parse_args(argv=None):
                     help="stream schedule: hands per warp (0 = automatic)")
     ap.add_argument("--term-nodes", type=int, choices=range(0, 9), default=0,
                     help="terminal nodes per block of the terminal launch (0 = automatic)")
+    ap.add_argument("--runout-tables", choices=["on", "off"], default="on",
+                    help="flop: evaluate the all-in run-outs by win-minus-loss tables (wide schedule) or board "
+                         "by board")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -696,7 +699,9 @@ def run_leaf(args):
     make = synth.ranked_flop_subgame if flop else synth.ranked_turn_subgame
     spec_leaf = make(depth_limit=1, **kw)
     spec_exact = make(depth_limit=0, **kw)
-    opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, precision=args.precision)
+    tables = flop and args.runout_tables == "on" and args.precision == "single"  # (FP32 values only)
+    opts = capi.make_opts("dcfr", 1.5, 0.0, 2.0, alternating=True, precision=args.precision,
+                          schedule="wide" if tables else "auto", runout_tables=tables)
     W, b = leafnet_train.load_weights()
     meta = np.load(os.path.join(ROOT, "paper_2605_19928_gb300", "leafnet_weights.npz"))["meta"]
     L = capi.cfr_tree_create(spec_leaf, opts, stream=stream.cuda_stream)
@@ -845,7 +850,7 @@ def run_leaf(args):
                                         "river card" if flop else
                                         "depth-limited turn subgame, leaf network at the river card"),
                            "board_cards": len(spec_leaf.board), "hands": spec_leaf.n_hands, "leaves": len(leaves),
-                           "nodes": n_leaf_nodes, "schedules": schedules,
+                           "nodes": n_leaf_nodes, "schedules": schedules, "runout_tables": tables,
                            "network": "2752-512-512-512-2688 BF16, GELU", "pot": spec_leaf.pot,
                            "stack": spec_leaf.stack,
                            "bet_sizes": ",".join("all-in" if x <= 0 else "%g" % x for x in spec_leaf.bet_sizes)

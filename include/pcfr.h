@@ -157,6 +157,18 @@ typedef struct cfr_game_spec {
  * hand rows padded to a multiple of 64, i.e. the hand count rounded up to 32 is a multiple
  * of 64, CFR_EINVAL otherwise), or 0 = automatic (32; cfr_autotune tries both).  Other
  * schedules ignore it.  Results are the same bits either way.
+ * runout_tables: 1 evaluates every all-in run-out -- a chance node below a decision whose
+ * subtree holds only chance and showdown nodes (nobody acts again) -- in one step instead of
+ * board by board (Stage 4 summed over the run-out's boards).  The value of hand h of player
+ * i at the run-out's top node is then u sum_o E[h][o] q(o): q the opponent's reach there, u
+ * the showdowns' payoff scale (chips in times the probability of the cards dealt, times
+ * 1/Z; the same at every board of a run-out) and E[h][o] the number of the run-out's boards
+ * on which h beats o less the number on which it loses, counting the boards that share no
+ * card with h or o (0 if h and o share a card).  E is built once per distinct run-out board
+ * at create (int8 when a run-out has at most 127 boards, else int16, [o][h]).  The nodes
+ * below the top node are then not evaluated: their values and reach stay unset, and
+ * cfr_read_values returns what their arrays hold.  Needs the wide schedule, FP32 values and
+ * two-card hands; CFR_EINVAL otherwise.  0 (default) evaluates every showdown node.
  */
 enum { CFR_PRECISION_PAIRS = 0, CFR_PRECISION_SINGLE = 1 };
 enum {
@@ -177,6 +189,7 @@ typedef struct cfr_solver_opts {
   int schedule;
   int term_nodes;
   int warp_hands;
+  int runout_tables;
 } cfr_solver_opts;
 
 typedef struct cfr_tree cfr_tree;

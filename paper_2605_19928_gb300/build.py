@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpcfr.so")
-SOURCES = ["kernels.cu", "capi.cu", "leafnet.cu", "tree.cpp"]
+SOURCES = ["kernels.cu", "capi.cu", "leafnet.cu", "runout.cu", "tree.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

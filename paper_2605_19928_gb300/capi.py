@@ -58,7 +58,7 @@ class cfr_game_spec(C.Structure):
 class cfr_solver_opts(C.Structure):
     _fields_ = [("variant", C.c_int), ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("alternating", C.c_int), ("chunk_hands", C.c_int), ("precision", C.c_int), ("schedule", C.c_int),
-                ("term_nodes", C.c_int), ("warp_hands", C.c_int)]
+                ("term_nodes", C.c_int), ("warp_hands", C.c_int), ("runout_tables", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -193,12 +193,12 @@ def make_spec(g) -> tuple[cfr_game_spec, tuple]:
 
 
 def make_opts(variant="dcfr", alpha=1.5, beta=0.0, gamma=2.0, alternating=True, chunk_hands=0,
-              precision="pairs", schedule="auto", term_nodes=0, warp_hands=0) -> cfr_solver_opts:
+              precision="pairs", schedule="auto", term_nodes=0, warp_hands=0, runout_tables=False) -> cfr_solver_opts:
     return cfr_solver_opts(VARIANTS[variant] if isinstance(variant, str) else int(variant), alpha, beta, gamma,
                            int(alternating), int(chunk_hands),
                            PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                            SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule), int(term_nodes),
-                           int(warp_hands))
+                           int(warp_hands), int(runout_tables))
 
 
 def _stream_arg(stream):

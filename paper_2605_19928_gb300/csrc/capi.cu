@@ -17,6 +17,7 @@
 
 #include "pcfr.h"
 #include "pcfr_internal.h"
+#include "runout.h"
 #include "tree.h"
 
 using namespace pcfr;
@@ -56,6 +57,12 @@ struct cfr_tree {
   int32_t* d_wide_inner = nullptr;  // wide schedule: inner node ids, level by level
   int32_t* d_wide_fwd = nullptr;    // wide schedule: nodes whose reach is stored, level by level
   int32_t* d_term_src = nullptr;    // reach source of each terminal work entry
+  // all-in run-outs evaluated by win-minus-loss tables (runout_tables; none: all zero)
+  RunoutItem* d_ro_items8 = nullptr;
+  RunoutItem* d_ro_items16 = nullptr;
+  int ro_n8 = 0, ro_n16 = 0;
+  RunoutTable* d_ro_tables = nullptr;
+  unsigned char* d_ro_pool = nullptr;
   std::vector<int> wide_inner_off, wide_fwd_off;
   int* d_iter = nullptr;
   unsigned* d_done = nullptr;
@@ -129,6 +136,21 @@ int upload(cfr_tree* t, const std::vector<T>& v, T** out) {
   t->h2d_bytes += (int64_t)(v.size() * sizeof(T));
   *out = (T*)p;
   return CFR_OK;
+}
+
+// Terminal values of the players in player_mask (Stages 2-4): the fold and showdown launch,
+// then the all-in run-outs evaluated by their tables (runout_tables).
+int launch_terminals(const cfr_tree* t, int player_mask, int use_bar, cudaStream_t s) {
+  if (launch_terminal(t->ctx, player_mask, use_bar, s)) return -1;
+  if (t->ro_n8 + t->ro_n16 == 0) return 0;
+  const HostGame& h = t->host[0];
+  return launch_runout_values(t->ctx.games, t->d_ro_items8, t->ro_n8, t->d_ro_items16, t->ro_n16, t->d_ro_tables,
+                              t->d_ro_pool, h.n_hands, h.hstride, player_mask, use_bar, s);
+}
+
+// Kernels one terminal stage launches.
+int terminal_launches(const cfr_tree* t) {
+  return (t->ctx.n_term_work > 0 ? 1 : 0) + (t->ro_n8 > 0 ? 1 : 0) + (t->ro_n16 > 0 ? 1 : 0);
 }
 
 // One device block for every subgame's tables and state: the tables are staged on the host
@@ -387,6 +409,9 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   if (o.warp_hands != 0 && o.warp_hands != 32 && o.warp_hands != 64)
     return fail(CFR_EINVAL, "warp_hands must be 0, 32 or 64");
   if (o.schedule < CFR_SCHEDULE_AUTO || o.schedule > CFR_SCHEDULE_RESIDENT) return fail(CFR_EINVAL, "unknown schedule");
+  if (o.runout_tables != 0 && o.runout_tables != 1) return fail(CFR_EINVAL, "runout_tables must be 0 or 1");
+  if (o.runout_tables && (o.precision != CFR_PRECISION_SINGLE || n_games != 1))
+    return fail(CFR_EINVAL, "runout_tables needs one subgame with FP32 values (precision = single)");
   int rc = check_device();
   if (rc != CFR_OK) return rc;
   static int configured = configure_kernels();
@@ -536,6 +561,18 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   } else if (o.schedule == CFR_SCHEDULE_AUTO && schedule == kScheduleLevel && wide_ok && !all_fit) {
     schedule = kScheduleWide;
   }
+  RunoutPlan ro;
+  if (o.runout_tables) {
+    if (schedule != kScheduleWide || t->host[0].hand_size != 2) {
+      delete t;
+      return fail(CFR_EINVAL, "runout_tables needs the wide schedule and two-card hands");
+    }
+    plan_runouts(t->host[0], ro);
+    if (ro.pool_bytes > ((size_t)8 << 30) || ro.tables.size() > 65535) {
+      delete t;
+      return fail(CFR_EINVAL, "the run-out tables would take more than 8 GB");
+    }
+  }
   // Resident schedule: one block per SM holds a chunk's state of both players beside a terminal
   // node's board table, and every chunk has a block.
   size_t res_term = 0, res_hand = 0;
@@ -563,7 +600,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     std::vector<int32_t> inner, fwd;
     for (int l = 0; l < L; ++l) {
       for (int n = h.level_start[l]; n < h.level_start[l + 1]; ++n) {
-        if (!is_end(h.nodes[(size_t)n].type)) inner.push_back(n);
+        const bool tabled = !ro.top.empty() && (ro.top[(size_t)n] || ro.inside[(size_t)n]);
+        if (!is_end(h.nodes[(size_t)n].type) && !tabled) inner.push_back(n);
         if (h.reach_src[(size_t)n] == n) fwd.push_back(n);
       }
       t->wide_inner_off.push_back((int)inner.size());
@@ -672,7 +710,9 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     for (int c = 0; c < d.n_chunks; ++c) chunk_work.push_back({g, c});
 
     // terminals grouped by board table (fold nodes read only the board-free part of table 0)
-    std::vector<int> term = h.terminals;
+    std::vector<int> term;
+    for (int n : h.terminals)
+      if (ro.inside.empty() || !ro.inside[(size_t)n]) term.push_back(n);  // run-outs: by their tables
     auto table = [&](int n) { return h.nodes[(size_t)n].type == kShowdown ? h.nodes[(size_t)n].row : 0; };
     std::stable_sort(term.begin(), term.end(), [&](int a, int b2) { return table(a) < table(b2); });
     for (int n : term) term_work.push_back({g, n});
@@ -682,6 +722,29 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     return rc;
   }
   for (int g = 0; g < n_games; ++g) t->dev[g].br_out = t->d_br_all + 2 * g;
+  if (!ro.tables.empty()) {  // the run-out tables, from each showdown board's tie groups
+    const HostGame& h = t->host[0];
+    RunoutBoard* d_boards = nullptr;
+    int32_t* d_gs = nullptr;
+    if ((rc = upload(t, ro.tables, &t->d_ro_tables)) || (rc = upload(t, ro.boards, &d_boards)) ||
+        (rc = upload(t, h.sd_gs, &d_gs)) || (rc = upload(t, ro.items8, &t->d_ro_items8)) ||
+        (rc = upload(t, ro.items16, &t->d_ro_items16))) {
+      delete t;
+      return rc;
+    }
+    t->d_ro_pool = static_cast<unsigned char*>(t->alloc(ro.pool_bytes));
+    if (!t->d_ro_pool) {
+      delete t;
+      return fail(CFR_ENOMEM, "device allocation failed");
+    }
+    if (launch_runout_build(t->d_ro_tables, (int)ro.tables.size(), d_boards, d_gs, t->dev[0].hand_mask, h.n_hands,
+                            h.hstride, t->d_ro_pool, t->stream) != 0) {
+      delete t;
+      return fail(CFR_ECUDA, "run-out table launch failed");
+    }
+    t->ro_n8 = (int)ro.items8.size();
+    t->ro_n16 = (int)ro.items16.size();
+  }
   std::vector<int32_t> term_src(term_work.size());
   for (size_t k = 0; k < term_work.size(); ++k)
     term_src[k] = t->host[term_work[k].game].reach_src[(size_t)term_work[k].unit];
@@ -789,7 +852,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   t->launches_per_iteration =
       (o.alternating ? pass_launches(t, kModeUpdate, 1, 0) + pass_launches(t, kModeUpdate, 2, 1)
                      : pass_launches(t, kModeUpdate, 3, 1)) +
-      (c.n_term_work > 0 ? (o.alternating ? 2 : 1) : 0) +
+      terminal_launches(t) * (o.alternating ? 2 : 1) +
       (o.alternating ? leaf_launches(t, 1) + leaf_launches(t, 2) : leaf_launches(t, 3));
   t->launches += pass_launches(t, kModeInit, 3, 0);
   if (launch_init(c, stream) != 0) {
@@ -833,11 +896,11 @@ int pass_launches(const cfr_tree* t, int which, int player_mask, int advance) {
 int enqueue_iteration(cfr_tree* t, cudaStream_t s) {
   const LaunchCtx& c = t->ctx;
   if (t->opts.alternating) {
-    if (enqueue_leaves(t, 1, 0, s) || launch_terminal(c, 1, 0, s) || launch_update(c, 1, 0, s) ||
-        enqueue_leaves(t, 2, 0, s) || launch_terminal(c, 2, 0, s) || launch_update(c, 2, 1, s))
+    if (enqueue_leaves(t, 1, 0, s) || launch_terminals(t, 1, 0, s) || launch_update(c, 1, 0, s) ||
+        enqueue_leaves(t, 2, 0, s) || launch_terminals(t, 2, 0, s) || launch_update(c, 2, 1, s))
       return -1;
   } else {
-    if (enqueue_leaves(t, 3, 0, s) || launch_terminal(c, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
+    if (enqueue_leaves(t, 3, 0, s) || launch_terminals(t, 3, 0, s) || launch_update(c, 3, 1, s)) return -1;
   }
   return 0;
 }
@@ -977,7 +1040,7 @@ int cfr_exploitability_async(cfr_tree* t) {
   if (!t) return fail(CFR_EINVAL, "tree is NULL");
   const LaunchCtx& c = t->ctx;
   if (!t->expl_graph && !t->expl_once) {  // a first pass runs without recording a graph
-    if (launch_avg_reach(c, t->stream) || enqueue_leaves(t, 3, 1, t->stream) || launch_terminal(c, 3, 1, t->stream) ||
+    if (launch_avg_reach(c, t->stream) || enqueue_leaves(t, 3, 1, t->stream) || launch_terminals(t, 3, 1, t->stream) ||
         launch_br(c, t->stream))
       return fail(CFR_ECUDA, "exploitability launch failed");
     t->expl_once = true;
@@ -987,7 +1050,7 @@ int cfr_exploitability_async(cfr_tree* t) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(t->capture, cudaStreamCaptureModeThreadLocal));
       const int rc = launch_avg_reach(c, t->capture) || enqueue_leaves(t, 3, 1, t->capture) ||
-                     launch_terminal(c, 3, 1, t->capture) || launch_br(c, t->capture);
+                     launch_terminals(t, 3, 1, t->capture) || launch_br(c, t->capture);
       cudaError_t e = cudaStreamEndCapture(t->capture, &graph);
       if (rc != 0) return fail(CFR_ECUDA, "kernel launch failed during capture");
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -998,7 +1061,7 @@ int cfr_exploitability_async(cfr_tree* t) {
     CK(cudaGraphLaunch(t->expl_graph, t->stream));
   }
   t->avg_gen = -1;  // the pass rewrites sigbar with its own normalisation
-  t->launches += (t->ctx.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) +
+  t->launches += terminal_launches(t) + pass_launches(t, kModeAvg, 3, 0) +
                  pass_launches(t, kModeBR, 3, 0) + leaf_launches(t, 3);
   return CFR_OK;
 }
@@ -1176,8 +1239,8 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
           rc = enqueue_leaves(t, 1 << p, 0, s);
           if (!rc) err = mark(CFR_STAGE_LEAF);
         }
-        if (!rc && err == cudaSuccess) rc = launch_terminal(c, 1 << p, 0, s);
-        if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
+        if (!rc && err == cudaSuccess) rc = launch_terminals(t, 1 << p, 0, s);
+        if (!rc && terminal_launches(t) > 0) err = mark(CFR_STAGE_TERMINAL);
         if (!rc && err == cudaSuccess) rc = launch_update(c, 1 << p, p == 1, s);
         if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
       }
@@ -1186,8 +1249,8 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
         rc = enqueue_leaves(t, 3, 0, s);
         if (!rc) err = mark(CFR_STAGE_LEAF);
       }
-      if (!rc && err == cudaSuccess) rc = launch_terminal(c, 3, 0, s);
-      if (!rc && c.n_term_work > 0) err = mark(CFR_STAGE_TERMINAL);
+      if (!rc && err == cudaSuccess) rc = launch_terminals(t, 3, 0, s);
+      if (!rc && terminal_launches(t) > 0) err = mark(CFR_STAGE_TERMINAL);
       if (!rc && err == cudaSuccess) rc = launch_update(c, 3, 1, s);
       if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_UPDATE);
     }
@@ -1198,8 +1261,8 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
     rc = enqueue_leaves(t, 3, 1, s);
     if (!rc) err = mark(CFR_STAGE_LEAF);
   }
-  if (!rc && err == cudaSuccess) rc = launch_terminal(c, 3, 1, s);
-  if (!rc && err == cudaSuccess && c.n_term_work > 0) err = mark(CFR_STAGE_BR_TERMINAL);
+  if (!rc && err == cudaSuccess) rc = launch_terminals(t, 3, 1, s);
+  if (!rc && err == cudaSuccess && terminal_launches(t) > 0) err = mark(CFR_STAGE_BR_TERMINAL);
   if (!rc && err == cudaSuccess) rc = launch_br(c, s);
   if (!rc && err == cudaSuccess) err = mark(CFR_STAGE_BR);
   cudaError_t serr = cudaStreamSynchronize(s);
@@ -1220,7 +1283,7 @@ int cfr_stage_times(cfr_tree* t, int n_iters, double* ms, int64_t* launches) {
     ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;
     if (launches) launches[k] = cnt[k];
   }
-  t->launches += (int64_t)n_iters * t->launches_per_iteration + (c.n_term_work > 0 ? 1 : 0) +
+  t->launches += (int64_t)n_iters * t->launches_per_iteration + terminal_launches(t) +
                  pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) + leaf_launches(t, 3);
   return CFR_OK;
 }
@@ -1553,11 +1616,11 @@ extern "C" int cfr_exploitability_noalloc(cfr_tree* t, double* expl, double* br)
   cudaStream_t s = t->stream;
   CK(cudaMemsetAsync(scratch + kStaticPartialBytes + kStaticOutBytes, 0, (size_t)c.n_games * sizeof(unsigned), s));
   t->avg_gen = -1;
-  if (launch_avg_reach(c, s) || enqueue_leaves(t, 3, 1, s) || launch_terminal(c, 3, 1, s) || launch_br(c, s))
+  if (launch_avg_reach(c, s) || enqueue_leaves(t, 3, 1, s) || launch_terminals(t, 3, 1, s) || launch_br(c, s))
     return fail(CFR_ECUDA, "exploitability launch failed");
   k_br_root_static<<<2 * c.n_chunk_work, 32, 0, s>>>(c.games, c.chunk_work, c.n_chunk_work, c.precision, scratch);
   CK(cudaGetLastError());
-  t->launches += (c.n_term_work > 0 ? 1 : 0) + pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) +
+  t->launches += terminal_launches(t) + pass_launches(t, kModeAvg, 3, 0) + pass_launches(t, kModeBR, 3, 0) +
                  leaf_launches(t, 3) + 1;
   CK(cudaMemcpyAsync(br, scratch + kStaticPartialBytes, (size_t)c.n_games * 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, s));

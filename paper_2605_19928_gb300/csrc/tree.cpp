@@ -670,4 +670,60 @@ std::vector<uint32_t> node_loads(const HostGame& g, int n, int p, bool backward,
   return mine;
 }
 
+void plan_runouts(const HostGame& h, RunoutPlan& r) {
+  const int N = (int)h.nodes.size();
+  std::vector<char> pure(N, 0);  // a showdown, or a chance node with only such nodes below
+  for (int n = N - 1; n >= 0; --n) {  // children come after their parent (level order)
+    const NodeDev& nd = h.nodes[(size_t)n];
+    if (nd.type == kShowdown) {
+      pure[n] = 1;
+    } else if (nd.type == kChance && nd.n_kids > 0) {
+      bool all = true;
+      for (int k = 0; k < nd.n_kids; ++k) all = all && pure[nd.first_kid + k];
+      pure[n] = all;
+    }
+  }
+  std::vector<int> top_of(N, -1);  // the candidate top above a node inside a run-out
+  std::vector<char> cand(N, 0);
+  for (int n = 1; n < N; ++n) {
+    const int par = h.nodes[(size_t)n].parent;
+    if (cand[par] || top_of[par] >= 0) top_of[n] = cand[par] ? par : top_of[par];
+    else if (pure[n] && h.nodes[(size_t)n].type == kChance && h.nodes[(size_t)par].type != kChance) cand[n] = 1;
+  }
+  std::vector<std::vector<int>> shows(N);
+  for (int n = 0; n < N; ++n)
+    if (top_of[n] >= 0 && h.nodes[(size_t)n].type == kShowdown) shows[top_of[n]].push_back(n);
+  std::vector<char> take(N, 0);
+  std::vector<std::vector<std::pair<uint64_t, int>>> sigs;  // each table's boards (cards, board table)
+  const double kappa = 1.0 / h.Z;
+  for (int n = 0; n < N; ++n) {
+    if (!cand[n] || shows[n].empty()) continue;
+    const double pay = h.payoff[(size_t)shows[n][0]];
+    bool same = true;
+    for (int sd : shows[n]) same = same && h.payoff[(size_t)sd] == pay;
+    if (!same) continue;  // evaluated board by board
+    std::vector<std::pair<uint64_t, int>> sig;
+    for (int sd : shows[n]) sig.push_back({h.nodes[(size_t)sd].board, h.nodes[(size_t)sd].row});
+    std::sort(sig.begin(), sig.end());
+    int tid = (int)(std::find(sigs.begin(), sigs.end(), sig) - sigs.begin());
+    if (tid == (int)sigs.size()) {
+      RunoutTable tb{};
+      tb.wide = sig.size() > 127 ? 1 : 0;
+      tb.n_boards = (int)sig.size();
+      tb.board0 = (int)r.boards.size();
+      tb.offset = (int64_t)r.pool_bytes;
+      r.pool_bytes += ((size_t)h.n_hands * h.hstride * (tb.wide ? 2 : 1) + 255) / 256 * 256;
+      for (const auto& b : sig) r.boards.push_back({b.first, b.second, 0});
+      r.tables.push_back(tb);
+      sigs.push_back(sig);
+    }
+    const RunoutItem it{n, tid, (float)(pay * kappa), 0};
+    (r.tables[(size_t)tid].wide ? r.items16 : r.items8).push_back(it);
+    take[n] = 1;
+  }
+  r.top = take;
+  r.inside.assign(N, 0);
+  for (int n = 0; n < N; ++n) r.inside[n] = top_of[n] >= 0 && take[top_of[n]];
+}
+
 }  // namespace pcfr

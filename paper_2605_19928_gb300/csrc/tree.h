@@ -6,6 +6,7 @@
 
 #include "pcfr.h"
 #include "pcfr_internal.h"
+#include "runout.h"
 
 namespace pcfr {
 
@@ -76,5 +77,18 @@ std::vector<ProgOp> program_ops(const HostGame& g, const std::vector<int32_t>& p
 std::vector<int32_t> stream_tables(const HostGame& g, const std::vector<int32_t>& pre, int half, bool pred,
                                    std::vector<uint32_t>& units, int unit_off[4], int unit_count[4],
                                    int chunk_off[4], int chunk_count[4]);
+
+// All-in run-outs of one game evaluated by win-minus-loss tables (runout.h): a run-out's top
+// is a chance node below a decision whose subtree holds only chance and showdown nodes, all of
+// them with one payoff; tops whose subtrees show down on the same boards share a table.
+struct RunoutPlan {
+  std::vector<char> top, inside;  // per node: tops a run-out / lies below a top
+  std::vector<RunoutItem> items8, items16;
+  std::vector<RunoutTable> tables;
+  std::vector<RunoutBoard> boards;
+  size_t pool_bytes = 0;
+};
+
+void plan_runouts(const HostGame& g, RunoutPlan& r);
 
 }  // namespace pcfr

@@ -123,8 +123,9 @@ def stored_cfv(tree, g, info):
     return g == 0 or info["type"] in (capi.CFR_NODE_FOLD, capi.CFR_NODE_SHOWDOWN, capi.CFR_NODE_LEAF)
 
 
-def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, floor_frac=FLOOR):
-    """R and S of one player's decision nodes and that player's counterfactual values."""
+def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, floor_frac=FLOOR, skip=()):
+    """R and S of one player's decision nodes and that player's counterfactual values (not at
+    the GPU nodes in `skip`, whose values the handle does not keep)."""
     pot = oracle.spec.pot if pot is None else pot
     floor = floor_frac * pot
     worst = {"R": 0.0, "S": 0.0, "cfv": 0.0}
@@ -137,7 +138,7 @@ def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, f
             if oracle.variant == "pcfr+":
                 M_g = capi.cfr_read_values(tree, capi.CFR_READ_PREDICTION, g, game=game)
                 close(M_g, oracle.prediction(o), rtol, floor=floor, what=f"prediction node {g}")
-        if not stored_cfv(tree, g, info):
+        if g in skip or not stored_cfv(tree, g, info):
             continue
         v_g = capi.cfr_read_values(tree, capi.CFR_READ_CFV, g, player=player, game=game)
         worst["cfv"] = max(worst["cfv"], close(v_g, oracle.cfv(player, o), rtol, floor=floor,
@@ -145,7 +146,8 @@ def compare_player(tree, oracle, mapping, player, game=0, pot=None, rtol=RTOL, f
     return worst
 
 
-def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=True, rtol=RTOL, floor_frac=FLOOR):
+def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=True, rtol=RTOL, floor_frac=FLOOR,
+                skip=()):
     """Iteration t from identical state.
 
     The GPU's R and S are loaded into the oracle, then the GPU runs one iteration and the
@@ -160,15 +162,15 @@ def forced_step(tree, oracle, mapping, t, alternating=True, game=0, advance_gpu=
     worst = {}
     if alternating:
         oracle.update_player(0, t)
-        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac)
+        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac, skip=skip)
         inject(tree, oracle, mapping, game, player=0)
         oracle.update_player(1, t)
-        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac)
+        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac, skip=skip)
         worst = {k: max(w0[k], w1[k]) for k in w0}
     else:
         oracle.update_both(t)
-        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac)
-        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac)
+        w0 = compare_player(tree, oracle, mapping, 0, game, rtol=rtol, floor_frac=floor_frac, skip=skip)
+        w1 = compare_player(tree, oracle, mapping, 1, game, rtol=rtol, floor_frac=floor_frac, skip=skip)
         worst = {k: max(w0[k], w1[k]) for k in w0}
     oracle.set_iterations(t)
     return worst

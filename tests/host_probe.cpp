@@ -140,4 +140,42 @@ int probe_term_tables(void* h, int32_t tt_out[10], uint16_t* out, int cap) {
   return (int)t.size();
 }
 
+// The all-in run-outs evaluated by tables (plan_runouts): sizes = (tops with uint8 tables,
+// tops with uint16 tables, tables, boards), *pool = table bytes.  With non-null outputs: per
+// node the top and inside flags; per top (uint8 tables first) node, table and u; per table
+// wide, board count, first board and byte offset; per board its cards and board table.
+void probe_runouts(void* h, int32_t sizes[4], int64_t* pool, int8_t* top, int8_t* inside, int32_t* items,
+                   float* u, int64_t* tables, uint64_t* board_cards, int32_t* board_tab) {
+  const Probe& p = *static_cast<Probe*>(h);
+  pcfr::RunoutPlan r;
+  pcfr::plan_runouts(p.g, r);
+  sizes[0] = (int32_t)r.items8.size();
+  sizes[1] = (int32_t)r.items16.size();
+  sizes[2] = (int32_t)r.tables.size();
+  sizes[3] = (int32_t)r.boards.size();
+  *pool = (int64_t)r.pool_bytes;
+  if (!top) return;
+  for (size_t n = 0; n < r.top.size(); ++n) {
+    top[n] = r.top[n];
+    inside[n] = r.inside[n];
+  }
+  std::vector<pcfr::RunoutItem> all = r.items8;
+  all.insert(all.end(), r.items16.begin(), r.items16.end());
+  for (size_t k = 0; k < all.size(); ++k) {
+    items[2 * k] = all[k].node;
+    items[2 * k + 1] = all[k].table;
+    u[k] = all[k].u;
+  }
+  for (size_t k = 0; k < r.tables.size(); ++k) {
+    tables[4 * k] = r.tables[k].wide;
+    tables[4 * k + 1] = r.tables[k].n_boards;
+    tables[4 * k + 2] = r.tables[k].board0;
+    tables[4 * k + 3] = r.tables[k].offset;
+  }
+  for (size_t k = 0; k < r.boards.size(); ++k) {
+    board_cards[k] = r.boards[k].cards;
+    board_tab[k] = r.boards[k].table;
+  }
+}
+
 }  // extern "C"

@@ -559,3 +559,135 @@ def test_exact_leaves_are_checked(probe):
     assert "exact_leaves" in _rejected(probe, turn(depth_limit=1, exact_leaves=(2, 2)))
     assert "exact_leaves" in _rejected(probe, turn(depth_limit=1, exact_leaves=(-1,)))
     assert "exact_leaves" in _rejected(probe, turn(depth_limit=0, exact_leaves=(0,)))
+
+
+@pytest.mark.parametrize("case", ["turn", "flop", "turn_limited", "river", "leduc"])
+def test_runout_plan_follows_its_definition(probe, case):
+    """The all-in run-outs the tables evaluate (`runout_tables`): the tops are the chance
+    nodes below a decision with only chance and showdown nodes beneath, every node below a
+    top is inside, a top's table lists the boards (cards, board table) of its showdowns and
+    tops that show down on the same boards share one, u is the showdowns' common payoff over
+    Z rounded to FP32, tables of more than 127 boards hold 16-bit entries, and the pool holds
+    each table's n_hands x hstride entries at 256-byte offsets."""
+    spec = SPECS[case]()
+    t = Built(probe, spec)
+    try:
+        N = t.n_nodes
+        sizes, pool = np.zeros(4, np.int32), C.c_int64()
+        probe.probe_runouts(C.c_void_p(t.h), sizes.ctypes.data_as(C.c_void_p), C.byref(pool), None, None, None,
+                            None, None, None, None)
+        n8, n16, nt, nb = (int(x) for x in sizes)
+        top, inside = np.zeros(N, np.int8), np.zeros(N, np.int8)
+        items, u = np.zeros((n8 + n16, 2), np.int32), np.zeros(n8 + n16, np.float32)
+        tables, bcards, btab = np.zeros((nt, 4), np.int64), np.zeros(nb, np.uint64), np.zeros(nb, np.int32)
+        probe.probe_runouts(C.c_void_p(t.h), sizes.ctypes.data_as(C.c_void_p), C.byref(pool),
+                            top.ctypes.data_as(C.c_void_p), inside.ctypes.data_as(C.c_void_p),
+                            items.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p),
+                            tables.ctypes.data_as(C.c_void_p), bcards.ctypes.data_as(C.c_void_p),
+                            btab.ctypes.data_as(C.c_void_p))
+        pay = np.zeros(N)
+        probe.probe_payoff(C.c_void_p(t.h), pay.ctypes.data_as(C.c_void_p))
+        boards = np.zeros(N, np.uint64)
+        probe.probe_boards(C.c_void_p(t.h), boards.ctypes.data_as(C.c_void_p))
+        probe.probe_Z.restype = C.c_double
+        z = probe.probe_Z(C.c_void_p(t.h))
+
+        def below(n):  # the nodes strictly below n
+            out, stack = [], list(t.kids(n))
+            while stack:
+                m = stack.pop()
+                out.append(m)
+                stack.extend(t.kids(m))
+            return out
+
+        want_top = [n for n in range(1, N) if t.type[n] == CHANCE and t.type[t.parent[n]] != CHANCE
+                    and all(t.type[m] in (CHANCE, SHOWDOWN) for m in below(n))]
+        assert list(np.nonzero(top)[0]) == want_top
+        want_inside = set()
+        for n in want_top:
+            want_inside |= set(below(n))
+        assert set(np.nonzero(inside)[0].tolist()) == want_inside
+        if case in ("turn", "flop"):
+            assert want_top, "the all-in bets leave run-outs"
+        if case in ("river", "leduc"):
+            assert not want_top
+        assert sorted(items[:, 0].tolist()) == want_top
+        sig_of = {}
+        for k, (n, tb) in enumerate(items.tolist()):
+            shows = [m for m in below(n) if t.type[m] == SHOWDOWN]
+            sig = sorted((int(boards[m]), int(t.row[m])) for m in shows)
+            wide, nbd, b0, off = (int(x) for x in tables[tb])
+            assert sorted(zip(bcards[b0:b0 + nbd].tolist(), btab[b0:b0 + nbd].tolist())) == sig
+            assert wide == (nbd > 127) and (k >= n8) == bool(wide)
+            assert len({pay[m] for m in shows}) == 1
+            assert u[k] == np.float32(pay[shows[0]] * (1.0 / z))
+            assert sig_of.setdefault(tuple(sig), tb) == tb
+        assert len(sig_of) == nt
+        offs = sorted((int(tables[k, 3]), int(tables[k, 0])) for k in range(nt))
+        at = 0
+        for off, wide in offs:
+            assert off == at and off % 256 == 0
+            at += (t.n_hands * t.hstride * (2 if wide else 1) + 255) // 256 * 256
+        assert pool.value == at
+    finally:
+        t.close()
+
+
+@pytest.mark.parametrize("case", ["turn", "flop"])
+def test_runout_tables_reproduce_the_oracle_runout_values(probe, oracle_mod, case):
+    """The table form of a run-out, restated in numpy from the host's plan and showdown
+    tables: u sum_o E[h][o] q(o), E counting the boards (of the top's table) that share no card
+    with h or o on which h's tie group ranks above o's less those on which it ranks below.
+    Against the oracle's value at each top -- its sum over the run-out's boards -- under the
+    strategies of two DCFR iterations, both players."""
+    spec = SPECS[case]()
+    t = Built(probe, spec)
+    o = oracle_mod.Oracle(spec, variant="dcfr", threads=1)
+    try:
+        N, H = t.n_nodes, t.n_hands
+        sizes, pool = np.zeros(4, np.int32), C.c_int64()
+        probe.probe_runouts(C.c_void_p(t.h), sizes.ctypes.data_as(C.c_void_p), C.byref(pool), None, None, None,
+                            None, None, None, None)
+        n8, n16, nt, nb = (int(x) for x in sizes)
+        top, inside = np.zeros(N, np.int8), np.zeros(N, np.int8)
+        items, u = np.zeros((n8 + n16, 2), np.int32), np.zeros(n8 + n16, np.float32)
+        tables, bcards, btab = np.zeros((nt, 4), np.int64), np.zeros(nb, np.uint64), np.zeros(nb, np.int32)
+        probe.probe_runouts(C.c_void_p(t.h), sizes.ctypes.data_as(C.c_void_p), C.byref(pool),
+                            top.ctypes.data_as(C.c_void_p), inside.ctypes.data_as(C.c_void_p),
+                            items.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p),
+                            tables.ctypes.data_as(C.c_void_p), bcards.ctypes.data_as(C.c_void_p),
+                            btab.ctypes.data_as(C.c_void_p))
+        assert n8 + n16 > 0
+        tt = np.zeros(10, np.int32)
+        n = probe.probe_term_tables(C.c_void_p(t.h), tt.ctypes.data_as(C.c_void_p), None, C.c_int(0))
+        tab = np.zeros(n, np.uint16)
+        probe.probe_term_tables(C.c_void_p(t.h), tt.ctypes.data_as(C.c_void_p), tab.ctypes.data_as(C.c_void_p),
+                                C.c_int(n))
+        length, off_gs = int(tt[9]), int(tt[5])
+        gs = np.stack([tab[b * length + off_gs: b * length + off_gs + H].astype(np.int64)
+                       for b in range(n // length)])
+        masks = np.array([(1 << int(a)) | (1 << int(c)) for a, c in spec.hands], dtype=np.uint64)
+        # GPU node -> oracle node, walking both trees by child index
+        info, g2o, todo = o.nodes(), {}, [(0, 0)]
+        while todo:
+            g, m = todo.pop()
+            g2o[g] = m
+            todo.extend(zip(t.kids(g), info[m]["kids"]))
+        o.iterate(2)
+        for i in (0, 1):
+            o.values_current(i)
+            for k, (node, tb) in enumerate(items.tolist()):
+                wide, nbd, b0, _ = (int(x) for x in tables[tb])
+                E = np.zeros((H, H))
+                for b in range(b0, b0 + nbd):
+                    r = gs[int(btab[b])]
+                    ok = (masks & np.uint64(int(bcards[b]))) == 0
+                    E += np.sign(r[:, None] - r[None, :]) * (ok[:, None] & ok[None, :])
+                E *= (masks[:, None] & masks[None, :]) == 0
+                assert np.abs(E).max() <= (32767 if wide else 127)
+                q = o.node_reach("current", 1 - i, g2o[node])
+                got = float(u[k]) * (E @ q)
+                want = o.cfv(i, g2o[node])
+                assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want)) + 1e-12, (case, i, node)
+    finally:
+        t.close()
