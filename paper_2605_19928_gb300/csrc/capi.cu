@@ -58,9 +58,10 @@ struct cfr_tree {
   int32_t* d_wide_fwd = nullptr;    // wide schedule: nodes whose reach is stored, level by level
   int32_t* d_term_src = nullptr;    // reach source of each terminal work entry
   // all-in run-outs evaluated by win-minus-loss tables (runout_tables; none: all zero)
-  RunoutItem* d_ro_items8 = nullptr;
-  RunoutItem* d_ro_items16 = nullptr;
-  int ro_n8 = 0, ro_n16 = 0;
+  RunoutItem* d_ro_items = nullptr;   // top nodes, sorted by table
+  RunoutGroup* d_ro_groups8 = nullptr;
+  RunoutGroup* d_ro_groups16 = nullptr;
+  int ro_n8 = 0, ro_n16 = 0;          // groups of tops on uint8 / uint16 tables
   RunoutTable* d_ro_tables = nullptr;
   unsigned char* d_ro_pool = nullptr;
   std::vector<int> wide_inner_off, wide_fwd_off;
@@ -144,8 +145,8 @@ int launch_terminals(const cfr_tree* t, int player_mask, int use_bar, cudaStream
   if (launch_terminal(t->ctx, player_mask, use_bar, s)) return -1;
   if (t->ro_n8 + t->ro_n16 == 0) return 0;
   const HostGame& h = t->host[0];
-  return launch_runout_values(t->ctx.games, t->d_ro_items8, t->ro_n8, t->d_ro_items16, t->ro_n16, t->d_ro_tables,
-                              t->d_ro_pool, h.n_hands, h.hstride, player_mask, use_bar, s);
+  return launch_runout_values(t->ctx.games, t->d_ro_items, t->d_ro_groups8, t->ro_n8, t->d_ro_groups16, t->ro_n16,
+                              t->d_ro_tables, t->d_ro_pool, h.n_hands, player_mask, use_bar, s);
 }
 
 // Kernels one terminal stage launches.
@@ -724,11 +725,25 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
   for (int g = 0; g < n_games; ++g) t->dev[g].br_out = t->d_br_all + 2 * g;
   if (!ro.tables.empty()) {  // the run-out tables, from each showdown board's tie groups
     const HostGame& h = t->host[0];
+    // tops sorted by table, in groups of up to kRunoutGroup that share a table (one block each)
+    std::vector<RunoutItem> items;
+    std::vector<RunoutGroup> groups[2];
+    for (const std::vector<RunoutItem>* list : {&ro.items8, &ro.items16}) {
+      std::vector<RunoutItem> l = *list;
+      std::stable_sort(l.begin(), l.end(), [](const RunoutItem& a, const RunoutItem& b) { return a.table < b.table; });
+      for (size_t k = 0; k < l.size(); ++k) {
+        std::vector<RunoutGroup>& gl = groups[ro.tables[(size_t)l[k].table].wide];
+        if (k == 0 || l[k].table != l[k - 1].table || gl.back().count == kRunoutGroup)
+          gl.push_back({l[k].table, (int32_t)items.size(), 0, 0});
+        gl.back().count += 1;
+        items.push_back(l[k]);
+      }
+    }
     RunoutBoard* d_boards = nullptr;
     int32_t* d_gs = nullptr;
     if ((rc = upload(t, ro.tables, &t->d_ro_tables)) || (rc = upload(t, ro.boards, &d_boards)) ||
-        (rc = upload(t, h.sd_gs, &d_gs)) || (rc = upload(t, ro.items8, &t->d_ro_items8)) ||
-        (rc = upload(t, ro.items16, &t->d_ro_items16))) {
+        (rc = upload(t, h.sd_gs, &d_gs)) || (rc = upload(t, items, &t->d_ro_items)) ||
+        (rc = upload(t, groups[0], &t->d_ro_groups8)) || (rc = upload(t, groups[1], &t->d_ro_groups16))) {
       delete t;
       return rc;
     }
@@ -742,8 +757,8 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
       delete t;
       return fail(CFR_ECUDA, "run-out table launch failed");
     }
-    t->ro_n8 = (int)ro.items8.size();
-    t->ro_n16 = (int)ro.items16.size();
+    t->ro_n8 = (int)groups[0].size();
+    t->ro_n16 = (int)groups[1].size();
   }
   std::vector<int32_t> term_src(term_work.size());
   for (size_t k = 0; k < term_work.size(); ++k)

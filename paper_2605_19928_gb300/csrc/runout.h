@@ -33,6 +33,14 @@ struct RunoutTable {  // E of one run-out board, stored [o][hstride] as unsigned
   int32_t pad;
 };
 
+struct RunoutGroup {  // up to kRunoutGroup top nodes of one table, evaluated by one block
+  int32_t table;
+  int32_t item0;      // its first item (items sorted by table)
+  int32_t count;
+  int32_t pad;
+};
+constexpr int kRunoutGroup = 8;
+
 struct RunoutBoard {  // one showdown board of a run-out table
   uint64_t cards;     // the board's public cards
   int32_t table;      // its showdown board table (rank tie-group starts per hand)
@@ -45,10 +53,11 @@ int launch_runout_build(const RunoutTable* tables, int n_tables, const RunoutBoa
                         const uint64_t* hand_mask, int n_hands, int hstride, unsigned char* pool, void* stream);
 
 // Values of the players in player_mask (1, 2 or 3) at every run-out top node of game 0, from
-// the opponent's reach (use_bar: the average-strategy reach, into cfv_br), FP32 values.  items8
-// use uint8 tables, items16 uint16 ones.  One launch per non-empty list.
-int launch_runout_values(const GameDev* games, const RunoutItem* items8, int n8, const RunoutItem* items16, int n16,
-                         const RunoutTable* tables, const unsigned char* pool, int n_hands, int hstride,
-                         int player_mask, int use_bar, void* stream);
+// the opponent's reach (use_bar: the average-strategy reach, into cfv_br), FP32 values.  The
+// groups8 use uint8 tables, groups16 uint16 ones; items are the top nodes, sorted by table.
+// One launch per non-empty group list.
+int launch_runout_values(const GameDev* games, const RunoutItem* items, const RunoutGroup* groups8, int n8,
+                         const RunoutGroup* groups16, int n16, const RunoutTable* tables, const unsigned char* pool,
+                         int n_hands, int player_mask, int use_bar, void* stream);
 
 }  // namespace pcfr
