@@ -262,9 +262,12 @@ int cfr_reset(cfr_tree* tree);
  * network), and writes the fastest options to *best (opts with schedule, chunk_hands and
  * term_nodes set; term_nodes stays 0 when the automatic count was fastest) and its mean
  * device time per iteration to *ms_per_iter (may be NULL).
- * Every candidate gives the same results bit for bit, so only time decides.  Handles are
- * created and destroyed one at a time (device memory of one handle at most).  Errors as
- * for cfr_batch_create; CFR_EINVAL when iters < 1.  Synchronises. */
+ * Every candidate gives the same results bit for bit, so only time decides.  opts'
+ * runout_tables applies to the wide candidate only (the others run with 0); the run-out
+ * tables change the summation order of the run-out values, so a wide candidate with them
+ * agrees with the others to FP32 rounding instead of bit for bit.  Handles are created and
+ * destroyed one at a time (device memory of one handle at most).  Errors as for
+ * cfr_batch_create; CFR_EINVAL when iters < 1.  Synchronises. */
 int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* opts, void* stream, int iters,
                  cfr_solver_opts* best, double* ms_per_iter);
 

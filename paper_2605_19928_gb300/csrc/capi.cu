@@ -1456,6 +1456,7 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
   double top_ms = INFINITY, ms = 0.0;
   int rc = CFR_OK;
   cand.term_nodes = 0;
+  cand.runout_tables = 0;  // the run-out tables apply to the wide candidate only
   const int chunks[4] = {4, 8, 16, 32};
   for (int k = 0; k < 4 && !rc; ++k) {  // level schedule, hands per block
     cand.schedule = CFR_SCHEDULE_LEVEL;
@@ -1467,6 +1468,7 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
     if (rc || (sch == CFR_SCHEDULE_WIDE && n_games != 1)) continue;
     cand.schedule = sch;
     cand.chunk_hands = 0;
+    cand.runout_tables = sch == CFR_SCHEDULE_WIDE ? opts->runout_tables : 0;
     for (int wh : {32, 64}) {  // stream schedule: hands per warp
       if (rc || (sch == CFR_SCHEDULE_WIDE && wh == 64)) continue;
       cand.warp_hands = sch == CFR_SCHEDULE_STREAM ? wh : 0;
@@ -1479,6 +1481,7 @@ int cfr_autotune(const cfr_game_spec* specs, int n_games, const cfr_solver_opts*
     cand.schedule = CFR_SCHEDULE_RESIDENT;
     cand.chunk_hands = 0;
     cand.warp_hands = 0;
+    cand.runout_tables = 0;
     rc = trial(cand, &ms);
     if (!rc && ms < top_ms) top_ms = ms, top = cand;
   }

@@ -691,3 +691,21 @@ def test_runout_tables_reproduce_the_oracle_runout_values(probe, oracle_mod, cas
                 assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want)) + 1e-12, (case, i, node)
     finally:
         t.close()
+
+
+def test_runout_plan_of_the_benchmarked_flop(probe):
+    """The learned-leaf flop of the benchmark (1176 hands, pot 100, stacks 150, sizes 0.33,
+    0.75, 1.25 pot and all-in): 10 flop all-ins run out turn and river (2352 boards, one 16-bit
+    table) and 1,470 turn all-ins the river (48 boards, one 8-bit table per turn card: 49),
+    71 MB of tables."""
+    t = Built(probe, synth.ranked_flop_subgame(depth_limit=1))
+    try:
+        sizes, pool = np.zeros(4, np.int32), C.c_int64()
+        probe.probe_runouts(C.c_void_p(t.h), sizes.ctypes.data_as(C.c_void_p), C.byref(pool), None, None, None,
+                            None, None, None, None)
+        n8, n16, nt, nb = (int(x) for x in sizes)
+        assert (n8, n16, nt) == (1470, 10, 50)
+        assert nb == 49 * 48 + 2352
+        assert pool.value == 49 * t.n_hands * t.hstride + 2 * t.n_hands * t.hstride == 71_011_584
+    finally:
+        t.close()
