@@ -571,7 +571,7 @@ int create_impl(const cfr_game_spec* specs, int n_games, const cfr_solver_opts* 
     plan_runouts(t->host[0], ro);
     if (ro.pool_bytes > ((size_t)8 << 30) || ro.tables.size() > 65535) {
       delete t;
-      return fail(CFR_EINVAL, "the run-out tables would take more than 8 GB");
+      return fail(CFR_EINVAL, "the run-out tables would take more than 8 GB (or number more than 65535)");
     }
   }
   // Resident schedule: one block per SM holds a chunk's state of both players beside a terminal
