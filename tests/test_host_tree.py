@@ -709,3 +709,15 @@ def test_runout_plan_of_the_benchmarked_flop(probe):
         assert pool.value == 49 * t.n_hands * t.hstride + 2 * t.n_hands * t.hstride == 71_011_584
     finally:
         t.close()
+
+
+def test_runout_table_entries_decode_exactly():
+    """The run-out kernel turns a biased table entry x (uint8: E + 128, uint16: E + 32768)
+    into E as FP32 by placing x in the mantissa of 2^23 and subtracting 2^23 + bias: exact
+    for every entry (IEEE FP32, as numpy computes it)."""
+    for bits, bias in ((8, 128), (16, 32768)):
+        x = np.arange(1 << bits, dtype=np.uint32)
+        as_float = (np.uint32(0x4B000000) | x).view(np.float32)
+        e = as_float - np.float32(8388608.0 + bias)
+        assert e.dtype == np.float32
+        assert np.array_equal(e.astype(np.int64), x.astype(np.int64) - bias)
